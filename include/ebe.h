@@ -1,0 +1,245 @@
+/*
+ * ebe.h -- C ABI of the GB300 element-by-element (EbE) finite-element library.
+ *
+ * The library evaluates the element-based residual of Marcinkowski & Valdman,
+ * "MATLAB Implementation of Element-based Solvers" (Sec. 2, Eq. residual and
+ * Algorithm 1),
+ *
+ *     r = b - A x = sum_e C_e^T (b_e - A_e C_e x),   A_e = K_e + nu M_e,
+ *
+ * directly from per-element matrices, never assembling the sparse A, and
+ * drives Jacobi-preconditioned conjugate gradients with it.  The calls follow
+ * the paper's problem statement (Sec. 1): a mesh (nodal coordinates and the
+ * element-to-node connectivity that replaces the Boolean matrices C_e), a
+ * parameter nu >= 0, nodal values of f, and Dirichlet / Neumann node sets.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an ebe_status; nothing is thrown or aborted across the
+ *   ABI.  On failure ebe_last_error(h) holds a one-line message.
+ * - Host pointers ("host") are read during the call only; the caller keeps
+ *   ownership and may free them afterwards.  Device pointers ("device") are
+ *   caller-owned CUDA global-memory buffers on the handle's device (for
+ *   example torch.Tensor.data_ptr()); they must stay valid until the work
+ *   enqueued by the call has finished on the handle's stream.
+ * - All device work of a handle is ordered on the CUDA stream given to
+ *   ebe_create (NULL means the legacy default stream).  Calls that return
+ *   host results (ebe_solve, ebe_get_*) synchronise that stream.
+ * - Node and element numbering is the caller's, 0-based, everywhere.  The
+ *   library reorders elements internally for locality; this never shows.
+ * - Vectors are dense arrays of length n_n indexed by node id.  The Dirichlet
+ *   rows of a residual or an operator application are set to zero, as in the
+ *   paper's listings (r(nd) = 0 after every residual, Sec. 2.1).
+ * - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef EBE_H
+#define EBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EBE_OK = 0,
+    EBE_INVALID_ARG = 1,        /* NULL pointer, bad size, dim/n_b mismatch, unused node, ... */
+    EBE_INDEX_RANGE = 2,        /* a node id outside [0, n_n) or repeated within an element   */
+    EBE_DEGENERATE_ELEMENT = 3, /* an element with zero area / volume                          */
+    EBE_SINGULAR = 4,           /* nu == 0 and no Dirichlet node (Sec. 1 requires a positive
+                                   Dirichlet measure when nu = 0)                             */
+    EBE_CUDA_ERROR = 5,         /* a CUDA runtime call failed                                  */
+    EBE_OOM = 6,                /* device allocation failed                                    */
+    EBE_MAXIT = 7,              /* solver stopped at maxit before reaching rtol                */
+    EBE_BREAKDOWN = 8,          /* p.Ap <= 0 or a non-finite value in the solver               */
+    EBE_STALL = 9,              /* the FP64 true residual stopped decreasing                   */
+    EBE_NOT_READY = 10          /* call order: ebe_set_problem / ebe_assemble not done yet     */
+} ebe_status;
+
+/* Arithmetic types for ebe_residual / ebe_apply. */
+enum { EBE_F64 = 0, EBE_F32 = 1 };
+
+/* Storage of the element matrices made by ebe_assemble. */
+enum {
+    EBE_STORE_FP64 = 0,   /* A_e in FP64 only                                               */
+    EBE_STORE_MIXED = 1   /* A_e in FP64 and a copy rounded to FP32 (round-to-nearest)      */
+};
+
+/* Solver precision for ebe_solve. */
+enum {
+    EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG                                          */
+    EBE_PREC_MIXED = 1    /* FP32 A_e and FP32 CG vectors with FP64 dot accumulation; the
+                             solution is accumulated in FP64 and the residual is replaced by
+                             the FP64 true residual (FP64 A_e) whenever the FP32 recurrence
+                             residual has dropped by the factor `delta` (reliable updates)   */
+};
+
+/* Scatter strategies of the residual (ebe_residual_variant). */
+enum {
+    EBE_SCATTER_PATCH = 0,  /* default: patch-local colour-ordered accumulation in shared
+                               memory + fixed-order halo sum (deterministic)                */
+    EBE_SCATTER_COLOUR = 1, /* global element colouring, one pass per colour, plain
+                               read-modify-write of r (deterministic)                       */
+    EBE_SCATTER_NODE = 2,   /* two-phase: per-element A_e x_e to a buffer, then a node-
+                               centric gather over the inverse connectivity (deterministic) */
+    EBE_SCATTER_ATOMIC = 3  /* FP64 atomic adds (NOT deterministic; for measurement only)   */
+};
+
+typedef struct ebe_handle ebe_handle;
+
+/* Mesh description (Sec. 1).  P1 simplices: dim = 2 -> triangles, n_b = 3;
+ * dim = 3 -> tetrahedra, n_b = 4. */
+typedef struct {
+    int32_t dim;             /* 2 or 3                                                   */
+    int32_t n_b;             /* dim + 1                                                  */
+    int64_t n_n;             /* number of nodes, 1 <= n_n < 2^31                         */
+    int64_t n_e;             /* number of elements, 1 <= n_e < 2^31 / n_b                */
+    const double* coords;    /* host, [n_n][dim] row-major                               */
+    const int32_t* elems;    /* host, [n_e][n_b] row-major node ids (the index arrays
+                                ind_e / indt of Sec. 2 in one array)                     */
+} ebe_mesh;
+
+/* Options of ebe_create; pass NULL for the defaults. */
+typedef struct {
+    int32_t device;          /* CUDA device ordinal (default 0)                          */
+    int32_t patch_elems;     /* elements per patch, 0 = default (1024); must be 1024 in
+                                this version                                             */
+} ebe_create_opts;
+
+typedef struct {
+    double rtol;             /* target FP64 true relative residual
+                                |mask(b - A x)|_2 / |mask(b - A x0)|_2, default 1e-8     */
+    int64_t maxit;           /* CG iteration cap, default 200000                         */
+    int32_t precision;       /* EBE_PREC_FP64 (default) or EBE_PREC_MIXED                */
+    int32_t chunk;           /* CG iterations per CUDA-graph launch, default 32          */
+    double delta;            /* reliable-update factor for EBE_PREC_MIXED, default 0.1   */
+    int32_t stall_updates;   /* true-residual checks without progress before EBE_STALL,
+                                default 8                                                */
+    int32_t use_graph;       /* 1 (default): iterations run as captured CUDA graphs      */
+} ebe_solve_opts;
+
+typedef struct {
+    int32_t status;          /* ebe_status of the solve                                  */
+    int64_t iterations;      /* CG iterations                                            */
+    int64_t true_residuals;  /* FP64 true-residual evaluations (incl. the initial one)    */
+    double rel_residual;     /* final FP64 true relative residual                        */
+    double r0_norm;          /* |mask(b - A x0)|_2                                        */
+    double solve_ms;         /* wall time of the solve on the host clock                 */
+} ebe_solve_info;
+
+typedef struct {
+    int64_t kernel_launches;   /* kernels launched by this handle so far (graph nodes count
+                                  once per graph launch)                                 */
+    int64_t n_patches;         /* patches of the element partition                         */
+    int64_t patch_elems;       /* elements per patch                                       */
+    int64_t n_shared_nodes;    /* nodes touched by more than one patch                    */
+    int64_t n_halo;            /* halo partial sums per residual (sum over patches of
+                                  their shared nodes)                                    */
+    int64_t max_colours;       /* largest colour count of a patch                         */
+    int64_t n_global_colours;  /* colours of the global colouring (0 until first used)    */
+    int64_t device_bytes;      /* device memory held by the handle                        */
+} ebe_stats;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Validate the mesh on the host, copy it to the device and build the element
+ * partition (patches, local connectivity, halo lists).  Sec. 1 / Sec. 2: the
+ * connectivity plays the role of C_e and R_e, which are never stored.
+ * Errors: EBE_INVALID_ARG, EBE_INDEX_RANGE, EBE_CUDA_ERROR, EBE_OOM.
+ * On error *h is NULL. */
+ebe_status ebe_create(ebe_handle** h, const ebe_mesh* mesh, const ebe_create_opts* opts,
+                      void* cuda_stream);
+
+/* Free every device and host resource of the handle (NULL is ignored). */
+void ebe_destroy(ebe_handle* h);
+
+/* Message of the last failed call on h (never NULL; "" if none).  With h NULL,
+ * the message of the last failed ebe_create in this thread. */
+const char* ebe_last_error(const ebe_handle* h);
+
+/* Static name of a status code. */
+const char* ebe_status_string(int status);
+
+/* Defaults for ebe_solve_opts. */
+void ebe_solve_opts_default(ebe_solve_opts* opts);
+
+/* ---------------------------------------------------------------- problem data */
+
+/* Set nu, f and the boundary node sets of the problem -Lap u + nu u = f
+ * (Sec. 1).  f_nodal: host [n_n], nodal values of f (b_j = int f Phi_j is
+ * evaluated as b = M f_I, f interpolated at the nodes).  dirichlet: host
+ * [n_d] node ids with prescribed values g (host [n_d], NULL = 0).  neumann:
+ * host [n_neu] node ids with homogeneous Neumann data; they add nothing to
+ * the system and are only validated.  A node may not be in both sets.
+ * Errors: EBE_INVALID_ARG (nu < 0 or not finite, bad sizes, overlap),
+ * EBE_INDEX_RANGE, EBE_SINGULAR (nu == 0 and n_d == 0). */
+ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal,
+                           const int32_t* dirichlet, int64_t n_d, const double* g,
+                           const int32_t* neumann, int64_t n_neu);
+
+/* Generate on the device, for every element, the P1 matrices of
+ * Eq. matrices_K_M, A_e = K_e + nu M_e (Sec. 2), the assembled load vector
+ * b = sum_e C_e^T M_e f_e and the inverse Jacobi diagonal
+ * dinv = 1 / sum_e C_e^T diag(A_e) (0 on Dirichlet nodes).  store:
+ * EBE_STORE_FP64 or EBE_STORE_MIXED.  Enqueued on the handle's stream; the
+ * degenerate-element check synchronises it.
+ * Errors: EBE_NOT_READY, EBE_DEGENERATE_ELEMENT, EBE_CUDA_ERROR, EBE_OOM. */
+ebe_status ebe_assemble(ebe_handle* h, int32_t store);
+
+/* Write K_e and M_e of every element (Eq. matrices_K_M) to device buffers in
+ * the paper's n_b x n_b x n_e layout (Fig. 2; entry (i,j) of element e at
+ * [e*n_b*n_b + j*n_b + i], element order = caller's).  Either may be NULL.
+ * Needs ebe_create only.  Errors: EBE_INVALID_ARG, EBE_CUDA_ERROR. */
+ebe_status ebe_element_matrices(ebe_handle* h, double* K_dev, double* M_dev);
+
+/* Copy the element matrices A_e held by the handle to a device buffer in the
+ * same layout.  dtype EBE_F64 (double*) or EBE_F32 (float*, MIXED storage).
+ * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
+ebe_status ebe_get_local_matrices(ebe_handle* h, void* A_dev, int32_t dtype);
+
+/* Copy b (device [n_n] double; Dirichlet rows not masked). */
+ebe_status ebe_get_rhs(ebe_handle* h, double* b_dev);
+
+/* Write the Jacobi diagonal d = sum_e C_e^T diag(A_e) (device [n_n] double,
+ * Dirichlet rows not masked). */
+ebe_status ebe_jacobi_diag(ebe_handle* h, double* d_dev);
+
+/* ---------------------------------------------------------------- operator */
+
+/* r = mask(b - A x) by the element-based residual (Eq. residual, Algorithm 1;
+ * mask = zero Dirichlet rows).  x_dev, r_dev: device [n_n] of double
+ * (dtype EBE_F64, FP64 A_e) or float (dtype EBE_F32, FP32 A_e; needs
+ * EBE_STORE_MIXED).  x and r must not overlap.  Deterministic.
+ * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
+ebe_status ebe_residual(ebe_handle* h, const void* x_dev, void* r_dev, int32_t dtype);
+
+/* y = mask(A x) = mask(sum_e C_e^T A_e C_e x).  Same arguments as ebe_residual. */
+ebe_status ebe_apply(ebe_handle* h, const void* x_dev, void* y_dev, int32_t dtype);
+
+/* FP64 residual r = mask(b - A x) with a chosen scatter strategy
+ * (EBE_SCATTER_*), for comparing them.  Builds the strategy's data on first
+ * use.  Errors as ebe_residual. */
+ebe_status ebe_residual_variant(ebe_handle* h, const double* x_dev, double* r_dev, int32_t scatter);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Jacobi-PCG on A x = b with x(nd) = g, stopping when the FP64 true relative
+ * residual |mask(b - A x)| / |mask(b - A x0)| <= rtol (x0 = the given x with
+ * x(nd) = g).  x_dev: device [n_n] double, in: x0, out: solution.  opts NULL =
+ * defaults.  info may be NULL.  Synchronises the stream once at the end.
+ * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
+ebe_status ebe_solve(ebe_handle* h, double* x_dev, const ebe_solve_opts* opts, ebe_solve_info* info);
+
+/* ebe_solve with a HOST x (host [n_n] double, in: x0, out: solution); the
+ * host<->device copies are part of the call. */
+ebe_status ebe_solve_host(ebe_handle* h, double* x_host, const ebe_solve_opts* opts,
+                          ebe_solve_info* info);
+
+/* Counters of the handle (see ebe_stats). */
+ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBE_H */

@@ -1,0 +1,239 @@
+"""GB300 element-by-element (EbE) finite-element residual and Jacobi-PCG.
+
+Python binding of ``libebe.so`` (C ABI in ``include/ebe.h``) with the same
+function names.  It only marshals arguments: every step of the residual, the
+element matrices and the solver runs in the library's CUDA kernels.  Host
+arrays are numpy arrays; device buffers are CUDA tensors (anything with
+``data_ptr()``, ``dtype``, ``is_cuda`` and ``numel()``).
+
+The library is loaded on first use; when it is missing the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (EBE_F32, EBE_F64, EBE_PREC_FP64, EBE_PREC_MIXED, EBE_SCATTER_ATOMIC,  # noqa: F401
+                   EBE_SCATTER_COLOUR, EBE_SCATTER_NODE, EBE_SCATTER_PATCH, EBE_STORE_FP64, EBE_STORE_MIXED)
+
+SOLVER_OUTCOMES = (_abi.EBE_OK, _abi.EBE_MAXIT, _abi.EBE_BREAKDOWN, _abi.EBE_STALL)
+
+
+class EbeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{ebe_status_string(status)}: {message}")
+        self.status = status
+
+
+class Handle:
+    """Owner of an ``ebe_handle*``; keeps the mesh sizes for argument checks."""
+
+    def __init__(self, ptr, dim, n_b, n_n, n_e):
+        self.ptr = ptr
+        self.dim, self.n_b, self.n_n, self.n_e = dim, n_b, n_n, n_e
+
+    def __del__(self):
+        try:
+            ebe_destroy(self)
+        except Exception:
+            pass
+
+
+def _lib():
+    return _abi.load()
+
+
+def ebe_status_string(status: int) -> str:
+    return _lib().ebe_status_string(int(status)).decode()
+
+
+def ebe_last_error(h: Handle | None) -> str:
+    return _lib().ebe_last_error(h.ptr if h is not None else None).decode()
+
+
+def _check(h, status):
+    if status != _abi.EBE_OK:
+        raise EbeError(status, ebe_last_error(h))
+
+
+def _dev(t, dtype_code=None, n=None, name="buffer"):
+    """Device pointer of a CUDA tensor (contiguous), with optional checks."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} entries, has {t.numel()}")
+    if dtype_code is not None:
+        want = "torch.float64" if dtype_code == EBE_F64 else "torch.float32"
+        if str(t.dtype) != want:
+            raise TypeError(f"{name} must be {want}, is {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    s = str(t.dtype)
+    if s == "torch.float64":
+        return EBE_F64
+    if s == "torch.float32":
+        return EBE_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _host_f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _host_i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def ebe_create(coords, elems, device: int = 0, stream: int | None = None) -> Handle:
+    """ebe_create: coords host [n_n][dim] float64, elems host [n_e][n_b] int32.
+
+    ``stream``: a ``cudaStream_t`` value (e.g. ``torch.cuda.current_stream().cuda_stream``);
+    None / 0 means the legacy default stream.
+    """
+    coords = _host_f64(coords)
+    elems = _host_i32(elems)
+    if coords.ndim != 2 or elems.ndim != 2:
+        raise ValueError("coords and elems must be 2-D")
+    mesh = _abi.ebe_mesh(coords.shape[1], elems.shape[1], coords.shape[0], elems.shape[0],
+                         coords.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    opts = _abi.ebe_create_opts(device, 0)
+    ptr = ctypes.c_void_p()
+    st = _lib().ebe_create(ctypes.byref(ptr), ctypes.byref(mesh), ctypes.byref(opts),
+                           ctypes.c_void_p(stream or 0))
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    return Handle(ptr, coords.shape[1], elems.shape[1], coords.shape[0], elems.shape[0])
+
+
+def ebe_destroy(h: Handle) -> None:
+    if h is not None and h.ptr is not None and h.ptr.value:
+        _lib().ebe_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+
+
+def ebe_set_problem(h: Handle, nu: float, f_nodal, dirichlet, g=None, neumann=None) -> None:
+    f = _host_f64(f_nodal)
+    if f.shape != (h.n_n,):
+        raise ValueError("f_nodal must have n_n entries")
+    nd = _host_i32(dirichlet if dirichlet is not None else np.zeros(0))
+    gv = None if g is None else _host_f64(g)
+    if gv is not None and gv.shape != nd.shape:
+        raise ValueError("g must match the Dirichlet set")
+    nn = _host_i32(neumann if neumann is not None else np.zeros(0))
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t)) if a is not None and a.size else None  # noqa: E731
+    _check(h, _lib().ebe_set_problem(h.ptr, float(nu), P(f, ctypes.c_double), P(nd, ctypes.c_int32), nd.size,
+                                     P(gv, ctypes.c_double), P(nn, ctypes.c_int32), nn.size))
+
+
+def ebe_assemble(h: Handle, store: int = EBE_STORE_FP64) -> None:
+    _check(h, _lib().ebe_assemble(h.ptr, int(store)))
+
+
+def ebe_element_matrices(h: Handle, K=None, M=None) -> None:
+    n = h.n_e * h.n_b * h.n_b
+    _check(h, _lib().ebe_element_matrices(h.ptr, _dev(K, EBE_F64, n, "K"), _dev(M, EBE_F64, n, "M")))
+
+
+def ebe_get_local_matrices(h: Handle, A) -> None:
+    code = _dtype_code(A)
+    _check(h, _lib().ebe_get_local_matrices(h.ptr, _dev(A, code, h.n_e * h.n_b * h.n_b, "A"), code))
+
+
+def ebe_get_rhs(h: Handle, b) -> None:
+    _check(h, _lib().ebe_get_rhs(h.ptr, _dev(b, EBE_F64, h.n_n, "b")))
+
+
+def ebe_jacobi_diag(h: Handle, d) -> None:
+    _check(h, _lib().ebe_jacobi_diag(h.ptr, _dev(d, EBE_F64, h.n_n, "d")))
+
+
+def ebe_residual(h: Handle, x, r) -> None:
+    code = _dtype_code(x)
+    _check(h, _lib().ebe_residual(h.ptr, _dev(x, code, h.n_n, "x"), _dev(r, code, h.n_n, "r"), code))
+
+
+def ebe_apply(h: Handle, x, y) -> None:
+    code = _dtype_code(x)
+    _check(h, _lib().ebe_apply(h.ptr, _dev(x, code, h.n_n, "x"), _dev(y, code, h.n_n, "y"), code))
+
+
+def ebe_residual_variant(h: Handle, x, r, scatter: int) -> None:
+    _check(h, _lib().ebe_residual_variant(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), _dev(r, EBE_F64, h.n_n, "r"),
+                                          int(scatter)))
+
+
+def ebe_solve_opts_default() -> dict:
+    """Defaults of ebe_solve_opts as a dict."""
+    o = _abi.ebe_solve_opts()
+    _lib().ebe_solve_opts_default(ctypes.byref(o))
+    return {k: getattr(o, k) for k, _ in _abi.ebe_solve_opts._fields_}
+
+
+def _opts(rtol, maxit, precision, chunk, delta, stall_updates, use_graph):
+    o = _abi.ebe_solve_opts()
+    _lib().ebe_solve_opts_default(ctypes.byref(o))
+    if rtol is not None:
+        o.rtol = rtol
+    if maxit is not None:
+        o.maxit = maxit
+    if precision is not None:
+        o.precision = precision
+    if chunk is not None:
+        o.chunk = chunk
+    if delta is not None:
+        o.delta = delta
+    if stall_updates is not None:
+        o.stall_updates = stall_updates
+    if use_graph is not None:
+        o.use_graph = int(use_graph)
+    return o
+
+
+def _info_dict(info):
+    return {"status": ebe_status_string(info.status), "status_code": info.status, "iterations": info.iterations,
+            "true_residuals": info.true_residuals, "rel_residual": info.rel_residual, "r0_norm": info.r0_norm,
+            "solve_ms": info.solve_ms}
+
+
+def ebe_solve(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=None, delta=None, stall_updates=None,
+              use_graph=None) -> dict:
+    """ebe_solve on a device x (float64 CUDA tensor, in: x0, out: solution).
+
+    Returns the ebe_solve_info fields; raises only for errors, not for the
+    solver outcomes EBE_MAXIT / EBE_BREAKDOWN / EBE_STALL (see ``status``).
+    """
+    o = _opts(rtol, maxit, precision, chunk, delta, stall_updates, use_graph)
+    info = _abi.ebe_solve_info()
+    st = _lib().ebe_solve(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), ctypes.byref(o), ctypes.byref(info))
+    if st not in SOLVER_OUTCOMES:
+        _check(h, st)
+    return _info_dict(info)
+
+
+def ebe_solve_host(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=None, delta=None,
+                   stall_updates=None, use_graph=None) -> dict:
+    """ebe_solve_host on a host float64 numpy array x (updated in place)."""
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous and x.size == h.n_n):
+        raise TypeError("x must be a contiguous float64 numpy array of n_n entries")
+    o = _opts(rtol, maxit, precision, chunk, delta, stall_updates, use_graph)
+    info = _abi.ebe_solve_info()
+    st = _lib().ebe_solve_host(h.ptr, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(o),
+                               ctypes.byref(info))
+    if st not in SOLVER_OUTCOMES:
+        _check(h, st)
+    return _info_dict(info)
+
+
+def ebe_get_stats(h: Handle) -> dict:
+    s = _abi.ebe_stats()
+    _check(h, _lib().ebe_get_stats(h.ptr, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in _abi.ebe_stats._fields_}

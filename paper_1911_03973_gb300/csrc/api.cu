@@ -1,0 +1,746 @@
+// C ABI of libebe.so (declared in include/ebe.h).
+//
+// The handle owns the element partition, the element matrices and all solver
+// workspaces on one device.  Every call validates its arguments on the host
+// before it enqueues anything, and reports failures as an ebe_status plus a
+// message; nothing is thrown across the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ebe.h"
+#include "ebe_internal.h"
+#include "kernels.h"
+
+using namespace ebe;
+
+struct ebe_handle {
+    int device = 0;
+    cudaStream_t st = nullptr;      // stream all work is ordered on
+    bool own_stream = false;
+    cudaStream_t user = nullptr;    // the caller's stream when it is the legacy stream
+    cudaEvent_t ev_join = nullptr;
+    HostPlan plan;
+    PlanDev pd;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int64_t launches = 0;
+    std::string err;
+
+    // mesh and partition on the device
+    double* coords = nullptr;
+    int32_t* pnode = nullptr;
+    int32_t* sh_node = nullptr;
+    int64_t n_pnode = 0;
+
+    // problem
+    bool problem_set = false;
+    double nu = 0.0;
+    int64_t n_d = 0;
+    double* f = nullptr;
+    int32_t* nd = nullptr;
+    double* g = nullptr;
+    uint8_t* dmask = nullptr;
+
+    // assembled operator
+    bool assembled = false;
+    int store = EBE_STORE_FP64;
+    double *A64 = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
+    float *A32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
+
+    // scratch of the patch passes
+    double* halo64 = nullptr;
+    float* halo32 = nullptr;
+    double* halo2 = nullptr;
+    double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
+    double* part_vec = nullptr;     // 2 * 1216
+    Scalars* sc = nullptr;
+    Scalars* sc_host = nullptr;     // pinned
+    unsigned long long* bad = nullptr;
+
+    // solver vectors
+    double *x64w = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float *xs32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_chunk[2] = {0, 0};
+    int graph_nodes[2] = {0, 0};
+
+    // comparison scatters
+    int32_t* gconn = nullptr;
+    std::vector<int32_t> gconn_host;   // [n_slots][nb]
+    double* Acol = nullptr;
+    int32_t* gcol = nullptr;
+    std::vector<int64_t> col_ptr;
+    int n_gcol = 0;
+    int32_t* node_ptr = nullptr;
+    int32_t* node_ent = nullptr;
+    double* Y = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct CudaFail {
+    cudaError_t e;
+    const char* what;
+};
+
+int fail(ebe_handle* h, int status, const std::string& msg) {
+    if (h) h->err = msg;
+    return status;
+}
+
+int cuda_fail(ebe_handle* h, cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? EBE_OOM : EBE_CUDA_ERROR, msg);
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ebe_status(cuda_fail(h, e_, what)); \
+    } while (0)
+
+template <typename T>
+int dalloc(ebe_handle* h, T** p, int64_t count, bool zero = false) {
+    if (*p) return EBE_OK;
+    void* v = nullptr;
+    size_t bytes = size_t(std::max<int64_t>(count, 1)) * sizeof(T);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(h, e, "cudaMalloc"); }
+    h->allocs.push_back(v);
+    h->bytes += int64_t(bytes);
+    if (zero) {
+        e = cudaMemsetAsync(v, 0, bytes, h->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    }
+    *p = static_cast<T*>(v);
+    return EBE_OK;
+}
+
+#define TRY(call)                    \
+    do {                             \
+        int s_ = (call);             \
+        if (s_ != EBE_OK) return ebe_status(s_); \
+    } while (0)
+
+template <typename T>
+int upload(ebe_handle* h, T** dst, const T* src, int64_t count) {
+    TRY(dalloc(h, dst, count));
+    if (count > 0) CK(cudaMemcpyAsync(*dst, src, sizeof(T) * size_t(count), cudaMemcpyHostToDevice, h->st), "upload");
+    return EBE_OK;
+}
+
+// Order the handle's stream after the caller's legacy stream (and back).
+void enter(ebe_handle* h) {
+    if (h->own_stream) {
+        cudaEventRecord(h->ev_join, h->user);
+        cudaStreamWaitEvent(h->st, h->ev_join, 0);
+    }
+}
+void leave(ebe_handle* h) {
+    if (h->own_stream) {
+        cudaEventRecord(h->ev_join, h->st);
+        cudaStreamWaitEvent(h->user, h->ev_join, 0);
+    }
+}
+
+struct Scope {
+    ebe_handle* h;
+    explicit Scope(ebe_handle* hh) : h(hh) {
+        cudaSetDevice(h->device);
+        enter(h);
+    }
+    ~Scope() { leave(h); }
+};
+
+int add_launches(ebe_handle* h, int n) {
+    h->launches += n;
+    return EBE_OK;
+}
+
+int check_ready(ebe_handle* h, bool need_assembled) {
+    if (!h) return EBE_INVALID_ARG;
+    if (!h->problem_set) return fail(h, EBE_NOT_READY, "ebe_set_problem has not been called");
+    if (need_assembled && !h->assembled) return fail(h, EBE_NOT_READY, "ebe_assemble has not been called");
+    return EBE_OK;
+}
+
+int sync_scalars(ebe_handle* h) {
+    CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st), "read scalars");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    return EBE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ebe_status_string(int s) {
+    switch (s) {
+        case EBE_OK: return "EBE_OK";
+        case EBE_INVALID_ARG: return "EBE_INVALID_ARG";
+        case EBE_INDEX_RANGE: return "EBE_INDEX_RANGE";
+        case EBE_DEGENERATE_ELEMENT: return "EBE_DEGENERATE_ELEMENT";
+        case EBE_SINGULAR: return "EBE_SINGULAR";
+        case EBE_CUDA_ERROR: return "EBE_CUDA_ERROR";
+        case EBE_OOM: return "EBE_OOM";
+        case EBE_MAXIT: return "EBE_MAXIT";
+        case EBE_BREAKDOWN: return "EBE_BREAKDOWN";
+        case EBE_STALL: return "EBE_STALL";
+        case EBE_NOT_READY: return "EBE_NOT_READY";
+        default: return "EBE_UNKNOWN";
+    }
+}
+
+const char* ebe_last_error(const ebe_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void ebe_solve_opts_default(ebe_solve_opts* o) {
+    if (!o) return;
+    o->rtol = 1e-8;
+    o->maxit = 200000;
+    o->precision = EBE_PREC_FP64;
+    o->chunk = 32;
+    o->delta = 0.1;
+    o->stall_updates = 8;
+    o->use_graph = 1;
+}
+
+void ebe_destroy(ebe_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->sc_host) cudaFreeHost(h->sc_host);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* opts) {
+    if (opts && opts->patch_elems != 0 && opts->patch_elems != kPatch)
+        return fail(h, EBE_INVALID_ARG, "patch_elems must be 0 or 1024");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (h->device < 0 || h->device >= ndev) return fail(h, EBE_INVALID_ARG, "no such CUDA device");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    if (h->own_stream) CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "cudaStreamCreate");
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    enter(h);
+    std::string err;
+    int s = build_plan(*m, h->plan, err);
+    if (s != EBE_OK) { leave(h); return fail(h, s, err); }
+    HostPlan& P = h->plan;
+    PlanDev& pd = h->pd;
+    pd.nb = P.nb;
+    pd.dim = P.dim;
+    pd.n_slots = P.n_slots;
+    pd.n_patches = int(P.n_patches);
+    pd.n_shared = int(P.sh_node.size());
+    pd.max_nodes = P.max_nodes;
+    pd.max_col = P.max_col;
+    int32_t* col_ptr = nullptr;
+    int32_t* sh_ptr = nullptr;
+    int32_t* sh_slot = nullptr;
+    int32_t* slot_elem = nullptr;
+    uint16_t* lconn = nullptr;
+    PatchMeta* meta = nullptr;
+    TRY(upload(h, &h->coords, m->coords, m->n_n * m->dim));
+    TRY(upload(h, &meta, P.meta.data(), int64_t(P.meta.size())));
+    TRY(upload(h, &h->pnode, P.pnode.data(), int64_t(P.pnode.size())));
+    TRY(upload(h, &lconn, P.lconn.data(), int64_t(P.lconn.size())));
+    TRY(upload(h, &col_ptr, P.col_ptr.data(), int64_t(P.col_ptr.size())));
+    TRY(upload(h, &h->sh_node, P.sh_node.data(), int64_t(P.sh_node.size())));
+    TRY(upload(h, &sh_ptr, P.sh_ptr.data(), int64_t(P.sh_ptr.size())));
+    TRY(upload(h, &sh_slot, P.sh_slot.data(), int64_t(P.sh_slot.size())));
+    TRY(upload(h, &slot_elem, P.slot_elem.data(), int64_t(P.slot_elem.size())));
+    h->n_pnode = int64_t(P.pnode.size());
+    pd.meta = meta;
+    pd.pnode = h->pnode;
+    pd.lconn = lconn;
+    pd.col_ptr = col_ptr;
+    pd.sh_node = h->sh_node;
+    pd.sh_ptr = sh_ptr;
+    pd.sh_slot = sh_slot;
+    pd.slot_elem = slot_elem;
+    TRY(dalloc(h, &h->part_patch, P.n_patches + 1216));
+    TRY(dalloc(h, &h->part_vec, 2 * 1216));
+    TRY(dalloc(h, &h->sc, 1, true));
+    TRY(dalloc(h, &h->bad, 1));
+    CK(cudaMallocHost(&h->sc_host, sizeof(Scalars)), "cudaMallocHost");
+    std::memset(h->sc_host, 0, sizeof(Scalars));
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");  // host arrays may go away now
+    leave(h);
+    return EBE_OK;
+}
+
+ebe_status ebe_create(ebe_handle** out, const ebe_mesh* m, const ebe_create_opts* opts, void* cuda_stream) {
+    if (!out || !m) { g_create_error = "out and mesh must be non-NULL"; return EBE_INVALID_ARG; }
+    *out = nullptr;
+    ebe_handle* h = new (std::nothrow) ebe_handle();
+    if (!h) { g_create_error = "host allocation failed"; return EBE_OOM; }
+    h->device = opts ? opts->device : 0;
+    h->user = static_cast<cudaStream_t>(cuda_stream);
+    if (cuda_stream == nullptr) h->own_stream = true;   // legacy default stream: work on a private stream
+    else h->st = static_cast<cudaStream_t>(cuda_stream);
+    int s = create_impl(h, m, opts);
+    if (s != EBE_OK) {
+        g_create_error = h->err;
+        ebe_destroy(h);
+        return ebe_status(s);
+    }
+    *out = h;
+    return EBE_OK;
+}
+
+ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal, const int32_t* dirichlet, int64_t n_d,
+                           const double* g, const int32_t* neumann, int64_t n_neu) {
+    if (!h) return EBE_INVALID_ARG;
+    const int64_t n_n = h->plan.n_n;
+    if (!std::isfinite(nu) || nu < 0.0) return ebe_status(fail(h, EBE_INVALID_ARG, "nu must be finite and >= 0"));
+    if (!f_nodal) return ebe_status(fail(h, EBE_INVALID_ARG, "f_nodal must be non-NULL"));
+    if (n_d < 0 || n_neu < 0 || (n_d > 0 && !dirichlet) || (n_neu > 0 && !neumann))
+        return ebe_status(fail(h, EBE_INVALID_ARG, "bad boundary node set"));
+    for (int64_t k = 0; k < n_n; ++k)
+        if (!std::isfinite(f_nodal[k])) return ebe_status(fail(h, EBE_INVALID_ARG, "f is not finite at node " + std::to_string(k)));
+    std::vector<uint8_t> mask(n_n, 0);
+    for (int64_t k = 0; k < n_d; ++k) {
+        int32_t v = dirichlet[k];
+        if (v < 0 || v >= n_n) return ebe_status(fail(h, EBE_INDEX_RANGE, "Dirichlet node id out of range"));
+        if (mask[v]) return ebe_status(fail(h, EBE_INVALID_ARG, "Dirichlet node listed twice: " + std::to_string(v)));
+        mask[v] = 1;
+        if (g && !std::isfinite(g[k])) return ebe_status(fail(h, EBE_INVALID_ARG, "g is not finite"));
+    }
+    for (int64_t k = 0; k < n_neu; ++k) {
+        int32_t v = neumann[k];
+        if (v < 0 || v >= n_n) return ebe_status(fail(h, EBE_INDEX_RANGE, "Neumann node id out of range"));
+        if (mask[v]) return ebe_status(fail(h, EBE_INVALID_ARG, "node in both the Dirichlet and the Neumann set: " + std::to_string(v)));
+    }
+    if (nu == 0.0 && n_d == 0)
+        return ebe_status(fail(h, EBE_SINGULAR, "nu = 0 needs a Dirichlet boundary of positive measure (Sec. 1)"));
+    Scope scp(h);
+    std::vector<double> gv(n_d, 0.0);
+    if (g) std::copy(g, g + n_d, gv.begin());
+    if (h->nd && h->n_d < n_d) { /* grow: old buffer stays allocated until destroy */ h->nd = nullptr; h->g = nullptr; }
+    TRY(upload(h, &h->f, f_nodal, n_n));
+    TRY(dalloc(h, &h->nd, std::max<int64_t>(n_d, 1)));
+    TRY(dalloc(h, &h->g, std::max<int64_t>(n_d, 1)));
+    if (n_d > 0) {
+        CK(cudaMemcpyAsync(h->nd, dirichlet, sizeof(int32_t) * n_d, cudaMemcpyHostToDevice, h->st), "upload");
+        CK(cudaMemcpyAsync(h->g, gv.data(), sizeof(double) * n_d, cudaMemcpyHostToDevice, h->st), "upload");
+    }
+    TRY(upload(h, &h->dmask, mask.data(), n_n));
+    int l = 0;
+    CK(launch_mark_dirichlet(h->pd, h->pnode, h->n_pnode, h->sh_node, h->dmask, h->st, &l), "mark Dirichlet");
+    add_launches(h, l);
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    h->nu = nu;
+    h->n_d = n_d;
+    h->problem_set = true;
+    h->assembled = false;
+    return EBE_OK;
+}
+
+ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
+    TRY(check_ready(h, false));
+    if (store != EBE_STORE_FP64 && store != EBE_STORE_MIXED) return ebe_status(fail(h, EBE_INVALID_ARG, "bad store"));
+    Scope scp(h);
+    const int64_t n_n = h->plan.n_n, nbb = int64_t(h->pd.nb) * h->pd.nb;
+    TRY(dalloc(h, &h->A64, nbb * h->pd.n_slots, true));
+    TRY(dalloc(h, &h->b, n_n));
+    TRY(dalloc(h, &h->d, n_n));
+    TRY(dalloc(h, &h->dinv, n_n));
+    TRY(dalloc(h, &h->halo2, 2 * std::max<int64_t>(h->plan.n_halo, 1)));
+    float *A32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
+    if (store == EBE_STORE_MIXED) {
+        TRY(dalloc(h, &h->A32, nbb * h->pd.n_slots, true));
+        TRY(dalloc(h, &h->b32, n_n));
+        TRY(dalloc(h, &h->dinv32, n_n));
+        A32 = h->A32; b32 = h->b32; dinv32 = h->dinv32;
+    }
+    CK(cudaMemsetAsync(h->bad, 0xff, sizeof(unsigned long long), h->st), "memset");
+    int l = 0;
+    CK(launch_assemble(h->pd, h->coords, h->f, h->nu, h->A64, A32, h->b, h->d, h->dinv, b32, dinv32, h->halo2,
+                       h->bad, h->st, &l), "assemble");
+    add_launches(h, l);
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st), "read flag");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    if (bad != ~0ull) {
+        h->assembled = false;
+        return ebe_status(fail(h, EBE_DEGENERATE_ELEMENT, "element " + std::to_string(bad) + " has zero measure"));
+    }
+    h->store = store;
+    h->assembled = true;
+    return EBE_OK;
+}
+
+ebe_status ebe_element_matrices(ebe_handle* h, double* K, double* M) {
+    if (!h) return EBE_INVALID_ARG;
+    Scope scp(h);
+    int l = 0;
+    CK(launch_export_km(h->pd, h->coords, K, M, h->st, &l), "export K_e, M_e");
+    add_launches(h, l);
+    return EBE_OK;
+}
+
+ebe_status ebe_get_local_matrices(ebe_handle* h, void* A, int32_t dtype) {
+    TRY(check_ready(h, true));
+    if (!A || (dtype != EBE_F64 && dtype != EBE_F32)) return ebe_status(fail(h, EBE_INVALID_ARG, "bad arguments"));
+    if (dtype == EBE_F32 && !h->A32) return ebe_status(fail(h, EBE_NOT_READY, "FP32 matrices need EBE_STORE_MIXED"));
+    Scope scp(h);
+    int l = 0;
+    CK(launch_export_A(h->pd, dtype, dtype == EBE_F64 ? static_cast<const void*>(h->A64) : h->A32, A, h->st, &l),
+       "export A_e");
+    add_launches(h, l);
+    return EBE_OK;
+}
+
+ebe_status ebe_get_rhs(ebe_handle* h, double* b) {
+    TRY(check_ready(h, true));
+    if (!b) return ebe_status(fail(h, EBE_INVALID_ARG, "b is NULL"));
+    Scope scp(h);
+    CK(cudaMemcpyAsync(b, h->b, sizeof(double) * h->plan.n_n, cudaMemcpyDeviceToDevice, h->st), "copy b");
+    return EBE_OK;
+}
+
+ebe_status ebe_jacobi_diag(ebe_handle* h, double* d) {
+    TRY(check_ready(h, true));
+    if (!d) return ebe_status(fail(h, EBE_INVALID_ARG, "d is NULL"));
+    Scope scp(h);
+    CK(cudaMemcpyAsync(d, h->d, sizeof(double) * h->plan.n_n, cudaMemcpyDeviceToDevice, h->st), "copy d");
+    return EBE_OK;
+}
+
+static int patch_call(ebe_handle* h, const void* x, void* y, int32_t dtype, int mode) {
+    TRY(check_ready(h, true));
+    if (!x || !y || x == y) return fail(h, EBE_INVALID_ARG, "x and y must be distinct non-NULL device buffers");
+    if (dtype != EBE_F64 && dtype != EBE_F32) return fail(h, EBE_INVALID_ARG, "dtype must be EBE_F64 or EBE_F32");
+    if (dtype == EBE_F32 && !h->A32) return fail(h, EBE_NOT_READY, "EBE_F32 needs ebe_assemble(EBE_STORE_MIXED)");
+    Scope scp(h);
+    void* halo;
+    if (dtype == EBE_F64) {
+        TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
+        halo = h->halo64;
+    } else {
+        TRY(dalloc(h, &h->halo32, std::max<int64_t>(h->plan.n_halo, 1)));
+        halo = h->halo32;
+    }
+    const void* A = dtype == EBE_F64 ? static_cast<const void*>(h->A64) : h->A32;
+    const void* b = dtype == EBE_F64 ? static_cast<const void*>(h->b) : h->b32;
+    int l = 0;
+    CK(launch_patch_pass(h->pd, dtype, mode, A, x, b, y, halo, h->part_patch, nullptr, h->sc, h->st, &l), "patch pass");
+    add_launches(h, l);
+    return EBE_OK;
+}
+
+ebe_status ebe_residual(ebe_handle* h, const void* x, void* r, int32_t dtype) {
+    return ebe_status(patch_call(h, x, r, dtype, kResidual));
+}
+
+ebe_status ebe_apply(ebe_handle* h, const void* x, void* y, int32_t dtype) {
+    return ebe_status(patch_call(h, x, y, dtype, kApply));
+}
+
+static int ensure_gconn(ebe_handle* h) {
+    if (h->gconn) return EBE_OK;
+    TRY(dalloc(h, &h->gconn, int64_t(h->pd.nb) * h->pd.n_slots));
+    int l = 0;
+    CK(launch_build_gconn(h->pd, h->gconn, h->st, &l), "build connectivity");
+    add_launches(h, l);
+    const HostPlan& P = h->plan;
+    h->gconn_host.assign(size_t(P.n_slots) * P.nb, 0);
+    for (int64_t s = 0; s < P.n_slots; ++s) {
+        if (P.slot_elem[s] < 0) continue;
+        const PatchMeta& m = P.meta[s / kPatch];
+        for (int i = 0; i < P.nb; ++i) h->gconn_host[s * P.nb + i] = P.pnode[m.node_off + P.lconn[size_t(i) * P.n_slots + s]];
+    }
+    return EBE_OK;
+}
+
+ebe_status ebe_residual_variant(ebe_handle* h, const double* x, double* r, int32_t scatter) {
+    if (scatter == EBE_SCATTER_PATCH) return ebe_residual(h, x, r, EBE_F64);
+    TRY(check_ready(h, true));
+    if (!x || !r || x == r) return ebe_status(fail(h, EBE_INVALID_ARG, "x and r must be distinct non-NULL device buffers"));
+    Scope scp(h);
+    TRY(ensure_gconn(h));
+    const HostPlan& P = h->plan;
+    int l = 0;
+    if (scatter == EBE_SCATTER_ATOMIC) {
+        CK(launch_residual_atomic(h->pd, h->A64, h->gconn, x, h->b, h->dmask, P.n_n, r, h->st, &l), "atomic residual");
+    } else if (scatter == EBE_SCATTER_NODE) {
+        if (!h->node_ptr) {
+            std::vector<int32_t> ptr(P.n_n + 1, 0), ent(size_t(P.n_e) * P.nb);
+            for (int64_t s = 0; s < P.n_slots; ++s)
+                if (P.slot_elem[s] >= 0)
+                    for (int i = 0; i < P.nb; ++i) ++ptr[h->gconn_host[s * P.nb + i] + 1];
+            for (int64_t k = 0; k < P.n_n; ++k) ptr[k + 1] += ptr[k];
+            std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+            for (int64_t s = 0; s < P.n_slots; ++s)
+                if (P.slot_elem[s] >= 0)
+                    for (int i = 0; i < P.nb; ++i)
+                        ent[fill[h->gconn_host[s * P.nb + i]]++] = int32_t(int64_t(i) * P.n_slots + s);
+            TRY(upload(h, &h->node_ptr, ptr.data(), int64_t(ptr.size())));
+            TRY(upload(h, &h->node_ent, ent.data(), int64_t(ent.size())));
+            TRY(dalloc(h, &h->Y, int64_t(P.nb) * P.n_slots));
+            CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+        }
+        CK(launch_residual_node(h->pd, h->A64, h->gconn, h->node_ptr, h->node_ent, x, h->b, h->dmask, P.n_n, h->Y, r,
+                                h->st, &l), "node residual");
+    } else if (scatter == EBE_SCATTER_COLOUR) {
+        if (!h->Acol) {
+            std::vector<int32_t> order;
+            std::string err;
+            int nc = global_colouring(P, h->gconn_host, order, h->col_ptr, err);
+            if (nc < 0) return ebe_status(fail(h, EBE_INVALID_ARG, err));
+            h->n_gcol = nc;
+            int32_t* order_d = nullptr;
+            TRY(upload(h, &order_d, order.data(), int64_t(order.size())));
+            TRY(dalloc(h, &h->Acol, int64_t(P.nb) * P.nb * P.n_e));
+            TRY(dalloc(h, &h->gcol, int64_t(P.nb) * P.n_e));
+            CK(launch_permute_slots(P.nb, P.n_slots, P.n_e, order_d, h->A64, h->gconn, h->Acol, h->gcol, h->st, &l),
+               "permute");
+            CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+        }
+        CK(launch_residual_colour(P.nb, h->n_gcol, h->col_ptr.data(), P.n_e, h->Acol, h->gcol, x, h->b, h->dmask, P.n_n,
+                                  r, h->st, &l), "colour residual");
+    } else {
+        return ebe_status(fail(h, EBE_INVALID_ARG, "unknown scatter"));
+    }
+    add_launches(h, l);
+    return EBE_OK;
+}
+
+// ---------------------------------------------------------------- solver
+
+namespace {
+
+struct SolveBufs {
+    int dt;
+    void* xw;      // iterate the CG updates (x64w, or the FP32 correction xs32)
+    void* r;
+    void* p;
+    void* q;
+    const void* A;
+    const void* dinv;
+    void* halo;
+};
+
+SolveBufs bufs_for(ebe_handle* h, bool mixed) {
+    SolveBufs s;
+    s.dt = mixed ? 1 : 0;
+    if (mixed) {
+        s.xw = h->xs32; s.r = h->r32; s.p = h->p32; s.q = h->q32; s.A = h->A32; s.dinv = h->dinv32; s.halo = h->halo32;
+    } else {
+        s.xw = h->x64w; s.r = h->r64; s.p = h->p64; s.q = h->q64; s.A = h->A64; s.dinv = h->dinv; s.halo = h->halo64;
+    }
+    return s;
+}
+
+// One CG iteration: q = mask(A p) and p.q (alpha), update (stop test), direction.
+int enqueue_iteration(ebe_handle* h, const SolveBufs& s, int* l) {
+    const int64_t n = h->plan.n_n;
+    CK(launch_patch_pass(h->pd, s.dt, kApplyDot, s.A, s.p, nullptr, s.q, s.halo, h->part_patch, &h->sc->done, h->sc,
+                         h->st, l),
+       "apply");
+    CK(launch_update(s.dt, n, s.xw, s.p, s.r, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
+    CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, l), "direction");
+    return EBE_OK;
+}
+
+int ensure_graph(ebe_handle* h, bool mixed, int chunk) {
+    const int k = mixed ? 1 : 0;
+    if (h->graph[k] && h->graph_chunk[k] == chunk) return EBE_OK;
+    if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+    const SolveBufs s = bufs_for(h, mixed);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    int l = 0, st = EBE_OK;
+    for (int it = 0; it < chunk && st == EBE_OK; ++it) st = enqueue_iteration(h, s, &l);
+    cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    if (st != EBE_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph[k], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->graph[k] = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    h->graph_chunk[k] = chunk;
+    h->graph_nodes[k] = l;
+    return EBE_OK;
+}
+
+int true_residual(ebe_handle* h, double& rr) {
+    int l = 0;
+    CK(launch_patch_pass(h->pd, 0, kResidualNorm, h->A64, h->x64w, h->b, h->r64, h->halo64, h->part_patch, nullptr, h->sc,
+                         h->st, &l), "true residual");
+    add_launches(h, l);
+    TRY(sync_scalars(h));
+    rr = h->sc_host->rrt;
+    return EBE_OK;
+}
+
+int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool mixed = o.precision == EBE_PREC_MIXED;
+    if (mixed && !h->A32) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
+    const int64_t n = h->plan.n_n;
+    const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
+    TRY(dalloc(h, &h->x64w, n));
+    TRY(dalloc(h, &h->r64, n));
+    TRY(dalloc(h, &h->halo64, nh));
+    if (mixed) {
+        TRY(dalloc(h, &h->xs32, n));
+        TRY(dalloc(h, &h->r32, n));
+        TRY(dalloc(h, &h->p32, n));
+        TRY(dalloc(h, &h->q32, n));
+        TRY(dalloc(h, &h->halo32, nh));
+    } else {
+        TRY(dalloc(h, &h->p64, n));
+        TRY(dalloc(h, &h->q64, n));
+    }
+    const SolveBufs s = bufs_for(h, mixed);
+    int l = 0;
+    CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x0");
+    CK(launch_set_dirichlet(h->x64w, h->nd, h->g, h->n_d, h->st, &l), "x(nd) = g");
+    CK(launch_control(h->sc, 0.0, o.maxit, 1, h->st, &l), "control");
+    add_launches(h, l);
+    double rr = 0.0;
+    TRY(true_residual(h, rr));
+    info.true_residuals = 1;
+    const double r0 = std::sqrt(rr);
+    info.r0_norm = r0;
+    info.iterations = 0;
+    info.rel_residual = r0 > 0.0 ? 1.0 : 0.0;
+    int status = EBE_OK;
+    if (!std::isfinite(r0)) status = EBE_BREAKDOWN;
+    if (r0 > 0.0 && std::isfinite(r0)) {
+        const double target = o.rtol * r0;
+        l = 0;
+        if (mixed) {
+            CK(launch_fill(1, n, h->xs32, 0.0, h->st, &l), "fill");
+            CK(launch_restart(1, n, h->r32, h->r64, h->dinv32, 1, h->part_vec, h->sc, h->st, &l), "restart");
+        } else {
+            CK(launch_restart(0, n, h->r64, nullptr, h->dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
+        }
+        CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 1, h->sc, h->st, &l), "direction");
+        // plain FP64: the recurrence residual tracks the true one, so the true
+        // residual is checked once the recurrence reaches rtol (as a textbook
+        // PCG stopping test would).  Mixed: a reliable update whenever the
+        // FP32 recurrence residual has dropped by delta, and a margin at the
+        // end because the FP32 recurrence drifts from the FP64 residual.
+        const double fin = mixed ? 0.7 * target : target;
+        double thr = mixed ? std::max(o.delta * r0, fin) : fin;
+        CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
+        add_launches(h, l);
+        if (o.use_graph) TRY(ensure_graph(h, mixed, o.chunk));
+        double best = 1.0;
+        int no_progress = 0;
+        for (;;) {
+            if (o.use_graph) {
+                CK(cudaGraphLaunch(h->graph[mixed ? 1 : 0], h->st), "cudaGraphLaunch");
+                add_launches(h, h->graph_nodes[mixed ? 1 : 0]);
+            } else {
+                l = 0;
+                for (int it = 0; it < o.chunk; ++it) TRY(enqueue_iteration(h, s, &l));
+                add_launches(h, l);
+            }
+            const int64_t before = info.iterations;
+            TRY(sync_scalars(h));
+            const Scalars sh = *h->sc_host;
+            info.iterations = sh.iter;
+            if (sh.reason == kRunning) {
+                if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
+                continue;
+            }
+            if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
+            l = 0;
+            if (mixed) CK(launch_accumulate(n, h->x64w, h->xs32, h->st, &l), "accumulate");
+            add_launches(h, l);
+            TRY(true_residual(h, rr));
+            info.true_residuals += 1;
+            const double rel = std::sqrt(rr) / r0;
+            info.rel_residual = rel;
+            if (!std::isfinite(rel)) { status = EBE_BREAKDOWN; break; }
+            if (rel <= o.rtol) { status = EBE_OK; break; }
+            if (sh.reason == kMaxit) { status = EBE_MAXIT; break; }
+            if (rel < 0.9 * best) { best = rel; no_progress = 0; }
+            else if (++no_progress >= o.stall_updates) { status = EBE_STALL; break; }
+            // residual replacement: continue CG from the FP64 true residual
+            l = 0;
+            if (mixed) CK(launch_restart(1, n, h->r32, h->r64, h->dinv32, 0, h->part_vec, h->sc, h->st, &l), "restart");
+            else CK(launch_restart(0, n, h->r64, nullptr, h->dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
+            CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, &l), "direction");
+            thr = mixed ? std::max(o.delta * std::sqrt(rr), fin) : fin;
+            CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
+            add_launches(h, l);
+        }
+        if (status == EBE_BREAKDOWN) {
+            // report the true residual of the iterate reached
+            l = 0;
+            if (mixed) CK(launch_accumulate(n, h->x64w, h->xs32, h->st, &l), "accumulate");
+            add_launches(h, l);
+            if (true_residual(h, rr) == EBE_OK) info.rel_residual = std::sqrt(rr) / r0;
+        }
+    }
+    CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    info.status = status;
+    info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (status != EBE_OK) {
+        const char* why = status == EBE_MAXIT ? "maxit reached" : status == EBE_STALL ? "true residual stalled"
+                                                                                        : "breakdown (p.Ap <= 0 or non-finite)";
+        h->err = std::string("solve stopped: ") + why;
+    }
+    return status;
+}
+
+int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts, ebe_solve_info* info) {
+    TRY(check_ready(h, true));
+    if (!x) return fail(h, EBE_INVALID_ARG, "x is NULL");
+    ebe_solve_opts o;
+    ebe_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || o.maxit < 1 || o.chunk < 1 || o.chunk > 4096 || !(o.delta > 0.0 && o.delta < 1.0) ||
+        o.stall_updates < 1 || (o.precision != EBE_PREC_FP64 && o.precision != EBE_PREC_MIXED))
+        return fail(h, EBE_INVALID_ARG, "bad solve options");
+    ebe_solve_info local{};
+    Scope scp(h);
+    int s = solve_impl(h, x, host, o, local);
+    if (info) *info = local;
+    return s;
+}
+
+}  // namespace
+
+ebe_status ebe_solve(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info) {
+    return ebe_status(solve_entry(h, x, false, opts, info));
+}
+
+ebe_status ebe_solve_host(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info) {
+    return ebe_status(solve_entry(h, x, true, opts, info));
+}
+
+ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
+    if (!h || !s) return EBE_INVALID_ARG;
+    s->kernel_launches = h->launches;
+    s->n_patches = h->plan.n_patches;
+    s->patch_elems = kPatch;
+    s->n_shared_nodes = int64_t(h->plan.sh_node.size());
+    s->n_halo = h->plan.n_halo;
+    s->max_colours = h->plan.max_col;
+    s->n_global_colours = h->n_gcol;
+    s->device_bytes = h->bytes;
+    return EBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Internal declarations shared by the translation units of libebe.so.
+// Not part of the public ABI (include/ebe.h is).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ebe.h"
+
+namespace ebe {
+
+// Elements per patch.  A patch is a run of elements that one CTA processes:
+// it gathers the patch's nodes into shared memory, applies every element
+// matrix and sums the contributions per node in shared memory.
+constexpr int kPatch = 1024;
+// Bit 31 of a stored node id marks a Dirichlet node (its rows are zeroed).
+constexpr uint32_t kDirichletBit = 0x80000000u;
+constexpr int32_t kNodeMask = 0x7fffffff;
+constexpr int kMaxColours = 64;
+
+// Per-patch metadata (32 bytes).
+struct PatchMeta {
+    int32_t node_off;   // first entry of this patch in the local-node table
+    int32_t n_nodes;    // local nodes: owned ones first, then shared ones
+    int32_t n_owned;    // nodes all of whose elements lie in this patch
+    int32_t halo_off;   // first halo slot of this patch (one per shared node)
+    int32_t n_el;       // elements in the patch (<= kPatch; slots beyond are padding)
+    int32_t col_off;    // first entry of this patch's colour offsets
+    int32_t n_col;      // colours used inside the patch
+    int32_t pad;
+};
+
+// Host-side element partition, built once per mesh.
+struct HostPlan {
+    int dim = 0, nb = 0;
+    int64_t n_n = 0, n_e = 0;
+    int64_t n_patches = 0, n_slots = 0;
+    std::vector<int32_t> slot_elem;   // [n_slots] caller's element id of each slot, -1 = padding
+    std::vector<uint16_t> lconn;      // [nb][n_slots] local node id of vertex i of each slot
+    std::vector<PatchMeta> meta;      // [n_patches]
+    std::vector<int32_t> pnode;       // local-node tables of all patches (global node ids)
+    std::vector<int32_t> col_ptr;     // colour offsets (n_col + 1 per patch), slot-relative
+    std::vector<int32_t> sh_node;     // [n_shared] nodes touched by >= 2 patches
+    std::vector<int32_t> sh_ptr;      // [n_shared + 1] CSR into sh_slot
+    std::vector<int32_t> sh_slot;     // [n_halo] halo slots of each shared node, patch order
+    int64_t n_halo = 0;
+    int max_nodes = 0;
+    int max_col = 0;
+};
+
+// Validate the mesh and build the partition.  Returns an ebe_status.
+int build_plan(const ebe_mesh& m, HostPlan& plan, std::string& err);
+
+// Greedy colouring of all elements (no two elements of a colour share a
+// node), elements of each colour listed in the given slot order.
+// Returns the colour count; order receives the slots grouped by colour and
+// col_ptr the colour offsets.
+int global_colouring(const HostPlan& plan, const std::vector<int32_t>& gconn_slot_major,
+                     std::vector<int32_t>& order, std::vector<int64_t>& col_ptr, std::string& err);
+
+}  // namespace ebe

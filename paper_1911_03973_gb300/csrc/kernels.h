@@ -1,0 +1,123 @@
+// Device-side views, solver scalars and kernel launchers of libebe.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ebe_internal.h"
+
+namespace ebe {
+
+// Read-only view of the element partition on the device.
+struct PlanDev {
+    int nb = 0;
+    int dim = 0;
+    int64_t n_slots = 0;
+    int n_patches = 0;
+    int n_shared = 0;
+    int max_nodes = 0;
+    int max_col = 0;
+    const PatchMeta* meta = nullptr;
+    const int32_t* pnode = nullptr;     // local-node tables, bit 31 = Dirichlet
+    const uint16_t* lconn = nullptr;    // [nb][n_slots]
+    const int32_t* col_ptr = nullptr;
+    const int32_t* sh_node = nullptr;   // bit 31 = Dirichlet
+    const int32_t* sh_ptr = nullptr;
+    const int32_t* sh_slot = nullptr;
+    const int32_t* slot_elem = nullptr; // [n_slots], -1 = padding
+};
+
+// What a patch pass produces at the nodes.
+enum PatchMode : int {
+    kResidual = 0,      // out = mask(b - A x)
+    kResidualNorm = 1,  // same, and sum of out^2 -> Scalars::rrt
+    kApply = 2,         // out = mask(A x)
+    kApplyDot = 3       // same, and sum of x.out -> Scalars::pq, alpha = rho / pq
+};
+
+// Why a solver graph stopped (Scalars::reason).
+enum StopReason : int { kRunning = 0, kTrigger = 1, kBreakdown = 2, kMaxit = 3 };
+
+// Solver scalars, kept on the device between kernels of an iteration.
+struct Scalars {
+    double rho;      // r.z of the current direction
+    double alpha;    // rho / p.Ap
+    double beta;     // rho_new / rho
+    double pq;       // p.Ap
+    double rr;       // recurrence r.r after the last update
+    double rz;       // recurrence r.z after the last update
+    double rrt;      // last true-residual r.r (kResidualNorm)
+    double thr2;     // stop the graph once rr <= thr2
+    int64_t iter;    // CG iterations done
+    int64_t maxit;
+    int32_t done;    // nonzero: every solver kernel returns at once
+    int32_t reason;  // StopReason
+    uint32_t ctr_fix;   // arrival counters of the last-block reductions
+    uint32_t ctr_vec;
+};
+
+// Fixed grid of the node-vector kernels for n nodes (deterministic partials).
+int vec_grid(int64_t n);
+int fix_grid(int n_shared);
+constexpr int kVecThreads = 256;
+
+// ---- patch passes (k_patch.cu) -------------------------------------------
+// dtype 0 = double (FP64 A_e), 1 = float (FP32 A_e).  part must hold
+// n_patches + fix_grid(n_shared) doubles; halo n_halo values of the dtype.
+// stop (nullable): the pass does nothing when *stop != 0 (solver graphs).
+// sc: receives the norm / dot of kResidualNorm / kApplyDot.
+cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x,
+                              const void* b, void* out, void* halo, double* part, const int32_t* stop,
+                              Scalars* sc, cudaStream_t st, int* launches);
+// Element matrices, load vector and Jacobi diagonal (FP64), Eq. matrices_K_M.
+cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu,
+                            double* A64, float* A32, double* b, double* d, double* dinv, float* b32,
+                            float* dinv32, double* halo2, unsigned long long* bad, cudaStream_t st,
+                            int* launches);
+// K_e, M_e (or A_e) in the caller's element order, paper layout [e][j][i].
+cudaError_t launch_export_km(const PlanDev& pd, const double* coords, double* K, double* M,
+                             cudaStream_t st, int* launches);
+cudaError_t launch_export_A(const PlanDev& pd, int dtype, const void* A, void* out, cudaStream_t st,
+                            int* launches);
+// Set / clear the Dirichlet bit of the node tables from a byte mask [n_n].
+cudaError_t launch_mark_dirichlet(const PlanDev& pd, int32_t* pnode, int64_t n_pnode, int32_t* sh_node,
+                                  const uint8_t* mask, cudaStream_t st, int* launches);
+
+// ---- node-vector kernels (k_vec.cu) ---------------------------------------
+cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, int64_t n_d,
+                                 cudaStream_t st, int* launches);
+// x += alpha p; r -= alpha q; sums r.(dinv r), r.r; stop test (last block).
+cudaError_t launch_update(int dtype, int64_t n, void* x, const void* p, void* r, const void* q,
+                          const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches);
+// p = dinv r + beta p  (init: p = dinv r).
+cudaError_t launch_direction(int dtype, int64_t n, void* p, const void* r, const void* dinv, int init,
+                             Scalars* sc, cudaStream_t st, int* launches);
+// After a residual replacement: sums r.(dinv r) and r.r; beta = rz/rho, rho = rz
+// (init: rho = rz, beta = 0).  With r64 given, first r = (float) r64.
+cudaError_t launch_restart(int dtype, int64_t n, void* r, const double* r64, const void* dinv, int init,
+                           double* part, Scalars* sc, cudaStream_t st, int* launches);
+// x64 += xs; xs = 0.
+cudaError_t launch_accumulate(int64_t n, double* x64, float* xs, cudaStream_t st, int* launches);
+// thr2 >= 0: new stop threshold; maxit >= 0: new cap; reset_iter: iter = 0.
+// Always clears done / reason.
+cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches);
+cudaError_t launch_fill(int dtype, int64_t n, void* v, double value, cudaStream_t st, int* launches);
+
+// ---- comparison scatters (k_alt.cu) ---------------------------------------
+cudaError_t launch_build_gconn(const PlanDev& pd, int32_t* gconn, cudaStream_t st, int* launches);
+cudaError_t launch_permute_slots(int nb, int64_t n_slots, int64_t n, const int32_t* order,
+                                 const double* A, const int32_t* gconn, double* A_out,
+                                 int32_t* gconn_out, cudaStream_t st, int* launches);
+cudaError_t launch_residual_colour(int nb, int n_col, const int64_t* col_ptr_host, int64_t n_el,
+                                   const double* Ac, const int32_t* gc, const double* x,
+                                   const double* b, const uint8_t* dmask, int64_t n_n, double* r,
+                                   cudaStream_t st, int* launches);
+cudaError_t launch_residual_atomic(const PlanDev& pd, const double* A, const int32_t* gconn,
+                                   const double* x, const double* b, const uint8_t* dmask,
+                                   int64_t n_n, double* r, cudaStream_t st, int* launches);
+cudaError_t launch_residual_node(const PlanDev& pd, const double* A, const int32_t* gconn,
+                                 const int32_t* node_ptr, const int32_t* node_ent, const double* x,
+                                 const double* b, const uint8_t* dmask, int64_t n_n, double* Y,
+                                 double* r, cudaStream_t st, int* launches);
+
+}  // namespace ebe

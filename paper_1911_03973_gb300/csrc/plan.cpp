@@ -1,0 +1,263 @@
+// Host-side element partition of the EbE operator.
+//
+// The paper replaces the Boolean matrices C_e, R_e by index arrays (Sec. 2,
+// ind_e / indt).  On the GPU the same information is regrouped once per mesh
+// so that the residual sum_e C_e^T A_e C_e x can be formed deterministically
+// without atomics:
+//   1. elements are sorted along a Morton (Z-order) curve of their centroids
+//      and cut into patches of kPatch consecutive elements;
+//   2. each patch lists its distinct nodes ("local nodes"); a node all of
+//      whose elements lie in the patch is "owned", the others are "shared";
+//   3. inside a patch the elements are greedily coloured so that no two
+//      elements of one colour share a node, and stored colour by colour;
+//   4. every shared local node gets a halo slot; for every shared node the
+//      halo slots are listed in patch order (a CSR), which fixes the order in
+//      which its partial sums are added.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#include "ebe_internal.h"
+
+namespace ebe {
+namespace {
+
+// Spread the low 32 bits of v so that bit k moves to bit 2k.
+uint64_t spread2(uint64_t v) {
+    v &= 0xffffffffull;
+    v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+    v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+    v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+// Spread the low 21 bits of v so that bit k moves to bit 3k.
+uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x001f00000000ffffull;
+    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+// LSD radix sort of 64-bit values, 16-bit digits; stable.
+void radix_sort_u64(std::vector<uint64_t>& a) {
+    std::vector<uint64_t> tmp(a.size());
+    std::vector<int64_t> count(1 << 16);
+    uint64_t hi = 0;
+    for (uint64_t v : a) hi |= v;
+    for (int shift = 0; shift < 64; shift += 16) {
+        if (((hi >> shift) & 0xffffull) == 0) continue;   // digit is zero everywhere
+        std::fill(count.begin(), count.end(), 0);
+        for (uint64_t v : a) ++count[(v >> shift) & 0xffff];
+        int64_t s = 0;
+        for (auto& c : count) { int64_t t = c; c = s; s += t; }
+        for (uint64_t v : a) tmp[count[(v >> shift) & 0xffff]++] = v;
+        a.swap(tmp);
+    }
+}
+
+int bits_for(uint64_t n) {  // smallest b with n <= 2^b
+    int b = 0;
+    while (b < 64 && (uint64_t(1) << b) < n) ++b;
+    return b;
+}
+
+}  // namespace
+
+int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
+    if (m.dim != 2 && m.dim != 3) { err = "dim must be 2 or 3"; return EBE_INVALID_ARG; }
+    if (m.n_b != m.dim + 1) { err = "n_b must be dim + 1 (P1 simplices)"; return EBE_INVALID_ARG; }
+    if (m.n_n < 1 || m.n_n > int64_t(kNodeMask)) { err = "n_n out of range"; return EBE_INVALID_ARG; }
+    if (m.n_e < 1 || m.n_e * m.n_b > int64_t(kNodeMask)) { err = "n_e out of range"; return EBE_INVALID_ARG; }
+    if (!m.coords || !m.elems) { err = "coords and elems must be non-NULL"; return EBE_INVALID_ARG; }
+    const int dim = m.dim, nb = m.n_b;
+    const int64_t n_n = m.n_n, n_e = m.n_e;
+    P = HostPlan();
+    P.dim = dim; P.nb = nb; P.n_n = n_n; P.n_e = n_e;
+
+    // ---- validation: ids in range, distinct within an element, finite coords
+    for (int64_t k = 0; k < n_n * dim; ++k)
+        if (!std::isfinite(m.coords[k])) { err = "non-finite coordinate at node " + std::to_string(k / dim); return EBE_INVALID_ARG; }
+    std::vector<int32_t> inc(n_n, 0);  // elements per node
+    for (int64_t e = 0; e < n_e; ++e) {
+        const int32_t* v = m.elems + e * nb;
+        for (int i = 0; i < nb; ++i) {
+            if (v[i] < 0 || v[i] >= n_n) {
+                err = "element " + std::to_string(e) + " has node id " + std::to_string(v[i]) + " outside [0, n_n)";
+                return EBE_INDEX_RANGE;
+            }
+            for (int j = 0; j < i; ++j)
+                if (v[j] == v[i]) { err = "element " + std::to_string(e) + " repeats node " + std::to_string(v[i]); return EBE_INDEX_RANGE; }
+            ++inc[v[i]];
+        }
+    }
+    for (int64_t g = 0; g < n_n; ++g)
+        if (inc[g] == 0) { err = "node " + std::to_string(g) + " belongs to no element"; return EBE_INVALID_ARG; }
+
+    // ---- Morton order of element centroids
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) { lo[d] = std::numeric_limits<double>::max(); hi[d] = -lo[d]; }
+    for (int64_t k = 0; k < n_n; ++k)
+        for (int d = 0; d < dim; ++d) { lo[d] = std::min(lo[d], m.coords[k * dim + d]); hi[d] = std::max(hi[d], m.coords[k * dim + d]); }
+    const int ebits = bits_for(uint64_t(n_e));
+    const int kbits_axis = std::min((64 - ebits) / dim, dim == 2 ? 32 : 21);
+    const double qmax = double((uint64_t(1) << kbits_axis) - 1);
+    std::vector<uint64_t> keys(n_e);
+    for (int64_t e = 0; e < n_e; ++e) {
+        const int32_t* v = m.elems + e * nb;
+        uint64_t q[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            double c = 0;
+            for (int i = 0; i < nb; ++i) c += m.coords[int64_t(v[i]) * dim + d];
+            c /= nb;
+            double span = hi[d] - lo[d];
+            double t = span > 0 ? (c - lo[d]) / span : 0.0;
+            q[d] = uint64_t(std::min(qmax, std::max(0.0, std::floor(t * qmax + 0.5))));
+        }
+        uint64_t key = dim == 2 ? (spread2(q[0]) | (spread2(q[1]) << 1))
+                                : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
+        keys[e] = (key << ebits) | uint64_t(e);
+    }
+    radix_sort_u64(keys);
+    const uint64_t emask = ebits >= 64 ? ~0ull : ((uint64_t(1) << ebits) - 1);
+
+    // ---- patches
+    P.n_patches = (n_e + kPatch - 1) / kPatch;
+    P.n_slots = P.n_patches * kPatch;
+    P.slot_elem.assign(P.n_slots, -1);
+    P.lconn.assign(size_t(nb) * P.n_slots, 0);
+    P.meta.resize(P.n_patches);
+    P.pnode.reserve(size_t(n_e) * 2);
+    P.col_ptr.reserve(size_t(P.n_patches) * 12);
+
+    std::vector<int32_t> mark(n_n, -1), local(n_n, 0), in_patch(n_n, 0);
+    std::vector<int32_t> el(kPatch), lnodes, first_touch;
+    std::vector<uint64_t> used;  // per local node: colours of its elements so far
+    std::vector<int> colour(kPatch);
+    std::vector<int32_t> halo_node;  // halo slot -> global node
+    halo_node.reserve(size_t(n_n));
+    int64_t halo_count = 0;
+
+    for (int64_t p = 0; p < P.n_patches; ++p) {
+        const int64_t e0 = p * kPatch;
+        const int n_el = int(std::min<int64_t>(kPatch, n_e - e0));
+        for (int s = 0; s < n_el; ++s) el[s] = int32_t(keys[e0 + s] & emask);
+        // local nodes in first-touch order
+        first_touch.clear();
+        for (int s = 0; s < n_el; ++s) {
+            const int32_t* v = m.elems + int64_t(el[s]) * nb;
+            for (int i = 0; i < nb; ++i) {
+                int32_t g = v[i];
+                if (mark[g] != int32_t(p)) { mark[g] = int32_t(p); in_patch[g] = 0; first_touch.push_back(g); }
+                ++in_patch[g];
+            }
+        }
+        // owned first, then shared, each in first-touch order
+        lnodes.clear();
+        int n_owned = 0;
+        for (int32_t g : first_touch) if (in_patch[g] == inc[g]) { lnodes.push_back(g); ++n_owned; }
+        for (int32_t g : first_touch) if (in_patch[g] != inc[g]) lnodes.push_back(g);
+        const int n_nodes = int(lnodes.size());
+        if (n_nodes > 65535) { err = "patch with more than 65535 nodes"; return EBE_INVALID_ARG; }
+        for (int l = 0; l < n_nodes; ++l) local[lnodes[l]] = l;
+        // greedy colouring in Morton order
+        used.assign(n_nodes, 0);
+        int n_col = 0;
+        for (int s = 0; s < n_el; ++s) {
+            const int32_t* v = m.elems + int64_t(el[s]) * nb;
+            uint64_t busy = 0;
+            for (int i = 0; i < nb; ++i) busy |= used[local[v[i]]];
+            if (busy == ~0ull) { err = "patch needs more than 64 colours"; return EBE_INVALID_ARG; }
+            int c = 0;
+            while (busy & (1ull << c)) ++c;
+            colour[s] = c;
+            n_col = std::max(n_col, c + 1);
+            for (int i = 0; i < nb; ++i) used[local[v[i]]] |= (1ull << c);
+        }
+        // slots: elements grouped by colour, Morton order within a colour
+        PatchMeta& mt = P.meta[p];
+        mt.node_off = int32_t(P.pnode.size());
+        mt.n_nodes = n_nodes;
+        mt.n_owned = n_owned;
+        mt.halo_off = int32_t(halo_count);
+        mt.n_el = n_el;
+        mt.col_off = int32_t(P.col_ptr.size());
+        mt.n_col = n_col;
+        mt.pad = 0;
+        int slot = 0;
+        for (int c = 0; c < n_col; ++c) {
+            P.col_ptr.push_back(slot);
+            for (int s = 0; s < n_el; ++s) {
+                if (colour[s] != c) continue;
+                const int64_t gs = e0 + slot;
+                P.slot_elem[gs] = el[s];
+                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(local[v[i]]);
+                ++slot;
+            }
+        }
+        P.col_ptr.push_back(slot);
+        for (int32_t g : lnodes) P.pnode.push_back(g);
+        for (int l = n_owned; l < n_nodes; ++l) halo_node.push_back(lnodes[l]);
+        halo_count += n_nodes - n_owned;
+        P.max_nodes = std::max(P.max_nodes, n_nodes);
+        P.max_col = std::max(P.max_col, n_col);
+        if (int64_t(P.pnode.size()) > int64_t(kNodeMask) || halo_count > int64_t(kNodeMask)) {
+            err = "partition tables exceed 2^31 entries"; return EBE_INVALID_ARG;
+        }
+    }
+    P.n_halo = halo_count;
+
+    // ---- shared nodes: CSR of halo slots in patch order (slots are numbered
+    // patch by patch, so ascending slot order is ascending patch order)
+    std::vector<int32_t> cnt(n_n, 0);
+    for (int32_t g : halo_node) ++cnt[g];
+    std::vector<int32_t> node_row(n_n, -1);
+    int64_t n_shared = 0;
+    for (int64_t g = 0; g < n_n; ++g) if (cnt[g] > 0) node_row[g] = int32_t(n_shared++);
+    P.sh_node.resize(n_shared);
+    P.sh_ptr.assign(n_shared + 1, 0);
+    for (int64_t g = 0; g < n_n; ++g)
+        if (cnt[g] > 0) { P.sh_node[node_row[g]] = int32_t(g); P.sh_ptr[node_row[g] + 1] = cnt[g]; }
+    for (int64_t k = 0; k < n_shared; ++k) P.sh_ptr[k + 1] += P.sh_ptr[k];
+    P.sh_slot.resize(halo_count);
+    std::vector<int32_t> fill(P.sh_ptr.begin(), P.sh_ptr.end() - 1);
+    for (int64_t s = 0; s < halo_count; ++s) P.sh_slot[fill[node_row[halo_node[s]]]++] = int32_t(s);
+    return EBE_OK;
+}
+
+int global_colouring(const HostPlan& P, const std::vector<int32_t>& gconn, std::vector<int32_t>& order,
+                     std::vector<int64_t>& col_ptr, std::string& err) {
+    // gconn: [n_slots][nb] global node ids per slot (padding slots ignored)
+    const int nb = P.nb;
+    std::vector<uint64_t> used(P.n_n, 0);
+    std::vector<uint8_t> colour(P.n_slots, 0xff);
+    int n_col = 0;
+    for (int64_t s = 0; s < P.n_slots; ++s) {
+        if (P.slot_elem[s] < 0) continue;
+        uint64_t busy = 0;
+        for (int i = 0; i < nb; ++i) busy |= used[gconn[s * nb + i]];
+        if (busy == ~0ull) { err = "global colouring needs more than 64 colours"; return -1; }
+        int c = 0;
+        while (busy & (1ull << c)) ++c;
+        colour[s] = uint8_t(c);
+        n_col = std::max(n_col, c + 1);
+        for (int i = 0; i < nb; ++i) used[gconn[s * nb + i]] |= (1ull << c);
+    }
+    std::vector<int64_t> cnt(n_col + 1, 0);
+    for (int64_t s = 0; s < P.n_slots; ++s) if (colour[s] != 0xff) ++cnt[colour[s] + 1];
+    for (int c = 0; c < n_col; ++c) cnt[c + 1] += cnt[c];
+    col_ptr = cnt;
+    order.assign(size_t(cnt[n_col]), 0);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t s = 0; s < P.n_slots; ++s) if (colour[s] != 0xff) order[fill[colour[s]]++] = int32_t(s);
+    return n_col;
+}
+
+}  // namespace ebe

@@ -1,0 +1,230 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design notes):
+  * FP64 residual / apply: |r_gpu - r_orc| / |r_orc| <= 1e-12 (the path and the
+    oracle differ only in summation order);
+  * FP64 element matrices, b, Jacobi diagonal: entrywise <= 1e-13 relative to
+    the largest entry of the element (closed form vs quadrature/inversion);
+  * FP32 residual: against the oracle evaluated in FP64 on the FP32-rounded
+    oracle A_e and FP32 x: relative norm error <= 1e-5;
+  * solves: the oracle recomputes |mask(b - A x)| / |mask(b - A x0)| of the
+    returned x in FP64 and it must be <= rtol = 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_03973_gb300 import meshgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ebe():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03973_gb300 as mod
+    return mod
+
+
+DEV = "cuda:0"
+
+
+def _cases():
+    return {
+        "tri_ragged": lambda: meshgen.config_square_jitter(100, nu=1.0, seed=2),        # 19602 el: 19 patches + tail
+        "tri_f1_small": lambda: meshgen.config_square_f1(33, nu=1.0),                    # 2048 el: exactly 2 patches
+        "tri_tiny": lambda: meshgen.config_square_f1(2, nu=1.0),                         # 2 elements, no shared nodes
+        "tri_nu0_perm": lambda: _permuted(meshgen.config_square_jitter(40, nu=0.0, seed=5), 9),
+        "tet_ragged": lambda: meshgen.config_cube_noise(18, nu=0.5, seed=3),            # 29478 tets
+        "tet_small": lambda: meshgen.config_cube_noise(5, nu=0.5, seed=3),              # 384 tets
+    }
+
+
+def _permuted(prob, seed):
+    c, e, (nd, nn), perm = meshgen.permute_nodes(prob["coords"], prob["elems"],
+                                                  [prob["dirichlet"], prob["neumann"]], seed)
+    f = np.empty_like(prob["f"])
+    f[perm] = prob["f"]
+    order = np.argsort(perm[prob["dirichlet"]])
+    out = dict(prob, coords=c, elems=e, dirichlet=nd, neumann=nn, f=f, g=prob["g"][order])
+    return out
+
+
+def _setup(ebe, prob, store=None):
+    h = ebe.ebe_create(prob["coords"], prob["elems"], device=0)
+    ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+    ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED if store is None else store)
+    return h
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+@pytest.mark.parametrize("case", list(_cases()))
+def test_element_matrices_match_oracle(ebe, case):
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    nb, n_e = orc.nb, orc.n_e
+    K = torch.empty(n_e * nb * nb, dtype=torch.float64, device=DEV)
+    M = torch.empty_like(K)
+    A = torch.empty_like(K)
+    ebe.ebe_element_matrices(h, K, M)
+    ebe.ebe_get_local_matrices(h, A)
+    torch.cuda.synchronize()
+    # device layout: element e, entry (i, j) at e*nb*nb + j*nb + i (paper's Fig. 2)
+    view = lambda t: t.cpu().numpy().reshape(n_e, nb, nb).transpose(0, 2, 1)  # noqa: E731
+    for got, ref in ((view(K), orc.K), (view(M), orc.M), (view(A), orc.A)):
+        scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+        assert np.abs(got - ref).max() <= 0 or (np.abs(got - ref) / scale).max() <= 1e-13
+    b = torch.empty(orc.n_n, dtype=torch.float64, device=DEV)
+    d = torch.empty_like(b)
+    ebe.ebe_get_rhs(h, b)
+    ebe.ebe_jacobi_diag(h, d)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(b.cpu().numpy(), orc.rhs(), rtol=1e-13, atol=1e-13 * np.abs(orc.rhs()).max())
+    np.testing.assert_allclose(d.cpu().numpy(), orc.jacobi_diag(), rtol=1e-13)
+
+
+@pytest.mark.parametrize("case", list(_cases()))
+def test_residual_fp64_matches_oracle(ebe, case):
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 17))
+    xd = _t(x)
+    rd = torch.empty_like(xd)
+    yd = torch.empty_like(xd)
+    ebe.ebe_residual(h, xd, rd)
+    ebe.ebe_apply(h, xd, yd)
+    torch.cuda.synchronize()
+    r_ref = orc.residual(x)
+    y_ref = orc.apply(x)
+    r = rd.cpu().numpy()
+    y = yd.cpu().numpy()
+    assert np.linalg.norm(r - r_ref) <= 1e-12 * np.linalg.norm(r_ref)
+    assert np.linalg.norm(y - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    assert np.all(r[prob["dirichlet"]] == 0.0) and np.all(y[prob["dirichlet"]] == 0.0)
+
+
+@pytest.mark.parametrize("case", ["tri_ragged", "tet_ragged", "tri_tiny"])
+def test_residual_fp32_matches_oracle_on_rounded_matrices(ebe, case):
+    prob = _cases()[case]()
+    orc64 = oracle.Problem(prob)
+    A32 = orc64.A.astype(np.float32).astype(np.float64)
+    orc = oracle.Problem(prob, A_override=A32)
+    h = _setup(ebe, prob)
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 18)).astype(np.float32)
+    xd = _t(x, torch.float32)
+    rd = torch.empty_like(xd)
+    ebe.ebe_residual(h, xd, rd)
+    torch.cuda.synchronize()
+    # b is rounded to FP32 on the device; the oracle keeps FP64 b (difference far below 1e-5)
+    r_ref = orc.residual(x.astype(np.float64))
+    r = rd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(r - r_ref) <= 1e-5 * np.linalg.norm(r_ref)
+
+
+def test_residual_is_bitwise_reproducible(ebe):
+    prob = _cases()["tri_ragged"]()
+    h = _setup(ebe, prob)
+    x = _t(meshgen.seeded_vector(prob["coords"].shape[0], 3))
+    outs = []
+    for _ in range(3):
+        r = torch.empty_like(x)
+        ebe.ebe_residual(h, x, r)
+        outs.append(r.cpu().numpy())
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("scatter", ["COLOUR", "NODE", "ATOMIC"])
+@pytest.mark.parametrize("case", ["tri_ragged", "tet_ragged"])
+def test_comparison_scatters_match_oracle(ebe, case, scatter):
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 19))
+    xd = _t(x)
+    rd = torch.empty_like(xd)
+    ebe.ebe_residual_variant(h, xd, rd, getattr(ebe, f"EBE_SCATTER_{scatter}"))
+    torch.cuda.synchronize()
+    r_ref = orc.residual(x)
+    assert np.linalg.norm(rd.cpu().numpy() - r_ref) <= 1e-12 * np.linalg.norm(r_ref)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("case", ["tri_f1_small", "tri_ragged", "tet_ragged", "tri_nu0_perm", "tri_tiny"])
+def test_solve_reaches_1e8_judged_by_oracle(ebe, case, precision):
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve(h, x, rtol=1e-8, precision=getattr(ebe, f"EBE_PREC_{precision}"))
+    assert info["status"] == "EBE_OK", info
+    rel = orc.rel_residual(x.cpu().numpy())
+    assert rel <= 1e-8, (rel, info)
+    if precision == "FP64" and orc.n_n > 10:
+        _, oinfo = orc.pcg(rtol=1e-8)
+        it, oit = info["iterations"], oinfo["iterations"]
+        assert abs(it - oit) <= max(2, 0.02 * oit), (it, oit)
+
+
+def test_solve_paper_experiment_lifted_dirichlet(ebe):
+    """Sec. 3 setting: nu = 0, u = 1 on the boundary, f = 1 (nonzero g)."""
+    prob = meshgen.config_square_f1(33, nu=0.0, g_value=1.0)
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve(h, x, rtol=1e-10)
+    assert info["status"] == "EBE_OK"
+    xh = x.cpu().numpy()
+    assert orc.rel_residual(xh) <= 1e-10
+    assert np.all(xh[prob["dirichlet"]] == 1.0)
+    ref, _ = orc.pcg(rtol=1e-12)
+    assert np.abs(xh - ref).max() <= 1e-8
+
+
+def test_solve_host_buffers(ebe):
+    prob = _cases()["tri_ragged"]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = np.zeros(orc.n_n)
+    info = ebe.ebe_solve_host(h, x, rtol=1e-8, precision=ebe.EBE_PREC_MIXED)
+    assert info["status"] == "EBE_OK"
+    assert orc.rel_residual(x) <= 1e-8
+
+
+def test_solver_outcomes(ebe):
+    prob = _cases()["tri_ragged"]()
+    h = _setup(ebe, prob)
+    x = torch.zeros(prob["coords"].shape[0], dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve(h, x, rtol=1e-8, maxit=5, chunk=4)
+    assert info["status"] == "EBE_MAXIT" and info["iterations"] == 5
+
+
+def test_errors_reported_not_raised_on_device(ebe):
+    c, e = meshgen.square_tri(5)
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_create(c, np.array([[0, 1, 25]], np.int32))
+    assert ei.value.status == 2
+    # a degenerate (zero-area) element is found by the element-matrix kernel
+    c2 = c.copy()
+    c2[6] = [0.125, 0.0]                    # node 6 onto the edge 0-1: triangle (0, 1, 6) has zero area
+    h = ebe.ebe_create(c2, e)
+    n = c.shape[0]
+    ebe.ebe_set_problem(h, 1.0, np.ones(n), meshgen.square_boundary_nodes(5))
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_assemble(h)
+    assert ei.value.status == 3
+    h2 = ebe.ebe_create(c, e)
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_set_problem(h2, 0.0, np.ones(n), np.zeros(0, np.int32))
+    assert ei.value.status == 4
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_residual(h2, torch.zeros(n, dtype=torch.float64, device=DEV),
+                         torch.zeros(n, dtype=torch.float64, device=DEV))
+    assert ei.value.status == 10

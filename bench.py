@@ -1,0 +1,451 @@
+#!/usr/bin/env python3
+"""Benchmark of the element-by-element (EbE) residual + Jacobi-PCG path on GB300.
+
+Workload (default): the unit square with 2049 x 2049 nodes, P1 triangles split
+SW-NE, interior nodes jittered by U[-0.2h, 0.2h] (seed 2), nu = 1,
+f = (2 pi^2 + nu) sin(pi x) sin(pi y), Dirichlet 0 on x = 0 and y = 0,
+homogeneous Neumann elsewhere: 4,198,401 nodes, 8,388,608 elements.
+
+One step = one pass of the whole hot path on that input: element matrices
+A_e = K_e + nu M_e (FP64, plus an FP32 copy), load vector and Jacobi diagonal,
+then Jacobi-PCG from x0 = 0 to FP64 true relative residual 1e-8 with FP32
+element matrices and vectors and FP64 reliable updates (the mixed-precision
+solver).  The mesh partition (built once per mesh, like the paper's index
+arrays) and the inputs are resident on the device before the timed region.
+
+value = algorithmic bytes of the step (every kernel's minimum traffic: each
+element matrix, connectivity index and node vector entry counted once per
+pass) / step time, in GB/s; the plain FP64 Jacobi-PCG of the same problem is
+timed beside it ("plain_fp64").  The roofline object is the FP32 operator
+application (patch kernel + halo fix-up) timed per launch with CUDA events on
+its stream.  e2e repeats the step through the C ABI from pinned host buffers:
+mesh, f and boundary sets in, solution out, including the partition build.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EbE residual GB/s (% HBM peak); PCG time to FP64 rel. residual 1e-8 vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=2049, help="nodes per side of the square")
+    ap.add_argument("--nu", type=float, default=1.0)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", action="store_true", help="also time the comparison scatters")
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble"], default=None,
+                    help="run a few launches of one kernel for an ncu capture (no JSON line)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- byte model
+def bytes_model(dim: int, n_n: int, n_e: int):
+    """Algorithmic bytes of each pass (each entry counted once per pass).
+
+    Element: n_b^2 matrix entries + n_b int32 connectivity indices.
+    Node vectors: every vector read or written by the pass, once.
+    """
+    nb = dim + 1
+    conn = 4 * nb * n_e
+    m = {}
+    # element matrices + load vector + Jacobi diagonal: coords (dim f64) + f (f64) in,
+    # A64 + A32 out, b, d, dinv (f64) + b32, dinv32 (f32) out
+    m["assemble_mixed"] = conn + n_n * 8 * (dim + 1) + n_e * nb * nb * (8 + 4) + n_n * (3 * 8 + 2 * 4)
+    m["assemble_fp64"] = conn + n_n * 8 * (dim + 1) + n_e * nb * nb * 8 + n_n * 3 * 8
+    m["residual64"] = conn + n_e * nb * nb * 8 + n_n * 3 * 8          # x, b in; r out
+    m["residual32"] = conn + n_e * nb * nb * 4 + n_n * 3 * 4
+    m["apply64"] = conn + n_e * nb * nb * 8 + n_n * 2 * 8             # p in; q out
+    m["apply32"] = conn + n_e * nb * nb * 4 + n_n * 2 * 4
+    m["vec64"] = n_n * 8 * (7 + 4)          # update: x,p,r,q,dinv in, x,r out; direction: r,dinv,p in, p out
+    m["vec32"] = n_n * 4 * (7 + 4)
+    m["restart32"] = n_n * (8 + 4 + 4) + n_n * (8 + 8 + 4 + 4)      # r64 -> r32 (+dinv), x64 += xs, xs = 0
+    m["restart64"] = n_n * 8 * 2
+    return m
+
+
+def step_bytes(m, info, mixed: bool):
+    it, tr = info["iterations"], info["true_residuals"]
+    if mixed:
+        return (m["assemble_mixed"] + it * (m["apply32"] + m["vec32"]) + tr * m["residual64"]
+                + max(tr - 1, 0) * m["restart32"])
+    return m["assemble_fp64"] + it * (m["apply64"] + m["vec64"]) + tr * m["residual64"] + max(tr - 1, 0) * m["restart64"]
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- dist helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, valid only
+    while the kernel source is unchanged (source hash recorded beside it)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1911_03973_gb300", "csrc", "k_patch.cu")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == digest:
+            return float(f[2])
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    from paper_1911_03973_gb300 import build as ebe_build
+    from paper_1911_03973_gb300 import meshgen
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+    if rank == 0:
+        ebe_build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
+    n_n, dim = prob["coords"].shape
+    n_e = prob["elems"].shape[0]
+    m = bytes_model(dim, n_n, n_e)
+
+    with torch.cuda.stream(stream):
+        h = ebe.ebe_create(prob["coords"], prob["elems"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+        x = torch.zeros(n_n, dtype=torch.float64, device=dev)
+
+        if args.profile_kernel:
+            ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+            p32 = torch.rand(n_n, dtype=torch.float32, device=dev)
+            q32 = torch.empty_like(p32)
+            x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
+            r64 = torch.empty_like(x64)
+            for _ in range(3):
+                if args.profile_kernel == "apply32":
+                    ebe.ebe_apply(h, p32, q32)
+                elif args.profile_kernel == "residual64":
+                    ebe.ebe_residual(h, x64, r64)
+                else:
+                    ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+            torch.cuda.synchronize()
+            return None
+
+        def step(mixed=True):
+            ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED if mixed else ebe.EBE_STORE_FP64)
+            x.zero_()
+            info = ebe.ebe_solve(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED if mixed else ebe.EBE_PREC_FP64)
+            if info["status"] != "EBE_OK":
+                raise RuntimeError(f"solve failed: {info}")
+            return info
+
+        for _ in range(args.warmup):
+            step()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = ebe.ebe_get_stats(h)["kernel_launches"]
+        clocks = Clocks(dev.index)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if dist:
+            dist.barrier()
+        ms_total = e0.elapsed_time(e1)
+        launches = ebe.ebe_get_stats(h)["kernel_launches"] - l0
+        bytes_total = sum(step_bytes(m, i, True) for i in infos)
+        if dist:
+            t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+            bt = torch.tensor([bytes_total], dtype=torch.float64, device=dev)
+            dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+            bytes_total = float(bt.item())
+        ms_step = ms_total / args.steps
+        value = bytes_total / (ms_total / 1e3) / 1e9
+
+        # plain FP64 Jacobi-PCG on the same problem ("vs plain")
+        pinfo = []
+        ms_plain = None
+        if args.plain_steps > 0:
+            ep0 = torch.cuda.Event(enable_timing=True)
+            ep1 = torch.cuda.Event(enable_timing=True)
+            step(mixed=False)
+            ep0.record(stream)
+            for _ in range(args.plain_steps):
+                pinfo.append(step(mixed=False))
+            ep1.record(stream)
+            torch.cuda.synchronize()
+            ms_plain = ep0.elapsed_time(ep1) / args.plain_steps
+
+        # roofline: FP32 operator application, per-launch events on its stream
+        ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        p32 = torch.rand(n_n, dtype=torch.float32, device=dev)
+        q32 = torch.empty_like(p32)
+        ms_patch, ms_fix = ebe.ebe_time_operator(h, p32, q32, apply=True, reps=20)
+        x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
+        r64 = torch.empty_like(x64)
+        ms_patch64, ms_fix64 = ebe.ebe_time_operator(h, x64, r64, apply=False, reps=20)
+        variants = None
+        if args.variants:
+            variants = {}
+            for name in ("PATCH", "COLOUR", "NODE", "ATOMIC"):
+                code = getattr(ebe, f"EBE_SCATTER_{name}")
+                ebe.ebe_residual_variant(h, x64, r64, code)
+                ev_a = torch.cuda.Event(enable_timing=True)
+                ev_b = torch.cuda.Event(enable_timing=True)
+                ev_a.record(stream)
+                for _ in range(10):
+                    ebe.ebe_residual_variant(h, x64, r64, code)
+                ev_b.record(stream)
+                torch.cuda.synchronize()
+                t = ev_a.elapsed_time(ev_b) / 10
+                variants[name.lower()] = {"ms": round(t, 4), "gbs": round(m["residual64"] / (t / 1e3) / 1e9, 1)}
+
+    peak, peak_kind = peaks()
+    ach = m["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9
+    ach64 = m["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9
+    trf = traffic_record("apply32")
+
+    # e2e: the user's whole call sequence from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hc, he, hf = pin(prob["coords"]), pin(prob["elems"]), pin(prob["f"])
+        hd, hg, hn = pin(prob["dirichlet"]), pin(prob["g"]), pin(prob["neumann"])
+        hx = pin(np.zeros(n_n))
+        h2d = hc.nbytes + he.nbytes + hf.nbytes + hd.nbytes + hg.nbytes + hn.nbytes + hx.nbytes
+        d2h = hx.nbytes
+        times, ebytes = [], 0
+        for _ in range(args.e2e_steps):
+            hx[:] = 0.0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2 = ebe.ebe_create(hc, he, device=dev.index)
+            ebe.ebe_set_problem(h2, prob["nu"], hf, hd, hg, hn)
+            ebe.ebe_assemble(h2, ebe.EBE_STORE_MIXED)
+            info = ebe.ebe_solve_host(h2, hx, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED)
+            ebe.ebe_destroy(h2)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            ebytes += step_bytes(m, info, True)
+        e2e_s = sum(times)
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+            bt = torch.tensor([float(ebytes)], dtype=torch.float64, device=dev)
+            dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+            ebytes = float(bt.item())
+        e2e = {"value": round(ebytes / e2e_s / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_s / args.e2e_steps, 2),
+               "includes": "ebe_create (host partition build) + ebe_set_problem + ebe_assemble + "
+                           "ebe_solve_host + ebe_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(prob, m, iters=40)
+
+    if rank != 0:
+        return None
+    info0 = infos[-1]
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n, "n_elements": n_e,
+                   "n_b": dim + 1, "solver": "Jacobi-PCG, FP32 A_e/vectors, FP64 reliable updates",
+                   "rtol": args.rtol, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) ** 2 * 12) / 1e6),
+                   "value_def": "algorithmic bytes of the step / step time"},
+        "pcg": {"ms_to_1e-8": round(ms_step, 2), "iterations": info0["iterations"],
+                "true_residuals": info0["true_residuals"], "rel_residual": info0["rel_residual"],
+                "plain_fp64_ms": round(ms_plain, 2) if ms_plain else None,
+                "plain_fp64_iterations": pinfo[-1]["iterations"] if pinfo else None,
+                "speedup_vs_plain": round(ms_plain / ms_step, 3) if ms_plain else None},
+        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4), "traffic": trf,
+                     "kernel": "FP32 operator application: patch pass + halo fix-up",
+                     "ms_per_launch": [round(ms_patch, 5), round(ms_fix, 5)],
+                     "bytes_per_launch": m["apply32"], "peak_kind": peak_kind},
+        "residual_fp64": {"gbs": round(ach64, 1), "frac": round(ach64 / peak, 4),
+                          "ms_per_launch": [round(ms_patch64, 5), round(ms_fix64, 5)],
+                          "bytes_per_launch": m["residual64"]},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if variants:
+        line["residual_variants_fp64"] = variants
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def oracle_sample(prob, m, iters=10):
+    """The FP64 oracle, single-threaded, on a bounded sample of the workload:
+    element matrices + local systems of the full mesh, then `iters` Jacobi-PCG
+    iterations.  Returns the cpu_baseline object (GB/s by the same byte model,
+    FP64 passes)."""
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.Problem(prob)
+    x, info = orc.pcg(rtol=1e-30, maxit=iters)
+    dt = time.perf_counter() - t0
+    nbytes = m["assemble_fp64"] + info["iterations"] * (m["apply64"] + m["vec64"]) + info["residual_evals"] * m["residual64"]
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "seconds": round(dt, 2),
+            "sample": f"element matrices of all {orc.n_e} elements + {info['iterations']} FP64 Jacobi-PCG "
+                      f"iterations ({info['residual_evals']} Algorithm-1 residuals), single thread"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1911_03973_gb300 import meshgen
+    oracle.build()
+    prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
+    n_n, dim = prob["coords"].shape
+    m = bytes_model(dim, n_n, prob["elems"].shape[0])
+    for _ in range(args.warmup):
+        oracle_sample(prob, m, iters=2)
+    samples = [oracle_sample(prob, m, iters=10) for _ in range(args.steps)]
+    secs = sum(s["seconds"] for s in samples)
+    val = sum(s["value"] * s["seconds"] for s in samples) / secs
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n,
+                       "n_elements": int(prob["elems"].shape[0])},
+            "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

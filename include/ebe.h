@@ -62,16 +62,23 @@ enum { EBE_F64 = 0, EBE_F32 = 1 };
 /* Storage of the element matrices made by ebe_assemble. */
 enum {
     EBE_STORE_FP64 = 0,   /* A_e in FP64 only                                               */
-    EBE_STORE_MIXED = 1   /* A_e in FP64 and a copy rounded to FP32 (round-to-nearest)      */
+    EBE_STORE_MIXED = 1   /* A_e in FP64 and an FP32 copy in difference form: the
+                             off-diagonal entries a_ij (i != j) rounded to nearest, and on
+                             the diagonal slots the row sums s_i = sum_j a_ij rounded to
+                             nearest.  The FP32 operator evaluates
+                             y_i = s_i x_i + sum_{j != i} a_ij (x_j - x_i), which keeps FP32
+                             relative accuracy for smooth x (K_e rows sum to zero).     */
 };
 
 /* Solver precision for ebe_solve. */
 enum {
     EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG                                          */
-    EBE_PREC_MIXED = 1    /* FP32 A_e and FP32 CG vectors with FP64 dot accumulation; the
-                             solution is accumulated in FP64 and the residual is replaced by
-                             the FP64 true residual (FP64 A_e) whenever the FP32 recurrence
-                             residual has dropped by the factor `delta` (reliable updates)   */
+    EBE_PREC_MIXED = 1    /* the operator pass runs on FP32 A_e (difference form) with the
+                             search direction p and q = A p in FP32; the solution x, the
+                             residual r, z = dinv r and every dot product stay FP64, and r
+                             is replaced by the FP64 true residual (FP64 A_e) whenever the
+                             recurrence residual has dropped by the factor `delta` since
+                             the last replacement (needs EBE_STORE_MIXED)              */
 };
 
 /* Scatter strategies of the residual (ebe_residual_variant). */
@@ -138,6 +145,9 @@ typedef struct {
     int64_t max_colours;       /* largest colour count of a patch                         */
     int64_t n_global_colours;  /* colours of the global colouring (0 until first used)    */
     int64_t device_bytes;      /* device memory held by the handle                        */
+    int64_t device_error;      /* nonzero if a bounded device-side wait gave up (the
+                                  affected results are invalid); reading it synchronises
+                                  the handle's stream                                    */
 } ebe_stats;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -193,7 +203,8 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store);
 ebe_status ebe_element_matrices(ebe_handle* h, double* K_dev, double* M_dev);
 
 /* Copy the element matrices A_e held by the handle to a device buffer in the
- * same layout.  dtype EBE_F64 (double*) or EBE_F32 (float*, MIXED storage).
+ * same layout.  dtype EBE_F64 (double*) or EBE_F32 (float*, MIXED storage; the
+ * stored difference form: diagonal entries hold the row sums s_i).
  * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
 ebe_status ebe_get_local_matrices(ebe_handle* h, void* A_dev, int32_t dtype);
 
@@ -216,6 +227,15 @@ ebe_status ebe_residual(ebe_handle* h, const void* x_dev, void* r_dev, int32_t d
 /* y = mask(A x) = mask(sum_e C_e^T A_e C_e x).  Same arguments as ebe_residual. */
 ebe_status ebe_apply(ebe_handle* h, const void* x_dev, void* y_dev, int32_t dtype);
 
+/* Measure the operator: run `reps` passes of ebe_residual (apply = 0) or
+ * ebe_apply (apply = 1) on the handle's stream, after one untimed pass, with
+ * CUDA events recorded on that stream around each of the pass's two kernels
+ * (the patch kernel and the halo fix-up kernel).  ms: host [2], receives the
+ * mean milliseconds per launch of the patch kernel and of the fix-up kernel.
+ * Synchronises the stream.  Arguments and errors as ebe_residual. */
+ebe_status ebe_time_operator(ebe_handle* h, const void* x_dev, void* y_dev, int32_t dtype, int32_t apply,
+                             int32_t reps, double* ms);
+
 /* FP64 residual r = mask(b - A x) with a chosen scatter strategy
  * (EBE_SCATTER_*), for comparing them.  Builds the strategy's data on first
  * use.  Errors as ebe_residual. */
@@ -237,6 +257,39 @@ ebe_status ebe_solve_host(ebe_handle* h, double* x_host, const ebe_solve_opts* o
 
 /* Counters of the handle (see ebe_stats). */
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* stats);
+
+/* ---------------------------------------------------------------- inspection */
+
+typedef struct {
+    int64_t n_patches;       /* patches                                                  */
+    int64_t n_slots;         /* n_patches * patch_elems (slots past an element are padding) */
+    int64_t n_pnode;         /* entries of the local-node tables of all patches          */
+    int64_t n_colptr;        /* entries of the colour-offset tables                      */
+    int64_t n_shared;        /* nodes touched by more than one patch                     */
+    int64_t n_halo;          /* halo slots                                               */
+    int32_t max_nodes;       /* largest local-node count of a patch                      */
+    int32_t max_colours;     /* largest colour count of a patch                          */
+    int32_t patch_elems;     /* elements per patch                                       */
+} ebe_partition_sizes;
+
+/* Host only, no device needed: validate the mesh and build the element
+ * partition that ebe_create uses, then copy it out (the data that replaces
+ * the index arrays ind_e / indt of Sec. 2 on the device).  With all arrays
+ * NULL only sizes is filled; otherwise each non-NULL array must hold:
+ *   slot_elem  [n_slots]          caller's element id per slot, -1 = padding
+ *   lconn      [n_b][n_slots]     local node id of vertex i of each slot
+ *   patch_meta [n_patches][8]     node_off, n_nodes, n_owned, halo_off, n_el,
+ *                                 col_off, n_col, 0
+ *   pnode      [n_pnode]          global node ids of each patch's local nodes
+ *                                 (owned nodes first, then shared nodes)
+ *   col_ptr    [n_colptr]         per patch n_col + 1 slot offsets (colour classes)
+ *   sh_node    [n_shared]         shared nodes
+ *   sh_ptr     [n_shared + 1]     CSR offsets into sh_slot
+ *   sh_slot    [n_halo]           halo slots of each shared node, in patch order
+ * Errors as ebe_create's validation (message: ebe_last_error(NULL)). */
+ebe_status ebe_partition_export(const ebe_mesh* mesh, ebe_partition_sizes* sizes, int32_t* slot_elem,
+                                uint16_t* lconn, int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr,
+                                int32_t* sh_node, int32_t* sh_ptr, int32_t* sh_slot);
 
 #ifdef __cplusplus
 }

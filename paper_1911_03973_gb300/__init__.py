@@ -166,6 +166,15 @@ def ebe_apply(h: Handle, x, y) -> None:
     _check(h, _lib().ebe_apply(h.ptr, _dev(x, code, h.n_n, "x"), _dev(y, code, h.n_n, "y"), code))
 
 
+def ebe_time_operator(h: Handle, x, y, apply: bool = True, reps: int = 20) -> tuple:
+    """Mean ms per launch of (patch kernel, fix-up kernel), CUDA events on the handle's stream."""
+    code = _dtype_code(x)
+    ms = (ctypes.c_double * 2)()
+    _check(h, _lib().ebe_time_operator(h.ptr, _dev(x, code, h.n_n, "x"), _dev(y, code, h.n_n, "y"), code,
+                                       int(bool(apply)), int(reps), ms))
+    return float(ms[0]), float(ms[1])
+
+
 def ebe_residual_variant(h: Handle, x, r, scatter: int) -> None:
     _check(h, _lib().ebe_residual_variant(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), _dev(r, EBE_F64, h.n_n, "r"),
                                           int(scatter)))
@@ -231,6 +240,34 @@ def ebe_solve_host(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=No
     if st not in SOLVER_OUTCOMES:
         _check(h, st)
     return _info_dict(info)
+
+
+def ebe_partition_export(coords, elems) -> dict:
+    """Host-only element partition (no device needed) as numpy arrays."""
+    coords = _host_f64(coords)
+    elems = _host_i32(elems)
+    mesh = _abi.ebe_mesh(coords.shape[1], elems.shape[1], coords.shape[0], elems.shape[0],
+                         coords.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    sz = _abi.ebe_partition_sizes()
+    lib = _lib()
+    st = lib.ebe_partition_export(ctypes.byref(mesh), ctypes.byref(sz), *([None] * 8))
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    nb = elems.shape[1]
+    out = {
+        "slot_elem": np.empty(sz.n_slots, np.int32), "lconn": np.empty((nb, sz.n_slots), np.uint16),
+        "patch_meta": np.empty((sz.n_patches, 8), np.int32), "pnode": np.empty(sz.n_pnode, np.int32),
+        "col_ptr": np.empty(sz.n_colptr, np.int32), "sh_node": np.empty(sz.n_shared, np.int32),
+        "sh_ptr": np.empty(sz.n_shared + 1, np.int32), "sh_slot": np.empty(sz.n_halo, np.int32),
+    }
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    st = lib.ebe_partition_export(ctypes.byref(mesh), ctypes.byref(sz), *[ptr(out[k]) for k in (
+        "slot_elem", "lconn", "patch_meta", "pnode", "col_ptr", "sh_node", "sh_ptr", "sh_slot")])
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    out.update({k: getattr(sz, k) for k, _ in _abi.ebe_partition_sizes._fields_})
+    return out
 
 
 def ebe_get_stats(h: Handle) -> dict:

@@ -61,7 +61,14 @@ class ebe_solve_info(ctypes.Structure):
 class ebe_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("n_patches", ctypes.c_int64), ("patch_elems", ctypes.c_int64),
                 ("n_shared_nodes", ctypes.c_int64), ("n_halo", ctypes.c_int64), ("max_colours", ctypes.c_int64),
-                ("n_global_colours", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("n_global_colours", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("device_error", ctypes.c_int64)]
+
+
+class ebe_partition_sizes(ctypes.Structure):
+    _fields_ = [("n_patches", ctypes.c_int64), ("n_slots", ctypes.c_int64), ("n_pnode", ctypes.c_int64),
+                ("n_colptr", ctypes.c_int64), ("n_shared", ctypes.c_int64), ("n_halo", ctypes.c_int64),
+                ("max_nodes", ctypes.c_int32), ("max_colours", ctypes.c_int32), ("patch_elems", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -85,10 +92,13 @@ SIGNATURES = [
     ("ebe_jacobi_diag", ctypes.c_int, [_H, _VP]),
     ("ebe_residual", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
     ("ebe_apply", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
+    ("ebe_time_operator", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _F64P]),
     ("ebe_residual_variant", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
     ("ebe_solve", ctypes.c_int, [_H, _VP, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
     ("ebe_solve_host", ctypes.c_int, [_H, _F64P, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
     ("ebe_get_stats", ctypes.c_int, [_H, ctypes.POINTER(ebe_stats)]),
+    ("ebe_partition_export", ctypes.c_int, [ctypes.POINTER(ebe_mesh), ctypes.POINTER(ebe_partition_sizes),
+                                            _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 ]
 
 _lock = threading.Lock()

@@ -63,10 +63,11 @@ struct ebe_handle {
     Scalars* sc = nullptr;
     Scalars* sc_host = nullptr;     // pinned
     unsigned long long* bad = nullptr;
+    int32_t* dev_err = nullptr;     // set by a device wait that gave up
 
     // solver vectors
     double *x64w = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
-    float *xs32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *p32 = nullptr, *q32 = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_chunk[2] = {0, 0};
     int graph_nodes[2] = {0, 0};
@@ -173,10 +174,18 @@ int check_ready(ebe_handle* h, bool need_assembled) {
     return EBE_OK;
 }
 
+// Reads the device error word on the handle's stream (synchronises it).
+int check_device(ebe_handle* h) {
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, h->dev_err, sizeof(e), cudaMemcpyDeviceToHost, h->st), "read device flag");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    if (e != 0) return fail(h, EBE_CUDA_ERROR, "a device-side wait timed out (bulk copy did not complete)");
+    return EBE_OK;
+}
+
 int sync_scalars(ebe_handle* h) {
     CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->st), "read scalars");
-    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
-    return EBE_OK;
+    return check_device(h);
 }
 
 }  // namespace
@@ -229,6 +238,10 @@ void ebe_destroy(ebe_handle* h) {
 static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* opts) {
     if (opts && opts->patch_elems != 0 && opts->patch_elems != kPatch)
         return fail(h, EBE_INVALID_ARG, "patch_elems must be 0 or 1024");
+    // host-side validation and partition first: no device work for a bad mesh
+    std::string err;
+    int s = build_plan(*m, h->plan, err);
+    if (s != EBE_OK) return fail(h, s, err);
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (h->device < 0 || h->device >= ndev) return fail(h, EBE_INVALID_ARG, "no such CUDA device");
@@ -236,9 +249,6 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     if (h->own_stream) CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "cudaStreamCreate");
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     enter(h);
-    std::string err;
-    int s = build_plan(*m, h->plan, err);
-    if (s != EBE_OK) { leave(h); return fail(h, s, err); }
     HostPlan& P = h->plan;
     PlanDev& pd = h->pd;
     pd.nb = P.nb;
@@ -276,6 +286,8 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     TRY(dalloc(h, &h->part_vec, 2 * 1216));
     TRY(dalloc(h, &h->sc, 1, true));
     TRY(dalloc(h, &h->bad, 1));
+    TRY(dalloc(h, &h->dev_err, 1, true));
+    pd.err = h->dev_err;
     CK(cudaMallocHost(&h->sc_host, sizeof(Scalars)), "cudaMallocHost");
     std::memset(h->sc_host, 0, sizeof(Scalars));
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");  // host arrays may go away now
@@ -396,7 +408,7 @@ ebe_status ebe_element_matrices(ebe_handle* h, double* K, double* M) {
 ebe_status ebe_get_local_matrices(ebe_handle* h, void* A, int32_t dtype) {
     TRY(check_ready(h, true));
     if (!A || (dtype != EBE_F64 && dtype != EBE_F32)) return ebe_status(fail(h, EBE_INVALID_ARG, "bad arguments"));
-    if (dtype == EBE_F32 && !h->A32) return ebe_status(fail(h, EBE_NOT_READY, "FP32 matrices need EBE_STORE_MIXED"));
+    if (dtype == EBE_F32 && h->store != EBE_STORE_MIXED) return ebe_status(fail(h, EBE_NOT_READY, "FP32 matrices need EBE_STORE_MIXED"));
     Scope scp(h);
     int l = 0;
     CK(launch_export_A(h->pd, dtype, dtype == EBE_F64 ? static_cast<const void*>(h->A64) : h->A32, A, h->st, &l),
@@ -425,7 +437,7 @@ static int patch_call(ebe_handle* h, const void* x, void* y, int32_t dtype, int 
     TRY(check_ready(h, true));
     if (!x || !y || x == y) return fail(h, EBE_INVALID_ARG, "x and y must be distinct non-NULL device buffers");
     if (dtype != EBE_F64 && dtype != EBE_F32) return fail(h, EBE_INVALID_ARG, "dtype must be EBE_F64 or EBE_F32");
-    if (dtype == EBE_F32 && !h->A32) return fail(h, EBE_NOT_READY, "EBE_F32 needs ebe_assemble(EBE_STORE_MIXED)");
+    if (dtype == EBE_F32 && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_F32 needs ebe_assemble(EBE_STORE_MIXED)");
     Scope scp(h);
     void* halo;
     if (dtype == EBE_F64) {
@@ -449,6 +461,44 @@ ebe_status ebe_residual(ebe_handle* h, const void* x, void* r, int32_t dtype) {
 
 ebe_status ebe_apply(ebe_handle* h, const void* x, void* y, int32_t dtype) {
     return ebe_status(patch_call(h, x, y, dtype, kApply));
+}
+
+ebe_status ebe_time_operator(ebe_handle* h, const void* x, void* y, int32_t dtype, int32_t apply, int32_t reps,
+                             double* ms) {
+    if (!ms || reps < 1 || reps > 100000) return ebe_status(fail(h, EBE_INVALID_ARG, "ms must be non-NULL, 1 <= reps <= 100000"));
+    // argument checks and scratch allocation as a plain call; also a warm-up launch
+    TRY(patch_call(h, x, y, dtype, apply ? kApply : kResidual));
+    Scope scp(h);
+    std::vector<cudaEvent_t> ev(size_t(3) * reps, nullptr);
+    for (auto& e : ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    const void* A = dtype == EBE_F64 ? static_cast<const void*>(h->A64) : h->A32;
+    const void* b = dtype == EBE_F64 ? static_cast<const void*>(h->b) : h->b32;
+    void* halo = dtype == EBE_F64 ? static_cast<void*>(h->halo64) : h->halo32;
+    int l = 0;
+    int status = EBE_OK;
+    for (int r = 0; r < reps && status == EBE_OK; ++r) {
+        cudaError_t e = launch_patch_pass(h->pd, dtype, apply ? kApply : kResidual, A, x, b, y, halo, h->part_patch,
+                                          nullptr, h->sc, h->st, &l, &ev[size_t(3) * r]);
+        if (e != cudaSuccess) status = cuda_fail(h, e, "timed patch pass");
+    }
+    add_launches(h, l);
+    double t_patch = 0.0, t_fix = 0.0;
+    if (status == EBE_OK) {
+        cudaError_t e = cudaEventSynchronize(ev.back());
+        if (e != cudaSuccess) status = cuda_fail(h, e, "cudaEventSynchronize");
+        for (int r = 0; r < reps && status == EBE_OK; ++r) {
+            float a = 0.f, c = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * r], ev[3 * r + 1]);
+            cudaEventElapsedTime(&c, ev[3 * r + 1], ev[3 * r + 2]);
+            t_patch += a;
+            t_fix += c;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (status != EBE_OK) return ebe_status(status);
+    ms[0] = t_patch / reps;
+    ms[1] = t_fix / reps;
+    return EBE_OK;
 }
 
 static int ensure_gconn(ebe_handle* h) {
@@ -525,13 +575,10 @@ ebe_status ebe_residual_variant(ebe_handle* h, const double* x, double* r, int32
 namespace {
 
 struct SolveBufs {
-    int dt;
-    void* xw;      // iterate the CG updates (x64w, or the FP32 correction xs32)
-    void* r;
+    int dt;        // type of A, p, q: 0 = FP64, 1 = FP32
     void* p;
     void* q;
     const void* A;
-    const void* dinv;
     void* halo;
 };
 
@@ -539,21 +586,22 @@ SolveBufs bufs_for(ebe_handle* h, bool mixed) {
     SolveBufs s;
     s.dt = mixed ? 1 : 0;
     if (mixed) {
-        s.xw = h->xs32; s.r = h->r32; s.p = h->p32; s.q = h->q32; s.A = h->A32; s.dinv = h->dinv32; s.halo = h->halo32;
+        s.p = h->p32; s.q = h->q32; s.A = h->A32; s.halo = h->halo32;
     } else {
-        s.xw = h->x64w; s.r = h->r64; s.p = h->p64; s.q = h->q64; s.A = h->A64; s.dinv = h->dinv; s.halo = h->halo64;
+        s.p = h->p64; s.q = h->q64; s.A = h->A64; s.halo = h->halo64;
     }
     return s;
 }
 
 // One CG iteration: q = mask(A p) and p.q (alpha), update (stop test), direction.
+// x, r and dinv are FP64 in both precisions.
 int enqueue_iteration(ebe_handle* h, const SolveBufs& s, int* l) {
     const int64_t n = h->plan.n_n;
     CK(launch_patch_pass(h->pd, s.dt, kApplyDot, s.A, s.p, nullptr, s.q, s.halo, h->part_patch, &h->sc->done, h->sc,
                          h->st, l),
        "apply");
-    CK(launch_update(s.dt, n, s.xw, s.p, s.r, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
-    CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, l), "direction");
+    CK(launch_update(s.dt, n, h->x64w, s.p, h->r64, s.q, h->dinv, h->part_vec, h->sc, h->st, l), "update");
+    CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 0, h->sc, h->st, l), "direction");
     return EBE_OK;
 }
 
@@ -577,6 +625,7 @@ int ensure_graph(ebe_handle* h, bool mixed, int chunk) {
     return EBE_OK;
 }
 
+// r64 = mask(b - A64 x64w) and its squared norm (FP64 element matrices).
 int true_residual(ebe_handle* h, double& rr) {
     int l = 0;
     CK(launch_patch_pass(h->pd, 0, kResidualNorm, h->A64, h->x64w, h->b, h->r64, h->halo64, h->part_patch, nullptr, h->sc,
@@ -587,18 +636,23 @@ int true_residual(ebe_handle* h, double& rr) {
     return EBE_OK;
 }
 
+// Jacobi-PCG.  The solution x, the residual r and z = dinv r are FP64 in both
+// precisions.  EBE_PREC_MIXED keeps the search direction p, q = A p and the
+// element matrices in FP32 (difference form), so the operator pass streams
+// half the bytes; its FP32 rounding makes the recurrence residual drift from
+// the true one, so whenever the recurrence residual has dropped by `delta`
+// since the last FP64 true residual, r is replaced by a fresh FP64 true
+// residual (FP64 element matrices) and CG continues with the same direction.
 int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool mixed = o.precision == EBE_PREC_MIXED;
-    if (mixed && !h->A32) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
+    if (mixed && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
     const int64_t n = h->plan.n_n;
     const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
     TRY(dalloc(h, &h->x64w, n));
     TRY(dalloc(h, &h->r64, n));
     TRY(dalloc(h, &h->halo64, nh));
     if (mixed) {
-        TRY(dalloc(h, &h->xs32, n));
-        TRY(dalloc(h, &h->r32, n));
         TRY(dalloc(h, &h->p32, n));
         TRY(dalloc(h, &h->q32, n));
         TRY(dalloc(h, &h->halo32, nh));
@@ -624,20 +678,14 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
     if (!std::isfinite(r0)) status = EBE_BREAKDOWN;
     if (r0 > 0.0 && std::isfinite(r0)) {
         const double target = o.rtol * r0;
-        l = 0;
-        if (mixed) {
-            CK(launch_fill(1, n, h->xs32, 0.0, h->st, &l), "fill");
-            CK(launch_restart(1, n, h->r32, h->r64, h->dinv32, 1, h->part_vec, h->sc, h->st, &l), "restart");
-        } else {
-            CK(launch_restart(0, n, h->r64, nullptr, h->dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
-        }
-        CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 1, h->sc, h->st, &l), "direction");
         // plain FP64: the recurrence residual tracks the true one, so the true
-        // residual is checked once the recurrence reaches rtol (as a textbook
-        // PCG stopping test would).  Mixed: a reliable update whenever the
-        // FP32 recurrence residual has dropped by delta, and a margin at the
-        // end because the FP32 recurrence drifts from the FP64 residual.
+        // residual is checked once the recurrence reaches rtol (a textbook
+        // stopping test).  Mixed: a replacement whenever the recurrence has
+        // dropped by delta, and a margin at the end for the drift.
         const double fin = mixed ? 0.7 * target : target;
+        l = 0;
+        CK(launch_restart(n, h->r64, h->dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
+        CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 1, h->sc, h->st, &l), "direction");
         double thr = mixed ? std::max(o.delta * r0, fin) : fin;
         CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
         add_launches(h, l);
@@ -662,9 +710,6 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
                 continue;
             }
             if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
-            l = 0;
-            if (mixed) CK(launch_accumulate(n, h->x64w, h->xs32, h->st, &l), "accumulate");
-            add_launches(h, l);
             TRY(true_residual(h, rr));
             info.true_residuals += 1;
             const double rel = std::sqrt(rr) / r0;
@@ -674,20 +719,17 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
             if (sh.reason == kMaxit) { status = EBE_MAXIT; break; }
             if (rel < 0.9 * best) { best = rel; no_progress = 0; }
             else if (++no_progress >= o.stall_updates) { status = EBE_STALL; break; }
-            // residual replacement: continue CG from the FP64 true residual
+            // residual replacement: r64 already holds the FP64 true residual;
+            // continue CG from it with the same direction
             l = 0;
-            if (mixed) CK(launch_restart(1, n, h->r32, h->r64, h->dinv32, 0, h->part_vec, h->sc, h->st, &l), "restart");
-            else CK(launch_restart(0, n, h->r64, nullptr, h->dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
-            CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, &l), "direction");
+            CK(launch_restart(n, h->r64, h->dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
+            CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 0, h->sc, h->st, &l), "direction");
             thr = mixed ? std::max(o.delta * std::sqrt(rr), fin) : fin;
             CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
             add_launches(h, l);
         }
         if (status == EBE_BREAKDOWN) {
             // report the true residual of the iterate reached
-            l = 0;
-            if (mixed) CK(launch_accumulate(n, h->x64w, h->xs32, h->st, &l), "accumulate");
-            add_launches(h, l);
             if (true_residual(h, rr) == EBE_OK) info.rel_residual = std::sqrt(rr) / r0;
         }
     }
@@ -730,6 +772,36 @@ ebe_status ebe_solve_host(ebe_handle* h, double* x, const ebe_solve_opts* opts, 
     return ebe_status(solve_entry(h, x, true, opts, info));
 }
 
+ebe_status ebe_partition_export(const ebe_mesh* m, ebe_partition_sizes* sz, int32_t* slot_elem, uint16_t* lconn,
+                                int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr, int32_t* sh_node,
+                                int32_t* sh_ptr, int32_t* sh_slot) {
+    if (!m || !sz) { g_create_error = "mesh and sizes must be non-NULL"; return EBE_INVALID_ARG; }
+    HostPlan P;
+    std::string err;
+    int s = build_plan(*m, P, err);
+    if (s != EBE_OK) { g_create_error = err; return ebe_status(s); }
+    sz->n_patches = P.n_patches;
+    sz->n_slots = P.n_slots;
+    sz->n_pnode = int64_t(P.pnode.size());
+    sz->n_colptr = int64_t(P.col_ptr.size());
+    sz->n_shared = int64_t(P.sh_node.size());
+    sz->n_halo = P.n_halo;
+    sz->max_nodes = P.max_nodes;
+    sz->max_colours = P.max_col;
+    sz->patch_elems = kPatch;
+    auto put = [](auto* dst, const auto& v) { if (dst) std::copy(v.begin(), v.end(), dst); };
+    put(slot_elem, P.slot_elem);
+    put(lconn, P.lconn);
+    put(pnode, P.pnode);
+    put(col_ptr, P.col_ptr);
+    put(sh_node, P.sh_node);
+    put(sh_ptr, P.sh_ptr);
+    put(sh_slot, P.sh_slot);
+    if (patch_meta)
+        for (int64_t p = 0; p < P.n_patches; ++p) std::memcpy(patch_meta + 8 * p, &P.meta[p], sizeof(PatchMeta));
+    return EBE_OK;
+}
+
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
     if (!h || !s) return EBE_INVALID_ARG;
     s->kernel_launches = h->launches;
@@ -740,6 +812,15 @@ ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
     s->max_colours = h->plan.max_col;
     s->n_global_colours = h->n_gcol;
     s->device_bytes = h->bytes;
+    s->device_error = 0;
+    if (h->dev_err) {
+        int32_t e = 0;
+        cudaSetDevice(h->device);
+        if (cudaMemcpyAsync(&e, h->dev_err, sizeof(e), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+            cudaStreamSynchronize(h->st) != cudaSuccess)
+            return EBE_CUDA_ERROR;
+        s->device_error = e;
+    }
     return EBE_OK;
 }
 

@@ -45,25 +45,97 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-template <typename T, int NB>
-struct PatchCfg {
-    // elements per thread: keeps a[EPT][NB*NB] + x[EPT][NB] within ~100 registers
-    static constexpr int EPT = (NB == 4 && sizeof(T) == 8) ? 2 : 4;
-    static constexpr int NT = kPatch / EPT;
-    static constexpr int MINB = (NT >= 512) ? 1 : 2;
-};
+// ---------------------------------------------------------------- TMA / mbarrier helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// L2 policy for data read exactly once per pass (element matrices, local
+// connectivity): evict first, so that the node vectors stay in L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// 1D bulk copy global -> shared on the TMA engine, completing on an mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
 
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (each poll
+// may suspend the thread for a hardware-chosen time) and reports it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, int32_t* err) {
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    if (err != nullptr) atomicExch(err, 1);
+    return false;
+}
+
+// Shared-memory layout of a patch pass (bytes from the dynamic base).
+struct PatchSmem {
+    uint32_t bar, red, co, A, L, G, xs, acc, total;
+};
+template <typename T, int NB>
+__host__ __device__ constexpr PatchSmem patch_smem_layout(int max_nodes) {
+    PatchSmem s{};
+    const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
+    s.bar = 0;
+    s.red = 16;                                         // 32 doubles
+    s.co = s.red + 32 * 8;                              // kMaxColours + 1 ints
+    s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
+    s.L = s.A + uint32_t(NB * NB * kPatch * sizeof(T));
+    s.G = s.L + uint32_t(NB * kPatch * 2);
+    s.xs = s.G + gcap * 4;
+    s.acc = (s.xs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
+    s.total = (s.acc + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
+    return s;
+}
+
+constexpr int kPatchThreads = 256;
+
+// One patch per CTA.  Thread 0 starts the bulk copies of the patch's element
+// matrices (n_b^2 runs of 1024 values), local connectivity (n_b runs) and node
+// table into shared memory; all threads wait on the mbarrier, gather x at the
+// patch nodes, then add A_e x_e into the per-node sums colour by colour
+// (within a colour no two elements share a node: no atomics, fixed order).
+// Registers stay low, so several CTAs per SM overlap their copy and compute
+// phases.
 template <typename T, int NB, int MODE>
-__global__ void __launch_bounds__(PatchCfg<T, NB>::NT, PatchCfg<T, NB>::MINB)
+__global__ void __launch_bounds__(kPatchThreads)
 k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
         T* __restrict__ out, T* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
-    constexpr int EPT = PatchCfg<T, NB>::EPT;
-    constexpr int NT = PatchCfg<T, NB>::NT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    double* red = reinterpret_cast<double*>(smem);
-    int* co = reinterpret_cast<int*>(smem + 32 * 8);
-    T* xs = reinterpret_cast<T*>(smem + kHead);
-    T* acc = xs + pd.max_nodes;
+    constexpr int NT = kPatchThreads;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const PatchSmem L = patch_smem_layout<T, NB>(pd.max_nodes);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    int* co = reinterpret_cast<int*>(smem + L.co);
+    const T* As = reinterpret_cast<const T*>(smem + L.A);
+    const uint16_t* Ls = reinterpret_cast<const uint16_t*>(smem + L.L);
+    const int32_t* Gs = reinterpret_cast<const int32_t*>(smem + L.G);
+    T* xs = reinterpret_cast<T*>(smem + L.xs);
+    T* acc = reinterpret_cast<T*>(smem + L.acc);
+    const uint32_t bar = smem_addr(smem + L.bar);
 
     if (stop != nullptr && *stop) return;
     const int p = blockIdx.x;
@@ -71,56 +143,71 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
+    const uint32_t gbytes = uint32_t((m.n_nodes + 3) / 4 * 4) * 4u;
 
-    // 1. element matrices and local connectivity of my elements
-    T a[EPT][NB * NB];
-    int ln[EPT][NB];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        const uint64_t pol = policy_evict_first();
+        mbar_expect_tx(bar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2) + gbytes);
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int s = tid + k * NT;
-        const bool ok = s < m.n_el;
+        for (int t = 0; t < NB * NB; ++t)
+            bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * sizeof(T)), bar, pol);
 #pragma unroll
-        for (int i = 0; i < NB; ++i) ln[k][i] = ok ? int(__ldcs(pd.lconn + i * ns + slot0 + s)) : 0;
-#pragma unroll
-        for (int t = 0; t < NB * NB; ++t) a[k][t] = ok ? __ldcs(A + t * ns + slot0 + s) : T(0);
-    }
-    // 2. restriction: x at the local nodes
-    const int32_t* gid = pd.pnode + m.node_off;
-    for (int l = tid; l < m.n_nodes; l += NT) {
-        xs[l] = __ldg(x + (__ldg(gid + l) & kNodeMask));
-        acc[l] = T(0);
+        for (int i = 0; i < NB; ++i)
+            bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
+        bulk_load(smem_addr(Gs), pd.pnode + m.node_off, gbytes, bar, pol);
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
-    __syncthreads();
-    T xe[EPT][NB];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k)
-#pragma unroll
-        for (int j = 0; j < NB; ++j) xe[k][j] = xs[ln[k][j]];
+    __syncthreads();                      // mbarrier initialised before anyone polls it
+    if (!mbar_wait_bounded(bar, 0, pd.err)) {
+        mbar_wait_bounded(bar, 0, nullptr);   // let copies in flight land before the CTA exits
+        return;
+    }
 
-    // 3. colour-ordered accumulation of A_e x_e
+    // restriction: x at the local nodes
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        xs[l] = __ldg(x + (Gs[l] & kNodeMask));
+        acc[l] = T(0);
+    }
+    __syncthreads();
+
+    // colour-ordered accumulation of A_e x_e
     for (int c = 0; c < m.n_col; ++c) {
-        const int lo = co[c], hi = co[c + 1];
+        const int hi = co[c + 1];
+        for (int s = co[c] + tid; s < hi; s += NT) {
+            int ln[NB];
+            T xe[NB];
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            const int s = tid + k * NT;
-            if (s >= lo && s < hi) {
+            for (int i = 0; i < NB; ++i) {
+                ln[i] = Ls[i * kPatch + s];
+                xe[i] = xs[ln[i]];
+            }
 #pragma unroll
-                for (int i = 0; i < NB; ++i) {
-                    T v = acc[ln[k][i]];
+            for (int i = 0; i < NB; ++i) {
+                T v = acc[ln[i]];
+                if constexpr (sizeof(T) == 8) {
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) v = fmadd(a[k][i * NB + j], xe[k][j], v);
-                    acc[ln[k][i]] = v;
+                    for (int j = 0; j < NB; ++j) v = fmadd(As[(i * NB + j) * kPatch + s], xe[j], v);
+                } else {
+                    // FP32 difference form: the diagonal slot holds the row sum s_i,
+                    // y_i = s_i x_i + sum_{j != i} a_ij (x_j - x_i).  For a smooth x
+                    // the difference is exact in FP32 and the result keeps FP32
+                    // relative accuracy instead of losing it to cancellation.
+                    v = fmadd(As[(i * NB + i) * kPatch + s], xe[i], v);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j != i) v = fmadd(As[(i * NB + j) * kPatch + s], xe[j] - xe[i], v);
                 }
+                acc[ln[i]] = v;
             }
         }
         __syncthreads();
     }
 
-    // 4. owned nodes: final value; shared nodes: halo partial
+    // owned nodes: final value; shared nodes: halo partial
     double dsum = 0.0;
     for (int l = tid; l < m.n_nodes; l += NT) {
-        const int32_t graw = __ldg(gid + l);
+        const int32_t graw = Gs[l];
         const int g = graw & kNodeMask;
         const bool dir = graw < 0;
         const T v = acc[l];
@@ -266,7 +353,7 @@ k_assemble(const PlanDev pd, const double* __restrict__ coords, const double* __
            double* __restrict__ dinv, float* __restrict__ b32, float* __restrict__ dinv32,
            double* __restrict__ halo2, unsigned long long* __restrict__ bad) {
     constexpr int DIM = NB - 1, NT = 256, EPT = kPatch / NT;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     int* co = reinterpret_cast<int*>(smem + 32 * 8);
     double* cs = reinterpret_cast<double*>(smem + kHead);   // [max_nodes][DIM]
     double* fs = cs + pd.max_nodes * DIM;
@@ -308,6 +395,8 @@ k_assemble(const PlanDev pd, const double* __restrict__ coords, const double* __
         double fsum = 0.0;
 #pragma unroll
         for (int j = 0; j < NB; ++j) fsum += fs[ln[k][j]];
+        // row sum of A_e: K_e rows sum to zero, M_e rows to |T|/3 (2D) or |T|/4 (3D)
+        const double rowsum = nu * (md + (NB - 1) * mo);
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
 #pragma unroll
@@ -315,7 +404,8 @@ k_assemble(const PlanDev pd, const double* __restrict__ coords, const double* __
                 const double aij = K[i][j] + nu * (i == j ? md : mo);
                 if (ok) {
                     A64[(i * NB + j) * ns + slot0 + s] = aij;
-                    if (A32 != nullptr) A32[(i * NB + j) * ns + slot0 + s] = float(aij);
+                    // FP32 copy in difference form: row sums on the diagonal slots
+                    if (A32 != nullptr) A32[(i * NB + j) * ns + slot0 + s] = float(i == j ? rowsum : aij);
                 }
                 if (i == j) di[k][i] = aij;
             }
@@ -424,34 +514,37 @@ __global__ void k_mark(int32_t* __restrict__ ids, int64_t n, const uint8_t* __re
     }
 }
 
-template <typename T>
-size_t patch_smem(const PlanDev& pd) { return kHead + size_t(2) * pd.max_nodes * sizeof(T); }
 
 template <typename T, int NB, int MODE>
 cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
-                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches) {
-    const size_t sm = patch_smem<T>(pd);
+                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev) {
+    const size_t sm = patch_smem_layout<T, NB>(pd.max_nodes).total;
     auto kern = k_patch<T, NB, MODE>;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
     }
-    kern<<<pd.n_patches, PatchCfg<T, NB>::NT, sm, st>>>(pd, A, x, b, out, halo, part, stop);
+    if (ev) cudaEventRecord(ev[0], st);
+    kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, x, b, out, halo, part, stop);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
     k_fixup<T, MODE><<<fix_grid(pd.n_shared), kFixThreads, 0, st>>>(pd, x, b, out, halo, part, stop, sc);
+    if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
 
 template <typename T, int NB>
 cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, const T* b, T* out, T* halo,
-                           double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches) {
+                           double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches,
+                           cudaEvent_t* ev) {
     switch (mode) {
-        case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches);
-        case kResidualNorm: return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches);
-        case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches);
-        case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches);
+        case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
+        case kResidualNorm:
+            return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
+        case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
+        case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -465,23 +558,23 @@ int fix_grid(int n_shared) {
 
 cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x, const void* b,
                               void* out, void* halo, double* part, const int32_t* stop, Scalars* sc, cudaStream_t st,
-                              int* launches) {
+                              int* launches, cudaEvent_t* ev) {
     if (dtype == 0) {
         auto a = static_cast<const double*>(A);
         auto xx = static_cast<const double*>(x);
         auto bb = static_cast<const double*>(b);
         auto o = static_cast<double*>(out);
         auto h = static_cast<double*>(halo);
-        return pd.nb == 3 ? run_patch_mode<double, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches)
-                          : run_patch_mode<double, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches);
+        return pd.nb == 3 ? run_patch_mode<double, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev)
+                          : run_patch_mode<double, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev);
     }
     auto a = static_cast<const float*>(A);
     auto xx = static_cast<const float*>(x);
     auto bb = static_cast<const float*>(b);
     auto o = static_cast<float*>(out);
     auto h = static_cast<float*>(halo);
-    return pd.nb == 3 ? run_patch_mode<float, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches)
-                      : run_patch_mode<float, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches);
+    return pd.nb == 3 ? run_patch_mode<float, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev)
+                      : run_patch_mode<float, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev);
 }
 
 cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu, double* A64,

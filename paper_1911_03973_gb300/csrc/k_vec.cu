@@ -66,20 +66,22 @@ __device__ __forceinline__ bool grid_sum2(double& a, double& b, double* part, ui
 }
 
 // x += alpha p;  r -= alpha q;  z = dinv r;  sums r.z, r.r.
+// TX: type of x, r, dinv (the recurrences); TP: type of p, q (the direction
+// and its product, which the operator pass reads and writes).
 // Last block: iteration count, stop tests, beta = r.z / rho, rho = r.z.
-template <typename T>
+template <typename TX, typename TP>
 __global__ void __launch_bounds__(NT)
-k_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r, const T* __restrict__ q,
-         const T* __restrict__ dinv, double* __restrict__ part, Scalars* __restrict__ sc) {
+k_update(int64_t n, TX* __restrict__ x, const TP* __restrict__ p, TX* __restrict__ r, const TP* __restrict__ q,
+         const TX* __restrict__ dinv, double* __restrict__ part, Scalars* __restrict__ sc) {
     __shared__ double red[64];
     if (sc->done) return;
-    const T al = T(sc->alpha);
+    const TX al = TX(sc->alpha);
     double rz = 0.0, rr = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        x[i] = fmadd(al, p[i], x[i]);
-        const T ri = fmadd(-al, q[i], r[i]);
+        x[i] = fmadd(al, TX(p[i]), x[i]);
+        const TX ri = fmadd(-al, TX(q[i]), r[i]);
         r[i] = ri;
-        const T zi = dinv[i] * ri;
+        const TX zi = dinv[i] * ri;
         rz = fmadd(double(ri), double(zi), rz);
         rr = fmadd(double(ri), double(ri), rr);
     }
@@ -103,34 +105,31 @@ k_update(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ 
     }
 }
 
-// p = dinv r + beta p   (init: p = dinv r)
-template <typename T>
+// p = dinv r + beta p   (init: p = dinv r), evaluated in TX, stored as TP.
+template <typename TX, typename TP>
 __global__ void __launch_bounds__(NT)
-k_direction(int64_t n, T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv, int init,
+k_direction(int64_t n, TP* __restrict__ p, const TX* __restrict__ r, const TX* __restrict__ dinv, int init,
             const Scalars* __restrict__ sc) {
     if (sc->done) return;
-    const T be = init ? T(0) : T(sc->beta);
+    const TX be = init ? TX(0) : TX(sc->beta);
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        const T zi = dinv[i] * r[i];
-        p[i] = init ? zi : fmadd(be, p[i], zi);
+        const TX zi = dinv[i] * r[i];
+        p[i] = TP(init ? zi : fmadd(be, TX(p[i]), zi));
     }
 }
 
-// After a true-residual replacement (optionally r = (T) r64 first): sums
-// r.z, r.r; beta = r.z / rho, rho = r.z (init: rho = r.z, beta = 0).
-template <typename T>
+// After a true-residual replacement: sums r.z, r.r; beta = r.z / rho,
+// rho = r.z (init: rho = r.z, beta = 0).
 __global__ void __launch_bounds__(NT)
-k_restart(int64_t n, T* __restrict__ r, const double* __restrict__ r64, const T* __restrict__ dinv, int init,
+k_restart(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv, int init,
           double* __restrict__ part, Scalars* __restrict__ sc) {
     __shared__ double red[64];
     double rz = 0.0, rr = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        T ri;
-        if (r64 != nullptr) { ri = T(r64[i]); r[i] = ri; }
-        else ri = r[i];
-        const T zi = dinv[i] * ri;
-        rz = fmadd(double(ri), double(zi), rz);
-        rr = fmadd(double(ri), double(ri), rr);
+        const double ri = r[i];
+        const double zi = dinv[i] * ri;
+        rz = fmadd(ri, zi, rz);
+        rr = fmadd(ri, ri, rr);
     }
     if (grid_sum2(rz, rr, part, &sc->ctr_vec, red) && threadIdx.x == 0) {
         sc->rz = rz;
@@ -140,13 +139,6 @@ k_restart(int64_t n, T* __restrict__ r, const double* __restrict__ r64, const T*
         sc->rho = rz;
         sc->done = 0;
         sc->reason = kRunning;
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_accumulate(int64_t n, double* __restrict__ x64, float* __restrict__ xs) {
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        x64[i] += double(xs[i]);
-        xs[i] = 0.0f;
     }
 }
 
@@ -184,46 +176,36 @@ int vec_grid(int64_t n) {
     return int(g < 1 ? 1 : (g > 1216 ? 1216 : g));
 }
 
-cudaError_t launch_update(int dtype, int64_t n, void* x, const void* p, void* r, const void* q, const void* dinv,
+// vt: 0 = all FP64; 1 = x, r, dinv FP64 with p, q FP32.
+cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q, const void* dinv,
                           double* part, Scalars* sc, cudaStream_t st, int* launches) {
-    if (dtype == 0)
-        k_update<double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
-                                                     static_cast<double*>(r), static_cast<const double*>(q),
-                                                     static_cast<const double*>(dinv), part, sc);
+    if (vt == 0)
+        k_update<double, double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
+                                                             static_cast<double*>(r), static_cast<const double*>(q),
+                                                             static_cast<const double*>(dinv), part, sc);
     else
-        k_update<float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(x), static_cast<const float*>(p),
-                                                    static_cast<float*>(r), static_cast<const float*>(q),
-                                                    static_cast<const float*>(dinv), part, sc);
+        k_update<double, float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const float*>(p),
+                                                            static_cast<double*>(r), static_cast<const float*>(q),
+                                                            static_cast<const double*>(dinv), part, sc);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_direction(int dtype, int64_t n, void* p, const void* r, const void* dinv, int init, Scalars* sc,
+cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init, Scalars* sc,
                              cudaStream_t st, int* launches) {
-    if (dtype == 0)
-        k_direction<double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(p), static_cast<const double*>(r),
-                                                        static_cast<const double*>(dinv), init, sc);
+    if (vt == 0)
+        k_direction<double, double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(p), static_cast<const double*>(r),
+                                                                static_cast<const double*>(dinv), init, sc);
     else
-        k_direction<float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(p), static_cast<const float*>(r),
-                                                       static_cast<const float*>(dinv), init, sc);
+        k_direction<double, float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(p), static_cast<const double*>(r),
+                                                               static_cast<const double*>(dinv), init, sc);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_restart(int dtype, int64_t n, void* r, const double* r64, const void* dinv, int init, double* part,
-                           Scalars* sc, cudaStream_t st, int* launches) {
-    if (dtype == 0)
-        k_restart<double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(r), r64, static_cast<const double*>(dinv),
-                                                      init, part, sc);
-    else
-        k_restart<float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(r), r64, static_cast<const float*>(dinv),
-                                                     init, part, sc);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_accumulate(int64_t n, double* x64, float* xs, cudaStream_t st, int* launches) {
-    k_accumulate<<<vec_grid(n), NT, 0, st>>>(n, x64, xs);
+cudaError_t launch_restart(int64_t n, const double* r, const double* dinv, int init, double* part, Scalars* sc,
+                           cudaStream_t st, int* launches) {
+    k_restart<<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -25,6 +25,7 @@ struct PlanDev {
     const int32_t* sh_ptr = nullptr;
     const int32_t* sh_slot = nullptr;
     const int32_t* slot_elem = nullptr; // [n_slots], -1 = padding
+    int32_t* err = nullptr;             // set to 1 when a bounded device wait gives up
 };
 
 // What a patch pass produces at the nodes.
@@ -66,9 +67,11 @@ constexpr int kVecThreads = 256;
 // n_patches + fix_grid(n_shared) doubles; halo n_halo values of the dtype.
 // stop (nullable): the pass does nothing when *stop != 0 (solver graphs).
 // sc: receives the norm / dot of kResidualNorm / kApplyDot.
+// ev (nullable): three events recorded before the patch kernel, between it
+// and the fix-up kernel, and after the fix-up.
 cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x,
                               const void* b, void* out, void* halo, double* part, const int32_t* stop,
-                              Scalars* sc, cudaStream_t st, int* launches);
+                              Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
 // Element matrices, load vector and Jacobi diagonal (FP64), Eq. matrices_K_M.
 cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu,
                             double* A64, float* A32, double* b, double* d, double* dinv, float* b32,
@@ -87,17 +90,16 @@ cudaError_t launch_mark_dirichlet(const PlanDev& pd, int32_t* pnode, int64_t n_p
 cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, int64_t n_d,
                                  cudaStream_t st, int* launches);
 // x += alpha p; r -= alpha q; sums r.(dinv r), r.r; stop test (last block).
-cudaError_t launch_update(int dtype, int64_t n, void* x, const void* p, void* r, const void* q,
+// vt: 0 = x, r, dinv, p, q all FP64; 1 = x, r, dinv FP64 and p, q FP32.
+cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q,
                           const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches);
-// p = dinv r + beta p  (init: p = dinv r).
-cudaError_t launch_direction(int dtype, int64_t n, void* p, const void* r, const void* dinv, int init,
+// p = dinv r + beta p  (init: p = dinv r); vt as launch_update.
+cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init,
                              Scalars* sc, cudaStream_t st, int* launches);
 // After a residual replacement: sums r.(dinv r) and r.r; beta = rz/rho, rho = rz
-// (init: rho = rz, beta = 0).  With r64 given, first r = (float) r64.
-cudaError_t launch_restart(int dtype, int64_t n, void* r, const double* r64, const void* dinv, int init,
-                           double* part, Scalars* sc, cudaStream_t st, int* launches);
-// x64 += xs; xs = 0.
-cudaError_t launch_accumulate(int64_t n, double* x64, float* xs, cudaStream_t st, int* launches);
+// (init: rho = rz, beta = 0).  FP64 r and dinv.
+cudaError_t launch_restart(int64_t n, const double* r, const double* dinv, int init, double* part,
+                           Scalars* sc, cudaStream_t st, int* launches);
 // thr2 >= 0: new stop threshold; maxit >= 0: new cap; reset_iter: iter = 0.
 // Always clears done / reason.
 cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches);

@@ -204,6 +204,8 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
         }
         P.col_ptr.push_back(slot);
         for (int32_t g : lnodes) P.pnode.push_back(g);
+        // each table starts on a 16-byte boundary (bulk copies need it)
+        while (P.pnode.size() % 4 != 0) P.pnode.push_back(lnodes[0]);
         for (int l = n_owned; l < n_nodes; ++l) halo_node.push_back(lnodes[l]);
         halo_count += n_nodes - n_owned;
         P.max_nodes = std::max(P.max_nodes, n_nodes);

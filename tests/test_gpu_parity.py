@@ -111,12 +111,24 @@ def test_residual_fp64_matches_oracle(ebe, case):
     assert np.all(r[prob["dirichlet"]] == 0.0) and np.all(y[prob["dirichlet"]] == 0.0)
 
 
+def fp32_difference_form(A64):
+    """The FP32 operator's matrices, built from the oracle's FP64 A_e: off-diagonal
+    entries rounded to FP32, row sums rounded to FP32, diagonal = row sum minus
+    the rounded off-diagonals (evaluated in FP64)."""
+    nb = A64.shape[1]
+    off = A64.astype(np.float32).astype(np.float64)
+    off[:, np.arange(nb), np.arange(nb)] = 0.0
+    s = A64.sum(axis=2).astype(np.float32).astype(np.float64)
+    A = off.copy()
+    A[:, np.arange(nb), np.arange(nb)] = s - off.sum(axis=2)
+    return A
+
+
 @pytest.mark.parametrize("case", ["tri_ragged", "tet_ragged", "tri_tiny"])
 def test_residual_fp32_matches_oracle_on_rounded_matrices(ebe, case):
     prob = _cases()[case]()
     orc64 = oracle.Problem(prob)
-    A32 = orc64.A.astype(np.float32).astype(np.float64)
-    orc = oracle.Problem(prob, A_override=A32)
+    orc = oracle.Problem(prob, A_override=fp32_difference_form(orc64.A))
     h = _setup(ebe, prob)
     x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 18)).astype(np.float32)
     xd = _t(x, torch.float32)

@@ -255,6 +255,23 @@ ebe_status ebe_solve(ebe_handle* h, double* x_dev, const ebe_solve_opts* opts, e
 ebe_status ebe_solve_host(ebe_handle* h, double* x_host, const ebe_solve_opts* opts,
                           ebe_solve_info* info);
 
+/* The paper's stationary iterations (Sec. 2), each step starting from the
+ * element-based residual r = mask(b - A x) (FP64).  x_dev: device [n_n]
+ * double, in: x0, out: x after `iters` steps; x(nd) = g is set first.  No
+ * stopping test: exactly `iters` steps, as in the paper's experiment.
+ * Synchronises the stream.  Errors: EBE_NOT_READY, EBE_INVALID_ARG,
+ * EBE_CUDA_ERROR. */
+/* Eq. richardson: x += omega r (the optimum is 2 / (lambda_1 + lambda_2)). */
+ebe_status ebe_richardson(ebe_handle* h, double* x_dev, int64_t iters, double omega);
+/* Eq. Czebyshev2lev: step k uses x += r / alphas[k mod N]; alphas host [N],
+ * the roots of the shifted and scaled Chebyshev polynomial in the order the
+ * caller chooses. */
+ebe_status ebe_chebyshev2(ebe_handle* h, double* x_dev, int64_t iters, const double* alphas, int64_t N);
+/* Eq. Czebyshev3lev (the three-term recurrence with the scaling factors of
+ * Eq. recrCk) for spectrum bounds 0 < lam1 < lam2, evaluated in the
+ * equivalent direction form p = r + beta p, x += alpha p. */
+ebe_status ebe_chebyshev3(ebe_handle* h, double* x_dev, int64_t iters, double lam1, double lam2);
+
 /* Counters of the handle (see ebe_stats). */
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* stats);
 

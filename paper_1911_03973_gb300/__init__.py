@@ -242,6 +242,23 @@ def ebe_solve_host(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=No
     return _info_dict(info)
 
 
+def ebe_richardson(h: Handle, x, iters: int, omega: float) -> None:
+    """Eq. richardson on a device x (float64 CUDA tensor), exactly `iters` steps."""
+    _check(h, _lib().ebe_richardson(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters), float(omega)))
+
+
+def ebe_chebyshev2(h: Handle, x, iters: int, alphas) -> None:
+    """Eq. Czebyshev2lev with the cyclic root sequence alphas (host array)."""
+    a = _host_f64(alphas)
+    _check(h, _lib().ebe_chebyshev2(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters),
+                                    a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def ebe_chebyshev3(h: Handle, x, iters: int, lam1: float, lam2: float) -> None:
+    """Eq. Czebyshev3lev for spectrum bounds lam1 < lam2."""
+    _check(h, _lib().ebe_chebyshev3(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters), float(lam1), float(lam2)))
+
+
 def ebe_partition_export(coords, elems) -> dict:
     """Host-only element partition (no device needed) as numpy arrays."""
     coords = _host_f64(coords)

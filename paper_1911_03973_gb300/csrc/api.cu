@@ -246,6 +246,7 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (h->device < 0 || h->device >= ndev) return fail(h, EBE_INVALID_ARG, "no such CUDA device");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaDeviceGetAttribute(&h->pd.num_sms, cudaDevAttrMultiProcessorCount, h->device), "cudaDeviceGetAttribute");
     if (h->own_stream) CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "cudaStreamCreate");
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     enter(h);
@@ -579,6 +580,7 @@ struct SolveBufs {
     void* p;
     void* q;
     const void* A;
+    const void* dinv;  // FP64 (plain) or FP32 (mixed) inverse Jacobi diagonal
     void* halo;
 };
 
@@ -586,9 +588,9 @@ SolveBufs bufs_for(ebe_handle* h, bool mixed) {
     SolveBufs s;
     s.dt = mixed ? 1 : 0;
     if (mixed) {
-        s.p = h->p32; s.q = h->q32; s.A = h->A32; s.halo = h->halo32;
+        s.p = h->p32; s.q = h->q32; s.A = h->A32; s.dinv = h->dinv32; s.halo = h->halo32;
     } else {
-        s.p = h->p64; s.q = h->q64; s.A = h->A64; s.halo = h->halo64;
+        s.p = h->p64; s.q = h->q64; s.A = h->A64; s.dinv = h->dinv; s.halo = h->halo64;
     }
     return s;
 }
@@ -600,8 +602,8 @@ int enqueue_iteration(ebe_handle* h, const SolveBufs& s, int* l) {
     CK(launch_patch_pass(h->pd, s.dt, kApplyDot, s.A, s.p, nullptr, s.q, s.halo, h->part_patch, &h->sc->done, h->sc,
                          h->st, l),
        "apply");
-    CK(launch_update(s.dt, n, h->x64w, s.p, h->r64, s.q, h->dinv, h->part_vec, h->sc, h->st, l), "update");
-    CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 0, h->sc, h->st, l), "direction");
+    CK(launch_update(s.dt, n, h->x64w, s.p, h->r64, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
+    CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 0, h->sc, h->st, l), "direction");
     return EBE_OK;
 }
 
@@ -684,8 +686,8 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
         // dropped by delta, and a margin at the end for the drift.
         const double fin = mixed ? 0.7 * target : target;
         l = 0;
-        CK(launch_restart(n, h->r64, h->dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
-        CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 1, h->sc, h->st, &l), "direction");
+        CK(launch_restart(s.dt, n, h->r64, s.dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
+        CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 1, h->sc, h->st, &l), "direction");
         double thr = mixed ? std::max(o.delta * r0, fin) : fin;
         CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
         add_launches(h, l);
@@ -722,8 +724,8 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
             // residual replacement: r64 already holds the FP64 true residual;
             // continue CG from it with the same direction
             l = 0;
-            CK(launch_restart(n, h->r64, h->dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
-            CK(launch_direction(s.dt, n, s.p, h->r64, h->dinv, 0, h->sc, h->st, &l), "direction");
+            CK(launch_restart(s.dt, n, h->r64, s.dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
+            CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 0, h->sc, h->st, &l), "direction");
             thr = mixed ? std::max(o.delta * std::sqrt(rr), fin) : fin;
             CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
             add_launches(h, l);
@@ -770,6 +772,70 @@ ebe_status ebe_solve(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_s
 
 ebe_status ebe_solve_host(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info) {
     return ebe_status(solve_entry(h, x, true, opts, info));
+}
+
+// Stationary iterations of Sec. 2 on a device x: method 0 Richardson
+// (Eq. richardson), 1 two-level Chebyshev (Eq. Czebyshev2lev), 2 three-level
+// Chebyshev (Eq. Czebyshev3lev) in its direction form: with d = (l1+l2)/2,
+// c = (l2-l1)/2, step 0 takes p = r, alpha = 1/d; step k > 0 takes
+// beta = (c alpha / 2)^2, p = r + beta p, alpha = 1/(d - beta/alpha); then
+// x += alpha p.  Every step starts from the residual r = mask(b - A x).
+static int stationary_impl(ebe_handle* h, double* x, int64_t iters, int method, const double* prm, int64_t np) {
+    TRY(check_ready(h, true));
+    if (!x || iters < 0) return fail(h, EBE_INVALID_ARG, "x must be non-NULL and iters >= 0");
+    if (method == 1) {
+        if (!prm || np < 1) return fail(h, EBE_INVALID_ARG, "alphas must hold N >= 1 roots");
+        for (int64_t k = 0; k < np; ++k)
+            if (!std::isfinite(prm[k]) || prm[k] == 0.0) return fail(h, EBE_INVALID_ARG, "roots must be finite and nonzero");
+    }
+    if (method == 2 && !(prm[0] > 0.0 && prm[1] > prm[0] && std::isfinite(prm[1])))
+        return fail(h, EBE_INVALID_ARG, "need 0 < lam1 < lam2");
+    if (method == 0 && !std::isfinite(prm[0])) return fail(h, EBE_INVALID_ARG, "omega must be finite");
+    Scope scp(h);
+    const int64_t n = h->plan.n_n;
+    TRY(dalloc(h, &h->r64, n));
+    TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
+    if (method == 2) TRY(dalloc(h, &h->p64, n));
+    int l = 0;
+    CK(launch_set_dirichlet(x, h->nd, h->g, h->n_d, h->st, &l), "x(nd) = g");
+    const double d = method == 2 ? 0.5 * (prm[0] + prm[1]) : 0.0, c = method == 2 ? 0.5 * (prm[1] - prm[0]) : 0.0;
+    double alpha = 0.0;
+    for (int64_t k = 0; k < iters; ++k) {
+        CK(launch_patch_pass(h->pd, 0, kResidual, h->A64, x, h->b, h->r64, h->halo64, h->part_patch, nullptr, h->sc, h->st,
+                             &l), "residual");
+        if (method == 0) {
+            CK(launch_stationary(n, x, h->r64, nullptr, 0, prm[0], 0.0, h->st, &l), "update");
+        } else if (method == 1) {
+            CK(launch_stationary(n, x, h->r64, nullptr, 0, 1.0 / prm[k % np], 0.0, h->st, &l), "update");
+        } else {
+            // From Eq. Czebyshev3lev: alpha_k = 2 C_k / (c C_{k+1}) and
+            // beta_k = (C_{k-1} / C_k)^2 = (c alpha_{k-1} / 2)^2 for k >= 2; the
+            // special first step x^1 = x^0 + r_0 / d makes beta_1 = (c alpha_0)^2 / 2.
+            double beta = 0.0;
+            if (k == 0) {
+                alpha = 1.0 / d;
+            } else {
+                beta = k == 1 ? 0.5 * (c * alpha) * (c * alpha) : (c * alpha / 2.0) * (c * alpha / 2.0);
+                alpha = 1.0 / (d - beta / alpha);
+            }
+            CK(launch_stationary(n, x, h->r64, h->p64, 1, alpha, beta, h->st, &l), "update");
+        }
+    }
+    add_launches(h, l);
+    return check_device(h);
+}
+
+ebe_status ebe_richardson(ebe_handle* h, double* x, int64_t iters, double omega) {
+    return ebe_status(stationary_impl(h, x, iters, 0, &omega, 1));
+}
+
+ebe_status ebe_chebyshev2(ebe_handle* h, double* x, int64_t iters, const double* alphas, int64_t N) {
+    return ebe_status(stationary_impl(h, x, iters, 1, alphas, N));
+}
+
+ebe_status ebe_chebyshev3(ebe_handle* h, double* x, int64_t iters, double lam1, double lam2) {
+    const double prm[2] = {lam1, lam2};
+    return ebe_status(stationary_impl(h, x, iters, 2, prm, 2));
 }
 
 ebe_status ebe_partition_export(const ebe_mesh* m, ebe_partition_sizes* sz, int32_t* slot_elem, uint16_t* lconn,

@@ -1,18 +1,21 @@
 // Patch passes of the element-by-element operator (sm_103a).
 //
-// One CTA per patch of kPatch elements (see plan.cpp).  A pass:
-//   1. streams the patch's element matrices (structure of arrays: entry t of
-//      all slots is contiguous, so a warp reads 32 consecutive values) and the
-//      16-bit local connectivity into registers, with evict-first loads;
-//   2. gathers x at the patch's local nodes into shared memory -- the
-//      restriction x_e = R_e x of Algorithm 1, shared by neighbouring elements;
-//   3. adds A_e x_e into per-node shared-memory sums colour by colour: within
-//      a colour no two elements share a node, so there are no atomics and the
-//      order of the additions is fixed (bitwise reproducible).  The product is
-//      folded into the sum (sum = fma(a_ij, x_j, sum)) to keep FP64 pipe work
-//      at n_b^2 FMAs per element;
-//   4. writes the result of every owned node (all of its elements are in this
-//      patch) and the partial sum of every shared node to its halo slot.
+// A patch is a run of kPatch elements (see plan.cpp); one CTA handles one
+// patch and several CTAs share an SM, so that one CTA's copies overlap
+// another's arithmetic:
+//   * the TMA engine bulk-copies the patch's element matrices (structure of
+//     arrays: entry t of the patch's 1024 slots is one contiguous run) and
+//     16-bit local connectivity into shared memory, evict-first in L2; while
+//     they are in flight the threads gather the patch's node table, x and b
+//     at the patch nodes -- the restriction x_e = R_e x of Algorithm 1,
+//     shared by neighbouring elements;
+//   * the threads add A_e x_e into per-node shared-memory sums colour by
+//     colour: within a colour no two elements share a node, so there are no
+//     atomics and the order of the additions is fixed (bitwise reproducible).
+//     The product is folded into the sum (sum = fma(a_ij, x_j, sum)), so the
+//     FP64 pipe does exactly n_b^2 FMAs per element;
+//   * they write the result of every owned node (all of its elements are in
+//     this patch) and the partial sum of every shared node to its halo slot.
 // The fix-up pass adds the halo partials of each shared node in patch order.
 #include <cstdint>
 
@@ -92,48 +95,56 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, 
     return false;
 }
 
-// Shared-memory layout of a patch pass (bytes from the dynamic base).
+// Shared-memory layout of a patch pass.  One patch per CTA: its element
+// matrices (n_b^2 runs of 1024 values) and local connectivity (n_b runs) come
+// in by TMA bulk copies; the node table, x and b at the patch nodes by plain
+// loads issued while the bulk copies are in flight.
 struct PatchSmem {
-    uint32_t bar, red, co, A, L, G, xs, acc, total;
+    uint32_t bar, flag, red, co, A, L, G, xs, bs, acc, total;
 };
 template <typename T, int NB>
-__host__ __device__ constexpr PatchSmem patch_smem_layout(int max_nodes) {
+__host__ __device__ constexpr PatchSmem patch_layout(int max_nodes) {
     PatchSmem s{};
     const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
-    s.bar = 0;
+    s.bar = 0;                                          // u64 mbarrier
+    s.flag = 8;                                         // int
     s.red = 16;                                         // 32 doubles
     s.co = s.red + 32 * 8;                              // kMaxColours + 1 ints
     s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
     s.L = s.A + uint32_t(NB * NB * kPatch * sizeof(T));
     s.G = s.L + uint32_t(NB * kPatch * 2);
     s.xs = s.G + gcap * 4;
-    s.acc = (s.xs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
-    s.total = (s.acc + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
+    s.bs = (s.xs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
+    s.acc = (s.bs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
+    s.total = (s.acc + gcap * uint32_t(sizeof(T)) + 127) / 128 * 128;
     return s;
 }
 
 constexpr int kPatchThreads = 256;
+constexpr int kEPT = kPatch / kPatchThreads;     // elements owned by a thread
 
-// One patch per CTA.  Thread 0 starts the bulk copies of the patch's element
-// matrices (n_b^2 runs of 1024 values), local connectivity (n_b runs) and node
-// table into shared memory; all threads wait on the mbarrier, gather x at the
-// patch nodes, then add A_e x_e into the per-node sums colour by colour
-// (within a colour no two elements share a node: no atomics, fixed order).
-// Registers stay low, so several CTAs per SM overlap their copy and compute
-// phases.
+// One patch per CTA, several CTAs per SM so that one CTA's copies overlap
+// another's arithmetic.  Thread 0 starts the bulk copies; meanwhile all
+// threads gather the node table, x and b.  Each thread owns the slots
+// tid + 256 k and keeps their local node ids and x values in registers, so a
+// colour round only reads the element matrix entries from shared memory and
+// updates the node sums.
 template <typename T, int NB, int MODE>
 __global__ void __launch_bounds__(kPatchThreads)
 k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
         T* __restrict__ out, T* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
     constexpr int NT = kPatchThreads;
+    constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
     extern __shared__ __align__(128) unsigned char smem[];
-    const PatchSmem L = patch_smem_layout<T, NB>(pd.max_nodes);
+    const PatchSmem L = patch_layout<T, NB>(pd.max_nodes);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + L.flag);
     double* red = reinterpret_cast<double*>(smem + L.red);
     int* co = reinterpret_cast<int*>(smem + L.co);
     const T* As = reinterpret_cast<const T*>(smem + L.A);
     const uint16_t* Ls = reinterpret_cast<const uint16_t*>(smem + L.L);
-    const int32_t* Gs = reinterpret_cast<const int32_t*>(smem + L.G);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + L.G);
     T* xs = reinterpret_cast<T*>(smem + L.xs);
+    T* bs = reinterpret_cast<T*>(smem + L.bs);
     T* acc = reinterpret_cast<T*>(smem + L.acc);
     const uint32_t bar = smem_addr(smem + L.bar);
 
@@ -143,62 +154,91 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
-    const uint32_t gbytes = uint32_t((m.n_nodes + 3) / 4 * 4) * 4u;
 
     if (tid == 0) {
         mbar_init(bar, 1);
         const uint64_t pol = policy_evict_first();
-        mbar_expect_tx(bar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2) + gbytes);
+        mbar_expect_tx(bar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
 #pragma unroll
         for (int t = 0; t < NB * NB; ++t)
             bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * sizeof(T)), bar, pol);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
             bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
-        bulk_load(smem_addr(Gs), pd.pnode + m.node_off, gbytes, bar, pol);
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
-    __syncthreads();                      // mbarrier initialised before anyone polls it
-    if (!mbar_wait_bounded(bar, 0, pd.err)) {
-        mbar_wait_bounded(bar, 0, nullptr);   // let copies in flight land before the CTA exits
-        return;
+    // restriction x_e = R_e x, shared by the patch: node table, x (and b)
+    const int32_t* pn = pd.pnode + m.node_off;
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        int32_t gr[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            gr[u] = l < m.n_nodes ? __ldg(pn + l) : 0;
+        }
+        T xv[2], bv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            const int g = gr[u] & kNodeMask;
+            xv[u] = l < m.n_nodes ? __ldg(x + g) : T(0);
+            bv[u] = (kRes && l < m.n_owned) ? __ldg(b + g) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            if (l < m.n_nodes) {
+                Gs[l] = gr[u];
+                xs[l] = xv[u];
+                acc[l] = T(0);
+                if (kRes) bs[l] = bv[u];
+            }
+        }
     }
-
-    // restriction: x at the local nodes
-    for (int l = tid; l < m.n_nodes; l += NT) {
-        xs[l] = __ldg(x + (Gs[l] & kNodeMask));
-        acc[l] = T(0);
-    }
+    // one thread waits (bounded) for the bulk copies and shares the outcome
+    if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
     __syncthreads();
+    if (*flag == 0) return;
+    while (!mbar_try_wait(bar, 0)) {
+    }                                             // completed already: acquire for this thread
 
+    // my slots: local node ids and x values in registers
+    int ln[kEPT][NB];
+    T xe[kEPT][NB];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            ln[k][i] = ok ? int(Ls[i * kPatch + s]) : 0;
+            xe[k][i] = xs[ln[k][i]];
+        }
+    }
     // colour-ordered accumulation of A_e x_e
     for (int c = 0; c < m.n_col; ++c) {
-        const int hi = co[c + 1];
-        for (int s = co[c] + tid; s < hi; s += NT) {
-            int ln[NB];
-            T xe[NB];
+        const int lo = co[c], hi = co[c + 1];
 #pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                ln[i] = Ls[i * kPatch + s];
-                xe[i] = xs[ln[i]];
-            }
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            if (s >= lo && s < hi) {
 #pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                T v = acc[ln[i]];
-                if constexpr (sizeof(T) == 8) {
+                for (int r = 0; r < NB; ++r) {
+                    T v = acc[ln[k][r]];
+                    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) v = fmadd(As[(i * NB + j) * kPatch + s], xe[j], v);
-                } else {
-                    // FP32 difference form: the diagonal slot holds the row sum s_i,
-                    // y_i = s_i x_i + sum_{j != i} a_ij (x_j - x_i).  For a smooth x
-                    // the difference is exact in FP32 and the result keeps FP32
-                    // relative accuracy instead of losing it to cancellation.
-                    v = fmadd(As[(i * NB + i) * kPatch + s], xe[i], v);
+                        for (int j = 0; j < NB; ++j) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j], v);
+                    } else {
+                        // FP32 difference form: the diagonal slot holds the row sum s_r,
+                        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
+                        // difference is exact in FP32 and no accuracy is lost to cancellation.
+                        v = fmadd(As[(r * NB + r) * kPatch + s], xe[k][r], v);
 #pragma unroll
-                    for (int j = 0; j < NB; ++j)
-                        if (j != i) v = fmadd(As[(i * NB + j) * kPatch + s], xe[j] - xe[i], v);
+                        for (int j = 0; j < NB; ++j)
+                            if (j != r) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j] - xe[k][r], v);
+                    }
+                    acc[ln[k][r]] = v;
                 }
-                acc[ln[i]] = v;
             }
         }
         __syncthreads();
@@ -213,7 +253,7 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
         const T v = acc[l];
         if (l < m.n_owned) {
             T o;
-            if (MODE == kResidual || MODE == kResidualNorm) o = dir ? T(0) : T(__ldg(b + g) - v);
+            if (kRes) o = dir ? T(0) : T(bs[l] - v);
             else o = dir ? T(0) : v;
             out[g] = o;
             if (MODE == kResidualNorm) dsum += double(o) * double(o);
@@ -257,18 +297,23 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
         if (MODE == kApplyDot) dsum += double(__ldg(x + g)) * double(o);
     }
     if (MODE == kResidualNorm || MODE == kApplyDot) {
+        // this block also adds a contiguous chunk of the patch partials (one per
+        // patch, written by the patch pass), so the last block has few to add
+        const int np = pd.n_patches;
+        const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
+        const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
+        for (int i = int(blockIdx.x) * chunk + threadIdx.x; i < p1; i += kFixThreads) dsum += part[i];
         dsum = block_sum<kFixThreads>(dsum, red);
         if (threadIdx.x == 0) {
-            part[pd.n_patches + blockIdx.x] = dsum;
+            part[np + blockIdx.x] = dsum;
             __threadfence();
             last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
         }
         __syncthreads();
         if (last) {
             __threadfence();
-            const int total = pd.n_patches + gridDim.x;
             double s = 0.0;
-            for (int i = threadIdx.x; i < total; i += kFixThreads) s += __ldcg(part + i);
+            for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads) s += __ldcg(part + np + i);
             s = block_sum<kFixThreads>(s, red);
             if (threadIdx.x == 0) {
                 sc->ctr_fix = 0;
@@ -518,15 +563,14 @@ __global__ void k_mark(int32_t* __restrict__ ids, int64_t n, const uint8_t* __re
 template <typename T, int NB, int MODE>
 cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
                       const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev) {
-    const size_t sm = patch_smem_layout<T, NB>(pd.max_nodes).total;
+    const size_t sm = patch_layout<T, NB>(pd.max_nodes).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;   // a patch does not fit in shared memory
     auto kern = k_patch<T, NB, MODE>;
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], st);
     kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, x, b, out, halo, part, stop);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     k_fixup<T, MODE><<<fix_grid(pd.n_shared), kFixThreads, 0, st>>>(pd, x, b, out, halo, part, stop, sc);

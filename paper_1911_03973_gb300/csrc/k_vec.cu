@@ -1,12 +1,18 @@
-// Node-vector kernels of the Jacobi-PCG iteration (sm_103a).
+// Node-vector kernels of the Jacobi-PCG iteration and of the paper's
+// stationary iterations (sm_103a).
 //
-// All dot products are accumulated in FP64 whatever the vector type, per
-// thread in a fixed index order, then over the block by fixed-pattern warp
-// butterflies, then over a fixed grid by the last block to arrive, which adds
-// the per-block partials in index order.  The results are therefore bitwise
-// reproducible for a given problem size.  The last block also takes the
-// iteration's scalar decisions (alpha, beta, stop) so that the host never has
-// to read anything inside a graph chunk.
+// All dot products end in FP64: per thread in a fixed index order, then over
+// the block by fixed-pattern warp butterflies, then over a fixed grid by the
+// last block to arrive, which adds the per-block partials in index order.  The
+// results are therefore bitwise reproducible for a given problem size.  The
+// last block also takes the iteration's scalar decisions (beta, stop) so that
+// the host never reads anything inside a graph chunk.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate, so the mixed-precision kernels
+// keep only what needs FP64 in FP64: the solution x and the residual r (the
+// two recurrences whose rounding would make the recurrence residual drift).
+// z = dinv r, the direction p and q = A p are FP32; the per-thread dot sums
+// use compensated FP32 (Neumaier) before the FP64 block reduction.
 #include <cstdint>
 
 #include "kernels.h"
@@ -17,7 +23,17 @@ namespace {
 constexpr int NT = kVecThreads;
 
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Neumaier-compensated FP32 sum: s + c carries the sum to about FP32^2.
+struct CompSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
 
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 #pragma unroll
@@ -65,78 +81,128 @@ __device__ __forceinline__ bool grid_sum2(double& a, double& b, double* part, ui
     return true;
 }
 
-// x += alpha p;  r -= alpha q;  z = dinv r;  sums r.z, r.r.
-// TX: type of x, r, dinv (the recurrences); TP: type of p, q (the direction
-// and its product, which the operator pass reads and writes).
-// Last block: iteration count, stop tests, beta = r.z / rho, rho = r.z.
-template <typename TX, typename TP>
+// Stop tests and beta of one CG iteration (last block, thread 0).
+__device__ __forceinline__ void decide(Scalars* sc, double rz, double rr) {
+    sc->iter += 1;
+    sc->rz = rz;
+    sc->rr = rr;
+    if (!isfinite(rz) || !isfinite(rr) || rz < 0.0) {
+        sc->done = 1;
+        sc->reason = kBreakdown;
+    } else if (rr <= sc->thr2) {
+        sc->done = 1;            // rho stays: the host recomputes r.z after the replacement
+        sc->reason = kTrigger;
+    } else if (sc->iter >= sc->maxit) {
+        sc->done = 1;
+        sc->reason = kMaxit;
+    } else {
+        sc->beta = rz / sc->rho;
+        sc->rho = rz;
+    }
+}
+
+// ------------------------------------------------------------------ FP64
+// x += alpha p;  r -= alpha q;  z = dinv r;  sums r.z, r.r (all FP64).
 __global__ void __launch_bounds__(NT)
-k_update(int64_t n, TX* __restrict__ x, const TP* __restrict__ p, TX* __restrict__ r, const TP* __restrict__ q,
-         const TX* __restrict__ dinv, double* __restrict__ part, Scalars* __restrict__ sc) {
+k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
+           const double* __restrict__ q, const double* __restrict__ dinv, double* __restrict__ part,
+           Scalars* __restrict__ sc) {
     __shared__ double red[64];
     if (sc->done) return;
-    const TX al = TX(sc->alpha);
+    const double al = sc->alpha;
     double rz = 0.0, rr = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        x[i] = fmadd(al, TX(p[i]), x[i]);
-        const TX ri = fmadd(-al, TX(q[i]), r[i]);
+        x[i] = fmadd(al, p[i], x[i]);
+        const double ri = fmadd(-al, q[i], r[i]);
         r[i] = ri;
-        const TX zi = dinv[i] * ri;
-        rz = fmadd(double(ri), double(zi), rz);
-        rr = fmadd(double(ri), double(ri), rr);
-    }
-    if (grid_sum2(rz, rr, part, &sc->ctr_vec, red) && threadIdx.x == 0) {
-        sc->iter += 1;
-        sc->rz = rz;
-        sc->rr = rr;
-        if (!isfinite(rz) || !isfinite(rr) || rz < 0.0) {
-            sc->done = 1;
-            sc->reason = kBreakdown;
-        } else if (rr <= sc->thr2) {
-            sc->done = 1;            // rho stays: the host recomputes r.z after the replacement
-            sc->reason = kTrigger;
-        } else if (sc->iter >= sc->maxit) {
-            sc->done = 1;
-            sc->reason = kMaxit;
-        } else {
-            sc->beta = rz / sc->rho;
-            sc->rho = rz;
-        }
-    }
-}
-
-// p = dinv r + beta p   (init: p = dinv r), evaluated in TX, stored as TP.
-template <typename TX, typename TP>
-__global__ void __launch_bounds__(NT)
-k_direction(int64_t n, TP* __restrict__ p, const TX* __restrict__ r, const TX* __restrict__ dinv, int init,
-            const Scalars* __restrict__ sc) {
-    if (sc->done) return;
-    const TX be = init ? TX(0) : TX(sc->beta);
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        const TX zi = dinv[i] * r[i];
-        p[i] = TP(init ? zi : fmadd(be, TX(p[i]), zi));
-    }
-}
-
-// After a true-residual replacement: sums r.z, r.r; beta = r.z / rho,
-// rho = r.z (init: rho = r.z, beta = 0).
-__global__ void __launch_bounds__(NT)
-k_restart(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv, int init,
-          double* __restrict__ part, Scalars* __restrict__ sc) {
-    __shared__ double red[64];
-    double rz = 0.0, rr = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        const double ri = r[i];
-        const double zi = dinv[i] * ri;
-        rz = fmadd(ri, zi, rz);
+        rz = fmadd(ri, dinv[i] * ri, rz);
         rr = fmadd(ri, ri, rr);
     }
-    if (grid_sum2(rz, rr, part, &sc->ctr_vec, red) && threadIdx.x == 0) {
-        sc->rz = rz;
-        sc->rr = rr;
+    if (grid_sum2(rz, rr, part, &sc->ctr_vec, red) && threadIdx.x == 0) decide(sc, rz, rr);
+}
+
+// p = dinv r + beta p  (init: p = dinv r), FP64.
+__global__ void __launch_bounds__(NT)
+k_direction64(int64_t n, double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ dinv,
+              int init, const Scalars* __restrict__ sc) {
+    if (sc->done) return;
+    const double be = init ? 0.0 : sc->beta;
+    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+        const double zi = dinv[i] * r[i];
+        p[i] = init ? zi : fmadd(be, p[i], zi);
+    }
+}
+
+// ------------------------------------------------------------------ mixed
+// x += alpha p and r -= alpha q in FP64 (p, q FP32); z = dinv32 * (float) r;
+// sums r.z, r.r per thread in compensated FP32.
+__global__ void __launch_bounds__(NT)
+k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, double* __restrict__ r,
+               const float* __restrict__ q, const float* __restrict__ dinv, double* __restrict__ part,
+               Scalars* __restrict__ sc) {
+    __shared__ double red[64];
+    if (sc->done) return;
+    const double al = sc->alpha;
+    CompSum rz, rr;
+    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+        x[i] = fmadd(al, double(p[i]), x[i]);
+        const double ri = fmadd(-al, double(q[i]), r[i]);
+        r[i] = ri;
+        const float rf = float(ri);
+        rz.add(rf * (dinv[i] * rf));
+        rr.add(rf * rf);
+    }
+    double a = rz.value(), b = rr.value();
+    if (grid_sum2(a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) decide(sc, a, b);
+}
+
+// p = dinv32 * (float) r + beta p  (init: p = dinv32 * (float) r), FP32.
+__global__ void __launch_bounds__(NT)
+k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r, const float* __restrict__ dinv,
+                  int init, const Scalars* __restrict__ sc) {
+    if (sc->done) return;
+    const float be = init ? 0.0f : float(sc->beta);
+    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+        const float zi = dinv[i] * float(r[i]);
+        p[i] = init ? zi : __fmaf_rn(be, p[i], zi);
+    }
+}
+
+// After a true-residual replacement: sums r.z, r.r with z as the update
+// kernel of the same precision forms it; beta = r.z / rho, rho = r.z
+// (init: rho = r.z, beta = 0).
+template <bool MIXED>
+__global__ void __launch_bounds__(NT)
+k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv_v, int init,
+          double* __restrict__ part, Scalars* __restrict__ sc) {
+    __shared__ double red[64];
+    double a, b;
+    if (MIXED) {
+        const float* dinv = static_cast<const float*>(dinv_v);
+        CompSum rz, rr;
+        for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+            const float rf = float(r[i]);
+            rz.add(rf * (dinv[i] * rf));
+            rr.add(rf * rf);
+        }
+        a = rz.value();
+        b = rr.value();
+    } else {
+        const double* dinv = static_cast<const double*>(dinv_v);
+        a = 0.0;
+        b = 0.0;
+        for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+            const double ri = r[i];
+            a = fmadd(ri, dinv[i] * ri, a);
+            b = fmadd(ri, ri, b);
+        }
+    }
+    if (grid_sum2(a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) {
+        sc->rz = a;
+        sc->rr = b;
         if (init || !(sc->rho != 0.0)) sc->beta = 0.0;
-        else sc->beta = rz / sc->rho;
-        sc->rho = rz;
+        else sc->beta = a / sc->rho;
+        sc->rho = a;
         sc->done = 0;
         sc->reason = kRunning;
     }
@@ -153,6 +219,23 @@ k_set_dirichlet(double* __restrict__ x, const int32_t* __restrict__ nd, const do
         x[nd[k]] = g ? g[k] : 0.0;
 }
 
+// Stationary steps of Sec. 2.  kind 0: x += w r (Richardson, two-level
+// Chebyshev with w = 1/alpha_k); kind 1: p = r + beta p, x += alpha p (the
+// three-level Chebyshev iteration in its direction form; beta = 0 starts it).
+__global__ void __launch_bounds__(NT)
+k_stationary(int64_t n, double* __restrict__ x, const double* __restrict__ r, double* __restrict__ p, int kind,
+             double w, double beta) {
+    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+        if (kind == 0) {
+            x[i] = fmadd(w, r[i], x[i]);
+        } else {
+            const double pi = beta == 0.0 ? r[i] : fmadd(beta, p[i], r[i]);
+            p[i] = pi;
+            x[i] = fmadd(w, pi, x[i]);
+        }
+    }
+}
+
 // Host-chosen controls of a solve: stop threshold, iteration cap, counters.
 __global__ void k_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -165,28 +248,21 @@ __global__ void k_control(Scalars* sc, double thr2, int64_t maxit, int reset_ite
 
 }  // namespace
 
-cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches) {
-    k_control<<<1, 32, 0, st>>>(sc, thr2, maxit, reset_iter);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
-}
-
 int vec_grid(int64_t n) {
     int64_t g = (n + NT - 1) / NT;
     return int(g < 1 ? 1 : (g > 1216 ? 1216 : g));
 }
 
-// vt: 0 = all FP64; 1 = x, r, dinv FP64 with p, q FP32.
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q, const void* dinv,
                           double* part, Scalars* sc, cudaStream_t st, int* launches) {
     if (vt == 0)
-        k_update<double, double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
-                                                             static_cast<double*>(r), static_cast<const double*>(q),
-                                                             static_cast<const double*>(dinv), part, sc);
+        k_update64<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
+                                               static_cast<double*>(r), static_cast<const double*>(q),
+                                               static_cast<const double*>(dinv), part, sc);
     else
-        k_update<double, float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const float*>(p),
-                                                            static_cast<double*>(r), static_cast<const float*>(q),
-                                                            static_cast<const double*>(dinv), part, sc);
+        k_update_mixed<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const float*>(p),
+                                                   static_cast<double*>(r), static_cast<const float*>(q),
+                                                   static_cast<const float*>(dinv), part, sc);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -194,18 +270,25 @@ cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, co
 cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init, Scalars* sc,
                              cudaStream_t st, int* launches) {
     if (vt == 0)
-        k_direction<double, double><<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(p), static_cast<const double*>(r),
-                                                                static_cast<const double*>(dinv), init, sc);
+        k_direction64<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(p), static_cast<const double*>(r),
+                                                  static_cast<const double*>(dinv), init, sc);
     else
-        k_direction<double, float><<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(p), static_cast<const double*>(r),
-                                                               static_cast<const double*>(dinv), init, sc);
+        k_direction_mixed<<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(p), static_cast<const double*>(r),
+                                                      static_cast<const float*>(dinv), init, sc);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_restart(int64_t n, const double* r, const double* dinv, int init, double* part, Scalars* sc,
+cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part, Scalars* sc,
                            cudaStream_t st, int* launches) {
-    k_restart<<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
+    if (vt == 0) k_restart<false><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
+    else k_restart<true><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches) {
+    k_control<<<1, 32, 0, st>>>(sc, thr2, maxit, reset_iter);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -221,6 +304,13 @@ cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, 
                                  int* launches) {
     if (n_d <= 0) return cudaSuccess;
     k_set_dirichlet<<<vec_grid(n_d), NT, 0, st>>>(x, nd, g, n_d);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stationary(int64_t n, double* x, const double* r, double* p, int kind, double w, double beta,
+                              cudaStream_t st, int* launches) {
+    k_stationary<<<vec_grid(n), NT, 0, st>>>(n, x, r, p, kind, w, beta);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ struct PlanDev {
     const int32_t* sh_slot = nullptr;
     const int32_t* slot_elem = nullptr; // [n_slots], -1 = padding
     int32_t* err = nullptr;             // set to 1 when a bounded device wait gives up
+    int num_sms = 1;                    // persistent grid size of the patch pass
 };
 
 // What a patch pass produces at the nodes.
@@ -90,20 +91,23 @@ cudaError_t launch_mark_dirichlet(const PlanDev& pd, int32_t* pnode, int64_t n_p
 cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, int64_t n_d,
                                  cudaStream_t st, int* launches);
 // x += alpha p; r -= alpha q; sums r.(dinv r), r.r; stop test (last block).
-// vt: 0 = x, r, dinv, p, q all FP64; 1 = x, r, dinv FP64 and p, q FP32.
+// vt 0: x, r, dinv, p, q FP64.  vt 1: x, r FP64; p, q, dinv FP32.
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q,
                           const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches);
 // p = dinv r + beta p  (init: p = dinv r); vt as launch_update.
 cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init,
                              Scalars* sc, cudaStream_t st, int* launches);
 // After a residual replacement: sums r.(dinv r) and r.r; beta = rz/rho, rho = rz
-// (init: rho = rz, beta = 0).  FP64 r and dinv.
-cudaError_t launch_restart(int64_t n, const double* r, const double* dinv, int init, double* part,
+// (init: rho = rz, beta = 0).  FP64 r; dinv FP64 (vt 0) or FP32 (vt 1).
+cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part,
                            Scalars* sc, cudaStream_t st, int* launches);
 // thr2 >= 0: new stop threshold; maxit >= 0: new cap; reset_iter: iter = 0.
 // Always clears done / reason.
 cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches);
 cudaError_t launch_fill(int dtype, int64_t n, void* v, double value, cudaStream_t st, int* launches);
+// kind 0: x += w r; kind 1: p = r + beta p (beta = 0: p = r), x += w p.
+cudaError_t launch_stationary(int64_t n, double* x, const double* r, double* p, int kind, double w, double beta,
+                              cudaStream_t st, int* launches);
 
 // ---- comparison scatters (k_alt.cu) ---------------------------------------
 cudaError_t launch_build_gconn(const PlanDev& pd, int32_t* gconn, cudaStream_t st, int* launches);

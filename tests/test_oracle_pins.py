@@ -386,3 +386,30 @@ def test_chebyshev3_bound():
     for N in (5, 20, 40):
         xN = p.chebyshev3(x0, N, l1, l2)
         assert np.linalg.norm(xN - u) <= 2 * q ** N * np.linalg.norm(x0 - u) * (1 + 1e-8)
+
+
+def test_paper_experiment_qualitative_outcome():
+    """Sec. 3: 33^2 nodes, nu = 0, u = 1 on the boundary, f = 1, 124 iterations
+    with the spectrum bounds of Sec. 3: only the three-level Chebyshev method
+    converges; Richardson needs more steps; the two-level method with N = 32
+    (roots in the listing's order) is visibly worse than the three-level one,
+    and its iterate at k = N no longer matches the three-level iterate (the
+    instability the paper mentions), while for small N they agree."""
+    n = 33
+    prob = meshgen.config_square_f1(n, nu=0.0, g_value=1.0)
+    lam = _closed_form_spectrum(n)
+    l1, l2 = lam[0], lam[-1]
+    p = oracle.Problem(prob)
+    u, _ = p.pcg(rtol=1e-13)
+    x0 = p.with_dirichlet(np.zeros(p.n_n))
+    e0 = np.abs(x0 - u).max()
+    err = lambda x: np.abs(x - u).max() / e0  # noqa: E731
+    e_rich = err(p.richardson(x0, 124, 2.0 / (l1 + l2)))
+    e_cheb2 = err(p.chebyshev2(x0, 124, oracle.chebyshev_roots(l1, l2, 32)))
+    e_cheb3 = err(p.chebyshev3(x0, 124, l1, l2))
+    assert e_rich > 0.5
+    assert e_cheb3 < 1e-4
+    assert e_cheb2 > 10 * e_cheb3
+    x2 = p.chebyshev2(x0, 32, oracle.chebyshev_roots(l1, l2, 32))
+    x3 = p.chebyshev3(x0, 32, l1, l2)
+    assert np.abs(x2 - x3).max() > 1e-6 * np.abs(x3).max()

@@ -275,6 +275,24 @@ ebe_status ebe_chebyshev3(ebe_handle* h, double* x_dev, int64_t iters, double la
 /* Counters of the handle (see ebe_stats). */
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* stats);
 
+/* ---------------------------------------------------------------- allocation-free residual */
+
+/* ebe_residual (FP64) for callers that must not allocate device memory during
+ * the call -- for instance code running while a stream is being captured into
+ * a CUDA graph, where cudaMalloc is not allowed, or a process whose device
+ * memory is owned by another allocator.  ebe_residual allocates its scratch
+ * on first use; this call takes it from a fixed device array compiled into
+ * the library (32 MiB: 4,194,304 doubles, held on every device that loads the
+ * library until the process exits) and calls no allocator.  The paper has no
+ * counterpart: this is an interface feature of the library.
+ * x_dev, r_dev: device [n_n] double (caller-owned), as for ebe_residual.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * whose kernels overlap on the GPU (several streams or handles at once) race.
+ * Errors: EBE_NOT_READY, EBE_INVALID_ARG (also when the mesh needs more than
+ * 4,194,304 halo slots, see ebe_stats.n_halo), EBE_CUDA_ERROR. */
+ebe_status ebe_residual_noalloc(ebe_handle* h, const double* x_dev, double* r_dev);
+
 /* ---------------------------------------------------------------- inspection */
 
 typedef struct {

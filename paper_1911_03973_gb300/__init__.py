@@ -242,6 +242,13 @@ def ebe_solve_host(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=No
     return _info_dict(info)
 
 
+def ebe_residual_noalloc(h: Handle, x, r) -> None:
+    """ebe_residual_noalloc: FP64 residual without any device allocation in the
+    call (scratch from a fixed device array in the library), for callers that
+    cannot allocate, e.g. inside a CUDA-graph capture."""
+    _check(h, _lib().ebe_residual_noalloc(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), _dev(r, EBE_F64, h.n_n, "r")))
+
+
 def ebe_richardson(h: Handle, x, iters: int, omega: float) -> None:
     """Eq. richardson on a device x (float64 CUDA tensor), exactly `iters` steps."""
     _check(h, _lib().ebe_richardson(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters), float(omega)))

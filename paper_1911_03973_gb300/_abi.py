@@ -96,6 +96,7 @@ SIGNATURES = [
     ("ebe_residual_variant", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
     ("ebe_solve", ctypes.c_int, [_H, _VP, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
     ("ebe_solve_host", ctypes.c_int, [_H, _F64P, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
+    ("ebe_residual_noalloc", ctypes.c_int, [_H, _VP, _VP]),
     ("ebe_richardson", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double]),
     ("ebe_chebyshev2", ctypes.c_int, [_H, _VP, ctypes.c_int64, _F64P, ctypes.c_int64]),
     ("ebe_chebyshev3", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double]),

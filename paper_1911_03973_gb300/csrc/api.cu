@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -891,3 +892,59 @@ ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free residual
+// Some callers cannot allocate device memory at the point where they need a
+// residual: code running while a stream is being captured into a CUDA graph
+// (cudaMalloc is not allowed there), a process whose device memory is owned
+// by another allocator, or a real-time loop that must not take the
+// allocator's locks.  ebe_residual allocates its halo scratch on first use;
+// ebe_residual_noalloc takes it from a fixed file-scope device array
+// instead: kNoAllocHaloMax doubles (32 MiB), present on every device that
+// loads the library for the life of the process.  Every call shares the
+// array, so calls whose kernels overlap on the GPU (several streams or
+// handles at once) race on it.  Each halo slot is written by the patch pass
+// before the fix-up pass reads it, so nothing in the array needs clearing.
+namespace {
+
+constexpr int64_t kNoAllocHaloMax = int64_t(1) << 22;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_halo[kNoAllocHaloMax];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the handle's device (in host code
+// the array's name is only a stand-in).  Looked up once per device, with that
+// device current.
+int noalloc_scratch(ebe_handle* h, double** out) {
+    if (h->device < 0 || h->device >= kNoAllocMaxDevices) return fail(h, EBE_INVALID_ARG, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[h->device]) {
+        void* p = nullptr;
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        CK(cudaGetSymbolAddress(&p, g_noalloc_halo), "cudaGetSymbolAddress");
+        g_noalloc_addr[h->device] = p;
+    }
+    *out = static_cast<double*>(g_noalloc_addr[h->device]);
+    return EBE_OK;
+}
+
+}  // namespace
+
+extern "C" ebe_status ebe_residual_noalloc(ebe_handle* h, const double* x, double* r) {
+    TRY(check_ready(h, true));
+    if (!x || !r || x == r) return ebe_status(fail(h, EBE_INVALID_ARG, "x and r must be distinct non-NULL device buffers"));
+    if (h->plan.n_halo > kNoAllocHaloMax)
+        return ebe_status(fail(h, EBE_INVALID_ARG,
+                               "mesh needs " + std::to_string(h->plan.n_halo) + " halo slots; ebe_residual_noalloc holds " +
+                                   std::to_string(kNoAllocHaloMax) + " (use ebe_residual)"));
+    double* halo = nullptr;
+    TRY(noalloc_scratch(h, &halo));
+    Scope scp(h);
+    int l = 0;
+    CK(launch_patch_pass(h->pd, 0, kResidual, h->A64, x, h->b, r, halo, h->part_patch, nullptr, h->sc, h->st, &l),
+       "patch pass");
+    add_launches(h, l);
+    return EBE_OK;
+}

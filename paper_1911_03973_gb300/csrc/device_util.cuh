@@ -1,0 +1,53 @@
+// Small device helpers shared by the kernels of libebe.so.
+#pragma once
+
+#include <cstdint>
+
+namespace ebe {
+
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// float -> double and double -> float by integer operations on the IEEE-754
+// bit layouts, so that the conversions stay off the FP64 pipe (GB300 runs
+// FP64 at 1/64 of the FP32 rate).  f2d is exact (normal numbers: rebias the
+// exponent by 1023 - 127 = 896 and shift the mantissa up by 29 bits); d2f
+// rounds to nearest, ties to even (round bit 28, sticky bits 0..27; a carry
+// out of the mantissa correctly bumps the exponent).  Zeros, subnormals,
+// infinities, NaNs and results outside the normal FP32 range take the
+// hardware conversion.
+// The rare cases call out of line: an inlined fallback would be if-converted
+// and the hardware conversion executed for every element.
+static __device__ __noinline__ double f2d_rare(float f) { return double(f); }
+static __device__ __noinline__ float d2f_rare(double v) { return float(v); }
+
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return f2d_rare(f);
+    const uint64_t d = (uint64_t(u & 0x80000000u) << 32) | (uint64_t(e + 896u) << 52) | (uint64_t(u & 0x7fffffu) << 29);
+    return __longlong_as_double(static_cast<long long>(d));
+}
+__device__ __forceinline__ float d2f(double v) {
+    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(v));
+    const int e = int((u >> 52) & 0x7ffu) - 896;
+    if (e <= 0 || e >= 254) return d2f_rare(v);
+    uint32_t bits = (uint32_t(e) << 23) | uint32_t((u >> 29) & 0x7fffffu);
+    const uint32_t rnd = uint32_t(u >> 28) & 1u;
+    const uint32_t sticky = (u & 0x0fffffffull) != 0ull ? 1u : 0u;
+    bits += rnd & (sticky | (bits & 1u));
+    return __uint_as_float((uint32_t(u >> 32) & 0x80000000u) | bits);
+}
+
+// Neumaier-compensated FP32 sum: s + c carries the sum to about FP32^2.
+struct CompSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+}  // namespace ebe

@@ -19,6 +19,7 @@
 // The fix-up pass adds the halo partials of each shared node in patch order.
 #include <cstdint>
 
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace ebe {
@@ -26,8 +27,20 @@ namespace {
 
 constexpr int kHead = 32 * 8 + ((kMaxColours + 1) * 4 + 15) / 16 * 16;  // reduction + colour offsets
 
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// Dot-product accumulator of a pass: FP64 products for FP64 data; for FP32
+// data, FP32 products in a compensated FP32 sum (no FP64 work per node).
+template <typename T>
+struct DotAcc {
+    double d = 0.0;
+    __device__ __forceinline__ void add(T a, T b) { d = fmadd(double(a), double(b), d); }
+    __device__ __forceinline__ double value() const { return d; }
+};
+template <>
+struct DotAcc<float> {
+    CompSum c;
+    __device__ __forceinline__ void add(float a, float b) { c.add(a * b); }
+    __device__ __forceinline__ double value() const { return c.value(); }
+};
 
 // Sum over the block in a fixed order: warp butterflies, then warp 0 over the
 // per-warp sums.  Every thread must call it; the result is valid in thread 0.
@@ -215,37 +228,63 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
             xe[k][i] = xs[ln[k][i]];
         }
     }
-    // colour-ordered accumulation of A_e x_e
-    for (int c = 0; c < m.n_col; ++c) {
-        const int lo = co[c], hi = co[c + 1];
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the product is folded into the node sum inside the colour
+        // rounds (acc = fma(a_rj, x_j, acc)), the minimum of n_b^2 FP64 FMAs
+        // per element -- the FP64 pipe, not DRAM, bounds this pass
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) {
+                        T v = acc[ln[k][r]];
+#pragma unroll
+                        for (int j = 0; j < NB; ++j) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j], v);
+                        acc[ln[k][r]] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        // FP32: every thread forms the products of its slots at once, then the
+        // colour rounds only add them into the node sums (short rounds).
+        // Difference form: the diagonal slot holds the row sum s_r,
+        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
+        // difference is exact in FP32 and no accuracy is lost to cancellation.
+        T y[kEPT][NB];
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
             const int s = tid + k * NT;
-            if (s >= lo && s < hi) {
+            const bool ok = s < m.n_el;
 #pragma unroll
-                for (int r = 0; r < NB; ++r) {
-                    T v = acc[ln[k][r]];
-                    if constexpr (sizeof(T) == 8) {
+            for (int r = 0; r < NB; ++r) {
+                T v = ok ? As[(r * NB + r) * kPatch + s] * xe[k][r] : T(0);
 #pragma unroll
-                        for (int j = 0; j < NB; ++j) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j], v);
-                    } else {
-                        // FP32 difference form: the diagonal slot holds the row sum s_r,
-                        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
-                        // difference is exact in FP32 and no accuracy is lost to cancellation.
-                        v = fmadd(As[(r * NB + r) * kPatch + s], xe[k][r], v);
-#pragma unroll
-                        for (int j = 0; j < NB; ++j)
-                            if (j != r) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j] - xe[k][r], v);
-                    }
-                    acc[ln[k][r]] = v;
-                }
+                for (int j = 0; j < NB; ++j)
+                    if (j != r) v = ok ? fmadd(As[(r * NB + j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
+                y[k][r] = v;
             }
         }
-        __syncthreads();
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
+                }
+            }
+            __syncthreads();
+        }
     }
 
     // owned nodes: final value; shared nodes: halo partial
-    double dsum = 0.0;
+    DotAcc<T> dot;
     for (int l = tid; l < m.n_nodes; l += NT) {
         const int32_t graw = Gs[l];
         const int g = graw & kNodeMask;
@@ -256,14 +295,14 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
             if (kRes) o = dir ? T(0) : T(bs[l] - v);
             else o = dir ? T(0) : v;
             out[g] = o;
-            if (MODE == kResidualNorm) dsum += double(o) * double(o);
-            if (MODE == kApplyDot) dsum += double(xs[l]) * double(o);
+            if (MODE == kResidualNorm) dot.add(o, o);
+            if (MODE == kApplyDot) dot.add(xs[l], o);
         } else {
             halo[m.halo_off + (l - m.n_owned)] = v;
         }
     }
     if (MODE == kResidualNorm || MODE == kApplyDot) {
-        dsum = block_sum<NT>(dsum, red);
+        const double dsum = block_sum<NT>(dot.value(), red);
         if (tid == 0) part[p] = dsum;
     }
 }
@@ -281,7 +320,7 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
     __shared__ double red[32];
     __shared__ bool last;
     if (stop != nullptr && *stop) return;
-    double dsum = 0.0;
+    DotAcc<T> dot;
     for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += gridDim.x * kFixThreads) {
         const int32_t graw = __ldg(pd.sh_node + k);
         const int g = graw & kNodeMask;
@@ -293,10 +332,11 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
         if (MODE == kResidual || MODE == kResidualNorm) o = dir ? T(0) : T(__ldg(b + g) - v);
         else o = dir ? T(0) : v;
         out[g] = o;
-        if (MODE == kResidualNorm) dsum += double(o) * double(o);
-        if (MODE == kApplyDot) dsum += double(__ldg(x + g)) * double(o);
+        if (MODE == kResidualNorm) dot.add(o, o);
+        if (MODE == kApplyDot) dot.add(__ldg(x + g), o);
     }
     if (MODE == kResidualNorm || MODE == kApplyDot) {
+        double dsum = dot.value();
         // this block also adds a contiguous chunk of the patch partials (one per
         // patch, written by the patch pass), so the last block has few to add
         const int np = pd.n_patches;

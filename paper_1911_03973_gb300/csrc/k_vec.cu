@@ -15,25 +15,13 @@
 // use compensated FP32 (Neumaier) before the FP64 block reduction.
 #include <cstdint>
 
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace ebe {
 namespace {
 
 constexpr int NT = kVecThreads;
-
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-// Neumaier-compensated FP32 sum: s + c carries the sum to about FP32^2.
-struct CompSum {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float v) {
-        const float t = s + v;
-        c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return double(s) + double(c); }
-};
 
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 #pragma unroll
@@ -145,10 +133,10 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
     const double al = sc->alpha;
     CompSum rz, rr;
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        x[i] = fmadd(al, double(p[i]), x[i]);
-        const double ri = fmadd(-al, double(q[i]), r[i]);
+        x[i] = fmadd(al, f2d(p[i]), x[i]);
+        const double ri = fmadd(-al, f2d(q[i]), r[i]);
         r[i] = ri;
-        const float rf = float(ri);
+        const float rf = d2f(ri);
         rz.add(rf * (dinv[i] * rf));
         rr.add(rf * rf);
     }
@@ -163,7 +151,7 @@ k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r
     if (sc->done) return;
     const float be = init ? 0.0f : float(sc->beta);
     for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        const float zi = dinv[i] * float(r[i]);
+        const float zi = dinv[i] * d2f(r[i]);
         p[i] = init ? zi : __fmaf_rn(be, p[i], zi);
     }
 }
@@ -181,7 +169,7 @@ k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv
         const float* dinv = static_cast<const float*>(dinv_v);
         CompSum rz, rr;
         for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-            const float rf = float(r[i]);
+            const float rf = d2f(r[i]);
             rz.add(rf * (dinv[i] * rf));
             rr.add(rf * rf);
         }

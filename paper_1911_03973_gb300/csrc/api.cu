@@ -601,7 +601,7 @@ SolveBufs bufs_for(ebe_handle* h, bool mixed) {
 int enqueue_iteration(ebe_handle* h, const SolveBufs& s, int* l) {
     const int64_t n = h->plan.n_n;
     CK(launch_patch_pass(h->pd, s.dt, kApplyDot, s.A, s.p, nullptr, s.q, s.halo, h->part_patch, &h->sc->done, h->sc,
-                         h->st, l),
+                         h->st, l, nullptr, true),
        "apply");
     CK(launch_update(s.dt, n, h->x64w, s.p, h->r64, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
     CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 0, h->sc, h->st, l), "direction");

@@ -39,6 +39,15 @@ __device__ __forceinline__ float d2f(double v) {
     return __uint_as_float((uint32_t(u >> 32) & 0x80000000u) | bits);
 }
 
+// Programmatic dependent launch.  pdl_trigger: once every CTA of this grid has
+// executed it (or exited), the next kernel in the stream may start launching
+// into free SM slots.  pdl_wait: blocks until the previous kernel has
+// completed and its memory is visible; code before it must not read that
+// kernel's results.  Both are no-ops for kernels launched without the
+// programmatic-serialisation attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Neumaier-compensated FP32 sum: s + c carries the sum to about FP32^2.
 struct CompSum {
     float s = 0.0f, c = 0.0f;

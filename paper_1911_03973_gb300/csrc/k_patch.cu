@@ -161,13 +161,17 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     T* acc = reinterpret_cast<T*>(smem + L.acc);
     const uint32_t bar = smem_addr(smem + L.bar);
 
-    if (stop != nullptr && *stop) return;
+    pdl_trigger();
     const int p = blockIdx.x;
     const PatchMeta m = pd.meta[p];
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
 
+    // The element matrices, connectivity and partition are constant while a
+    // solver iterates, so their copies start before waiting for the previous
+    // kernel of the stream (programmatic dependent launch); x, b and the stop
+    // flag are read after the wait.
     if (tid == 0) {
         mbar_init(bar, 1);
         const uint64_t pol = policy_evict_first();
@@ -180,6 +184,11 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
             bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
+    pdl_wait();
+    if (stop != nullptr && *stop) {                // uniform: the solver has stopped
+        if (tid == 0) mbar_wait_bounded(bar, 0, nullptr);   // let the copies land before the CTA exits
+        return;
+    }
     // restriction x_e = R_e x, shared by the patch: node table, x (and b)
     const int32_t* pn = pd.pnode + m.node_off;
     for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
@@ -319,6 +328,8 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
         Scalars* __restrict__ sc) {
     __shared__ double red[32];
     __shared__ bool last;
+    pdl_trigger();
+    pdl_wait();
     if (stop != nullptr && *stop) return;
     DotAcc<T> dot;
     for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += gridDim.x * kFixThreads) {
@@ -602,14 +613,19 @@ __global__ void k_mark(int32_t* __restrict__ ids, int64_t n, const uint8_t* __re
 
 template <typename T, int NB, int MODE>
 cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
-                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev) {
+                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev, bool pdl) {
     const size_t sm = patch_layout<T, NB>(pd.max_nodes).total;
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;   // a patch does not fit in shared memory
     auto kern = k_patch<T, NB, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], st);
-    kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, x, b, out, halo, part, stop);
+    if (pdl) {
+        e = launch_pdl(kern, dim3(pd.n_patches), dim3(kPatchThreads), sm, st, pd, A, x, b, out, halo, part, stop);
+        if (e != cudaSuccess) return e;
+    } else {
+        kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, x, b, out, halo, part, stop);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
@@ -622,13 +638,13 @@ cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* 
 template <typename T, int NB>
 cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, const T* b, T* out, T* halo,
                            double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches,
-                           cudaEvent_t* ev) {
+                           cudaEvent_t* ev, bool pdl) {
     switch (mode) {
-        case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
+        case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
         case kResidualNorm:
-            return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
-        case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
-        case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev);
+            return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+        case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+        case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -642,23 +658,23 @@ int fix_grid(int n_shared) {
 
 cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x, const void* b,
                               void* out, void* halo, double* part, const int32_t* stop, Scalars* sc, cudaStream_t st,
-                              int* launches, cudaEvent_t* ev) {
+                              int* launches, cudaEvent_t* ev, bool pdl) {
     if (dtype == 0) {
         auto a = static_cast<const double*>(A);
         auto xx = static_cast<const double*>(x);
         auto bb = static_cast<const double*>(b);
         auto o = static_cast<double*>(out);
         auto h = static_cast<double*>(halo);
-        return pd.nb == 3 ? run_patch_mode<double, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev)
-                          : run_patch_mode<double, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev);
+        return pd.nb == 3 ? run_patch_mode<double, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev, pdl)
+                          : run_patch_mode<double, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev, pdl);
     }
     auto a = static_cast<const float*>(A);
     auto xx = static_cast<const float*>(x);
     auto bb = static_cast<const float*>(b);
     auto o = static_cast<float*>(out);
     auto h = static_cast<float*>(halo);
-    return pd.nb == 3 ? run_patch_mode<float, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev)
-                      : run_patch_mode<float, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev);
+    return pd.nb == 3 ? run_patch_mode<float, 3>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev, pdl)
+                      : run_patch_mode<float, 4>(pd, mode, a, xx, bb, o, h, part, stop, sc, st, launches, ev, pdl);
 }
 
 cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu, double* A64,

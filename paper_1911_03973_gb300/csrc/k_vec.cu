@@ -14,6 +14,7 @@
 // z = dinv r, the direction p and q = A p are FP32; the per-thread dot sums
 // use compensated FP32 (Neumaier) before the FP64 block reduction.
 #include <cstdint>
+#include <tuple>
 
 #include "device_util.cuh"
 #include "kernels.h"
@@ -90,16 +91,44 @@ __device__ __forceinline__ void decide(Scalars* sc, double rz, double rr) {
 }
 
 // ------------------------------------------------------------------ FP64
+// The node loops visit this thread's nodes in grid-stride order, four at a
+// time: the loads of four nodes are issued before any of them is used, so
+// that each thread keeps several memory requests in flight.  All four kernels
+// of a CG iteration use programmatic dependent launch: pdl_trigger lets the
+// next kernel start launching, pdl_wait orders the reads after the previous
+// kernel.
+
 // x += alpha p;  r -= alpha q;  z = dinv r;  sums r.z, r.r (all FP64).
 __global__ void __launch_bounds__(NT)
 k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
            const double* __restrict__ q, const double* __restrict__ dinv, double* __restrict__ part,
            Scalars* __restrict__ sc) {
     __shared__ double red[64];
+    pdl_trigger();
+    pdl_wait();
     if (sc->done) return;
     const double al = sc->alpha;
     double rz = 0.0, rr = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+    const int64_t st = int64_t(gridDim.x) * NT;
+    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        double pv[4], qv[4], xv[4], rv[4], dv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            pv[u] = p[j]; qv[u] = q[j]; xv[u] = x[j]; rv[u] = r[j]; dv[u] = dinv[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            x[j] = fmadd(al, pv[u], xv[u]);
+            const double ri = fmadd(-al, qv[u], rv[u]);
+            r[j] = ri;
+            rz = fmadd(ri, dv[u] * ri, rz);
+            rr = fmadd(ri, ri, rr);
+        }
+    }
+    for (; i < n; i += st) {
         x[i] = fmadd(al, p[i], x[i]);
         const double ri = fmadd(-al, q[i], r[i]);
         r[i] = ri;
@@ -113,9 +142,26 @@ k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, doub
 __global__ void __launch_bounds__(NT)
 k_direction64(int64_t n, double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ dinv,
               int init, const Scalars* __restrict__ sc) {
+    pdl_trigger();
+    pdl_wait();
     if (sc->done) return;
     const double be = init ? 0.0 : sc->beta;
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+    const int64_t st = int64_t(gridDim.x) * NT;
+    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        double rv[4], dv[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            rv[u] = r[j]; dv[u] = dinv[j]; pv[u] = init ? 0.0 : p[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double zi = dv[u] * rv[u];
+            p[i + u * st] = init ? zi : fmadd(be, pv[u], zi);
+        }
+    }
+    for (; i < n; i += st) {
         const double zi = dinv[i] * r[i];
         p[i] = init ? zi : fmadd(be, p[i], zi);
     }
@@ -129,10 +175,33 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
                const float* __restrict__ q, const float* __restrict__ dinv, double* __restrict__ part,
                Scalars* __restrict__ sc) {
     __shared__ double red[64];
+    pdl_trigger();
+    pdl_wait();
     if (sc->done) return;
     const double al = sc->alpha;
     CompSum rz, rr;
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+    const int64_t st = int64_t(gridDim.x) * NT;
+    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        float pv[4], qv[4], dv[4];
+        double xv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            pv[u] = p[j]; qv[u] = q[j]; dv[u] = dinv[j]; xv[u] = x[j]; rv[u] = r[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            x[j] = fmadd(al, f2d(pv[u]), xv[u]);
+            const double ri = fmadd(-al, f2d(qv[u]), rv[u]);
+            r[j] = ri;
+            const float rf = d2f(ri);
+            rz.add(rf * (dv[u] * rf));
+            rr.add(rf * rf);
+        }
+    }
+    for (; i < n; i += st) {
         x[i] = fmadd(al, f2d(p[i]), x[i]);
         const double ri = fmadd(-al, f2d(q[i]), r[i]);
         r[i] = ri;
@@ -148,9 +217,27 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
 __global__ void __launch_bounds__(NT)
 k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r, const float* __restrict__ dinv,
                   int init, const Scalars* __restrict__ sc) {
+    pdl_trigger();
+    pdl_wait();
     if (sc->done) return;
     const float be = init ? 0.0f : float(sc->beta);
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
+    const int64_t st = int64_t(gridDim.x) * NT;
+    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        double rv[4];
+        float dv[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = i + u * st;
+            rv[u] = r[j]; dv[u] = dinv[j]; pv[u] = init ? 0.0f : p[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float zi = dv[u] * d2f(rv[u]);
+            p[i + u * st] = init ? zi : __fmaf_rn(be, pv[u], zi);
+        }
+    }
+    for (; i < n; i += st) {
         const float zi = dinv[i] * d2f(r[i]);
         p[i] = init ? zi : __fmaf_rn(be, p[i], zi);
     }
@@ -242,29 +329,43 @@ int vec_grid(int64_t n) {
 }
 
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q, const void* dinv,
-                          double* part, Scalars* sc, cudaStream_t st, int* launches) {
-    if (vt == 0)
-        k_update64<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const double*>(p),
-                                               static_cast<double*>(r), static_cast<const double*>(q),
-                                               static_cast<const double*>(dinv), part, sc);
-    else
-        k_update_mixed<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(x), static_cast<const float*>(p),
-                                                   static_cast<double*>(r), static_cast<const float*>(q),
-                                                   static_cast<const float*>(dinv), part, sc);
+                          double* part, Scalars* sc, cudaStream_t st, int* launches, bool pdl) {
+    cudaError_t e;
+    if (vt == 0) {
+        auto kern = k_update64;
+        auto args = std::make_tuple(n, static_cast<double*>(x), static_cast<const double*>(p), static_cast<double*>(r),
+                                    static_cast<const double*>(q), static_cast<const double*>(dinv), part, sc);
+        e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
+                : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
+    } else {
+        auto kern = k_update_mixed;
+        auto args = std::make_tuple(n, static_cast<double*>(x), static_cast<const float*>(p), static_cast<double*>(r),
+                                    static_cast<const float*>(q), static_cast<const float*>(dinv), part, sc);
+        e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
+                : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
+    }
     if (launches) *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init, Scalars* sc,
-                             cudaStream_t st, int* launches) {
-    if (vt == 0)
-        k_direction64<<<vec_grid(n), NT, 0, st>>>(n, static_cast<double*>(p), static_cast<const double*>(r),
-                                                  static_cast<const double*>(dinv), init, sc);
-    else
-        k_direction_mixed<<<vec_grid(n), NT, 0, st>>>(n, static_cast<float*>(p), static_cast<const double*>(r),
-                                                      static_cast<const float*>(dinv), init, sc);
+                             cudaStream_t st, int* launches, bool pdl) {
+    cudaError_t e;
+    if (vt == 0) {
+        auto kern = k_direction64;
+        auto args = std::make_tuple(n, static_cast<double*>(p), static_cast<const double*>(r),
+                                    static_cast<const double*>(dinv), init, static_cast<const Scalars*>(sc));
+        e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
+                : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
+    } else {
+        auto kern = k_direction_mixed;
+        auto args = std::make_tuple(n, static_cast<float*>(p), static_cast<const double*>(r),
+                                    static_cast<const float*>(dinv), init, static_cast<const Scalars*>(sc));
+        e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
+                : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
+    }
     if (launches) *launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part, Scalars* sc,

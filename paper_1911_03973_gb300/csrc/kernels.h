@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "ebe_internal.h"
@@ -58,6 +59,25 @@ struct Scalars {
     uint32_t ctr_vec;
 };
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous kernel in the stream drains; it synchronises with
+// griddepcontrol.wait before reading that kernel's results.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Fixed grid of the node-vector kernels for n nodes (deterministic partials).
 int vec_grid(int64_t n);
 int fix_grid(int n_shared);
@@ -69,10 +89,13 @@ constexpr int kVecThreads = 256;
 // stop (nullable): the pass does nothing when *stop != 0 (solver graphs).
 // sc: receives the norm / dot of kResidualNorm / kApplyDot.
 // ev (nullable): three events recorded before the patch kernel, between it
-// and the fix-up kernel, and after the fix-up.
+// and the fix-up kernel, and after the fix-up.  pdl: launch both kernels with
+// programmatic dependent launch (only where the element matrices cannot have
+// been written by the preceding kernel, i.e. inside a solver iteration).
 cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x,
                               const void* b, void* out, void* halo, double* part, const int32_t* stop,
-                              Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
+                              Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr,
+                              bool pdl = false);
 // Element matrices, load vector and Jacobi diagonal (FP64), Eq. matrices_K_M.
 cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu,
                             double* A64, float* A32, double* b, double* d, double* dinv, float* b32,
@@ -93,10 +116,11 @@ cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, 
 // x += alpha p; r -= alpha q; sums r.(dinv r), r.r; stop test (last block).
 // vt 0: x, r, dinv, p, q FP64.  vt 1: x, r FP64; p, q, dinv FP32.
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q,
-                          const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches);
+                          const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches,
+                          bool pdl = false);
 // p = dinv r + beta p  (init: p = dinv r); vt as launch_update.
 cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init,
-                             Scalars* sc, cudaStream_t st, int* launches);
+                             Scalars* sc, cudaStream_t st, int* launches, bool pdl = false);
 // After a residual replacement: sums r.(dinv r) and r.r; beta = rz/rho, rho = rz
 // (init: rho = rz, beta = 0).  FP64 r; dinv FP64 (vt 0) or FP32 (vt 1).
 cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part,

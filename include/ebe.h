@@ -74,11 +74,12 @@ enum {
 enum {
     EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG                                          */
     EBE_PREC_MIXED = 1    /* the operator pass runs on FP32 A_e (difference form) with the
-                             search direction p and q = A p in FP32; the solution x, the
-                             residual r, z = dinv r and every dot product stay FP64, and r
-                             is replaced by the FP64 true residual (FP64 A_e) whenever the
-                             recurrence residual has dropped by the factor `delta` since
-                             the last replacement (needs EBE_STORE_MIXED)              */
+                             search direction p, q = A p and z = dinv r in FP32; the
+                             solution x and the residual r stay FP64; dot products add
+                             per thread in compensated FP32 and across threads in FP64;
+                             r is replaced by the FP64 true residual (FP64 A_e) whenever
+                             the recurrence residual has dropped by the factor `delta`
+                             since the last replacement (needs EBE_STORE_MIXED)        */
 };
 
 /* Scatter strategies of the residual (ebe_residual_variant). */
@@ -275,6 +276,89 @@ ebe_status ebe_chebyshev3(ebe_handle* h, double* x_dev, int64_t iters, double la
 /* Counters of the handle (see ebe_stats). */
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* stats);
 
+/* ---------------------------------------------------------------- batches of problems */
+
+/* A batch handle holds n_problems independent meshes of the same dim as one
+ * disjoint union: node i of problem k is node node_off[k] + i of the union and
+ * element e of problem k is element elem_off[k] + e (ebe_batch_layout), in
+ * the order given.  Each mesh is partitioned exactly as ebe_create would
+ * partition it, so no patch mixes two problems; ebe_create is the batch of
+ * one.  Every call above works on a batch handle and acts on the union (the
+ * residual of the union is every problem's residual at once; ebe_solve solves
+ * the union as one system with global dot products).  ebe_solve_batch solves
+ * the problems independently.  meshes: host [n_problems], each validated as
+ * by ebe_create.  1 <= n_problems <= 4096, total nodes < 2^31.
+ * Errors as ebe_create; the message names the failing problem. */
+ebe_status ebe_create_batch(ebe_handle** h, const ebe_mesh* meshes, int32_t n_problems,
+                            const ebe_create_opts* opts, void* cuda_stream);
+
+/* Problem count and offsets of the union numbering.  node_off, elem_off: host
+ * [n_problems + 1] or NULL. */
+ebe_status ebe_batch_layout(const ebe_handle* h, int32_t* n_problems, int64_t* node_off, int64_t* elem_off);
+
+/* ebe_set_problem with one nu per problem (Sec. 1 for each problem):
+ * nu host [n_problems]; f_nodal, dirichlet, g, neumann as for
+ * ebe_set_problem, in the union numbering.  A problem with nu = 0 needs at
+ * least one Dirichlet node.  Errors as ebe_set_problem. */
+ebe_status ebe_set_problem_batch(ebe_handle* h, const double* nu, const double* f_nodal,
+                                 const int32_t* dirichlet, int64_t n_d, const double* g,
+                                 const int32_t* neumann, int64_t n_neu);
+
+/* Launch shape of the batched solver. */
+typedef struct {
+    int32_t ctas_per_sm;     /* CTAs per SM of the persistent kernel; 0 = as many as fit */
+    int32_t tile_nodes;      /* nodes per work item of the vector phases: 1024, 2048 or 4096;
+                                0 = 2048                                                 */
+} ebe_batch_config;
+
+typedef struct {
+    int64_t loops;           /* iterations of the persistent loop (each is a CG step or a
+                                true residual for every problem still running)           */
+    int32_t launches;        /* persistent-kernel launches                               */
+    int32_t n_converged;     /* problems that reached rtol                               */
+    double solve_ms;         /* wall time of the call on the host clock                  */
+    ebe_batch_config config; /* launch shape used                                        */
+} ebe_batch_info;
+
+/* Jacobi-PCG on every problem of the batch at once, each stopping on its own
+ * FP64 true relative residual |mask(b_k - A_k x_k)| / |mask(b_k - A_k x0_k)|
+ * <= rtol, with the per-problem rules of ebe_solve (precision, delta,
+ * maxit, stall_updates; chunk is not used).  All iterations of all problems
+ * run in one persistent cooperative kernel with grid-wide barriers (each
+ * wait bounded in time); problems that have finished drop out of the work.
+ * With use_graph = 1 the solve (x0 Dirichlet values, state reset, the
+ * persistent kernel) is replayed from a CUDA graph captured once per handle,
+ * launch shape and options.  x_dev: device [n_n] double (union numbering),
+ * in: x0, out: solutions.  info: host [n_problems] or NULL; summary: NULL
+ * allowed.  Launch shape: the handle's (ebe_set_batch_config,
+ * ebe_batch_tune), else the defaults.  Synchronises the stream.
+ * Returns EBE_OK when every problem reached rtol, otherwise the status of the
+ * first problem that did not (every problem's status is in info). */
+ebe_status ebe_solve_batch(ebe_handle* h, double* x_dev, const ebe_solve_opts* opts, ebe_solve_info* info,
+                           ebe_batch_info* summary);
+
+/* ebe_solve_batch with a HOST x; the host<->device copies are part of the call. */
+ebe_status ebe_solve_batch_host(ebe_handle* h, double* x_host, const ebe_solve_opts* opts,
+                                ebe_solve_info* info, ebe_batch_info* summary);
+
+/* Set the launch shape of ebe_solve_batch (NULL: back to the defaults).
+ * Errors: EBE_INVALID_ARG (tile_nodes not 0/1024/2048/4096, ctas_per_sm
+ * negative or more than fit on an SM). */
+ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg);
+
+/* Autotuner of the batched solver: for every launch shape (ctas_per_sm from
+ * 1 to the most that fit, tile_nodes 1024, 2048, 4096) run the solver on the
+ * handle's own problems from x0 = 0 -- `loops` persistent-loop iterations, or
+ * complete solves with loops = 0 -- timed with CUDA events, and keep the
+ * fastest shape as the handle's launch shape.  Caller data is not touched.
+ * precision: as in ebe_solve_opts.  best: the chosen shape (NULL allowed).
+ * shapes, ms: host [capacity] or NULL; receive each candidate and its time
+ * (ms per loop iteration with loops > 0, ms per solve with loops = 0);
+ * n_written: candidates written.  Errors: EBE_NOT_READY, EBE_INVALID_ARG,
+ * EBE_CUDA_ERROR. */
+ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_batch_config* best,
+                          ebe_batch_config* shapes, double* ms, int32_t capacity, int32_t* n_written);
+
 /* ---------------------------------------------------------------- allocation-free residual */
 
 /* ebe_residual (FP64) for callers that must not allocate device memory during
@@ -325,6 +409,15 @@ typedef struct {
 ebe_status ebe_partition_export(const ebe_mesh* mesh, ebe_partition_sizes* sizes, int32_t* slot_elem,
                                 uint16_t* lconn, int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr,
                                 int32_t* sh_node, int32_t* sh_ptr, int32_t* sh_slot);
+
+/* ebe_partition_export for the union of a batch (the partition that
+ * ebe_create_batch uses): every array in the union numbering, plus
+ * patch_off host [n_problems + 1] (problem k owns patches
+ * [patch_off[k], patch_off[k+1])) or NULL. */
+ebe_status ebe_partition_export_batch(const ebe_mesh* meshes, int32_t n_problems, ebe_partition_sizes* sizes,
+                                      int32_t* patch_off, int32_t* slot_elem, uint16_t* lconn,
+                                      int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr, int32_t* sh_node,
+                                      int32_t* sh_ptr, int32_t* sh_slot);
 
 #ifdef __cplusplus
 }

@@ -242,6 +242,120 @@ def ebe_solve_host(h: Handle, x, rtol=None, maxit=None, precision=None, chunk=No
     return _info_dict(info)
 
 
+def ebe_create_batch(meshes, device: int = 0, stream: int | None = None) -> Handle:
+    """ebe_create_batch: meshes = [(coords, elems), ...] host arrays, one pair per problem.
+
+    The handle's node / element numbering is the concatenation in the given
+    order; ``h.node_off`` / ``h.elem_off`` hold the offsets (ebe_batch_layout).
+    """
+    if len(meshes) < 1:
+        raise ValueError("a batch needs at least one mesh")
+    arr, keep = _mesh_array(meshes)
+    opts = _abi.ebe_create_opts(device, 0)
+    ptr = ctypes.c_void_p()
+    st = _lib().ebe_create_batch(ctypes.byref(ptr), arr, len(meshes), ctypes.byref(opts),
+                                 ctypes.c_void_p(stream or 0))
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    h = Handle(ptr, keep[0].shape[1], keep[1].shape[1], sum(a.shape[0] for a in keep[0::2]),
+               sum(a.shape[0] for a in keep[1::2]))
+    h.n_problems, h.node_off, h.elem_off = ebe_batch_layout(h)
+    return h
+
+
+def ebe_batch_layout(h: Handle):
+    """(n_problems, node_off[n_problems + 1], elem_off[n_problems + 1]) of the union numbering."""
+    n = ctypes.c_int32()
+    _check(h, _lib().ebe_batch_layout(h.ptr, ctypes.byref(n), None, None))
+    no = np.empty(n.value + 1, np.int64)
+    eo = np.empty(n.value + 1, np.int64)
+    _check(h, _lib().ebe_batch_layout(h.ptr, ctypes.byref(n), no.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      eo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return n.value, no, eo
+
+
+def ebe_set_problem_batch(h: Handle, nu, f_nodal, dirichlet, g=None, neumann=None) -> None:
+    """ebe_set_problem_batch: nu host [n_problems]; the rest as ebe_set_problem (union numbering)."""
+    nuv = _host_f64(nu)
+    f = _host_f64(f_nodal)
+    if f.shape != (h.n_n,):
+        raise ValueError("f_nodal must have n_n entries")
+    nd = _host_i32(dirichlet if dirichlet is not None else np.zeros(0))
+    gv = None if g is None else _host_f64(g)
+    if gv is not None and gv.shape != nd.shape:
+        raise ValueError("g must match the Dirichlet set")
+    nn = _host_i32(neumann if neumann is not None else np.zeros(0))
+    n_prob = ebe_batch_layout(h)[0]
+    if nuv.shape != (n_prob,):
+        raise ValueError(f"nu must have one value per problem ({n_prob})")
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t)) if a is not None and a.size else None  # noqa: E731
+    _check(h, _lib().ebe_set_problem_batch(h.ptr, P(nuv, ctypes.c_double), P(f, ctypes.c_double),
+                                           P(nd, ctypes.c_int32), nd.size, P(gv, ctypes.c_double),
+                                           P(nn, ctypes.c_int32), nn.size))
+
+
+def _batch_result(h, infos, summary):
+    return ([_info_dict(i) for i in infos],
+            {"loops": summary.loops, "launches": summary.launches, "n_converged": summary.n_converged,
+             "solve_ms": summary.solve_ms, "ctas_per_sm": summary.config.ctas_per_sm,
+             "tile_nodes": summary.config.tile_nodes})
+
+
+def ebe_solve_batch(h: Handle, x, rtol=None, maxit=None, precision=None, delta=None, stall_updates=None,
+                    use_graph=None):
+    """ebe_solve_batch on a device x (float64 CUDA tensor, union numbering).
+
+    Returns (per-problem ebe_solve_info dicts, ebe_batch_info dict); raises
+    only for errors, not for the solver outcomes of single problems.
+    """
+    o = _opts(rtol, maxit, precision, None, delta, stall_updates, use_graph)
+    n_prob = ebe_batch_layout(h)[0]
+    infos = (_abi.ebe_solve_info * n_prob)()
+    summary = _abi.ebe_batch_info()
+    st = _lib().ebe_solve_batch(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), ctypes.byref(o), infos, ctypes.byref(summary))
+    if st not in SOLVER_OUTCOMES:
+        _check(h, st)
+    return _batch_result(h, infos, summary)
+
+
+def ebe_solve_batch_host(h: Handle, x, rtol=None, maxit=None, precision=None, delta=None, stall_updates=None,
+                         use_graph=None):
+    """ebe_solve_batch_host on a host float64 numpy array x (updated in place)."""
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous and x.size == h.n_n):
+        raise TypeError("x must be a contiguous float64 numpy array of n_n entries")
+    o = _opts(rtol, maxit, precision, None, delta, stall_updates, use_graph)
+    n_prob = ebe_batch_layout(h)[0]
+    infos = (_abi.ebe_solve_info * n_prob)()
+    summary = _abi.ebe_batch_info()
+    st = _lib().ebe_solve_batch_host(h.ptr, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(o),
+                                     infos, ctypes.byref(summary))
+    if st not in SOLVER_OUTCOMES:
+        _check(h, st)
+    return _batch_result(h, infos, summary)
+
+
+def ebe_set_batch_config(h: Handle, ctas_per_sm: int = 0, tile_nodes: int = 0) -> None:
+    """Launch shape of ebe_solve_batch (0 = default for either field)."""
+    c = _abi.ebe_batch_config(int(ctas_per_sm), int(tile_nodes))
+    _check(h, _lib().ebe_set_batch_config(h.ptr, ctypes.byref(c)))
+
+
+def ebe_batch_tune(h: Handle, precision: int = EBE_PREC_MIXED, loops: int = 0) -> dict:
+    """Autotune the batched solver's launch shape (kept by the handle).
+
+    Returns {"best": (ctas_per_sm, tile_nodes), "candidates": [(ctas, tile, ms), ...]}.
+    """
+    cap = 64
+    shapes = (_abi.ebe_batch_config * cap)()
+    ms = (ctypes.c_double * cap)()
+    best = _abi.ebe_batch_config()
+    n = ctypes.c_int32()
+    _check(h, _lib().ebe_batch_tune(h.ptr, int(precision), int(loops), ctypes.byref(best), shapes, ms, cap,
+                                    ctypes.byref(n)))
+    return {"best": (best.ctas_per_sm, best.tile_nodes),
+            "candidates": [(shapes[i].ctas_per_sm, shapes[i].tile_nodes, ms[i]) for i in range(n.value)]}
+
+
 def ebe_residual_noalloc(h: Handle, x, r) -> None:
     """ebe_residual_noalloc: FP64 residual without any device allocation in the
     call (scratch from a fixed device array in the library), for callers that
@@ -266,28 +380,63 @@ def ebe_chebyshev3(h: Handle, x, iters: int, lam1: float, lam2: float) -> None:
     _check(h, _lib().ebe_chebyshev3(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters), float(lam1), float(lam2)))
 
 
-def ebe_partition_export(coords, elems) -> dict:
-    """Host-only element partition (no device needed) as numpy arrays."""
-    coords = _host_f64(coords)
-    elems = _host_i32(elems)
-    mesh = _abi.ebe_mesh(coords.shape[1], elems.shape[1], coords.shape[0], elems.shape[0],
-                         coords.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         elems.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-    sz = _abi.ebe_partition_sizes()
-    lib = _lib()
-    st = lib.ebe_partition_export(ctypes.byref(mesh), ctypes.byref(sz), *([None] * 8))
-    if st != _abi.EBE_OK:
-        raise EbeError(st, ebe_last_error(None))
-    nb = elems.shape[1]
-    out = {
+def _mesh_array(meshes):
+    keep = []
+    arr = (_abi.ebe_mesh * len(meshes))()
+    for k, (c, e) in enumerate(meshes):
+        c = _host_f64(c)
+        e = _host_i32(e)
+        if c.ndim != 2 or e.ndim != 2:
+            raise ValueError("coords and elems must be 2-D")
+        keep += [c, e]
+        arr[k] = _abi.ebe_mesh(c.shape[1], e.shape[1], c.shape[0], e.shape[0],
+                               c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return arr, keep
+
+
+_PARTITION_ARRAYS = ("slot_elem", "lconn", "patch_meta", "pnode", "col_ptr", "sh_node", "sh_ptr", "sh_slot")
+
+
+def _partition_out(sz, nb):
+    return {
         "slot_elem": np.empty(sz.n_slots, np.int32), "lconn": np.empty((nb, sz.n_slots), np.uint16),
         "patch_meta": np.empty((sz.n_patches, 8), np.int32), "pnode": np.empty(sz.n_pnode, np.int32),
         "col_ptr": np.empty(sz.n_colptr, np.int32), "sh_node": np.empty(sz.n_shared, np.int32),
         "sh_ptr": np.empty(sz.n_shared + 1, np.int32), "sh_slot": np.empty(sz.n_halo, np.int32),
     }
+
+
+def ebe_partition_export(coords, elems) -> dict:
+    """Host-only element partition (no device needed) as numpy arrays."""
+    arr, keep = _mesh_array([(coords, elems)])
+    sz = _abi.ebe_partition_sizes()
+    lib = _lib()
+    st = lib.ebe_partition_export(arr, ctypes.byref(sz), *([None] * 8))
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    out = _partition_out(sz, keep[1].shape[1])
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
-    st = lib.ebe_partition_export(ctypes.byref(mesh), ctypes.byref(sz), *[ptr(out[k]) for k in (
-        "slot_elem", "lconn", "patch_meta", "pnode", "col_ptr", "sh_node", "sh_ptr", "sh_slot")])
+    st = lib.ebe_partition_export(arr, ctypes.byref(sz), *[ptr(out[k]) for k in _PARTITION_ARRAYS])
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    out.update({k: getattr(sz, k) for k, _ in _abi.ebe_partition_sizes._fields_})
+    return out
+
+
+def ebe_partition_export_batch(meshes) -> dict:
+    """Host-only partition of a batch's union (as ebe_create_batch builds it), plus ``patch_off``."""
+    arr, keep = _mesh_array(meshes)
+    sz = _abi.ebe_partition_sizes()
+    lib = _lib()
+    st = lib.ebe_partition_export_batch(arr, len(meshes), ctypes.byref(sz), *([None] * 9))
+    if st != _abi.EBE_OK:
+        raise EbeError(st, ebe_last_error(None))
+    out = _partition_out(sz, keep[1].shape[1])
+    out["patch_off"] = np.empty(len(meshes) + 1, np.int32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    st = lib.ebe_partition_export_batch(arr, len(meshes), ctypes.byref(sz), ptr(out["patch_off"]),
+                                        *[ptr(out[k]) for k in _PARTITION_ARRAYS])
     if st != _abi.EBE_OK:
         raise EbeError(st, ebe_last_error(None))
     out.update({k: getattr(sz, k) for k, _ in _abi.ebe_partition_sizes._fields_})

@@ -71,10 +71,20 @@ class ebe_partition_sizes(ctypes.Structure):
                 ("max_nodes", ctypes.c_int32), ("max_colours", ctypes.c_int32), ("patch_elems", ctypes.c_int32)]
 
 
+class ebe_batch_config(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("tile_nodes", ctypes.c_int32)]
+
+
+class ebe_batch_info(ctypes.Structure):
+    _fields_ = [("loops", ctypes.c_int64), ("launches", ctypes.c_int32), ("n_converged", ctypes.c_int32),
+                ("solve_ms", ctypes.c_double), ("config", ebe_batch_config)]
+
+
 _H = ctypes.c_void_p
 _VP = ctypes.c_void_p
 _I32P = ctypes.POINTER(ctypes.c_int32)
 _F64P = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
 
 # (name, restype, argtypes) of every entry point declared in include/ebe.h
 SIGNATURES = [
@@ -96,6 +106,18 @@ SIGNATURES = [
     ("ebe_residual_variant", ctypes.c_int, [_H, _VP, _VP, ctypes.c_int32]),
     ("ebe_solve", ctypes.c_int, [_H, _VP, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
     ("ebe_solve_host", ctypes.c_int, [_H, _F64P, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info)]),
+    ("ebe_create_batch", ctypes.c_int, [ctypes.POINTER(_H), ctypes.POINTER(ebe_mesh), ctypes.c_int32,
+                                        ctypes.POINTER(ebe_create_opts), _VP]),
+    ("ebe_batch_layout", ctypes.c_int, [_H, _I32P, _I64P, _I64P]),
+    ("ebe_set_problem_batch", ctypes.c_int, [_H, _F64P, _F64P, _I32P, ctypes.c_int64, _F64P, _I32P,
+                                             ctypes.c_int64]),
+    ("ebe_solve_batch", ctypes.c_int, [_H, _VP, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info),
+                                       ctypes.POINTER(ebe_batch_info)]),
+    ("ebe_solve_batch_host", ctypes.c_int, [_H, _F64P, ctypes.POINTER(ebe_solve_opts),
+                                            ctypes.POINTER(ebe_solve_info), ctypes.POINTER(ebe_batch_info)]),
+    ("ebe_set_batch_config", ctypes.c_int, [_H, ctypes.POINTER(ebe_batch_config)]),
+    ("ebe_batch_tune", ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ebe_batch_config),
+                                      ctypes.POINTER(ebe_batch_config), _F64P, ctypes.c_int32, _I32P]),
     ("ebe_residual_noalloc", ctypes.c_int, [_H, _VP, _VP]),
     ("ebe_richardson", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double]),
     ("ebe_chebyshev2", ctypes.c_int, [_H, _VP, ctypes.c_int64, _F64P, ctypes.c_int64]),
@@ -103,6 +125,9 @@ SIGNATURES = [
     ("ebe_get_stats", ctypes.c_int, [_H, ctypes.POINTER(ebe_stats)]),
     ("ebe_partition_export", ctypes.c_int, [ctypes.POINTER(ebe_mesh), ctypes.POINTER(ebe_partition_sizes),
                                             _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ebe_partition_export_batch", ctypes.c_int, [ctypes.POINTER(ebe_mesh), ctypes.c_int32,
+                                                  ctypes.POINTER(ebe_partition_sizes), _VP, _VP, _VP, _VP, _VP,
+                                                  _VP, _VP, _VP, _VP]),
 ]
 
 _lock = threading.Lock()

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ebe.h"
@@ -72,6 +73,28 @@ struct ebe_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_chunk[2] = {0, 0};
     int graph_nodes[2] = {0, 0};
+
+    // batches (ebe_create makes a batch of one)
+    int n_prob = 1;
+    BatchLayout lay;
+    double* nu_patch = nullptr;          // [n_patches] nu of each patch's problem (batches of > 1)
+    int32_t* patch_prob = nullptr;       // [n_patches] problem of each patch
+    BatchItem* bfix = nullptr;           // fix-up items
+    int n_bfix = 0;
+    BatchItem* btile[3] = {nullptr, nullptr, nullptr};   // node tiles of 1024, 2048, 4096 nodes
+    int n_btile[3] = {0, 0, 0};
+    double* bpart_f = nullptr;
+    double* bpart_u = nullptr;
+    BatchProblem* bprob = nullptr;
+    BatchProblem* bprob_host = nullptr;  // pinned [n_prob]
+    uint32_t* bctr = nullptr;
+    uint32_t* bbar = nullptr;
+    int32_t* blive = nullptr;
+    int64_t* bloops = nullptr;
+    int64_t* bcount_host = nullptr;      // pinned: loops, live
+    ebe_batch_config bcfg = {0, 0};
+    cudaGraphExec_t bgraph = nullptr;
+    std::vector<double> bgraph_key;
 
     // comparison scatters
     int32_t* gconn = nullptr;
@@ -229,20 +252,19 @@ void ebe_destroy(ebe_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st);
     for (int k = 0; k < 2; ++k)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
     for (void* p : h->allocs) cudaFree(p);
     if (h->sc_host) cudaFreeHost(h->sc_host);
+    if (h->bprob_host) cudaFreeHost(h->bprob_host);
+    if (h->bcount_host) cudaFreeHost(h->bcount_host);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
 }
 
-static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* opts) {
-    if (opts && opts->patch_elems != 0 && opts->patch_elems != kPatch)
-        return fail(h, EBE_INVALID_ARG, "patch_elems must be 0 or 1024");
-    // host-side validation and partition first: no device work for a bad mesh
-    std::string err;
-    int s = build_plan(*m, h->plan, err);
-    if (s != EBE_OK) return fail(h, s, err);
+// Device side of ebe_create / ebe_create_batch, once h->plan and h->lay hold
+// the partition.  coords: host [n_n][dim] in the union numbering.
+static int create_device(ebe_handle* h, const double* coords_host) {
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (h->device < 0 || h->device >= ndev) return fail(h, EBE_INVALID_ARG, "no such CUDA device");
@@ -266,7 +288,7 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     int32_t* slot_elem = nullptr;
     uint16_t* lconn = nullptr;
     PatchMeta* meta = nullptr;
-    TRY(upload(h, &h->coords, m->coords, m->n_n * m->dim));
+    TRY(upload(h, &h->coords, coords_host, P.n_n * P.dim));
     TRY(upload(h, &meta, P.meta.data(), int64_t(P.meta.size())));
     TRY(upload(h, &h->pnode, P.pnode.data(), int64_t(P.pnode.size())));
     TRY(upload(h, &lconn, P.lconn.data(), int64_t(P.lconn.size())));
@@ -275,6 +297,10 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     TRY(upload(h, &sh_ptr, P.sh_ptr.data(), int64_t(P.sh_ptr.size())));
     TRY(upload(h, &sh_slot, P.sh_slot.data(), int64_t(P.sh_slot.size())));
     TRY(upload(h, &slot_elem, P.slot_elem.data(), int64_t(P.slot_elem.size())));
+    std::vector<int32_t> pprob(size_t(P.n_patches), 0);
+    for (int k = 0; k < h->n_prob; ++k)
+        std::fill(pprob.begin() + h->lay.patch_off[k], pprob.begin() + h->lay.patch_off[k + 1], k);
+    TRY(upload(h, &h->patch_prob, pprob.data(), int64_t(pprob.size())));
     h->n_pnode = int64_t(P.pnode.size());
     pd.meta = meta;
     pd.pnode = h->pnode;
@@ -297,6 +323,45 @@ static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* 
     return EBE_OK;
 }
 
+static int check_create_opts(ebe_handle* h, const ebe_create_opts* opts) {
+    if (opts && opts->patch_elems != 0 && opts->patch_elems != kPatch)
+        return fail(h, EBE_INVALID_ARG, "patch_elems must be 0 or 1024");
+    return EBE_OK;
+}
+
+static int create_impl(ebe_handle* h, const ebe_mesh* m, const ebe_create_opts* opts) {
+    TRY(check_create_opts(h, opts));
+    // host-side validation and partition first: no device work for a bad mesh
+    std::string err;
+    int s = build_plan(*m, h->plan, err);
+    if (s != EBE_OK) return fail(h, s, err);
+    h->n_prob = 1;
+    h->lay.node_off = {0, h->plan.n_n};
+    h->lay.elem_off = {0, h->plan.n_e};
+    h->lay.patch_off = {0, int32_t(h->plan.n_patches)};
+    h->lay.shared_off = {0, int32_t(h->plan.sh_node.size())};
+    return create_device(h, m->coords);
+}
+
+static int create_batch_impl(ebe_handle* h, const ebe_mesh* meshes, int n_prob, const ebe_create_opts* opts) {
+    TRY(check_create_opts(h, opts));
+    if (n_prob < 1 || n_prob > kBatchMaxProblems)
+        return fail(h, EBE_INVALID_ARG, "n_problems must be in [1, " + std::to_string(kBatchMaxProblems) + "]");
+    for (int k = 0; k < n_prob; ++k)
+        if (!meshes[k].coords || !meshes[k].elems)
+            return fail(h, EBE_INVALID_ARG, "problem " + std::to_string(k) + ": coords and elems must be non-NULL");
+    std::string err;
+    const int threads = int(std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+    int s = build_batch_plan(meshes, n_prob, threads, h->plan, h->lay, err);
+    if (s != EBE_OK) return fail(h, s, err);
+    h->n_prob = n_prob;
+    const int dim = h->plan.dim;
+    std::vector<double> coords(size_t(h->plan.n_n) * size_t(dim));
+    for (int k = 0; k < n_prob; ++k)
+        std::copy(meshes[k].coords, meshes[k].coords + meshes[k].n_n * dim, coords.begin() + h->lay.node_off[k] * dim);
+    return create_device(h, coords.data());
+}
+
 ebe_status ebe_create(ebe_handle** out, const ebe_mesh* m, const ebe_create_opts* opts, void* cuda_stream) {
     if (!out || !m) { g_create_error = "out and mesh must be non-NULL"; return EBE_INVALID_ARG; }
     *out = nullptr;
@@ -316,31 +381,67 @@ ebe_status ebe_create(ebe_handle** out, const ebe_mesh* m, const ebe_create_opts
     return EBE_OK;
 }
 
-ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal, const int32_t* dirichlet, int64_t n_d,
-                           const double* g, const int32_t* neumann, int64_t n_neu) {
+ebe_status ebe_create_batch(ebe_handle** out, const ebe_mesh* meshes, int32_t n_problems, const ebe_create_opts* opts,
+                            void* cuda_stream) {
+    if (!out || !meshes) { g_create_error = "out and meshes must be non-NULL"; return EBE_INVALID_ARG; }
+    *out = nullptr;
+    ebe_handle* h = new (std::nothrow) ebe_handle();
+    if (!h) { g_create_error = "host allocation failed"; return EBE_OOM; }
+    h->device = opts ? opts->device : 0;
+    h->user = static_cast<cudaStream_t>(cuda_stream);
+    if (cuda_stream == nullptr) h->own_stream = true;
+    else h->st = static_cast<cudaStream_t>(cuda_stream);
+    int s = create_batch_impl(h, meshes, n_problems, opts);
+    if (s != EBE_OK) {
+        g_create_error = h->err;
+        ebe_destroy(h);
+        return ebe_status(s);
+    }
+    *out = h;
+    return EBE_OK;
+}
+
+ebe_status ebe_batch_layout(const ebe_handle* h, int32_t* n_problems, int64_t* node_off, int64_t* elem_off) {
     if (!h) return EBE_INVALID_ARG;
+    if (n_problems) *n_problems = h->n_prob;
+    if (node_off) std::copy(h->lay.node_off.begin(), h->lay.node_off.end(), node_off);
+    if (elem_off) std::copy(h->lay.elem_off.begin(), h->lay.elem_off.end(), elem_off);
+    return EBE_OK;
+}
+
+// nu: one value per problem.
+static int set_problem_impl(ebe_handle* h, const double* nu, const double* f_nodal, const int32_t* dirichlet,
+                            int64_t n_d, const double* g, const int32_t* neumann, int64_t n_neu) {
     const int64_t n_n = h->plan.n_n;
-    if (!std::isfinite(nu) || nu < 0.0) return ebe_status(fail(h, EBE_INVALID_ARG, "nu must be finite and >= 0"));
-    if (!f_nodal) return ebe_status(fail(h, EBE_INVALID_ARG, "f_nodal must be non-NULL"));
+    for (int k = 0; k < h->n_prob; ++k)
+        if (!std::isfinite(nu[k]) || nu[k] < 0.0)
+            return fail(h, EBE_INVALID_ARG, h->n_prob == 1 ? std::string("nu must be finite and >= 0")
+                                                           : "nu of problem " + std::to_string(k) + " must be finite and >= 0");
+    if (!f_nodal) return fail(h, EBE_INVALID_ARG, "f_nodal must be non-NULL");
     if (n_d < 0 || n_neu < 0 || (n_d > 0 && !dirichlet) || (n_neu > 0 && !neumann))
-        return ebe_status(fail(h, EBE_INVALID_ARG, "bad boundary node set"));
+        return fail(h, EBE_INVALID_ARG, "bad boundary node set");
     for (int64_t k = 0; k < n_n; ++k)
-        if (!std::isfinite(f_nodal[k])) return ebe_status(fail(h, EBE_INVALID_ARG, "f is not finite at node " + std::to_string(k)));
+        if (!std::isfinite(f_nodal[k])) return fail(h, EBE_INVALID_ARG, "f is not finite at node " + std::to_string(k));
     std::vector<uint8_t> mask(n_n, 0);
     for (int64_t k = 0; k < n_d; ++k) {
         int32_t v = dirichlet[k];
-        if (v < 0 || v >= n_n) return ebe_status(fail(h, EBE_INDEX_RANGE, "Dirichlet node id out of range"));
-        if (mask[v]) return ebe_status(fail(h, EBE_INVALID_ARG, "Dirichlet node listed twice: " + std::to_string(v)));
+        if (v < 0 || v >= n_n) return fail(h, EBE_INDEX_RANGE, "Dirichlet node id out of range");
+        if (mask[v]) return fail(h, EBE_INVALID_ARG, "Dirichlet node listed twice: " + std::to_string(v));
         mask[v] = 1;
-        if (g && !std::isfinite(g[k])) return ebe_status(fail(h, EBE_INVALID_ARG, "g is not finite"));
+        if (g && !std::isfinite(g[k])) return fail(h, EBE_INVALID_ARG, "g is not finite");
     }
     for (int64_t k = 0; k < n_neu; ++k) {
         int32_t v = neumann[k];
-        if (v < 0 || v >= n_n) return ebe_status(fail(h, EBE_INDEX_RANGE, "Neumann node id out of range"));
-        if (mask[v]) return ebe_status(fail(h, EBE_INVALID_ARG, "node in both the Dirichlet and the Neumann set: " + std::to_string(v)));
+        if (v < 0 || v >= n_n) return fail(h, EBE_INDEX_RANGE, "Neumann node id out of range");
+        if (mask[v]) return fail(h, EBE_INVALID_ARG, "node in both the Dirichlet and the Neumann set: " + std::to_string(v));
     }
-    if (nu == 0.0 && n_d == 0)
-        return ebe_status(fail(h, EBE_SINGULAR, "nu = 0 needs a Dirichlet boundary of positive measure (Sec. 1)"));
+    for (int k = 0; k < h->n_prob; ++k) {
+        if (nu[k] != 0.0) continue;
+        const auto lo = mask.begin() + h->lay.node_off[k], hi = mask.begin() + h->lay.node_off[k + 1];
+        if (std::find(lo, hi, uint8_t(1)) == hi)
+            return fail(h, EBE_SINGULAR, std::string("nu = 0 needs a Dirichlet boundary of positive measure (Sec. 1)") +
+                                             (h->n_prob > 1 ? ": problem " + std::to_string(k) : std::string()));
+    }
     Scope scp(h);
     std::vector<double> gv(n_d, 0.0);
     if (g) std::copy(g, g + n_d, gv.begin());
@@ -353,15 +454,37 @@ ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal, cons
         CK(cudaMemcpyAsync(h->g, gv.data(), sizeof(double) * n_d, cudaMemcpyHostToDevice, h->st), "upload");
     }
     TRY(upload(h, &h->dmask, mask.data(), n_n));
+    std::vector<double> nup;
+    if (h->n_prob > 1) {
+        nup.resize(size_t(h->plan.n_patches));
+        for (int k = 0; k < h->n_prob; ++k)
+            std::fill(nup.begin() + h->lay.patch_off[k], nup.begin() + h->lay.patch_off[k + 1], nu[k]);
+        TRY(dalloc(h, &h->nu_patch, int64_t(nup.size())));
+        CK(cudaMemcpyAsync(h->nu_patch, nup.data(), sizeof(double) * nup.size(), cudaMemcpyHostToDevice, h->st), "upload");
+    }
     int l = 0;
     CK(launch_mark_dirichlet(h->pd, h->pnode, h->n_pnode, h->sh_node, h->dmask, h->st, &l), "mark Dirichlet");
     add_launches(h, l);
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
-    h->nu = nu;
+    h->nu = nu[0];
     h->n_d = n_d;
     h->problem_set = true;
     h->assembled = false;
     return EBE_OK;
+}
+
+ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal, const int32_t* dirichlet, int64_t n_d,
+                           const double* g, const int32_t* neumann, int64_t n_neu) {
+    if (!h) return EBE_INVALID_ARG;
+    const std::vector<double> nus(size_t(h->n_prob), nu);
+    return ebe_status(set_problem_impl(h, nus.data(), f_nodal, dirichlet, n_d, g, neumann, n_neu));
+}
+
+ebe_status ebe_set_problem_batch(ebe_handle* h, const double* nu, const double* f_nodal, const int32_t* dirichlet,
+                                 int64_t n_d, const double* g, const int32_t* neumann, int64_t n_neu) {
+    if (!h) return EBE_INVALID_ARG;
+    if (!nu) return ebe_status(fail(h, EBE_INVALID_ARG, "nu must be non-NULL (one value per problem)"));
+    return ebe_status(set_problem_impl(h, nu, f_nodal, dirichlet, n_d, g, neumann, n_neu));
 }
 
 ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
@@ -383,7 +506,7 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
     }
     CK(cudaMemsetAsync(h->bad, 0xff, sizeof(unsigned long long), h->st), "memset");
     int l = 0;
-    CK(launch_assemble(h->pd, h->coords, h->f, h->nu, h->A64, A32, h->b, h->d, h->dinv, b32, dinv32, h->halo2,
+    CK(launch_assemble(h->pd, h->coords, h->f, h->nu, h->nu_patch, h->A64, A32, h->b, h->d, h->dinv, b32, dinv32, h->halo2,
                        h->bad, h->st, &l), "assemble");
     add_launches(h, l);
     unsigned long long bad = 0;
@@ -839,14 +962,354 @@ ebe_status ebe_chebyshev3(ebe_handle* h, double* x, int64_t iters, double lam1, 
     return ebe_status(stationary_impl(h, x, iters, 2, prm, 2));
 }
 
-ebe_status ebe_partition_export(const ebe_mesh* m, ebe_partition_sizes* sz, int32_t* slot_elem, uint16_t* lconn,
-                                int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr, int32_t* sh_node,
-                                int32_t* sh_ptr, int32_t* sh_slot) {
-    if (!m || !sz) { g_create_error = "mesh and sizes must be non-NULL"; return EBE_INVALID_ARG; }
-    HostPlan P;
-    std::string err;
-    int s = build_plan(*m, P, err);
-    if (s != EBE_OK) { g_create_error = err; return ebe_status(s); }
+// ---------------------------------------------------------------- batched solver
+
+namespace {
+
+constexpr int kFixRows = 1024;                        // shared-node rows per fix-up item
+constexpr int kTileSizes[3] = {1024, 2048, 4096};     // node-tile sizes of the vector phases
+
+int tile_index(int tile_nodes) {
+    for (int i = 0; i < 3; ++i)
+        if (kTileSizes[i] == tile_nodes) return i;
+    return -1;
+}
+
+// Work items of the batched solver (host-built once per handle and tile size)
+// and its per-problem state.
+int ensure_batch_tables(ebe_handle* h, int ti) {
+    const BatchLayout& L = h->lay;
+    if (!h->bfix) {
+        std::vector<BatchItem> fx;
+        for (int k = 0; k < h->n_prob; ++k) {
+            const int r0 = L.shared_off[k], r1 = L.shared_off[k + 1];
+            const int p0 = L.patch_off[k], p1 = L.patch_off[k + 1];
+            const int cnt = std::max(1, (r1 - r0 + kFixRows - 1) / kFixRows);
+            const int pch = (p1 - p0 + cnt - 1) / cnt;
+            const int first = int(fx.size());
+            for (int c = 0; c < cnt; ++c) {
+                BatchItem it{};
+                it.k = k;
+                it.lo = std::min(r1, r0 + c * kFixRows);
+                it.hi = std::min(r1, r0 + (c + 1) * kFixRows);
+                it.plo = std::min(p1, p0 + c * pch);
+                it.phi = std::min(p1, p0 + (c + 1) * pch);
+                it.first = first;
+                it.count = cnt;
+                fx.push_back(it);
+            }
+        }
+        TRY(upload(h, &h->bfix, fx.data(), int64_t(fx.size())));
+        h->n_bfix = int(fx.size());
+        TRY(dalloc(h, &h->bpart_f, h->n_bfix));
+    }
+    auto tiles = [&](int tn, std::vector<BatchItem>* out) {
+        int64_t n = 0;
+        for (int k = 0; k < h->n_prob; ++k) {
+            const int64_t n0 = L.node_off[k], n1 = L.node_off[k + 1];
+            const int cnt = int(std::max<int64_t>(1, (n1 - n0 + tn - 1) / tn));
+            if (out) {
+                const int first = int(out->size());
+                for (int c = 0; c < cnt; ++c) {
+                    BatchItem it{};
+                    it.k = k;
+                    it.lo = int32_t(std::min(n1, n0 + int64_t(c) * tn));
+                    it.hi = int32_t(std::min(n1, n0 + int64_t(c + 1) * tn));
+                    it.first = first;
+                    it.count = cnt;
+                    out->push_back(it);
+                }
+            }
+            n += cnt;
+        }
+        return n;
+    };
+    if (!h->btile[ti]) {
+        std::vector<BatchItem> tl;
+        tiles(kTileSizes[ti], &tl);
+        TRY(upload(h, &h->btile[ti], tl.data(), int64_t(tl.size())));
+        h->n_btile[ti] = int(tl.size());
+    }
+    if (!h->bpart_u) TRY(dalloc(h, &h->bpart_u, 2 * tiles(kTileSizes[0], nullptr)));   // the most tiles
+    if (!h->bprob) {
+        TRY(dalloc(h, &h->bprob, h->n_prob, true));
+        TRY(dalloc(h, &h->bctr, 2 * h->n_prob, true));
+        TRY(dalloc(h, &h->bbar, 2, true));
+        TRY(dalloc(h, &h->blive, 1, true));
+        TRY(dalloc(h, &h->bloops, 1, true));
+        CK(cudaMallocHost(&h->bprob_host, sizeof(BatchProblem) * size_t(h->n_prob)), "cudaMallocHost");
+        CK(cudaMallocHost(&h->bcount_host, 2 * sizeof(int64_t)), "cudaMallocHost");
+    }
+    return EBE_OK;
+}
+
+int batch_buffers(ebe_handle* h, bool mixed) {
+    const int64_t n = h->plan.n_n;
+    const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
+    TRY(dalloc(h, &h->x64w, n));
+    TRY(dalloc(h, &h->r64, n));
+    TRY(dalloc(h, &h->halo64, nh));
+    if (mixed) {
+        TRY(dalloc(h, &h->p32, n));
+        TRY(dalloc(h, &h->q32, n));
+        TRY(dalloc(h, &h->halo32, nh));
+    } else {
+        TRY(dalloc(h, &h->p64, n));
+        TRY(dalloc(h, &h->q64, n));
+    }
+    return EBE_OK;
+}
+
+BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts& o, int64_t budget) {
+    BatchDev bd;
+    bd.pd = h->pd;
+    bd.n_prob = h->n_prob;
+    bd.n_fix = h->n_bfix;
+    bd.n_tile = h->n_btile[ti];
+    bd.patch_prob = h->patch_prob;
+    bd.fix = h->bfix;
+    bd.tile = h->btile[ti];
+    bd.A = mixed ? static_cast<const void*>(h->A32) : h->A64;
+    bd.A64 = h->A64;
+    bd.b = h->b;
+    bd.dinv = mixed ? static_cast<const void*>(h->dinv32) : h->dinv;
+    bd.x = h->x64w;
+    bd.r = h->r64;
+    bd.p = mixed ? static_cast<void*>(h->p32) : h->p64;
+    bd.q = mixed ? static_cast<void*>(h->q32) : h->q64;
+    bd.halo = mixed ? static_cast<void*>(h->halo32) : h->halo64;
+    bd.halo64 = h->halo64;
+    bd.part_p = h->part_patch;
+    bd.part_f = h->bpart_f;
+    bd.part_u = h->bpart_u;
+    bd.prob = h->bprob;
+    bd.ctr = h->bctr;
+    bd.bar = h->bbar;
+    bd.live = h->blive;
+    bd.loops = h->bloops;
+    bd.rtol = o.rtol;
+    bd.delta = o.delta;
+    bd.margin = 0.7;
+    bd.maxit = o.maxit;
+    bd.stall_updates = o.stall_updates;
+    bd.iter_budget = budget;
+    return bd;
+}
+
+// The launch shape to use: cfg's fields, 0 = default; checked against what fits.
+int resolve_shape(ebe_handle* h, const BatchDev& bd, bool mixed, const ebe_batch_config& cfg, int& ctas) {
+    const int maxc = batch_max_ctas_per_sm(bd, mixed, nullptr);
+    if (maxc < 1) return fail(h, EBE_INVALID_ARG, "the batched solver's shared memory does not fit on an SM");
+    ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : maxc;
+    if (ctas > maxc) return fail(h, EBE_INVALID_ARG, "ctas_per_sm = " + std::to_string(ctas) + " does not fit (at most " +
+                                                         std::to_string(maxc) + ")");
+    return EBE_OK;
+}
+
+int enqueue_batch(ebe_handle* h, const BatchDev& bd, bool mixed, int ctas, int* l) {
+    CK(launch_set_dirichlet(h->x64w, h->nd, h->g, h->n_d, h->st, l), "x(nd) = g");
+    CK(launch_batch_init(bd, h->st, l), "batch init");
+    CK(launch_batch_solve(bd, mixed, ctas, h->st, l), "batched solver");
+    return EBE_OK;
+}
+
+// Reads the problems' state and the loop counters (synchronises the stream).
+int read_batch_state(ebe_handle* h, int64_t& loops, int32_t& live) {
+    CK(cudaMemcpyAsync(h->bprob_host, h->bprob, sizeof(BatchProblem) * size_t(h->n_prob), cudaMemcpyDeviceToHost, h->st),
+       "read batch state");
+    CK(cudaMemcpyAsync(h->bcount_host, h->bloops, sizeof(int64_t), cudaMemcpyDeviceToHost, h->st), "read loops");
+    CK(cudaMemcpyAsync(h->bcount_host + 1, h->blive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "read live");
+    TRY(check_device(h));
+    loops = h->bcount_host[0];
+    live = *reinterpret_cast<const int32_t*>(h->bcount_host + 1);
+    return EBE_OK;
+}
+
+int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info* info,
+                     ebe_batch_info* summary) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool mixed = o.precision == EBE_PREC_MIXED;
+    if (mixed && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
+    const int tile = h->bcfg.tile_nodes > 0 ? h->bcfg.tile_nodes : 2048;
+    const int ti = tile_index(tile);
+    TRY(batch_buffers(h, mixed));
+    TRY(ensure_batch_tables(h, ti));
+    // one launch runs up to maxit CG steps plus the true residuals of every
+    // problem; a launch that ends with problems left is followed by another
+    const int64_t budget = o.maxit + 65536;
+    const BatchDev bd = make_batch_dev(h, mixed, ti, o, budget);
+    int ctas = 0;
+    TRY(resolve_shape(h, bd, mixed, h->bcfg, ctas));
+    const int64_t n = h->plan.n_n;
+    CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st),
+       "copy x0");
+    int l = 0;
+    if (o.use_graph) {
+        const std::vector<double> key = {double(mixed), double(ctas), double(tile), o.rtol, o.delta, double(o.maxit),
+                                         double(o.stall_updates)};
+        if (!h->bgraph || h->bgraph_key != key) {
+            if (h->bgraph) { cudaGraphExecDestroy(h->bgraph); h->bgraph = nullptr; }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            int lc = 0;
+            const int st = enqueue_batch(h, bd, mixed, ctas, &lc);
+            cudaError_t e = cudaStreamEndCapture(h->st, &g);
+            if (st != EBE_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture (batched solver)");
+            e = cudaGraphInstantiate(&h->bgraph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { h->bgraph = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate (batched solver)"); }
+            h->bgraph_key = key;
+        }
+        CK(cudaGraphLaunch(h->bgraph, h->st), "cudaGraphLaunch");
+        l += 2 + (h->n_d > 0 ? 1 : 0);
+    } else {
+        TRY(enqueue_batch(h, bd, mixed, ctas, &l));
+    }
+    int launches = 1;
+    int64_t loops = 0, prev = -1;
+    int32_t live = 0;
+    for (;;) {
+        TRY(read_batch_state(h, loops, live));
+        if (live <= 0) break;
+        if (loops == prev) return fail(h, EBE_CUDA_ERROR, "batched solver made no progress");
+        prev = loops;
+        CK(launch_batch_solve(bd, mixed, ctas, h->st, &l), "batched solver");
+        ++launches;
+    }
+    add_launches(h, l);
+    CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st),
+       "copy x");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int status = EBE_OK, n_ok = 0;
+    for (int k = 0; k < h->n_prob; ++k) {
+        const BatchProblem& P = h->bprob_host[k];
+        if (P.status == EBE_OK) ++n_ok;
+        else if (status == EBE_OK) status = P.status;
+        if (info) {
+            info[k].status = P.status;
+            info[k].iterations = P.iter;
+            info[k].true_residuals = P.n_true;
+            info[k].rel_residual = P.rel;
+            info[k].r0_norm = P.r0;
+            info[k].solve_ms = ms;
+        }
+    }
+    if (summary) {
+        summary->loops = loops;
+        summary->launches = launches;
+        summary->n_converged = n_ok;
+        summary->solve_ms = ms;
+        summary->config.ctas_per_sm = ctas;
+        summary->config.tile_nodes = tile;
+    }
+    if (status != EBE_OK)
+        h->err = std::to_string(h->n_prob - n_ok) + " of " + std::to_string(h->n_prob) + " problems did not reach rtol (" +
+                 ebe_status_string(status) + " first)";
+    return status;
+}
+
+int solve_batch_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts, ebe_solve_info* info,
+                      ebe_batch_info* summary) {
+    TRY(check_ready(h, true));
+    if (!x) return fail(h, EBE_INVALID_ARG, "x is NULL");
+    ebe_solve_opts o;
+    ebe_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || o.maxit < 1 || !(o.delta > 0.0 && o.delta < 1.0) || o.stall_updates < 1 ||
+        (o.precision != EBE_PREC_FP64 && o.precision != EBE_PREC_MIXED))
+        return fail(h, EBE_INVALID_ARG, "bad solve options");
+    Scope scp(h);
+    return solve_batch_impl(h, x, host, o, info, summary);
+}
+
+}  // namespace
+
+ebe_status ebe_solve_batch(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info,
+                           ebe_batch_info* summary) {
+    return ebe_status(solve_batch_entry(h, x, false, opts, info, summary));
+}
+
+ebe_status ebe_solve_batch_host(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info,
+                                ebe_batch_info* summary) {
+    return ebe_status(solve_batch_entry(h, x, true, opts, info, summary));
+}
+
+ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg) {
+    if (!h) return EBE_INVALID_ARG;
+    if (!cfg) { h->bcfg = ebe_batch_config{0, 0}; return EBE_OK; }
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8 || (cfg->tile_nodes != 0 && tile_index(cfg->tile_nodes) < 0))
+        return ebe_status(fail(h, EBE_INVALID_ARG, "ctas_per_sm must be in [0, 8], tile_nodes 0, 1024, 2048 or 4096"));
+    h->bcfg = *cfg;
+    return EBE_OK;
+}
+
+ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_batch_config* best,
+                          ebe_batch_config* shapes, double* ms_out, int32_t capacity, int32_t* n_written) {
+    TRY(check_ready(h, true));
+    if (loops < 0 || (precision != EBE_PREC_FP64 && precision != EBE_PREC_MIXED) || capacity < 0)
+        return ebe_status(fail(h, EBE_INVALID_ARG, "bad tuning arguments"));
+    const bool mixed = precision == EBE_PREC_MIXED;
+    if (mixed && h->store != EBE_STORE_MIXED) return ebe_status(fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs EBE_STORE_MIXED"));
+    Scope scp(h);
+    TRY(batch_buffers(h, mixed));
+    ebe_solve_opts o;
+    ebe_solve_opts_default(&o);
+    o.precision = precision;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]), "cudaEventCreate");
+    CK(cudaEventCreate(&ev[1]), "cudaEventCreate");
+    struct Cand { ebe_batch_config c; double ms; };
+    std::vector<Cand> cands;
+    int status = EBE_OK;
+    for (int ti = 0; ti < 3 && status == EBE_OK; ++ti) {
+        status = ensure_batch_tables(h, ti);
+        if (status != EBE_OK) break;
+        const BatchDev bd = make_batch_dev(h, mixed, ti, o, loops > 0 ? loops : o.maxit + 65536);
+        const int maxc = batch_max_ctas_per_sm(bd, mixed, nullptr);
+        for (int c = 1; c <= maxc && status == EBE_OK; ++c) {
+            // one untimed run for the first candidate (module load, attributes)
+            for (int rep = cands.empty() ? 0 : 1; rep < 2 && status == EBE_OK; ++rep) {
+                int l = 0;
+                cudaError_t e = cudaMemsetAsync(h->x64w, 0, sizeof(double) * size_t(h->plan.n_n), h->st);
+                if (e != cudaSuccess) { status = cuda_fail(h, e, "cudaMemsetAsync"); break; }
+                cudaEventRecord(ev[0], h->st);
+                status = enqueue_batch(h, bd, mixed, c, &l);
+                cudaEventRecord(ev[1], h->st);
+                add_launches(h, l);
+                int64_t done_loops = 0;
+                int32_t live = 0;
+                if (status == EBE_OK) status = read_batch_state(h, done_loops, live);
+                if (status != EBE_OK || rep == 0) continue;
+                float t = 0.f;
+                cudaEventElapsedTime(&t, ev[0], ev[1]);
+                const double per = loops > 0 ? double(t) / double(std::max<int64_t>(done_loops, 1)) : double(t);
+                cands.push_back({ebe_batch_config{c, kTileSizes[ti]}, per});
+            }
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (status != EBE_OK) return ebe_status(status);
+    if (cands.empty()) return ebe_status(fail(h, EBE_INVALID_ARG, "no launch shape of the batched solver fits"));
+    size_t bi = 0;
+    for (size_t i = 1; i < cands.size(); ++i)
+        if (cands[i].ms < cands[bi].ms) bi = i;
+    h->bcfg = cands[bi].c;
+    if (best) *best = cands[bi].c;
+    int nw = 0;
+    for (size_t i = 0; i < cands.size() && nw < capacity; ++i, ++nw) {
+        if (shapes) shapes[nw] = cands[i].c;
+        if (ms_out) ms_out[nw] = cands[i].ms;
+    }
+    if (n_written) *n_written = nw;
+    return EBE_OK;
+}
+
+static void export_plan(const HostPlan& P, ebe_partition_sizes* sz, int32_t* slot_elem, uint16_t* lconn,
+                        int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr, int32_t* sh_node, int32_t* sh_ptr,
+                        int32_t* sh_slot) {
     sz->n_patches = P.n_patches;
     sz->n_slots = P.n_slots;
     sz->n_pnode = int64_t(P.pnode.size());
@@ -866,6 +1329,36 @@ ebe_status ebe_partition_export(const ebe_mesh* m, ebe_partition_sizes* sz, int3
     put(sh_slot, P.sh_slot);
     if (patch_meta)
         for (int64_t p = 0; p < P.n_patches; ++p) std::memcpy(patch_meta + 8 * p, &P.meta[p], sizeof(PatchMeta));
+}
+
+ebe_status ebe_partition_export(const ebe_mesh* m, ebe_partition_sizes* sz, int32_t* slot_elem, uint16_t* lconn,
+                                int32_t* patch_meta, int32_t* pnode, int32_t* col_ptr, int32_t* sh_node,
+                                int32_t* sh_ptr, int32_t* sh_slot) {
+    if (!m || !sz) { g_create_error = "mesh and sizes must be non-NULL"; return EBE_INVALID_ARG; }
+    HostPlan P;
+    std::string err;
+    int s = build_plan(*m, P, err);
+    if (s != EBE_OK) { g_create_error = err; return ebe_status(s); }
+    export_plan(P, sz, slot_elem, lconn, patch_meta, pnode, col_ptr, sh_node, sh_ptr, sh_slot);
+    return EBE_OK;
+}
+
+ebe_status ebe_partition_export_batch(const ebe_mesh* meshes, int32_t n_problems, ebe_partition_sizes* sz,
+                                      int32_t* patch_off, int32_t* slot_elem, uint16_t* lconn, int32_t* patch_meta,
+                                      int32_t* pnode, int32_t* col_ptr, int32_t* sh_node, int32_t* sh_ptr,
+                                      int32_t* sh_slot) {
+    if (!meshes || !sz || n_problems < 1 || n_problems > kBatchMaxProblems) {
+        g_create_error = "meshes and sizes must be non-NULL, 1 <= n_problems <= " + std::to_string(kBatchMaxProblems);
+        return EBE_INVALID_ARG;
+    }
+    HostPlan P;
+    BatchLayout L;
+    std::string err;
+    const int threads = int(std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+    int s = build_batch_plan(meshes, n_problems, threads, P, L, err);
+    if (s != EBE_OK) { g_create_error = err; return ebe_status(s); }
+    export_plan(P, sz, slot_elem, lconn, patch_meta, pnode, col_ptr, sh_node, sh_ptr, sh_slot);
+    if (patch_off) std::copy(L.patch_off.begin(), L.patch_off.end(), patch_off);
     return EBE_OK;
 }
 

@@ -52,6 +52,25 @@ struct HostPlan {
 // Validate the mesh and build the partition.  Returns an ebe_status.
 int build_plan(const ebe_mesh& m, HostPlan& plan, std::string& err);
 
+// Where each problem of a batch sits in the concatenated numbering:
+// problem k owns nodes [node_off[k], node_off[k+1]), elements
+// [elem_off[k], elem_off[k+1]), patches [patch_off[k], patch_off[k+1]) and
+// shared-node rows [shared_off[k], shared_off[k+1]).  A single mesh is a
+// batch of one.
+struct BatchLayout {
+    std::vector<int64_t> node_off, elem_off;
+    std::vector<int32_t> patch_off, shared_off;
+};
+
+// Partition every mesh of a batch on its own (exactly as build_plan would,
+// on up to `threads` host threads) and concatenate the partitions: node and
+// element ids, local-node tables, halo slots and colour offsets are shifted
+// by the sizes of the problems before.  No patch mixes two problems.
+// All meshes must have the same dim.  Returns an ebe_status; err names the
+// failing problem.
+int build_batch_plan(const ebe_mesh* meshes, int n_prob, int threads, HostPlan& plan, BatchLayout& lay,
+                     std::string& err);
+
 // Greedy colouring of all elements (no two elements of a colour share a
 // node), elements of each colour listed in the given slot order.
 // Returns the colour count; order receives the slots grouped by colour and

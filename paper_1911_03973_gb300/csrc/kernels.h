@@ -96,9 +96,12 @@ cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void
                               const void* b, void* out, void* halo, double* part, const int32_t* stop,
                               Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr,
                               bool pdl = false);
+
+// ---- element data (k_assemble.cu) -----------------------------------------
 // Element matrices, load vector and Jacobi diagonal (FP64), Eq. matrices_K_M.
+// nu_patch (nullable): nu of every patch (batches of problems); else nu.
 cudaError_t launch_assemble(const PlanDev& pd, const double* coords, const double* f, double nu,
-                            double* A64, float* A32, double* b, double* d, double* dinv, float* b32,
+                            const double* nu_patch, double* A64, float* A32, double* b, double* d, double* dinv, float* b32,
                             float* dinv32, double* halo2, unsigned long long* bad, cudaStream_t st,
                             int* launches);
 // K_e, M_e (or A_e) in the caller's element order, paper layout [e][j][i].
@@ -132,6 +135,86 @@ cudaError_t launch_fill(int dtype, int64_t n, void* v, double value, cudaStream_
 // kind 0: x += w r; kind 1: p = r + beta p (beta = 0: p = r), x += w p.
 cudaError_t launch_stationary(int64_t n, double* x, const double* r, double* p, int kind, double w, double beta,
                               cudaStream_t st, int* launches);
+
+// ---- batched solver (k_batch.cu) ------------------------------------------
+constexpr int kBatchMaxProblems = 4096;   // problems of one batch (a mode byte each in shared memory)
+
+// Phase of one problem of a batch inside the persistent solver.
+enum BatchMode : int32_t {
+    kBNormal = 0,    // next iteration: q = A p, x and r updates, new direction
+    kBReplace = 1,   // next iteration: FP64 true residual r = b - A x replaces r
+    kBDone = 2       // finished (status set)
+};
+
+// Per-problem solver state of a batch, on the device (64-bit fields first).
+struct BatchProblem {
+    double rho;        // r.z of the current direction
+    double alpha;      // rho / p.Ap
+    double beta;       // direction factor of the next direction step
+    double thr2;       // replacement threshold on the recurrence r.r
+    double r0;         // |r0|, FP64 true residual of x0
+    double rrt;        // last true-residual r.r
+    double rel;        // last true relative residual
+    double best;       // best true relative residual so far (stall test)
+    int64_t iter;      // CG iterations done
+    int32_t mode;      // BatchMode
+    int32_t status;    // ebe_status once done
+    int32_t n_true;    // true residuals evaluated
+    int32_t no_progress;
+    int32_t init;      // the pending replacement is the initial residual
+    int32_t bd;        // breakdown seen: finish after a last true residual
+    int32_t dir_init;  // the pending direction step starts from p = z
+    int32_t pad;
+};
+
+// A work item of the fix-up or node phases: one problem's shared-node rows
+// [lo, hi) (fix-up) or nodes [lo, hi) (node phases).  A fix-up item also
+// adds the patch partials [plo, phi) of its problem.  The items of problem
+// k are [first, first + count).
+struct BatchItem {
+    int32_t k, lo, hi, plo, phi, first, count, pad;
+};
+
+// Everything the persistent batched solver reads and writes.
+struct BatchDev {
+    PlanDev pd;
+    int32_t n_prob = 0;
+    int32_t n_fix = 0, n_tile = 0;
+    const int32_t* patch_prob = nullptr;   // [n_patches] problem of each patch
+    const BatchItem* fix = nullptr;        // [n_fix]
+    const BatchItem* tile = nullptr;       // [n_tile]
+    const void* A = nullptr;               // element matrices of the inner operator (FP32 difference form or FP64)
+    const double* A64 = nullptr;           // FP64 element matrices (true residuals)
+    const double* b = nullptr;             // FP64 load vector
+    const void* dinv = nullptr;            // inverse Jacobi diagonal, inner type
+    double* x = nullptr;
+    double* r = nullptr;
+    void* p = nullptr;                     // direction, inner type
+    void* q = nullptr;                     // A p, inner type
+    void* halo = nullptr;                  // halo partials, inner type
+    double* halo64 = nullptr;
+    double* part_p = nullptr;              // [n_patches]
+    double* part_f = nullptr;              // [n_fix]
+    double* part_u = nullptr;              // [2 n_tile]
+    BatchProblem* prob = nullptr;          // [n_prob]
+    uint32_t* ctr = nullptr;               // [2 n_prob] arrival counters: fix-up, node phase
+    uint32_t* bar = nullptr;               // [2] grid barrier
+    int32_t* live = nullptr;               // problems not done
+    int64_t* loops = nullptr;              // iterations (of any kind) run by the persistent kernel
+    double rtol = 1e-8, delta = 0.1, margin = 0.7;
+    int64_t maxit = 0;
+    int32_t stall_updates = 8;
+    int64_t iter_budget = 0;               // loop iterations of one launch
+    uint64_t barrier_ns = 2000000000ull;   // bound of one grid-barrier wait
+};
+
+// Per-problem state reset: every problem starts with the true residual of x0.
+cudaError_t launch_batch_init(const BatchDev& bd, cudaStream_t st, int* launches);
+// CTAs per SM that fit for the persistent kernel of this batch (0: none).
+int batch_max_ctas_per_sm(const BatchDev& bd, bool mixed, int* smem_bytes);
+// The persistent solver: one cooperative launch of ctas_per_sm x SM CTAs that
+// iterates until every problem is done or iter_budget loops have run.
+cudaError_t launch_batch_solve(const BatchDev& bd, bool mixed, int ctas_per_sm, cudaStream_t st, int* launches);
 
 // ---- comparison scatters (k_alt.cu) ---------------------------------------
 cudaError_t launch_build_gconn(const PlanDev& pd, int32_t* gconn, cudaStream_t st, int* launches);

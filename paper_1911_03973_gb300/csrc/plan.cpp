@@ -14,9 +14,11 @@
 //      halo slots are listed in patch order (a CSR), which fixes the order in
 //      which its partial sums are added.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <thread>
 
 #include "ebe_internal.h"
 
@@ -260,6 +262,103 @@ int global_colouring(const HostPlan& P, const std::vector<int32_t>& gconn, std::
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
     for (int64_t s = 0; s < P.n_slots; ++s) if (colour[s] != 0xff) order[fill[colour[s]]++] = int32_t(s);
     return n_col;
+}
+
+int build_batch_plan(const ebe_mesh* meshes, int n_prob, int threads, HostPlan& P, BatchLayout& L, std::string& err) {
+    if (!meshes || n_prob < 1) { err = "a batch needs at least one mesh"; return EBE_INVALID_ARG; }
+    for (int k = 0; k < n_prob; ++k)
+        if (meshes[k].dim != meshes[0].dim) { err = "all meshes of a batch must have the same dim"; return EBE_INVALID_ARG; }
+    // 1. every problem on its own, in parallel (each plan is independent)
+    std::vector<HostPlan> parts(n_prob);
+    std::vector<int> status(n_prob, EBE_OK);
+    std::vector<std::string> errs(n_prob);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int k = next++; k < n_prob; k = next++) status[k] = build_plan(meshes[k], parts[k], errs[k]);
+    };
+    const int nt = std::max(1, std::min(threads, n_prob));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int k = 0; k < n_prob; ++k)
+        if (status[k] != EBE_OK) { err = "problem " + std::to_string(k) + ": " + errs[k]; return status[k]; }
+
+    // 2. sizes and offsets
+    L = BatchLayout();
+    L.node_off.assign(n_prob + 1, 0);
+    L.elem_off.assign(n_prob + 1, 0);
+    L.patch_off.assign(n_prob + 1, 0);
+    L.shared_off.assign(n_prob + 1, 0);
+    int64_t n_pnode = 0, n_col = 0, n_halo = 0, n_patch = 0, n_sh = 0;
+    for (int k = 0; k < n_prob; ++k) {
+        const HostPlan& Q = parts[k];
+        L.node_off[k + 1] = L.node_off[k] + Q.n_n;
+        L.elem_off[k + 1] = L.elem_off[k] + Q.n_e;
+        n_patch += Q.n_patches;
+        n_sh += int64_t(Q.sh_node.size());
+        n_pnode += int64_t(Q.pnode.size());
+        n_col += int64_t(Q.col_ptr.size());
+        n_halo += Q.n_halo;
+        const int64_t lim = int64_t(kNodeMask);
+        if (L.node_off[k + 1] > lim || L.elem_off[k + 1] * Q.nb > lim || n_patch > lim || n_pnode > lim ||
+            n_halo > lim || n_col > lim) {
+            err = "batch exceeds 2^31 nodes, element entries or table entries";
+            return EBE_INVALID_ARG;
+        }
+        L.patch_off[k + 1] = int32_t(n_patch);
+        L.shared_off[k + 1] = int32_t(n_sh);
+    }
+
+    // 3. concatenation
+    P = HostPlan();
+    P.dim = parts[0].dim;
+    P.nb = parts[0].nb;
+    P.n_n = L.node_off[n_prob];
+    P.n_e = L.elem_off[n_prob];
+    P.n_patches = n_patch;
+    P.n_slots = n_patch * kPatch;
+    P.n_halo = n_halo;
+    P.slot_elem.resize(size_t(P.n_slots));
+    P.lconn.resize(size_t(P.nb) * size_t(P.n_slots));
+    P.meta.resize(size_t(n_patch));
+    P.pnode.resize(size_t(n_pnode));
+    P.col_ptr.resize(size_t(n_col));
+    P.sh_node.resize(size_t(n_sh));
+    P.sh_ptr.assign(size_t(n_sh) + 1, 0);
+    P.sh_slot.resize(size_t(n_halo));
+    int64_t o_pnode = 0, o_col = 0, o_halo = 0;
+    for (int k = 0; k < n_prob; ++k) {
+        const HostPlan& Q = parts[k];
+        const int32_t nbase = int32_t(L.node_off[k]), ebase = int32_t(L.elem_off[k]);
+        const int64_t sbase = int64_t(L.patch_off[k]) * kPatch, shbase = L.shared_off[k];
+        for (int64_t s = 0; s < Q.n_slots; ++s) P.slot_elem[sbase + s] = Q.slot_elem[s] < 0 ? -1 : Q.slot_elem[s] + ebase;
+        for (int i = 0; i < P.nb; ++i)
+            std::copy(Q.lconn.begin() + size_t(i) * Q.n_slots, Q.lconn.begin() + size_t(i + 1) * Q.n_slots,
+                      P.lconn.begin() + size_t(i) * P.n_slots + sbase);
+        for (int64_t p = 0; p < Q.n_patches; ++p) {
+            PatchMeta m = Q.meta[p];
+            m.node_off += int32_t(o_pnode);
+            m.halo_off += int32_t(o_halo);
+            m.col_off += int32_t(o_col);
+            P.meta[L.patch_off[k] + p] = m;
+        }
+        // tables stay 16-byte aligned: every part's node table is a multiple of 4 entries
+        for (size_t j = 0; j < Q.pnode.size(); ++j) P.pnode[o_pnode + j] = Q.pnode[j] + nbase;
+        std::copy(Q.col_ptr.begin(), Q.col_ptr.end(), P.col_ptr.begin() + o_col);
+        for (size_t j = 0; j < Q.sh_node.size(); ++j) {
+            P.sh_node[shbase + j] = Q.sh_node[j] + nbase;
+            P.sh_ptr[shbase + j + 1] = Q.sh_ptr[j + 1] + int32_t(o_halo);
+        }
+        for (int64_t j = 0; j < Q.n_halo; ++j) P.sh_slot[o_halo + j] = Q.sh_slot[j] + int32_t(o_halo);
+        o_pnode += int64_t(Q.pnode.size());
+        o_col += int64_t(Q.col_ptr.size());
+        o_halo += Q.n_halo;
+        P.max_nodes = std::max(P.max_nodes, Q.max_nodes);
+        P.max_col = std::max(P.max_col, Q.max_col);
+        parts[k] = HostPlan();   // release this part early
+    }
+    return EBE_OK;
 }
 
 }  // namespace ebe

@@ -256,6 +256,44 @@ def fourier_square(n: int, nu: float, seed: int, modes: int = 8, kmax: int = 8):
                                 f"fourier{n}_nu{nu:g}_s{seed}")
 
 
+def config_batch(n_problems: int = 256, side_lo: int = 17, side_hi: int = 513, nu_lo: float = 1e-2,
+                 nu_hi: float = 10.0, seed: int = 4):
+    """Batch of independent structured squares (full Dirichlet 0, Fourier f).
+
+    Side lengths s = round(exp(U[ln side_lo, ln side_hi])) nodes, nu =
+    exp(U[ln nu_lo, ln nu_hi]), f a sum of 8 Fourier modes (fourier_square)
+    with its own seed per problem.  Returns a list of problem dicts.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = np.rint(np.exp(rng.uniform(math.log(side_lo), math.log(side_hi), size=n_problems))).astype(int)
+    nus = np.exp(rng.uniform(math.log(nu_lo), math.log(nu_hi), size=n_problems))
+    seeds = rng.integers(0, 2 ** 31 - 1, size=n_problems)
+    return [fourier_square(int(s), float(nu), int(sd)) for s, nu, sd in zip(sides, nus, seeds)]
+
+
+def batch_union(problems):
+    """Concatenate problem dicts into the union numbering of a batch.
+
+    Returns a dict with node_off / elem_off offsets, the per-problem meshes
+    [(coords, elems)], nu [n_problems], and f, dirichlet, g, neumann in the
+    union numbering.
+    """
+    node_off = np.zeros(len(problems) + 1, np.int64)
+    elem_off = np.zeros(len(problems) + 1, np.int64)
+    for k, pr in enumerate(problems):
+        node_off[k + 1] = node_off[k] + pr["coords"].shape[0]
+        elem_off[k + 1] = elem_off[k] + pr["elems"].shape[0]
+    return {
+        "node_off": node_off, "elem_off": elem_off,
+        "meshes": [(pr["coords"], pr["elems"]) for pr in problems],
+        "nu": np.array([pr["nu"] for pr in problems], np.float64),
+        "f": np.concatenate([pr["f"] for pr in problems]),
+        "dirichlet": np.concatenate([pr["dirichlet"] + node_off[k] for k, pr in enumerate(problems)]).astype(np.int32),
+        "g": np.concatenate([pr["g"] for pr in problems]),
+        "neumann": np.concatenate([pr["neumann"] + node_off[k] for k, pr in enumerate(problems)]).astype(np.int32),
+    }
+
+
 def seeded_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """A reproducible U[lo, hi] vector (test iterates x)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", action="store_true", help="also time the comparison scatters")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble"], default=None,
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload (256 independent squares)")
+    ap.add_argument("--batch-problems", type=int, default=256)
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "batch"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -79,19 +81,26 @@ def bytes_model(dim: int, n_n: int, n_e: int):
     m["residual32"] = conn + n_e * nb * nb * 4 + n_n * 3 * 4
     m["apply64"] = conn + n_e * nb * nb * 8 + n_n * 2 * 8             # p in; q out
     m["apply32"] = conn + n_e * nb * nb * 4 + n_n * 2 * 4
-    m["vec64"] = n_n * 8 * (7 + 4)          # update: x,p,r,q,dinv in, x,r out; direction: r,dinv,p in, p out
-    m["vec32"] = n_n * 4 * (7 + 4)
-    m["restart32"] = n_n * (8 + 4 + 4) + n_n * (8 + 8 + 4 + 4)      # r64 -> r32 (+dinv), x64 += xs, xs = 0
-    m["restart64"] = n_n * 8 * 2
+    # update (x, p, r, q, dinv in; x, r out) + direction (r, dinv, p in; p out)
+    m["vec64"] = n_n * 8 * (7 + 4)
+    m["vec_mixed"] = n_n * ((8 + 4 + 8 + 4 + 4) + (8 + 8) + (8 + 4 + 4) + 4)   # x, r FP64; p, q, dinv FP32
+    # after a true residual: r.z and r.r (r, dinv in), then a direction step
+    m["restart_mixed"] = n_n * ((8 + 4) + (8 + 4 + 4 + 4))
+    m["restart64"] = n_n * ((8 + 8) + (8 + 8 + 8 + 8))
     return m
 
 
 def step_bytes(m, info, mixed: bool):
     it, tr = info["iterations"], info["true_residuals"]
     if mixed:
-        return (m["assemble_mixed"] + it * (m["apply32"] + m["vec32"]) + tr * m["residual64"]
-                + max(tr - 1, 0) * m["restart32"])
+        return (m["assemble_mixed"] + it * (m["apply32"] + m["vec_mixed"]) + tr * m["residual64"]
+                + max(tr - 1, 0) * m["restart_mixed"])
     return m["assemble_fp64"] + it * (m["apply64"] + m["vec64"]) + tr * m["residual64"] + max(tr - 1, 0) * m["restart64"]
+
+
+def solve_bytes(m, info, mixed: bool):
+    """step_bytes without the element-matrix generation."""
+    return step_bytes(m, info, mixed) - m["assemble_mixed" if mixed else "assemble_fp64"]
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -180,6 +189,100 @@ def traffic_record(kernel: str):
     return None
 
 
+# ----------------------------------------------------------------------------- batched workload
+def run_batch(args, dev, stream, profile=False):
+    """Many independent problems: 256 squares with sides log-uniform in [17, 513]
+    nodes, nu log-uniform in [1e-2, 10], 8 random Fourier modes of f, Dirichlet 0
+    (seed 4).  The batched persistent solver (mixed precision, autotuned launch
+    shape) against the same problems solved one by one with ebe_solve."""
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    from paper_1911_03973_gb300 import meshgen
+
+    n_prob = 64 if profile else args.batch_problems
+    probs = meshgen.config_batch(n_prob, seed=4)
+    U = meshgen.batch_union(probs)
+    n = int(U["node_off"][-1])
+    with torch.cuda.stream(stream):
+        h = ebe.ebe_create_batch(U["meshes"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem_batch(h, U["nu"], U["f"], U["dirichlet"], U["g"], U["neumann"])
+        ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        if profile:
+            # one persistent launch of a few loop iterations (every problem stops at maxit)
+            for _ in range(2):
+                x.zero_()
+                ebe.ebe_solve_batch(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED, maxit=20)
+            torch.cuda.synchronize()
+            ebe.ebe_destroy(h)
+            return None
+        tune = ebe.ebe_batch_tune(h, ebe.EBE_PREC_MIXED, loops=40)
+
+        def timed(prec, reps):
+            best, res = None, None
+            for _ in range(reps):
+                x.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                infos, summ = ebe.ebe_solve_batch(h, x, rtol=args.rtol, precision=prec)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                t = ev0.elapsed_time(ev1)
+                if summ["n_converged"] != n_prob:
+                    raise RuntimeError(f"batched solve: {n_prob - summ['n_converged']} problems did not converge")
+                if best is None or t < best:
+                    best, res = t, (infos, summ)
+            return best, res
+
+        ms_mixed, (infos, summ) = timed(ebe.EBE_PREC_MIXED, 3)
+        ms_b64, (infos64, _) = timed(ebe.EBE_PREC_FP64, 1)
+        ebe.ebe_destroy(h)
+        # the same problems one by one (a handle per problem, as a user without batches would)
+        handles = []
+        for p in probs:
+            hh = ebe.ebe_create(p["coords"], p["elems"], device=dev.index, stream=stream.cuda_stream)
+            ebe.ebe_set_problem(hh, p["nu"], p["f"], p["dirichlet"], p["g"], p["neumann"])
+            ebe.ebe_assemble(hh, ebe.EBE_STORE_MIXED)
+            handles.append(hh)
+        xs = [torch.zeros(p["coords"].shape[0], dtype=torch.float64, device=dev) for p in probs]
+        seq = {}
+        for name, prec in (("fp64", ebe.EBE_PREC_FP64), ("mixed", ebe.EBE_PREC_MIXED)):
+            ebe.ebe_solve(handles[0], xs[0], rtol=args.rtol, precision=prec)     # graph capture outside the timing
+            for v in xs:
+                v.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for hh, v in zip(handles, xs):
+                i = ebe.ebe_solve(hh, v, rtol=args.rtol, precision=prec)
+                if i["status"] != "EBE_OK":
+                    raise RuntimeError(f"sequential solve failed: {i}")
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            seq[name] = ev0.elapsed_time(ev1)
+        for hh in handles:
+            ebe.ebe_destroy(hh)
+    byt = 0
+    for p, i in zip(probs, infos):
+        mk = bytes_model(p["coords"].shape[1], p["coords"].shape[0], p["elems"].shape[0])
+        byt += solve_bytes(mk, i, True)
+    its = [i["iterations"] for i in infos]
+    return {
+        "workload": f"batch{n_prob}_squares17-513_seed4", "n_problems": n_prob, "n_nodes": n,
+        "n_elements": int(U["elem_off"][-1]), "solver": "one persistent cooperative launch, mixed precision",
+        "ms_to_1e-8": round(ms_mixed, 2), "loops": summ["loops"], "iterations_max": max(its),
+        "iterations_sum": sum(its), "shape": [summ["ctas_per_sm"], summ["tile_nodes"]],
+        "phase_ms": {k: round(v, 2) for k, v in summ["phase_ms"].items()},
+        "tuned_ms_per_loop": {f"{c}x{t}": round(ms, 4) for c, t, ms in tune["candidates"]},
+        "gbs": round(byt / (ms_mixed / 1e3) / 1e9, 1),
+        "batched_fp64_ms": round(ms_b64, 2),
+        "sequential_fp64_ms": round(seq["fp64"], 2), "sequential_mixed_ms": round(seq["mixed"], 2),
+        "speedup_vs_sequential_fp64": round(seq["fp64"] / ms_mixed, 3),
+        "speedup_vs_sequential_mixed": round(seq["mixed"] / ms_mixed, 3),
+    }
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -201,6 +304,9 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
+    if args.profile_kernel == "batch":
+        run_batch(args, dev, stream, profile=True)
+        return None
     prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
     n_n, dim = prob["coords"].shape
     n_e = prob["elems"].shape[0]
@@ -345,6 +451,10 @@ def run_ours(args):
                "includes": "ebe_create (host partition build) + ebe_set_problem + ebe_assemble + "
                            "ebe_solve_host + ebe_destroy"}
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batch(args, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(prob, m, iters=40)
@@ -388,6 +498,8 @@ def run_ours(args):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if batched:
+        line["batched"] = batched
     if variants:
         line["residual_variants_fp64"] = variants
     print(json.dumps(line), flush=True)

@@ -318,6 +318,9 @@ typedef struct {
     int32_t n_converged;     /* problems that reached rtol                               */
     double solve_ms;         /* wall time of the call on the host clock                  */
     ebe_batch_config config; /* launch shape used                                        */
+    double phase_ms[4];      /* device time of the loop's four phases summed over the
+                                loops: patch pass, halo fix-up, update, direction (each
+                                from one grid barrier to the next, seen by CTA 0)        */
 } ebe_batch_info;
 
 /* Jacobi-PCG on every problem of the batch at once, each stopping on its own
@@ -341,9 +344,11 @@ ebe_status ebe_solve_batch(ebe_handle* h, double* x_dev, const ebe_solve_opts* o
 ebe_status ebe_solve_batch_host(ebe_handle* h, double* x_host, const ebe_solve_opts* opts,
                                 ebe_solve_info* info, ebe_batch_info* summary);
 
-/* Set the launch shape of ebe_solve_batch (NULL: back to the defaults).
- * Errors: EBE_INVALID_ARG (tile_nodes not 0/1024/2048/4096, ctas_per_sm
- * negative or more than fit on an SM). */
+/* Set the launch shape of ebe_solve_batch for both precisions (NULL: back to
+ * the defaults).  Errors: EBE_INVALID_ARG (tile_nodes not 0/1024/2048/4096,
+ * ctas_per_sm outside [0, 8]); a ctas_per_sm that does not fit on an SM for
+ * the precision of a later ebe_solve_batch makes that call fail with
+ * EBE_INVALID_ARG. */
 ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg);
 
 /* Autotuner of the batched solver: for every launch shape (ctas_per_sm from
@@ -354,7 +359,8 @@ ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg);
  * precision: as in ebe_solve_opts.  best: the chosen shape (NULL allowed).
  * shapes, ms: host [capacity] or NULL; receive each candidate and its time
  * (ms per loop iteration with loops > 0, ms per solve with loops = 0);
- * n_written: candidates written.  Errors: EBE_NOT_READY, EBE_INVALID_ARG,
+ * n_written: candidates written.  The chosen shape is kept for ebe_solve_batch
+ * calls of this precision only.  Errors: EBE_NOT_READY, EBE_INVALID_ARG,
  * EBE_CUDA_ERROR. */
 ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_batch_config* best,
                           ebe_batch_config* shapes, double* ms, int32_t capacity, int32_t* n_written);

@@ -298,7 +298,8 @@ def _batch_result(h, infos, summary):
     return ([_info_dict(i) for i in infos],
             {"loops": summary.loops, "launches": summary.launches, "n_converged": summary.n_converged,
              "solve_ms": summary.solve_ms, "ctas_per_sm": summary.config.ctas_per_sm,
-             "tile_nodes": summary.config.tile_nodes})
+             "tile_nodes": summary.config.tile_nodes,
+             "phase_ms": dict(zip(("patch", "fixup", "update", "direction"), list(summary.phase_ms)))})
 
 
 def ebe_solve_batch(h: Handle, x, rtol=None, maxit=None, precision=None, delta=None, stall_updates=None,

@@ -77,7 +77,7 @@ class ebe_batch_config(ctypes.Structure):
 
 class ebe_batch_info(ctypes.Structure):
     _fields_ = [("loops", ctypes.c_int64), ("launches", ctypes.c_int32), ("n_converged", ctypes.c_int32),
-                ("solve_ms", ctypes.c_double), ("config", ebe_batch_config)]
+                ("solve_ms", ctypes.c_double), ("config", ebe_batch_config), ("phase_ms", ctypes.c_double * 4)]
 
 
 _H = ctypes.c_void_p

@@ -78,11 +78,11 @@ struct ebe_handle {
     int n_prob = 1;
     BatchLayout lay;
     double* nu_patch = nullptr;          // [n_patches] nu of each patch's problem (batches of > 1)
-    int32_t* patch_prob = nullptr;       // [n_patches] problem of each patch
     BatchItem* bfix = nullptr;           // fix-up items
     int n_bfix = 0;
     BatchItem* btile[3] = {nullptr, nullptr, nullptr};   // node tiles of 1024, 2048, 4096 nodes
     int n_btile[3] = {0, 0, 0};
+    BatchProbInfo* bpinfo[3] = {nullptr, nullptr, nullptr};   // per problem item ranges, per tile size
     double* bpart_f = nullptr;
     double* bpart_u = nullptr;
     BatchProblem* bprob = nullptr;
@@ -91,8 +91,9 @@ struct ebe_handle {
     uint32_t* bbar = nullptr;
     int32_t* blive = nullptr;
     int64_t* bloops = nullptr;
-    int64_t* bcount_host = nullptr;      // pinned: loops, live
-    ebe_batch_config bcfg = {0, 0};
+    unsigned long long* bphase = nullptr;   // [4] phase times of the persistent kernel
+    int64_t* bcount_host = nullptr;      // pinned: loops, live, phase times [4]
+    ebe_batch_config bcfg[2] = {{0, 0}, {0, 0}};   // launch shape per precision (FP64, mixed)
     cudaGraphExec_t bgraph = nullptr;
     std::vector<double> bgraph_key;
 
@@ -297,10 +298,6 @@ static int create_device(ebe_handle* h, const double* coords_host) {
     TRY(upload(h, &sh_ptr, P.sh_ptr.data(), int64_t(P.sh_ptr.size())));
     TRY(upload(h, &sh_slot, P.sh_slot.data(), int64_t(P.sh_slot.size())));
     TRY(upload(h, &slot_elem, P.slot_elem.data(), int64_t(P.slot_elem.size())));
-    std::vector<int32_t> pprob(size_t(P.n_patches), 0);
-    for (int k = 0; k < h->n_prob; ++k)
-        std::fill(pprob.begin() + h->lay.patch_off[k], pprob.begin() + h->lay.patch_off[k + 1], k);
-    TRY(upload(h, &h->patch_prob, pprob.data(), int64_t(pprob.size())));
     h->n_pnode = int64_t(P.pnode.size());
     pd.meta = meta;
     pd.pnode = h->pnode;
@@ -966,7 +963,7 @@ ebe_status ebe_chebyshev3(ebe_handle* h, double* x, int64_t iters, double lam1, 
 
 namespace {
 
-constexpr int kFixRows = 1024;                        // shared-node rows per fix-up item
+constexpr int kFixRows = 512;                         // shared-node rows per fix-up item (2 per thread)
 constexpr int kTileSizes[3] = {1024, 2048, 4096};     // node-tile sizes of the vector phases
 
 int tile_index(int tile_nodes) {
@@ -1029,6 +1026,19 @@ int ensure_batch_tables(ebe_handle* h, int ti) {
         tiles(kTileSizes[ti], &tl);
         TRY(upload(h, &h->btile[ti], tl.data(), int64_t(tl.size())));
         h->n_btile[ti] = int(tl.size());
+        std::vector<BatchProbInfo> pi(size_t(h->n_prob));
+        std::vector<BatchItem> fx(size_t(h->n_bfix));
+        CK(cudaMemcpyAsync(fx.data(), h->bfix, sizeof(BatchItem) * fx.size(), cudaMemcpyDeviceToHost, h->st), "read items");
+        CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+        for (const BatchItem& it : fx)
+            if (it.first == int(&it - fx.data())) { pi[it.k].fix_first = it.first; pi[it.k].fix_count = it.count; }
+        for (size_t t = 0; t < tl.size(); ++t)
+            if (tl[t].first == int(t)) { pi[tl[t].k].tile_first = tl[t].first; pi[tl[t].k].tile_count = tl[t].count; }
+        for (int k = 0; k < h->n_prob; ++k) {
+            pi[k].patch_first = L.patch_off[k];
+            pi[k].patch_count = L.patch_off[k + 1] - L.patch_off[k];
+        }
+        TRY(upload(h, &h->bpinfo[ti], pi.data(), int64_t(pi.size())));
     }
     if (!h->bpart_u) TRY(dalloc(h, &h->bpart_u, 2 * tiles(kTileSizes[0], nullptr)));   // the most tiles
     if (!h->bprob) {
@@ -1037,8 +1047,9 @@ int ensure_batch_tables(ebe_handle* h, int ti) {
         TRY(dalloc(h, &h->bbar, 2, true));
         TRY(dalloc(h, &h->blive, 1, true));
         TRY(dalloc(h, &h->bloops, 1, true));
+        TRY(dalloc(h, &h->bphase, 4, true));
         CK(cudaMallocHost(&h->bprob_host, sizeof(BatchProblem) * size_t(h->n_prob)), "cudaMallocHost");
-        CK(cudaMallocHost(&h->bcount_host, 2 * sizeof(int64_t)), "cudaMallocHost");
+        CK(cudaMallocHost(&h->bcount_host, 6 * sizeof(int64_t)), "cudaMallocHost");
     }
     return EBE_OK;
 }
@@ -1066,7 +1077,7 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.n_prob = h->n_prob;
     bd.n_fix = h->n_bfix;
     bd.n_tile = h->n_btile[ti];
-    bd.patch_prob = h->patch_prob;
+    bd.pinfo = h->bpinfo[ti];
     bd.fix = h->bfix;
     bd.tile = h->btile[ti];
     bd.A = mixed ? static_cast<const void*>(h->A32) : h->A64;
@@ -1087,6 +1098,7 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.bar = h->bbar;
     bd.live = h->blive;
     bd.loops = h->bloops;
+    bd.phase_ns = h->bphase;
     bd.rtol = o.rtol;
     bd.delta = o.delta;
     bd.margin = 0.7;
@@ -1119,6 +1131,8 @@ int read_batch_state(ebe_handle* h, int64_t& loops, int32_t& live) {
        "read batch state");
     CK(cudaMemcpyAsync(h->bcount_host, h->bloops, sizeof(int64_t), cudaMemcpyDeviceToHost, h->st), "read loops");
     CK(cudaMemcpyAsync(h->bcount_host + 1, h->blive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st), "read live");
+    CK(cudaMemcpyAsync(h->bcount_host + 2, h->bphase, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st),
+       "read phase times");
     TRY(check_device(h));
     loops = h->bcount_host[0];
     live = *reinterpret_cast<const int32_t*>(h->bcount_host + 1);
@@ -1130,7 +1144,8 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     const auto t0 = std::chrono::steady_clock::now();
     const bool mixed = o.precision == EBE_PREC_MIXED;
     if (mixed && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
-    const int tile = h->bcfg.tile_nodes > 0 ? h->bcfg.tile_nodes : 2048;
+    const ebe_batch_config& cfg = h->bcfg[mixed ? 1 : 0];
+    const int tile = cfg.tile_nodes > 0 ? cfg.tile_nodes : 2048;
     const int ti = tile_index(tile);
     TRY(batch_buffers(h, mixed));
     TRY(ensure_batch_tables(h, ti));
@@ -1139,7 +1154,7 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     const int64_t budget = o.maxit + 65536;
     const BatchDev bd = make_batch_dev(h, mixed, ti, o, budget);
     int ctas = 0;
-    TRY(resolve_shape(h, bd, mixed, h->bcfg, ctas));
+    TRY(resolve_shape(h, bd, mixed, cfg, ctas));
     const int64_t n = h->plan.n_n;
     CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st),
        "copy x0");
@@ -1203,6 +1218,7 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
         summary->solve_ms = ms;
         summary->config.ctas_per_sm = ctas;
         summary->config.tile_nodes = tile;
+        for (int ph = 0; ph < 4; ++ph) summary->phase_ms[ph] = double(h->bcount_host[2 + ph]) * 1e-6;
     }
     if (status != EBE_OK)
         h->err = std::to_string(h->n_prob - n_ok) + " of " + std::to_string(h->n_prob) + " problems did not reach rtol (" +
@@ -1238,10 +1254,10 @@ ebe_status ebe_solve_batch_host(ebe_handle* h, double* x, const ebe_solve_opts* 
 
 ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg) {
     if (!h) return EBE_INVALID_ARG;
-    if (!cfg) { h->bcfg = ebe_batch_config{0, 0}; return EBE_OK; }
+    if (!cfg) { h->bcfg[0] = h->bcfg[1] = ebe_batch_config{0, 0}; return EBE_OK; }
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8 || (cfg->tile_nodes != 0 && tile_index(cfg->tile_nodes) < 0))
         return ebe_status(fail(h, EBE_INVALID_ARG, "ctas_per_sm must be in [0, 8], tile_nodes 0, 1024, 2048 or 4096"));
-    h->bcfg = *cfg;
+    h->bcfg[0] = h->bcfg[1] = *cfg;
     return EBE_OK;
 }
 
@@ -1296,7 +1312,7 @@ ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_b
     size_t bi = 0;
     for (size_t i = 1; i < cands.size(); ++i)
         if (cands[i].ms < cands[bi].ms) bi = i;
-    h->bcfg = cands[bi].c;
+    h->bcfg[mixed ? 1 : 0] = cands[bi].c;
     if (best) *best = cands[bi].c;
     int nw = 0;
     for (size_t i = 0; i < cands.size() && nw < capacity; ++i, ++nw) {

@@ -15,12 +15,21 @@
 //      the sums); the last tile of a problem sums r.z and r.r and takes the
 //      problem's decisions (beta, replacement, convergence, breakdown, stall);
 //   D  node tiles: p = z + beta p for the problems still iterating.
+// (Forming p inside the next patch pass instead, which saves D's pass and a
+// barrier, measured slower: the extra gathers of r and dinv lengthen the
+// patch pass's latency-bound critical path by more than D costs.)
+// Scheduling: every CTA keeps in shared memory the list of the problems still
+// running with prefix sums of their patch, fix-up and tile counts, rebuilt
+// (block-wide scan) whenever a problem finishes; item i of a phase belongs to
+// CTA i mod gridDim, so the live work is spread evenly however many problems
+// have finished.
 // The per-problem decisions follow the single-problem solver: mixed
 // precision keeps x and r in FP64 and replaces the recurrence residual by
 // the FP64 true residual whenever it has dropped by delta; a problem is done
 // when its true relative residual reaches rtol.  Problems that are done cost
 // nothing but a shared-memory lookup per item.  Every sum is taken in a fixed
-// order, so a solve is bitwise reproducible for a given launch shape.
+// order, so a solve is bitwise reproducible (for any launch shape with the
+// same tile size: the sums do not depend on which CTA runs an item).
 #include <cstdint>
 
 #include "device_util.cuh"
@@ -55,7 +64,7 @@ __device__ __forceinline__ V ld_l2(const V* p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------- shared memory
 struct BatchSmem {
-    uint32_t bar, flag, broken, live, last, red, co, mode, sp, sf, st;
+    uint32_t bar, flag, broken, live, last, nl, ver, timer, red, co, mode, list, pre;
     uint32_t A, L, G, xs, acc;        // inner-operator patch pass
     uint32_t G2, xs2, bs2, acc2;      // FP64 true-residual patch pass (same region)
     uint32_t total;
@@ -63,7 +72,7 @@ struct BatchSmem {
 __host__ __device__ constexpr uint32_t up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
 template <typename T, int NB>
-__host__ __device__ constexpr BatchSmem batch_layout(int max_nodes, int n_prob, int cap_p, int cap_f, int cap_t) {
+__host__ __device__ constexpr BatchSmem batch_layout(int max_nodes, int n_prob) {
     BatchSmem s{};
     const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
     s.bar = 0;
@@ -71,13 +80,15 @@ __host__ __device__ constexpr BatchSmem batch_layout(int max_nodes, int n_prob, 
     s.broken = 12;
     s.live = 16;
     s.last = 20;
-    s.red = 32;                                      // 2 * NT / 32 doubles
+    s.nl = 24;
+    s.ver = 28;
+    s.timer = 32;                                    // 5 u64
+    s.red = 80;                                      // 2 * NT / 32 doubles (also the scan's scratch)
     s.co = s.red + 2 * (NT / 32) * 8;
     s.mode = up(s.co + (kMaxColours + 1) * 4, 16);   // int8 per problem
-    s.sp = up(s.mode + uint32_t(n_prob), 16);
-    s.sf = s.sp + uint32_t(cap_p) * 4;
-    s.st = s.sf + uint32_t(cap_f) * 4;
-    s.A = up(s.st + uint32_t(cap_t) * 4, 128);
+    s.list = up(s.mode + uint32_t(n_prob), 16);      // live problems
+    s.pre = s.list + uint32_t(n_prob) * 4;           // prefix sums: patches, fix-up items, tiles [3][n_prob + 1]
+    s.A = up(s.pre + 3u * uint32_t(n_prob + 1) * 4, 128);
     s.L = s.A + uint32_t(NB * NB * kPatch * sizeof(T));
     s.G = s.L + uint32_t(NB * kPatch * 2);
     s.xs = up(s.G + gcap * 4, 16);
@@ -92,54 +103,74 @@ __host__ __device__ constexpr BatchSmem batch_layout(int max_nodes, int n_prob, 
     return s;
 }
 
+// The shared-memory layout is recomputed where it is used (a few integer
+// operations on kernel parameters) rather than carried in registers.
+template <typename T, int NB>
+__device__ __forceinline__ BatchSmem layout_of(const BatchDev& bd) {
+    return batch_layout<T, NB>(bd.pd.max_nodes, bd.n_prob);
+}
+
 struct Ctx {
     const BatchDev* bd;
     unsigned char* smem;
-    BatchSmem L;
-    uint32_t mbar;
-    uint32_t mph;
+    uint32_t mph;      // parity of the CTA's mbarrier phase
 };
 
 // ---------------------------------------------------------------- phase P
+// Bulk copies of one patch's element matrices and local connectivity into
+// the CTA's buffers (thread 0; completes on the CTA's mbarrier).
+template <typename T, int NB>
+__device__ __forceinline__ void issue_patch_copies(const BatchDev& bd, unsigned char* smem, int p) {
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    const T* A = static_cast<const T*>(bd.A);
+    const int64_t ns = bd.pd.n_slots;
+    const int64_t slot0 = int64_t(p) * kPatch;
+    const uint32_t mbar = tma::smem_addr(smem + Lo.bar);
+    const uint64_t pol = tma::policy_evict_first();
+    tma::mbar_expect_tx(mbar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
+#pragma unroll
+    for (int t = 0; t < NB * NB; ++t)
+        tma::bulk_load(tma::smem_addr(smem + Lo.A + t * kPatch * sizeof(T)), A + t * ns + slot0,
+                       uint32_t(kPatch * sizeof(T)), mbar, pol);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+        tma::bulk_load(tma::smem_addr(smem + Lo.L + i * kPatch * 2), bd.pd.lconn + i * ns + slot0, uint32_t(kPatch * 2),
+                       mbar, pol);
+}
+
 // q = A p on one patch (inner type T): the element matrices and local
 // connectivity come in by TMA bulk copies while the threads gather the node
 // table and p; products first, then colour rounds add them into the node
 // sums (FP32: difference form, the diagonal slot holds the row sum).
-// Returns false in every thread if the bulk copies did not arrive in time
-// (the device error flag is set; the CTA stops its patch work).
+// have: the copies of p were issued already (prefetch).  next_p >= 0: issue
+// the copies of the CTA's next patch as soon as this patch's products are
+// formed, so that they land during this patch's colour rounds and the next
+// patch's gathers.  Returns false in every thread if the copies did not
+// arrive in time (the device error flag is set; the CTA stops its patch work).
 template <typename T, int NB>
-__device__ __forceinline__ bool apply_patch(Ctx& c, int p) {
+__device__ __forceinline__ bool apply_patch(Ctx& c, int p, bool have, int next_p) {
     const BatchDev& bd = *c.bd;
     const PlanDev& pd = bd.pd;
     unsigned char* smem = c.smem;
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + c.L.broken);
-    double* red = reinterpret_cast<double*>(smem + c.L.red);
-    int* co = reinterpret_cast<int*>(smem + c.L.co);
-    T* As = reinterpret_cast<T*>(smem + c.L.A);
-    uint16_t* Ls = reinterpret_cast<uint16_t*>(smem + c.L.L);
-    int32_t* Gs = reinterpret_cast<int32_t*>(smem + c.L.G);
-    T* xs = reinterpret_cast<T*>(smem + c.L.xs);
-    T* acc = reinterpret_cast<T*>(smem + c.L.acc);
-    const T* A = static_cast<const T*>(bd.A);
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + Lo.broken);
+    double* red = reinterpret_cast<double*>(smem + Lo.red);
+    int* co = reinterpret_cast<int*>(smem + Lo.co);
+    const T* As = reinterpret_cast<const T*>(smem + Lo.A);
+    const uint16_t* Ls = reinterpret_cast<const uint16_t*>(smem + Lo.L);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + Lo.G);
+    T* xs = reinterpret_cast<T*>(smem + Lo.xs);
+    T* acc = reinterpret_cast<T*>(smem + Lo.acc);
+    const uint32_t mbar = tma::smem_addr(smem + Lo.bar);
     const T* pv = static_cast<const T*>(bd.p);
     T* q = static_cast<T*>(bd.q);
     T* halo = static_cast<T*>(bd.halo);
     const int tid = threadIdx.x;
-    const int64_t ns = pd.n_slots;
-    const int64_t slot0 = int64_t(p) * kPatch;
     const PatchMeta m = pd.meta[p];
 
-    __syncthreads();   // the previous item's reads of shared memory are done
-    if (tid == 0) {
-        const uint64_t pol = tma::policy_evict_first();
-        tma::mbar_expect_tx(c.mbar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
-#pragma unroll
-        for (int t = 0; t < NB * NB; ++t)
-            tma::bulk_load(tma::smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * sizeof(T)), c.mbar, pol);
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-            tma::bulk_load(tma::smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), c.mbar, pol);
-    }
+    // (the previous item's reads of these buffers ended before its block
+    // reduction's barriers)
+    if (!have && tid == 0) issue_patch_copies<T, NB>(bd, smem, p);
     for (int k = tid; k <= m.n_col; k += NT) co[k] = __ldg(pd.col_ptr + m.col_off + k);
     const int32_t* pn = pd.pnode + m.node_off;
     for (int l = tid; l < m.n_nodes; l += NT) {
@@ -150,12 +181,12 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p) {
     }
     // *flag (the CTA's "broken" word) stays 1 from here on if the copies are lost:
     // this CTA does no more patch work and the next grid barrier ends the launch
-    if (tid == 0 && !tma::mbar_wait_bounded(c.mbar, c.mph, pd.err)) *flag = 1;
+    if (tid == 0 && !tma::mbar_wait_bounded(mbar, c.mph, pd.err)) *flag = 1;
     __syncthreads();
     const uint32_t ph = c.mph;
     c.mph ^= 1u;
     if (*flag != 0) return false;
-    while (!tma::mbar_try_wait(c.mbar, ph)) {
+    while (!tma::mbar_try_wait(mbar, ph)) {
     }
 
     int ln[kEPT][NB];
@@ -186,6 +217,10 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p) {
             y[k][r] = v;
         }
     }
+    if (next_p >= 0) {
+        __syncthreads();   // every thread is done with As, Ls
+        if (tid == 0) issue_patch_copies<T, NB>(bd, smem, next_p);
+    }
     for (int cc = 0; cc < m.n_col; ++cc) {
         const int lo = co[cc], hi = co[cc + 1];
 #pragma unroll
@@ -215,19 +250,22 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p) {
     return true;
 }
 
-// FP64 true residual r = mask(b - A x) on one patch; element matrices read
-// straight from global memory (coalesced: slot-major runs), products first.
-template <int NB>
+// FP64 true residual r = mask(b - A x) on one patch.  A replacement happens a
+// few times per problem and solve, so this pass favours few registers over
+// speed: element matrices are read straight from global memory (coalesced
+// slot-major runs) inside the colour rounds, products folded into the sums.
+template <typename T, int NB>
 __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
     const BatchDev& bd = *c.bd;
     const PlanDev& pd = bd.pd;
     unsigned char* smem = c.smem;
-    double* red = reinterpret_cast<double*>(smem + c.L.red);
-    int* co = reinterpret_cast<int*>(smem + c.L.co);
-    int32_t* Gs = reinterpret_cast<int32_t*>(smem + c.L.G2);
-    double* xs = reinterpret_cast<double*>(smem + c.L.xs2);
-    double* bs = reinterpret_cast<double*>(smem + c.L.bs2);
-    double* acc = reinterpret_cast<double*>(smem + c.L.acc2);
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    double* red = reinterpret_cast<double*>(smem + Lo.red);
+    int* co = reinterpret_cast<int*>(smem + Lo.co);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + Lo.G2);
+    double* xs = reinterpret_cast<double*>(smem + Lo.xs2);
+    double* bs = reinterpret_cast<double*>(smem + Lo.bs2);
+    double* acc = reinterpret_cast<double*>(smem + Lo.acc2);
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
@@ -245,34 +283,18 @@ __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
         acc[l] = 0.0;
     }
     __syncthreads();
-    int ln[kEPT][NB];
-    double y[kEPT][NB];
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int s = tid + k * NT;
-        const bool ok = s < m.n_el;
-        double xe[NB];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            ln[k][i] = ok ? int(__ldg(pd.lconn + i * ns + slot0 + s)) : 0;
-            xe[i] = xs[ln[k][i]];
-        }
-#pragma unroll
-        for (int r = 0; r < NB; ++r) {
-            double v = 0.0;
-#pragma unroll
-            for (int j = 0; j < NB; ++j) v = ok ? fmadd(__ldg(bd.A64 + (r * NB + j) * ns + slot0 + s), xe[j], v) : v;
-            y[k][r] = v;
-        }
-    }
     for (int cc = 0; cc < m.n_col; ++cc) {
         const int lo = co[cc], hi = co[cc + 1];
+        for (int s = lo + tid; s < hi; s += NT) {
+            int ln[NB];
 #pragma unroll
-        for (int k = 0; k < kEPT; ++k) {
-            const int s = tid + k * NT;
-            if (s >= lo && s < hi) {
+            for (int i = 0; i < NB; ++i) ln[i] = int(__ldg(pd.lconn + i * ns + slot0 + s));
 #pragma unroll
-                for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
+            for (int r = 0; r < NB; ++r) {
+                double v = acc[ln[r]];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) v = fmadd(__ldg(bd.A64 + (r * NB + j) * ns + slot0 + s), xs[ln[j]], v);
+                acc[ln[r]] = v;
             }
         }
         __syncthreads();
@@ -293,56 +315,74 @@ __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
 }
 
 // ---------------------------------------------------------------- phase F
-template <typename T>
+template <typename T, int NB>
 __device__ __forceinline__ void fix_item(Ctx& c, int ci, int md) {
     const BatchDev& bd = *c.bd;
     const PlanDev& pd = bd.pd;
     unsigned char* smem = c.smem;
-    double* red = reinterpret_cast<double*>(smem + c.L.red);
-    volatile int* last = reinterpret_cast<volatile int*>(smem + c.L.last);
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    double* red = reinterpret_cast<double*>(smem + Lo.red);
+    volatile int* last = reinterpret_cast<volatile int*>(smem + Lo.last);
     const int tid = threadIdx.x;
     const BatchItem it = bd.fix[ci];
+    // two shared rows per thread, their index and halo loads interleaved
     double dsum;
-    if (md == kBNormal) {
+    {
         const T* halo = static_cast<const T*>(bd.halo);
         const T* pv = static_cast<const T*>(bd.p);
         T* q = static_cast<T*>(bd.q);
         DotAcc<T> dot;
-        for (int row = it.lo + tid; row < it.hi; row += NT) {
-            const int32_t graw = __ldg(pd.sh_node + row);
-            const int g = graw & kNodeMask;
-            T v = T(0);
-            const int s1 = __ldg(pd.sh_ptr + row + 1);
-            for (int s = __ldg(pd.sh_ptr + row); s < s1; ++s) v += ld_l2(halo + __ldg(pd.sh_slot + s));
-            const T o = graw < 0 ? T(0) : v;
-            q[g] = o;
-            dot.add(ld_l2(pv + g), o);
+        double dot64 = 0.0;
+        for (int r0 = it.lo + tid; r0 < it.hi; r0 += 2 * NT) {
+            const int r1 = r0 + NT;
+            const bool two = r1 < it.hi;
+            const int32_t g0 = __ldg(pd.sh_node + r0), g1 = two ? __ldg(pd.sh_node + r1) : 0;
+            const int a0 = __ldg(pd.sh_ptr + r0), a1 = __ldg(pd.sh_ptr + r0 + 1);
+            const int b0 = two ? __ldg(pd.sh_ptr + r1) : 0, b1 = two ? __ldg(pd.sh_ptr + r1 + 1) : 0;
+            const int na = a1 - a0, nb = b1 - b0, nmax = na > nb ? na : nb;
+            if (md == kBNormal) {
+                T v0 = T(0), v1 = T(0);
+                for (int t = 0; t < nmax; ++t) {
+                    if (t < na) v0 += ld_l2(halo + __ldg(pd.sh_slot + a0 + t));
+                    if (t < nb) v1 += ld_l2(halo + __ldg(pd.sh_slot + b0 + t));
+                }
+                const int h0 = g0 & kNodeMask, h1 = g1 & kNodeMask;
+                const T o0 = g0 < 0 ? T(0) : v0;
+                q[h0] = o0;
+                dot.add(ld_l2(pv + h0), o0);
+                if (two) {
+                    const T o1 = g1 < 0 ? T(0) : v1;
+                    q[h1] = o1;
+                    dot.add(ld_l2(pv + h1), o1);
+                }
+            } else {
+                double v0 = 0.0, v1 = 0.0;
+                for (int t = 0; t < nmax; ++t) {
+                    if (t < na) v0 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + a0 + t));
+                    if (t < nb) v1 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + b0 + t));
+                }
+                const double o0 = g0 < 0 ? 0.0 : __ldg(bd.b + (g0 & kNodeMask)) - v0;
+                bd.r[g0 & kNodeMask] = o0;
+                dot64 = fmadd(o0, o0, dot64);
+                if (two) {
+                    const double o1 = g1 < 0 ? 0.0 : __ldg(bd.b + (g1 & kNodeMask)) - v1;
+                    bd.r[g1 & kNodeMask] = o1;
+                    dot64 = fmadd(o1, o1, dot64);
+                }
+            }
         }
-        dsum = dot.value();
-    } else {
-        double dot = 0.0;
-        for (int row = it.lo + tid; row < it.hi; row += NT) {
-            const int32_t graw = __ldg(pd.sh_node + row);
-            const int g = graw & kNodeMask;
-            double v = 0.0;
-            const int s1 = __ldg(pd.sh_ptr + row + 1);
-            for (int s = __ldg(pd.sh_ptr + row); s < s1; ++s) v += ld_l2(bd.halo64 + __ldg(pd.sh_slot + s));
-            const double o = graw < 0 ? 0.0 : __ldg(bd.b + g) - v;
-            bd.r[g] = o;
-            dot = fmadd(o, o, dot);
-        }
-        dsum = dot;
+        dsum = md == kBNormal ? dot.value() : dot64;
     }
     for (int i = it.plo + tid; i < it.phi; i += NT) dsum += ld_l2(bd.part_p + i);
     dsum = block_sum<NT>(dsum, red);
+    // last item of the problem to finish: the acquire-release arrival makes
+    // every earlier item's partial visible to it
     if (tid == 0) {
         bd.part_f[ci] = dsum;
-        __threadfence();
-        *last = atomicAdd(bd.ctr + it.k, 1u) == uint32_t(it.count - 1) ? 1 : 0;
+        *last = tma::atom_add_acq_rel(bd.ctr + it.k, 1u) == uint32_t(it.count - 1) ? 1 : 0;
     }
     __syncthreads();
     if (!*last) return;
-    __threadfence();
     double s = 0.0;
     for (int i = tid; i < it.count; i += NT) s += ld_l2(bd.part_f + it.first + i);
     s = block_sum<NT>(s, red);
@@ -429,13 +469,14 @@ __device__ __forceinline__ void decide(const BatchDev& bd, int k, int md, double
 }
 
 // ---------------------------------------------------------------- phase U
-template <typename T>
+template <typename T, int NB>
 __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
     constexpr bool MIXED = sizeof(T) == 4;
     const BatchDev& bd = *c.bd;
     unsigned char* smem = c.smem;
-    double* red = reinterpret_cast<double*>(smem + c.L.red);
-    volatile int* last = reinterpret_cast<volatile int*>(smem + c.L.last);
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    double* red = reinterpret_cast<double*>(smem + Lo.red);
+    volatile int* last = reinterpret_cast<volatile int*>(smem + Lo.last);
     const int tid = threadIdx.x;
     const BatchItem it = bd.tile[ti];
     const T* pv = static_cast<const T*>(bd.p);
@@ -534,12 +575,10 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
     if (tid == 0) {
         bd.part_u[2 * ti] = a;
         bd.part_u[2 * ti + 1] = b;
-        __threadfence();
-        *last = atomicAdd(bd.ctr + bd.n_prob + it.k, 1u) == uint32_t(it.count - 1) ? 1 : 0;
+        *last = tma::atom_add_acq_rel(bd.ctr + bd.n_prob + it.k, 1u) == uint32_t(it.count - 1) ? 1 : 0;
     }
     __syncthreads();
     if (!*last) return;
-    __threadfence();
     double sa = 0.0, sb = 0.0;
     for (int i = tid; i < it.count; i += NT) {
         sa += ld_l2(bd.part_u + 2 * (it.first + i));
@@ -588,104 +627,224 @@ __device__ __forceinline__ void direction_item(Ctx& c, int ti) {
     }
 }
 
+// ---------------------------------------------------------------- scheduling
+// Exclusive block scan of four counters; scratch: 8 int4 (NT = 256).
+__device__ __forceinline__ int4 block_exscan4(int4 v, int4* scratch, int4& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int4 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, inc.x, o), b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int c = __shfl_up_sync(0xffffffffu, inc.z, o), d = __shfl_up_sync(0xffffffffu, inc.w, o);
+        if (lane >= o) { inc.x += a; inc.y += b; inc.z += c; inc.w += d; }
+    }
+    __syncthreads();
+    if (lane == 31) scratch[w] = inc;
+    __syncthreads();
+    int4 base = make_int4(0, 0, 0, 0);
+    total = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+        const int4 t = scratch[i];
+        if (i < w) { base.x += t.x; base.y += t.y; base.z += t.z; base.w += t.w; }
+        total.x += t.x; total.y += t.y; total.z += t.z; total.w += t.w;
+    }
+    return make_int4(base.x + inc.x - v.x, base.y + inc.y - v.y, base.z + inc.z - v.z, base.w + inc.w - v.w);
+}
+
+// The live-problem list and the prefix sums of their item counts (all threads).
+__device__ __forceinline__ void rebuild_lists(const BatchDev& bd, const int8_t* smode, int32_t* list, int32_t* pre,
+                                              volatile int* snl, int4* scratch) {
+    const int n = bd.n_prob;
+    const int per = (n + NT - 1) / NT;
+    const int k0 = min(n, int(threadIdx.x) * per), k1 = min(n, k0 + per);
+    int4 c = make_int4(0, 0, 0, 0);
+    for (int k = k0; k < k1; ++k) {
+        if (smode[k] == kBDone) continue;
+        const BatchProbInfo pi = bd.pinfo[k];
+        c.x += 1; c.y += pi.patch_count; c.z += pi.fix_count; c.w += pi.tile_count;
+    }
+    int4 tot;
+    int4 o = block_exscan4(c, scratch, tot);
+    int32_t* pp = pre;
+    int32_t* pf = pre + (n + 1);
+    int32_t* pt = pre + 2 * (n + 1);
+    for (int k = k0; k < k1; ++k) {
+        if (smode[k] == kBDone) continue;
+        const BatchProbInfo pi = bd.pinfo[k];
+        list[o.x] = k;
+        pp[o.x] = o.y;
+        pf[o.x] = o.z;
+        pt[o.x] = o.w;
+        o.x += 1; o.y += pi.patch_count; o.z += pi.fix_count; o.w += pi.tile_count;
+    }
+    if (threadIdx.x == 0) {
+        pp[tot.x] = tot.y;
+        pf[tot.x] = tot.z;
+        pt[tot.x] = tot.w;
+        *snl = tot.x;
+    }
+    __syncthreads();
+}
+
+// Position j of the live list whose items contain item i: pre[j] <= i < pre[j + 1].
+__device__ __forceinline__ int find_item(const int32_t* pre, int nl, int i) {
+    int lo = 0, hi = nl;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 template <typename T, int NB>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NB == 3) ? 4 : 2)
-k_batch_pcg(const __grid_constant__ BatchDev bd, int cap_p, int cap_f, int cap_t) {
-    constexpr bool MIXED = sizeof(T) == 4;
+k_batch_pcg(const __grid_constant__ BatchDev bd) {
     extern __shared__ __align__(128) unsigned char smem[];
     Ctx c;
     c.bd = &bd;
     c.smem = smem;
-    c.L = batch_layout<T, NB>(bd.pd.max_nodes, bd.n_prob, cap_p, cap_f, cap_t);
-    c.mbar = tma::smem_addr(smem + c.L.bar);
     c.mph = 0;
-    volatile int* sflag = reinterpret_cast<volatile int*>(smem + c.L.flag);
-    volatile int* broken = reinterpret_cast<volatile int*>(smem + c.L.broken);
-    volatile int* slive = reinterpret_cast<volatile int*>(smem + c.L.live);
-    int8_t* smode = reinterpret_cast<int8_t*>(smem + c.L.mode);
-    int32_t* sp = reinterpret_cast<int32_t*>(smem + c.L.sp);
-    int32_t* sf = reinterpret_cast<int32_t*>(smem + c.L.sf);
-    int32_t* stl = reinterpret_cast<int32_t*>(smem + c.L.st);
+    const BatchSmem Lo = layout_of<T, NB>(bd);
+    volatile int* sflag = reinterpret_cast<volatile int*>(smem + Lo.flag);
+    volatile int* broken = reinterpret_cast<volatile int*>(smem + Lo.broken);
+    volatile int* slive = reinterpret_cast<volatile int*>(smem + Lo.live);
+    volatile int* snl = reinterpret_cast<volatile int*>(smem + Lo.nl);
+    volatile int* sver = reinterpret_cast<volatile int*>(smem + Lo.ver);
+    int8_t* smode = reinterpret_cast<int8_t*>(smem + Lo.mode);
+    int32_t* list = reinterpret_cast<int32_t*>(smem + Lo.list);
+    int32_t* pre = reinterpret_cast<int32_t*>(smem + Lo.pre);
+    const int32_t* pre_p = pre;
+    const int32_t* pre_f = pre + (bd.n_prob + 1);
+    const int32_t* pre_t = pre + 2 * (bd.n_prob + 1);
+    int4* scratch = reinterpret_cast<int4*>(smem + Lo.red);
+    uint64_t* tph = reinterpret_cast<uint64_t*>(smem + Lo.timer);   // [5]: phase times, last lap
     const int tid = threadIdx.x;
     const uint32_t G = gridDim.x;
-    const int np = bd.pd.n_patches;
 
-    // this CTA's items (static: item blockIdx.x + j G) and their problems
-    for (int j = tid; j < cap_p; j += NT) {
-        const int64_t p = int64_t(blockIdx.x) + int64_t(j) * G;
-        sp[j] = p < np ? __ldg(bd.patch_prob + p) : -1;
-    }
-    for (int j = tid; j < cap_f; j += NT) {
-        const int64_t i = int64_t(blockIdx.x) + int64_t(j) * G;
-        sf[j] = i < bd.n_fix ? __ldg(&bd.fix[i].k) : -1;
-    }
-    for (int j = tid; j < cap_t; j += NT) {
-        const int64_t i = int64_t(blockIdx.x) + int64_t(j) * G;
-        stl[j] = i < bd.n_tile ? __ldg(&bd.tile[i].k) : -1;
-    }
+    // problem modes and, when a problem has finished since the last look,
+    // the live list (every CTA sees the same state after a grid barrier)
     auto refresh = [&]() {
         for (int k = tid; k < bd.n_prob; k += NT) smode[k] = int8_t(ld_l2(&bd.prob[k].mode));
         if (tid == 0) *slive = ld_l2(bd.live);
         __syncthreads();
+        if (*slive != *sver) {
+            rebuild_lists(bd, smode, list, pre, snl, scratch);
+            if (tid == 0) *sver = *slive;
+            __syncthreads();
+        }
     };
+    // phase times (thread 0 of CTA 0, in shared memory): from one barrier exit to the next
+    const bool timer = blockIdx.x == 0 && tid == 0;
     if (tid == 0) {
-        tma::mbar_init(c.mbar, 1);
+        tma::mbar_init(tma::smem_addr(smem + Lo.bar), 1);
         *broken = 0;
+        *sver = -1;
+        for (int ph = 0; ph < 4; ++ph) tph[ph] = 0;
+        tph[4] = tma::globaltimer_ns();
     }
+    __syncthreads();
     refresh();
     const uint64_t lim = bd.barrier_ns;
+    auto lap = [&](int ph) {
+        if (timer) {
+            const uint64_t t = tma::globaltimer_ns();
+            tph[ph] += t - tph[4];
+            tph[4] = t;
+        }
+    };
+    auto flush = [&]() {
+        if (timer)
+            for (int ph = 0; ph < 4; ++ph) atomicAdd(bd.phase_ns + ph, (unsigned long long)tph[ph]);
+    };
+
+    // patch whose bulk copies are in flight for this CTA's next apply (-1: none)
+    int pf = -1;
+    const uint32_t mbar = tma::smem_addr(smem + Lo.bar);
+    // the patch of item i if it is an operator application, else -1
+    auto next_apply = [&](int i, int nlv) {
+        if (i >= pre_p[nlv]) return -1;
+        const int j = find_item(pre_p, nlv, i);
+        const int k = list[j];
+        return smode[k] == kBNormal ? __ldg(&bd.pinfo[k].patch_first) + (i - pre_p[j]) : -1;
+    };
+    // copies still in flight when the CTA leaves: wait for them (bounded)
+    auto drain = [&]() {
+        if (pf >= 0 && tid == 0) tma::mbar_wait_bounded(mbar, c.mph, nullptr);
+    };
 
     for (int64_t loop = 0; loop < bd.iter_budget; ++loop) {
         if (*slive <= 0) break;
+        const int nl = *snl;
         // P
         if (!*broken)
-            for (int j = 0; j < cap_p; ++j) {
-                const int k = sp[j];
-                if (k < 0) break;
-                const int md = smode[k];
-                if (md == kBDone) continue;
-                const int p = int(blockIdx.x + uint32_t(j) * G);
-                if (md == kBNormal) {
-                    if (!apply_patch<T, NB>(c, p)) break;
+            for (int i = int(blockIdx.x); i < pre_p[nl]; i += int(G)) {
+                const int j = find_item(pre_p, nl, i);
+                const int k = list[j];
+                const int p = __ldg(&bd.pinfo[k].patch_first) + (i - pre_p[j]);
+                if (smode[k] == kBNormal) {
+                    const int nxt = next_apply(i + int(G), nl);
+                    if (!apply_patch<T, NB>(c, p, pf == p, nxt)) {
+                        pf = -1;
+                        break;
+                    }
+                    pf = nxt;
                 } else {
-                    residual_patch<NB>(c, p);
+                    residual_patch<T, NB>(c, p);
                 }
             }
-        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) return;
+        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) { drain(); return; }
+        lap(0);
+        // The element matrices are constant: the copies of this CTA's first
+        // patch of the next loop start now and land during F, U and D (if U
+        // changes which patch that is, they are waited for and dropped).
+        if (!*broken && pf < 0 && loop + 1 < bd.iter_budget) {
+            pf = next_apply(int(blockIdx.x), nl);
+            if (pf >= 0 && tid == 0) issue_patch_copies<T, NB>(bd, smem, pf);
+        }
         // F
-        for (int j = 0; j < cap_f; ++j) {
-            const int k = sf[j];
-            if (k < 0) break;
-            const int md = smode[k];
-            if (md == kBDone) continue;
-            fix_item<T>(c, int(blockIdx.x + uint32_t(j) * G), md);
+        for (int i = int(blockIdx.x); i < pre_f[nl]; i += int(G)) {
+            const int j = find_item(pre_f, nl, i);
+            const int k = list[j];
+            fix_item<T, NB>(c, __ldg(&bd.pinfo[k].fix_first) + (i - pre_f[j]), smode[k]);
         }
-        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) return;
+        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) { drain(); return; }
+        lap(1);
         // U
-        for (int j = 0; j < cap_t; ++j) {
-            const int k = stl[j];
-            if (k < 0) break;
-            const int md = smode[k];
-            if (md == kBDone) continue;
-            update_item<T>(c, int(blockIdx.x + uint32_t(j) * G), md);
+        for (int i = int(blockIdx.x); i < pre_t[nl]; i += int(G)) {
+            const int j = find_item(pre_t, nl, i);
+            const int k = list[j];
+            update_item<T, NB>(c, __ldg(&bd.pinfo[k].tile_first) + (i - pre_t[j]), smode[k]);
         }
-        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) return;
+        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) { drain(); return; }
         refresh();
-        // D
-        for (int j = 0; j < cap_t; ++j) {
-            const int k = stl[j];
-            if (k < 0) break;
+        if (pf >= 0 && pf != next_apply(int(blockIdx.x), *snl)) {
+            if (tid == 0 && !tma::mbar_wait_bounded(mbar, c.mph, bd.pd.err)) *broken = 1;
+            c.mph ^= 1u;
+            pf = -1;
+            __syncthreads();
+        }
+        lap(2);
+        // D (the list may have shrunk: problems finished in U are gone)
+        const int nl2 = *snl;
+        for (int i = int(blockIdx.x); i < pre_t[nl2]; i += int(G)) {
+            const int j = find_item(pre_t, nl2, i);
+            const int k = list[j];
             if (smode[k] != kBNormal) continue;
-            direction_item<T>(c, int(blockIdx.x + uint32_t(j) * G));
+            direction_item<T>(c, __ldg(&bd.pinfo[k].tile_first) + (i - pre_t[j]));
         }
         if (blockIdx.x == 0 && tid == 0) *bd.loops += 1;
-        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) return;
+        if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) { drain(); return; }
+        lap(3);
     }
+    drain();
+    flush();
 }
 
 __global__ void k_batch_init(BatchProblem* prob, int n_prob, uint32_t* ctr, uint32_t* bar, int32_t* live,
-                             int64_t* loops) {
+                             int64_t* loops, unsigned long long* phase_ns) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n_prob) {
         BatchProblem P{};
@@ -701,21 +860,13 @@ __global__ void k_batch_init(BatchProblem* prob, int n_prob, uint32_t* ctr, uint
         bar[1] = 0u;
         *live = n_prob;
         *loops = 0;
+        for (int ph = 0; ph < 4; ++ph) phase_ns[ph] = 0ull;
     }
 }
 
-int caps(const BatchDev& bd, int grid, int* cp, int* cf, int* ct) {
-    *cp = (bd.pd.n_patches + grid - 1) / grid;
-    *cf = (bd.n_fix + grid - 1) / grid;
-    *ct = (bd.n_tile + grid - 1) / grid;
-    return 0;
-}
-
 template <typename T, int NB>
-int smem_for(const BatchDev& bd, int grid) {
-    int cp, cf, ct;
-    caps(bd, grid, &cp, &cf, &ct);
-    return int(batch_layout<T, NB>(bd.pd.max_nodes, bd.n_prob, cp, cf, ct).total);
+int smem_for(const BatchDev& bd) {
+    return int(batch_layout<T, NB>(bd.pd.max_nodes, bd.n_prob).total);
 }
 
 template <typename T, int NB>
@@ -723,7 +874,7 @@ int max_ctas(const BatchDev& bd, int* smem_bytes) {
     auto kern = k_batch_pcg<T, NB>;
     int best = 0;
     for (int c = 1; c <= 8; ++c) {
-        const int sm = smem_for<T, NB>(bd, c * bd.pd.num_sms);
+        const int sm = smem_for<T, NB>(bd);
         if (sm > 227 * 1024) break;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) break;
         int occ = 0;
@@ -740,9 +891,7 @@ template <typename T, int NB>
 cudaError_t run_batch(const BatchDev& bd, int ctas_per_sm, cudaStream_t st) {
     auto kern = k_batch_pcg<T, NB>;
     const int grid = ctas_per_sm * bd.pd.num_sms;
-    int cp, cf, ct;
-    caps(bd, grid, &cp, &cf, &ct);
-    const int sm = smem_for<T, NB>(bd, grid);
+    const int sm = smem_for<T, NB>(bd);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
@@ -756,14 +905,15 @@ cudaError_t run_batch(const BatchDev& bd, int ctas_per_sm, cudaStream_t st) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, bd, cp, cf, ct);
+    return cudaLaunchKernelEx(&cfg, kern, bd);
 }
 
 }  // namespace
 
 cudaError_t launch_batch_init(const BatchDev& bd, cudaStream_t st, int* launches) {
     const int nt = 256;
-    k_batch_init<<<(bd.n_prob + nt - 1) / nt, nt, 0, st>>>(bd.prob, bd.n_prob, bd.ctr, bd.bar, bd.live, bd.loops);
+    k_batch_init<<<(bd.n_prob + nt - 1) / nt, nt, 0, st>>>(bd.prob, bd.n_prob, bd.ctr, bd.bar, bd.live, bd.loops,
+                                                                bd.phase_ns);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

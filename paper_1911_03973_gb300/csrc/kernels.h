@@ -175,12 +175,19 @@ struct BatchItem {
     int32_t k, lo, hi, plo, phi, first, count, pad;
 };
 
+// Where the work items of one problem of a batch are: patches
+// [patch_first, +patch_count), fix-up items [fix_first, +fix_count), node
+// tiles [tile_first, +tile_count) (of the launch's tile size); all counts >= 1.
+struct BatchProbInfo {
+    int32_t patch_first, patch_count, fix_first, fix_count, tile_first, tile_count, pad0, pad1;
+};
+
 // Everything the persistent batched solver reads and writes.
 struct BatchDev {
     PlanDev pd;
     int32_t n_prob = 0;
     int32_t n_fix = 0, n_tile = 0;
-    const int32_t* patch_prob = nullptr;   // [n_patches] problem of each patch
+    const BatchProbInfo* pinfo = nullptr;  // [n_prob]
     const BatchItem* fix = nullptr;        // [n_fix]
     const BatchItem* tile = nullptr;       // [n_tile]
     const void* A = nullptr;               // element matrices of the inner operator (FP32 difference form or FP64)
@@ -201,6 +208,7 @@ struct BatchDev {
     uint32_t* bar = nullptr;               // [2] grid barrier
     int32_t* live = nullptr;               // problems not done
     int64_t* loops = nullptr;              // iterations (of any kind) run by the persistent kernel
+    unsigned long long* phase_ns = nullptr;   // [4] time of the phases P, F, U, D (barrier to barrier, CTA 0)
     double rtol = 1e-8, delta = 0.1, margin = 0.7;
     int64_t maxit = 0;
     int32_t stall_updates = 8;

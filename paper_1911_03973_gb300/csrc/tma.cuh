@@ -60,6 +60,18 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Atomic add with acquire-release semantics at GPU scope: publishes the
+// calling thread's earlier writes (and, through a preceding __syncthreads,
+// its CTA's) to whoever later acquires this location, and makes visible to
+// the caller everything published by earlier arrivals.
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -67,12 +79,12 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1]
-// is the generation.  Thread 0 of each CTA publishes the CTA's writes
-// (__syncthreads, then a GPU-scope fence), arrives, and waits for the
-// generation to move on; the last CTA to arrive resets the count and
-// releases the generation.  The wait is bounded: after limit_ns of global
-// time, or as soon as *err is nonzero, the CTA stops waiting and sets *err
-// (2 = barrier timeout).  Returns false in every thread of a CTA that must
+// is the generation.  After a __syncthreads, thread 0 of each CTA arrives
+// with an acquire-release atomic (publishing the CTA's writes) and waits
+// with acquire loads for the generation to move on; the last CTA to arrive
+// resets the count and releases the next generation.  The wait is bounded:
+// after limit_ns of global time, or as soon as *err is nonzero, the CTA
+// stops waiting and sets *err (2 = barrier timeout).  Returns false in every thread of a CTA that must
 // stop (a timeout or an error raised anywhere); every CTA that gets past the
 // barrier sees the same *err, so the decision is uniform.
 __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32_t* err, volatile int* sflag,
@@ -81,10 +93,9 @@ __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t gen = ld_acquire(bar + 1);
-        __threadfence();
-        const uint32_t arrived = atomicAdd(bar, 1u);
+        const uint32_t arrived = atom_add_acq_rel(bar, 1u);
         if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
+            st_relaxed(bar, 0u);
             st_release(bar + 1, gen + 1u);
         } else {
             const uint64_t t0 = globaltimer_ns();
@@ -96,7 +107,6 @@ __device__ __forceinline__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32
                 }
             }
         }
-        __threadfence();
         if (ok && *reinterpret_cast<volatile int32_t*>(err) != 0) ok = 0;
         *sflag = ok;
     }

@@ -172,11 +172,20 @@ def test_batch_tuner_and_config(ebe, batch):
     x, infos, summary = _solve(ebe, h, U, stream, rtol=1e-8, precision=ebe.EBE_PREC_MIXED)
     assert (summary["ctas_per_sm"], summary["tile_nodes"]) == res["best"]
     assert summary["n_converged"] == len(probs)
+    assert summary["phase_ms"]["patch"] > 0.0 and sum(summary["phase_ms"].values()) < summary["solve_ms"]
+    # the shape tuned for mixed precision is not imposed on FP64 solves (fewer CTAs fit)
+    x, infos, summary = _solve(ebe, h, U, stream, rtol=1e-8, precision=ebe.EBE_PREC_FP64)
+    assert summary["n_converged"] == len(probs)
+    by_tile = {}
     for c, t, _ in cands:                            # every shape gives a valid solve
         ebe.ebe_set_batch_config(h, c, t)
         x, infos, summary = _solve(ebe, h, U, stream, rtol=1e-8, precision=ebe.EBE_PREC_MIXED)
         assert summary["n_converged"] == len(probs), (c, t)
         assert orcs[5].rel_residual(_split(x, U)[5]) <= 1e-8
+        # which CTA runs an item does not change any sum: same tile size, same bits
+        if t in by_tile:
+            np.testing.assert_array_equal(x, by_tile[t])
+        by_tile[t] = x
     with pytest.raises(ebe.EbeError):
         ebe.ebe_set_batch_config(h, 1, 3000)
     with pytest.raises(ebe.EbeError):

@@ -21,6 +21,11 @@ application (patch kernel + halo fix-up) timed per launch with CUDA events on
 its stream.  e2e repeats the step through the C ABI from pinned host buffers:
 mesh, f and boundary sets in, solution out, including the partition build.
 
+"batched" (skip with --no-batch): 256 independent squares (sides log-uniform
+in [17, 513] nodes, seed 4) solved by the batched persistent solver in mixed
+precision with an autotuned launch shape, against the same problems solved
+one by one with ebe_solve (plain FP64 and mixed) and the batched FP64 solve.
+
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
 sample of the same workload.
 """

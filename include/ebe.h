@@ -365,6 +365,71 @@ ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg);
 ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_batch_config* best,
                           ebe_batch_config* shapes, double* ms, int32_t capacity, int32_t* n_written);
 
+/* ---------------------------------------------------------------- learned preconditioner */
+
+/* A small message-passing network in the preconditioner slot of the solver
+ * loop (the paper's listings apply z = r where a preconditioner would act,
+ * Sec. 2; the network is this library's own addition).  For a residual r on
+ * the mesh of a handle, with dinv the inverse Jacobi diagonal (0 on
+ * Dirichlet nodes) and rms taken over the free nodes:
+ *   x_i = [r_i / rms(r), (dinv r)_i / rms(dinv r)]                (2 features)
+ *   h_i = W_in x_i + b_in                                         (32)
+ *   4 layers: a_i = mean_{j in N(i)} h_j - h_i, h_i += relu(W_l [h_i; a_i] + b_l)
+ *   z_i = (dinv r)_i + rms(dinv r) (w_out . h_i + b_out),  z_i = 0 on Dirichlet nodes
+ * N(i): the nodes sharing an element with node i.  z is homogeneous of degree
+ * one in r, and a zero decoder gives the Jacobi step.  Weights and hidden
+ * features are BF16 (round to nearest even), sums FP32; the per-node layers
+ * run on the tensor cores (tcgen05).  Parameter vector (ebe_mpnn_n_params()
+ * doubles): W_in [32][2], b_in [32], then per layer W_l [32][64], b_l [32],
+ * then w_out [32], b_out.  A network object holds FP32 master parameters,
+ * Adam moments and work buffers on one device and can be used with any
+ * handle on that device (train on one mesh, use on another). */
+typedef struct ebe_mpnn ebe_mpnn;
+
+int64_t ebe_mpnn_n_params(void);
+/* theta: host [n_params] or NULL for the library's seeded initial weights
+ * (zero decoder).  Errors: EBE_INVALID_ARG (no such device, non-finite
+ * theta), EBE_OOM, EBE_CUDA_ERROR (message: ebe_mpnn_last_error(NULL)). */
+ebe_status ebe_mpnn_create(ebe_mpnn** net, int32_t device, const double* theta);
+void ebe_mpnn_destroy(ebe_mpnn* net);
+const char* ebe_mpnn_last_error(const ebe_mpnn* net);
+/* Replace the parameters (host [n_params], NULL = initial weights) and reset
+ * the optimiser; get: host [n_params] (FP32 masters as doubles). */
+ebe_status ebe_mpnn_set_params(ebe_mpnn* net, const double* theta);
+ebe_status ebe_mpnn_get_params(const ebe_mpnn* net, double* theta);
+
+/* z = B(r) on the mesh of h (assembled).  r_dev, z_dev: device [n_n] double.
+ * Builds the handle's mesh graph on first use.  Synchronises the stream.
+ * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
+ebe_status ebe_mpnn_apply(ebe_mpnn* net, ebe_handle* h, const double* r_dev, double* z_dev);
+
+/* Gradient of a loss L(z) with respect to the parameters for
+ * gz_dev = dL/dz (device [n_n] double): forward pass at r_dev (z written to
+ * z_dev if not NULL), then the backward pass.  grad: host [n_params].  The
+ * BF16 roundings of the forward pass count as the identity. */
+ebe_status ebe_mpnn_grad(ebe_mpnn* net, ebe_handle* h, const double* r_dev, const double* gz_dev, double* z_dev,
+                         double* grad);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the
+ * energy-norm loss L = (e - z)' A (e - z) / e' A e of one sample: a residual
+ * r_dev and the error e_dev = x* - x that it belongs to (device [n_n]
+ * double, zero on Dirichlet nodes), A the FP64 operator of h.  loss: host,
+ * the loss before the step (NULL allowed).  Synchronises the stream. */
+ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev, const double* e_dev, double lr,
+                               double* loss);
+
+/* Flexible CG (one stored direction: p = z - (z.q_prev / p_prev.q_prev) p_prev,
+ * alpha = p.r / p.q) with z = B(r) from net, or the Jacobi step with net NULL,
+ * FP64 vectors and element matrices, stopping on the FP64 true relative
+ * residual as ebe_solve.  With a network the solve falls back to Jacobi from
+ * the current iterate on a breakdown, when the residual stops decreasing
+ * (64 chunks without halving) or when the true residual stalls
+ * (stall_updates checks); *fell_back (may be NULL) reports it.  opts:
+ * rtol, maxit, chunk (iterations between host checks), stall_updates.
+ * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
+ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x_dev, const ebe_solve_opts* opts,
+                             ebe_solve_info* info, int32_t* fell_back);
+
 /* ---------------------------------------------------------------- allocation-free residual */
 
 /* ebe_residual (FP64) for callers that must not allocate device memory during

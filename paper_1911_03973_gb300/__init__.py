@@ -357,6 +357,100 @@ def ebe_batch_tune(h: Handle, precision: int = EBE_PREC_MIXED, loops: int = 0) -
             "candidates": [(shapes[i].ctas_per_sm, shapes[i].tile_nodes, ms[i]) for i in range(n.value)]}
 
 
+class Mpnn:
+    """Owner of an ``ebe_mpnn*`` (learned preconditioner: weights, optimiser state)."""
+
+    def __init__(self, ptr, device):
+        self.ptr = ptr
+        self.device = device
+
+    def __del__(self):
+        try:
+            ebe_mpnn_destroy(self)
+        except Exception:
+            pass
+
+
+def ebe_mpnn_last_error(net: Mpnn | None) -> str:
+    return _lib().ebe_mpnn_last_error(net.ptr if net is not None else None).decode()
+
+
+def _net_check(net, status):
+    if status != _abi.EBE_OK:
+        raise EbeError(status, ebe_mpnn_last_error(net))
+
+
+def ebe_mpnn_n_params() -> int:
+    return int(_lib().ebe_mpnn_n_params())
+
+
+def ebe_mpnn_create(device: int = 0, theta=None) -> Mpnn:
+    """ebe_mpnn_create: theta host [n_params] or None (seeded initial weights, zero decoder)."""
+    t = None if theta is None else _host_f64(theta)
+    if t is not None and t.shape != (ebe_mpnn_n_params(),):
+        raise ValueError("theta must have ebe_mpnn_n_params() entries")
+    ptr = ctypes.c_void_p()
+    st = _lib().ebe_mpnn_create(ctypes.byref(ptr), int(device),
+                                t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if t is not None else None)
+    if st != _abi.EBE_OK:
+        raise EbeError(st, _lib().ebe_mpnn_last_error(None).decode())
+    return Mpnn(ptr, device)
+
+
+def ebe_mpnn_destroy(net: Mpnn) -> None:
+    if net is not None and net.ptr is not None and net.ptr.value:
+        _lib().ebe_mpnn_destroy(net.ptr)
+        net.ptr = ctypes.c_void_p()
+
+
+def ebe_mpnn_set_params(net: Mpnn, theta=None) -> None:
+    t = None if theta is None else _host_f64(theta)
+    _net_check(net, _lib().ebe_mpnn_set_params(
+        net.ptr, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if t is not None else None))
+
+
+def ebe_mpnn_get_params(net: Mpnn) -> np.ndarray:
+    t = np.empty(ebe_mpnn_n_params())
+    _net_check(net, _lib().ebe_mpnn_get_params(net.ptr, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return t
+
+
+def ebe_mpnn_apply(net: Mpnn, h: Handle, r, z) -> None:
+    """z = B(r) (float64 CUDA tensors of n_n entries) on the mesh of h."""
+    _check(h, _lib().ebe_mpnn_apply(net.ptr, h.ptr, _dev(r, EBE_F64, h.n_n, "r"), _dev(z, EBE_F64, h.n_n, "z")))
+
+
+def ebe_mpnn_grad(net: Mpnn, h: Handle, r, gz, z=None) -> np.ndarray:
+    """Parameter gradient for dL/dz = gz (device); returns a host array, writes z if given."""
+    g = np.empty(ebe_mpnn_n_params())
+    _check(h, _lib().ebe_mpnn_grad(net.ptr, h.ptr, _dev(r, EBE_F64, h.n_n, "r"), _dev(gz, EBE_F64, h.n_n, "gz"),
+                                   _dev(z, EBE_F64, h.n_n, "z") if z is not None else None,
+                                   g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return g
+
+
+def ebe_mpnn_train_step(net: Mpnn, h: Handle, r, e, lr: float) -> float:
+    """One Adam step on the energy-norm loss of sample (r, e); returns the loss before the step."""
+    loss = ctypes.c_double()
+    _check(h, _lib().ebe_mpnn_train_step(net.ptr, h.ptr, _dev(r, EBE_F64, h.n_n, "r"), _dev(e, EBE_F64, h.n_n, "e"),
+                                         float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def ebe_solve_learned(h: Handle, net, x, rtol=None, maxit=None, chunk=None, stall_updates=None) -> dict:
+    """Flexible CG with the network (or Jacobi with net=None) on a device x; adds "fell_back"."""
+    o = _opts(rtol, maxit, None, chunk, None, stall_updates, None)
+    info = _abi.ebe_solve_info()
+    fb = ctypes.c_int32()
+    st = _lib().ebe_solve_learned(h.ptr, net.ptr if net is not None else None, _dev(x, EBE_F64, h.n_n, "x"),
+                                  ctypes.byref(o), ctypes.byref(info), ctypes.byref(fb))
+    if st not in SOLVER_OUTCOMES:
+        _check(h, st)
+    out = _info_dict(info)
+    out["fell_back"] = bool(fb.value)
+    return out
+
+
 def ebe_residual_noalloc(h: Handle, x, r) -> None:
     """ebe_residual_noalloc: FP64 residual without any device allocation in the
     call (scratch from a fixed device array in the library), for callers that

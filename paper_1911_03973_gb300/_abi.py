@@ -118,6 +118,17 @@ SIGNATURES = [
     ("ebe_set_batch_config", ctypes.c_int, [_H, ctypes.POINTER(ebe_batch_config)]),
     ("ebe_batch_tune", ctypes.c_int, [_H, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ebe_batch_config),
                                       ctypes.POINTER(ebe_batch_config), _F64P, ctypes.c_int32, _I32P]),
+    ("ebe_mpnn_n_params", ctypes.c_int64, []),
+    ("ebe_mpnn_create", ctypes.c_int, [ctypes.POINTER(_H), ctypes.c_int32, _F64P]),
+    ("ebe_mpnn_destroy", None, [_H]),
+    ("ebe_mpnn_last_error", ctypes.c_char_p, [_H]),
+    ("ebe_mpnn_set_params", ctypes.c_int, [_H, _F64P]),
+    ("ebe_mpnn_get_params", ctypes.c_int, [_H, _F64P]),
+    ("ebe_mpnn_apply", ctypes.c_int, [_H, _H, _VP, _VP]),
+    ("ebe_mpnn_grad", ctypes.c_int, [_H, _H, _VP, _VP, _VP, _F64P]),
+    ("ebe_mpnn_train_step", ctypes.c_int, [_H, _H, _VP, _VP, ctypes.c_double, _F64P]),
+    ("ebe_solve_learned", ctypes.c_int, [_H, _H, _VP, ctypes.POINTER(ebe_solve_opts), ctypes.POINTER(ebe_solve_info),
+                                         _I32P]),
     ("ebe_residual_noalloc", ctypes.c_int, [_H, _VP, _VP]),
     ("ebe_richardson", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double]),
     ("ebe_chebyshev2", ctypes.c_int, [_H, _VP, ctypes.c_int64, _F64P, ctypes.c_int64]),

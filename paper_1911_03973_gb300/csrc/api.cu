@@ -61,7 +61,7 @@ struct ebe_handle {
     float* halo32 = nullptr;
     double* halo2 = nullptr;
     double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
-    double* part_vec = nullptr;     // 2 * 1216
+    double* part_vec = nullptr;     // 3 * 1216
     Scalars* sc = nullptr;
     Scalars* sc_host = nullptr;     // pinned
     unsigned long long* bad = nullptr;
@@ -96,6 +96,12 @@ struct ebe_handle {
     ebe_batch_config bcfg[2] = {{0, 0}, {0, 0}};   // launch shape per precision (FP64, mixed)
     cudaGraphExec_t bgraph = nullptr;
     std::vector<double> bgraph_key;
+
+    // mesh graph (learned preconditioner) and flexible-CG vectors
+    int32_t* g_ptr = nullptr;
+    int32_t* g_nbr = nullptr;
+    float* g_invdeg = nullptr;
+    double* z64 = nullptr;
 
     // comparison scatters
     int32_t* gconn = nullptr;
@@ -308,7 +314,7 @@ static int create_device(ebe_handle* h, const double* coords_host) {
     pd.sh_slot = sh_slot;
     pd.slot_elem = slot_elem;
     TRY(dalloc(h, &h->part_patch, P.n_patches + 1216));
-    TRY(dalloc(h, &h->part_vec, 2 * 1216));
+    TRY(dalloc(h, &h->part_vec, 3 * 1216));   // up to three partial sums per block
     TRY(dalloc(h, &h->sc, 1, true));
     TRY(dalloc(h, &h->bad, 1));
     TRY(dalloc(h, &h->dev_err, 1, true));
@@ -1376,6 +1382,427 @@ ebe_status ebe_partition_export_batch(const ebe_mesh* meshes, int32_t n_problems
     export_plan(P, sz, slot_elem, lconn, patch_meta, pnode, col_ptr, sh_node, sh_ptr, sh_slot);
     if (patch_off) std::copy(L.patch_off.begin(), L.patch_off.end(), patch_off);
     return EBE_OK;
+}
+
+// ---------------------------------------------------------------- learned preconditioner
+
+struct ebe_mpnn {
+    int device = 0;
+    std::vector<void*> allocs;
+    MpnnDev md;
+    double* grad = nullptr;          // [kMpnnParams]
+    int64_t cap_inf = 0, cap_train = 0, cap_vec = 0;
+    double *z = nullptr, *w = nullptr, *aw = nullptr, *ae = nullptr, *gz = nullptr;
+    int32_t* err = nullptr;
+    int step = 0;
+    std::string msg;
+};
+
+extern "C++" {
+namespace {
+
+int mfail(ebe_mpnn* m, int status, const std::string& msg) {
+    if (m) m->msg = msg;
+    return status;
+}
+
+template <typename T>
+int malloc_net(ebe_mpnn* m, T** p, int64_t count, bool zero = false) {
+    void* v = nullptr;
+    const size_t bytes = size_t(std::max<int64_t>(count, 1)) * sizeof(T);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return mfail(m, EBE_OOM, "cudaMalloc failed"); }
+    m->allocs.push_back(v);
+    if (zero && cudaMemset(v, 0, bytes) != cudaSuccess) return mfail(m, EBE_CUDA_ERROR, "cudaMemset failed");
+    *p = static_cast<T*>(v);
+    return EBE_OK;
+}
+
+#define MTRY(call)                        \
+    do {                                  \
+        int s_ = (call);                  \
+        if (s_ != EBE_OK) return s_;      \
+    } while (0)
+
+// Mesh graph of the handle: every node's neighbours (nodes sharing an element),
+// ascending, from the partition's element lists; built once per handle.
+int ensure_mesh_graph(ebe_handle* h) {
+    if (h->g_ptr) return EBE_OK;
+    const HostPlan& P = h->plan;
+    const int64_t n = P.n_n;
+    const int nb = P.nb;
+    std::vector<int32_t> el(size_t(P.n_e) * nb);
+    int64_t e = 0;
+    for (int64_t p = 0; p < P.n_patches; ++p) {
+        const PatchMeta& m = P.meta[p];
+        for (int s = 0; s < m.n_el; ++s, ++e)
+            for (int i = 0; i < nb; ++i)
+                el[size_t(e) * nb + i] =
+                    P.pnode[m.node_off + P.lconn[size_t(i) * P.n_slots + size_t(p) * kPatch + s]] & kNodeMask;
+    }
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int32_t v : el) ++cnt[v + 1];
+    for (int64_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+    std::vector<int32_t> inc(el.size());
+    {
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (size_t k = 0; k < el.size(); ++k) inc[fill[el[k]]++] = int32_t(k / nb);
+    }
+    std::vector<int32_t> ptr(n + 1, 0), nbr;
+    std::vector<float> invdeg(n);
+    nbr.reserve(size_t(n) * 7);
+    std::vector<int32_t> tmp;
+    for (int64_t v = 0; v < n; ++v) {
+        tmp.clear();
+        for (int64_t k = cnt[v]; k < cnt[v + 1]; ++k)
+            for (int i = 0; i < nb; ++i) {
+                const int32_t u = el[size_t(inc[k]) * nb + i];
+                if (u != v) tmp.push_back(u);
+            }
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        nbr.insert(nbr.end(), tmp.begin(), tmp.end());
+        if (nbr.size() > size_t(INT32_MAX)) return fail(h, EBE_INVALID_ARG, "mesh graph exceeds 2^31 entries");
+        ptr[v + 1] = int32_t(nbr.size());
+        invdeg[v] = tmp.empty() ? 0.0f : 1.0f / float(tmp.size());
+    }
+    TRY(upload(h, &h->g_ptr, ptr.data(), int64_t(ptr.size())));
+    TRY(upload(h, &h->g_nbr, nbr.data(), int64_t(nbr.size())));
+    TRY(upload(h, &h->g_invdeg, invdeg.data(), int64_t(invdeg.size())));
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    return EBE_OK;
+}
+
+int net_buffers(ebe_mpnn* m, int64_t n, bool train) {
+    MpnnDev& d = m->md;
+    if (n > m->cap_inf) {
+        MTRY(malloc_net(m, &d.h[0], n * kMpnnHidden));
+        MTRY(malloc_net(m, &d.h[1], n * kMpnnHidden));
+        m->cap_inf = n;
+        m->cap_train = 0;   // training layers reuse h[0], h[1]
+    }
+    if (train && n > m->cap_train) {
+        for (int l = 2; l <= kMpnnLayers; ++l) MTRY(malloc_net(m, &d.h[l], n * kMpnnHidden));
+        if (n > m->cap_inf) return EBE_INVALID_ARG;
+        MTRY(malloc_net(m, &d.save_u, int64_t(kMpnnLayers) * n * 2 * kMpnnHidden));
+        MTRY(malloc_net(m, &d.save_v, int64_t(kMpnnLayers) * n * kMpnnHidden));
+        MTRY(malloc_net(m, &d.save_x, 2 * n));
+        MTRY(malloc_net(m, &d.gh, n * kMpnnHidden));
+        MTRY(malloc_net(m, &d.ghp, n * kMpnnHidden));
+        MTRY(malloc_net(m, &d.ga, n * kMpnnHidden));
+        m->cap_train = n;
+    }
+    if (n > m->cap_vec) {
+        MTRY(malloc_net(m, &m->z, n));
+        MTRY(malloc_net(m, &m->w, n));
+        MTRY(malloc_net(m, &m->aw, n));
+        MTRY(malloc_net(m, &m->ae, n));
+        MTRY(malloc_net(m, &m->gz, n));
+        m->cap_vec = n;
+    }
+    return EBE_OK;
+}
+
+// Bind the network to the handle's mesh for the next launches.
+int net_bind(ebe_mpnn* m, ebe_handle* h, bool train) {
+    if (!m || !h) return EBE_INVALID_ARG;
+    if (m->device != h->device) return fail(h, EBE_INVALID_ARG, "network and handle are on different devices");
+    TRY(check_ready(h, true));
+    TRY(ensure_mesh_graph(h));
+    const int s = net_buffers(m, h->plan.n_n, train);
+    if (s != EBE_OK) return fail(h, s, "network buffers: " + m->msg);
+    m->md.nbr_ptr = h->g_ptr;
+    m->md.nbr = h->g_nbr;
+    m->md.inv_deg = h->g_invdeg;
+    m->md.num_sms = h->pd.num_sms;
+    return EBE_OK;
+}
+
+int net_check_device(ebe_handle* h, ebe_mpnn* m) {
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, m->err, sizeof(e), cudaMemcpyDeviceToHost, h->st), "read device flag");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    if (e != 0) return fail(h, EBE_CUDA_ERROR, "a device-side wait timed out in the network (tensor-core result missing)");
+    return EBE_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+int64_t ebe_mpnn_n_params(void) { return kMpnnParams; }
+
+ebe_status ebe_mpnn_create(ebe_mpnn** out, int32_t device, const double* theta) {
+    if (!out) return EBE_INVALID_ARG;
+    *out = nullptr;
+    ebe_mpnn* m = new (std::nothrow) ebe_mpnn();
+    if (!m) return EBE_OOM;
+    m->device = device;
+    auto bail = [&](int s) {
+        g_create_error = m->msg;
+        ebe_mpnn_destroy(m);
+        return ebe_status(s);
+    };
+    if (cudaSetDevice(device) != cudaSuccess) { m->msg = "no such CUDA device"; return bail(EBE_INVALID_ARG); }
+    MpnnDev& d = m->md;
+    int s = EBE_OK;
+    if ((s = malloc_net(m, &d.theta, kMpnnParams)) || (s = malloc_net(m, &d.adam_m, kMpnnParams, true)) ||
+        (s = malloc_net(m, &d.adam_v, kMpnnParams, true)) || (s = malloc_net(m, &d.wl, kMpnnLayers * 2 * kMpnnHidden * kMpnnHidden, true)) ||
+        (s = malloc_net(m, &d.wT, kMpnnLayers * 2 * kMpnnHidden * kMpnnHidden)) || (s = malloc_net(m, &d.wsm, kMpnnSmall)) ||
+        (s = malloc_net(m, &m->grad, kMpnnParams, true)) || (s = malloc_net(m, &d.part, 256 * (2 * kMpnnHidden * kMpnnHidden + kMpnnHidden))) ||
+        (s = malloc_net(m, &d.ctr, 1, true)) || (s = malloc_net(m, &d.sc, 8, true)) || (s = malloc_net(m, &m->err, 1, true)))
+        return bail(s);
+    d.err = m->err;
+    s = int(ebe_mpnn_set_params(m, theta));
+    if (s != EBE_OK) return bail(s);
+    *out = m;
+    return EBE_OK;
+}
+
+void ebe_mpnn_destroy(ebe_mpnn* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+ebe_status ebe_mpnn_set_params(ebe_mpnn* m, const double* theta) {
+    if (!m) return EBE_INVALID_ARG;
+    std::vector<float> t(kMpnnParams, 0.0f);
+    if (theta) {
+        for (int k = 0; k < kMpnnParams; ++k) {
+            if (!std::isfinite(theta[k])) return ebe_status(mfail(m, EBE_INVALID_ARG, "parameters must be finite"));
+            t[k] = float(theta[k]);
+        }
+    } else {
+        // seeded default: uniform +-1/sqrt(fan_in) layers, zero decoder (the Jacobi preconditioner)
+        uint64_t st = 0x9E3779B97F4A7C15ull;
+        auto uni = [&]() {
+            st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+            return double(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        };
+        for (int k = 0; k < 2 * kMpnnHidden; ++k) t[k] = float(uni() / std::sqrt(2.0));
+        for (int l = 0; l < kMpnnLayers; ++l)
+            for (int k = 0; k < 2 * kMpnnHidden * kMpnnHidden; ++k)
+                t[kMpnnW0 + l * kMpnnLayerParams + k] = float(uni() / std::sqrt(2.0 * kMpnnHidden));
+    }
+    cudaSetDevice(m->device);
+    if (cudaMemcpy(m->md.theta, t.data(), sizeof(float) * kMpnnParams, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->md.adam_m, 0, sizeof(float) * kMpnnParams) != cudaSuccess ||
+        cudaMemset(m->md.adam_v, 0, sizeof(float) * kMpnnParams) != cudaSuccess)
+        return ebe_status(mfail(m, EBE_CUDA_ERROR, "upload of the parameters failed"));
+    m->step = 0;
+    if (launch_mpnn_pack(m->md, nullptr, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return ebe_status(mfail(m, EBE_CUDA_ERROR, "packing the parameters failed"));
+    return EBE_OK;
+}
+
+ebe_status ebe_mpnn_get_params(const ebe_mpnn* m, double* theta) {
+    if (!m || !theta) return EBE_INVALID_ARG;
+    std::vector<float> t(kMpnnParams);
+    cudaSetDevice(m->device);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(t.data(), m->md.theta, sizeof(float) * kMpnnParams, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EBE_CUDA_ERROR;
+    std::copy(t.begin(), t.end(), theta);
+    return EBE_OK;
+}
+
+ebe_status ebe_mpnn_apply(ebe_mpnn* m, ebe_handle* h, const double* r, double* z) {
+    if (!r || !z) return EBE_INVALID_ARG;
+    TRY(net_bind(m, h, false));
+    Scope scp(h);
+    int l = 0;
+    CK(launch_mpnn_forward(m->md, h->plan.n_n, r, h->dinv, z, false, h->st, &l), "network forward");
+    add_launches(h, l);
+    return ebe_status(net_check_device(h, m));
+}
+
+ebe_status ebe_mpnn_grad(ebe_mpnn* m, ebe_handle* h, const double* r, const double* gz, double* z_out, double* grad) {
+    if (!r || !gz || !grad) return EBE_INVALID_ARG;
+    TRY(net_bind(m, h, true));
+    Scope scp(h);
+    const int64_t n = h->plan.n_n;
+    int l = 0;
+    CK(launch_mpnn_forward(m->md, n, r, h->dinv, m->z, true, h->st, &l), "network forward");
+    CK(launch_mpnn_backward(m->md, n, gz, h->dinv, m->grad, h->st, &l), "network backward");
+    add_launches(h, l);
+    if (z_out) CK(cudaMemcpyAsync(z_out, m->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy z");
+    CK(cudaMemcpyAsync(grad, m->grad, sizeof(double) * kMpnnParams, cudaMemcpyDeviceToHost, h->st), "copy gradient");
+    return ebe_status(net_check_device(h, m));
+}
+
+ebe_status ebe_mpnn_train_step(ebe_mpnn* m, ebe_handle* h, const double* r, const double* e, double lr, double* loss) {
+    if (!r || !e || !(lr > 0.0) || !std::isfinite(lr)) return EBE_INVALID_ARG;
+    TRY(net_bind(m, h, true));
+    Scope scp(h);
+    const int64_t n = h->plan.n_n;
+    TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
+    int l = 0;
+    double* sc = m->md.sc;
+    CK(launch_mpnn_forward(m->md, n, r, h->dinv, m->z, true, h->st, &l), "network forward");
+    CK(launch_sub(n, e, m->z, m->w, h->st, &l), "e - z");
+    CK(launch_patch_pass(h->pd, 0, kApply, h->A64, m->w, nullptr, m->aw, h->halo64, h->part_patch, nullptr, h->sc, h->st,
+                         &l), "A (e - z)");
+    CK(launch_patch_pass(h->pd, 0, kApply, h->A64, e, nullptr, m->ae, h->halo64, h->part_patch, nullptr, h->sc, h->st, &l),
+       "A e");
+    CK(launch_dot2(n, m->w, m->aw, nullptr, m->md.part, m->md.ctr, sc + 2, h->st, &l), "w'Aw");
+    CK(launch_dot2(n, e, m->ae, nullptr, m->md.part, m->md.ctr, sc + 4, h->st, &l), "e'Ae");
+    CK(launch_scale(n, m->aw, sc + 4, -2.0, m->gz, h->st, &l), "dL/dz");
+    CK(launch_mpnn_backward(m->md, n, m->gz, h->dinv, m->grad, h->st, &l), "network backward");
+    m->step += 1;
+    CK(launch_mpnn_adam(m->md, m->grad, float(lr), m->step, h->st, &l), "Adam");
+    add_launches(h, l);
+    double v[6];
+    CK(cudaMemcpyAsync(v, sc, sizeof(v), cudaMemcpyDeviceToHost, h->st), "read loss");
+    TRY(net_check_device(h, m));
+    if (loss) *loss = v[4] > 0.0 ? v[2] / v[4] : 0.0;
+    return EBE_OK;
+}
+
+const char* ebe_mpnn_last_error(const ebe_mpnn* m) { return m ? m->msg.c_str() : g_create_error.c_str(); }
+
+namespace {
+
+// Flexible CG (one stored direction) with the network (or Jacobi) as the
+// preconditioner, FP64 vectors and FP64 element matrices.  On a breakdown or
+// when the residual stops decreasing, the solve falls back to Jacobi from the
+// current iterate.
+int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info,
+                 int32_t* fell_back) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = h->plan.n_n;
+    const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
+    TRY(dalloc(h, &h->x64w, n));
+    TRY(dalloc(h, &h->r64, n));
+    TRY(dalloc(h, &h->p64, n));
+    TRY(dalloc(h, &h->q64, n));
+    TRY(dalloc(h, &h->z64, n));
+    TRY(dalloc(h, &h->halo64, nh));
+    if (net) TRY(net_bind(net, h, false));
+    bool use_net = net != nullptr;
+    if (fell_back) *fell_back = 0;
+    int l = 0;
+    CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x0");
+    CK(launch_set_dirichlet(h->x64w, h->nd, h->g, h->n_d, h->st, &l), "x(nd) = g");
+    CK(launch_control(h->sc, 0.0, o.maxit, 1, h->st, &l), "control");
+    add_launches(h, l);
+    double rr = 0.0;
+    TRY(true_residual(h, rr));
+    info.true_residuals = 1;
+    const double r0 = std::sqrt(rr);
+    info.r0_norm = r0;
+    info.iterations = 0;
+    info.rel_residual = r0 > 0.0 ? 1.0 : 0.0;
+    int status = EBE_OK;
+    if (!std::isfinite(r0)) status = EBE_BREAKDOWN;
+    if (r0 > 0.0 && std::isfinite(r0)) {
+        const double target = o.rtol * r0;
+        l = 0;
+        CK(launch_control(h->sc, target * target, -1, 0, h->st, &l), "control");
+        add_launches(h, l);
+        int first = 1;
+        double best = 1.0, best_rr = rr;
+        int no_progress = 0, flat_chunks = 0;
+        auto fallback = [&]() -> int {
+            use_net = false;
+            if (fell_back) *fell_back = 1;
+            first = 1;
+            best_rr = HUGE_VAL;
+            flat_chunks = 0;
+            double t = 0.0;
+            TRY(true_residual(h, t));
+            info.true_residuals += 1;
+            int ll = 0;
+            CK(launch_control(h->sc, -1.0, -1, 0, h->st, &ll), "control");
+            add_launches(h, ll);
+            return EBE_OK;
+        };
+        for (;;) {
+            l = 0;
+            for (int it = 0; it < o.chunk; ++it) {
+                if (use_net) CK(launch_mpnn_forward(net->md, n, h->r64, h->dinv, h->z64, false, h->st, &l), "network");
+                else CK(launch_jacobi(n, h->r64, h->dinv, h->z64, &h->sc->done, h->st, &l), "Jacobi");
+                CK(launch_fcg_dots(n, h->z64, h->r64, h->p64, h->q64, first, h->part_vec, h->sc, h->st, &l), "FCG dots");
+                CK(launch_fcg_dir(n, h->z64, h->p64, first, h->sc, h->st, &l), "FCG direction");
+                CK(launch_patch_pass(h->pd, 0, kApplyDot, h->A64, h->p64, nullptr, h->q64, h->halo64, h->part_patch,
+                                     &h->sc->done, h->sc, h->st, &l), "apply");
+                CK(launch_update(0, n, h->x64w, h->p64, h->r64, h->q64, h->dinv, h->part_vec, h->sc, h->st, &l), "update");
+                first = 0;
+            }
+            add_launches(h, l);
+            const int64_t before = info.iterations;
+            TRY(sync_scalars(h));
+            if (use_net) TRY(net_check_device(h, net));
+            const Scalars sh = *h->sc_host;
+            info.iterations = sh.iter;
+            if (sh.reason == kRunning) {
+                if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
+                if (use_net) {
+                    // the learned step must keep reducing the residual
+                    if (!(sh.rr < 0.5 * best_rr)) {
+                        if (++flat_chunks >= 64) TRY(fallback());
+                    } else {
+                        best_rr = sh.rr;
+                        flat_chunks = 0;
+                    }
+                }
+                continue;
+            }
+            if (sh.reason == kBreakdown) {
+                if (use_net) { TRY(fallback()); continue; }
+                status = EBE_BREAKDOWN;
+                break;
+            }
+            TRY(true_residual(h, rr));
+            info.true_residuals += 1;
+            const double rel = std::sqrt(rr) / r0;
+            info.rel_residual = rel;
+            if (!std::isfinite(rel)) {
+                if (use_net) { TRY(fallback()); continue; }
+                status = EBE_BREAKDOWN;
+                break;
+            }
+            if (rel <= o.rtol) { status = EBE_OK; break; }
+            if (sh.reason == kMaxit) { status = EBE_MAXIT; break; }
+            if (rel < 0.9 * best) { best = rel; no_progress = 0; }
+            else if (++no_progress >= o.stall_updates) {
+                if (use_net) { TRY(fallback()); no_progress = 0; continue; }
+                status = EBE_STALL;
+                break;
+            }
+            // residual replacement: restart the flexible recurrence from the true residual
+            first = 1;
+            l = 0;
+            CK(launch_control(h->sc, -1.0, -1, 0, h->st, &l), "control");
+            add_launches(h, l);
+        }
+    }
+    CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    info.status = status;
+    info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+}  // namespace
+
+ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x, const ebe_solve_opts* opts, ebe_solve_info* info,
+                             int32_t* fell_back) {
+    TRY(check_ready(h, true));
+    if (!x) return ebe_status(fail(h, EBE_INVALID_ARG, "x is NULL"));
+    ebe_solve_opts o;
+    ebe_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || o.maxit < 1 || o.chunk < 1 || o.chunk > 4096 || o.stall_updates < 1)
+        return ebe_status(fail(h, EBE_INVALID_ARG, "bad solve options"));
+    ebe_solve_info local{};
+    Scope scp(h);
+    const int s = learned_impl(h, net, x, false, o, local, fell_back);
+    if (info) *info = local;
+    return ebe_status(s);
 }
 
 ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {

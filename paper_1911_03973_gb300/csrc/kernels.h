@@ -224,6 +224,68 @@ int batch_max_ctas_per_sm(const BatchDev& bd, bool mixed, int* smem_bytes);
 // iterates until every problem is done or iter_budget loops have run.
 cudaError_t launch_batch_solve(const BatchDev& bd, bool mixed, int ctas_per_sm, cudaStream_t st, int* launches);
 
+// ---- learned preconditioner (k_mpnn.cu) -----------------------------------
+constexpr int kMpnnHidden = 32;
+constexpr int kMpnnLayers = 4;
+constexpr int kMpnnLayerParams = 2 * kMpnnHidden * kMpnnHidden + kMpnnHidden;   // W_l [32][64], b_l [32]
+// parameter vector: W_in [32][2], b_in [32], per layer W_l, b_l, w_out [32], b_out
+constexpr int kMpnnW0 = 3 * kMpnnHidden;                                        // first layer's W_l
+constexpr int kMpnnThWout = kMpnnW0 + kMpnnLayers * kMpnnLayerParams;           // w_out
+constexpr int kMpnnParams = kMpnnThWout + kMpnnHidden + 1;                       // 8449
+// small-weight array of the forward pass (BF16-rounded values as FP32):
+// W_in, b_in, the layer biases, w_out, b_out
+constexpr int kMpnnWin = 0, kMpnnBin = 64, kMpnnBl = 96, kMpnnWout = kMpnnBl + kMpnnLayers * kMpnnHidden,
+              kMpnnBout = kMpnnWout + kMpnnHidden, kMpnnSmall = kMpnnBout + 1;
+
+// Network state and work buffers on the device (BF16 data as uint16_t).
+struct MpnnDev {
+    int num_sms = 1;
+    const int32_t* nbr_ptr = nullptr;   // mesh graph of the current handle (CSR, no self loops)
+    const int32_t* nbr = nullptr;
+    const float* inv_deg = nullptr;
+    float* theta = nullptr;             // [kMpnnParams] FP32 master parameters
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    uint16_t* wl = nullptr;             // [layers][32 * 64] BF16 layer weights, tensor-core layout
+    float* wT = nullptr;                // [layers][64][32] the same values transposed (backward)
+    float* wsm = nullptr;               // [kMpnnSmall]
+    uint16_t* h[kMpnnLayers + 1] = {};  // node features [n][32]; inference uses h[0], h[1] only
+    uint16_t* save_u = nullptr;         // training: [layers][n][64] layer inputs
+    float* save_v = nullptr;            // training: [layers][n][32] pre-activations
+    float* save_x = nullptr;            // training: [n][2] input features
+    float* gh = nullptr;                // backward work [n][32] x 3
+    float* ghp = nullptr;
+    float* ga = nullptr;
+    double* part = nullptr;             // block partials
+    uint32_t* ctr = nullptr;
+    double* sc = nullptr;               // sc[0] = rms(r), sc[1] = rms(dinv r); sc[2..3] dot results
+    int32_t* err = nullptr;
+};
+
+// z = B(r) on n nodes (save: keep what backward needs).
+cudaError_t launch_mpnn_forward(const MpnnDev& m, int64_t n, const double* r, const double* dinv, double* z, bool save,
+                                cudaStream_t st, int* launches);
+// grad [kMpnnParams] = dL/dtheta for gz = dL/dz, after a forward with save.
+cudaError_t launch_mpnn_backward(const MpnnDev& m, int64_t n, const double* gz, const double* dinv, double* grad,
+                                 cudaStream_t st, int* launches);
+// Refresh the BF16 / FP32 copies the forward pass reads from theta.
+cudaError_t launch_mpnn_pack(const MpnnDev& m, cudaStream_t st, int* launches);
+// One Adam step on theta (step >= 1), then pack.
+cudaError_t launch_mpnn_adam(const MpnnDev& m, const double* grad, float lr, int step, cudaStream_t st, int* launches);
+// w = e - z;  out[0] = a.b, out[1] = a.c (c nullable);  out = factor * a / num[0].
+cudaError_t launch_sub(int64_t n, const double* e, const double* z, double* w, cudaStream_t st, int* launches);
+cudaError_t launch_dot2(int64_t n, const double* a, const double* b, const double* c, double* part, uint32_t* ctr,
+                        double* out, cudaStream_t st, int* launches);
+cudaError_t launch_scale(int64_t n, const double* a, const double* num, double factor, double* out, cudaStream_t st,
+                         int* launches);
+// Flexible CG: dots z.q_prev, z.r, p_prev.r -> sc->beta, sc->rho = p.r; p = z + beta p; Jacobi z = dinv r.
+cudaError_t launch_fcg_dots(int64_t n, const double* z, const double* r, const double* p, const double* q, int first,
+                            double* part, Scalars* sc, cudaStream_t st, int* launches);
+cudaError_t launch_fcg_dir(int64_t n, const double* z, double* p, int first, const Scalars* sc, cudaStream_t st,
+                           int* launches);
+cudaError_t launch_jacobi(int64_t n, const double* r, const double* dinv, double* z, const int32_t* stop, cudaStream_t st,
+                          int* launches);
+
 // ---- comparison scatters (k_alt.cu) ---------------------------------------
 cudaError_t launch_build_gconn(const PlanDev& pd, int32_t* gconn, cudaStream_t st, int* launches);
 cudaError_t launch_permute_slots(int nb, int64_t n_slots, int64_t n, const int32_t* order,

@@ -1,0 +1,185 @@
+"""The learned preconditioner on the GPU (through the C ABI), judged by the oracle.
+
+Forward pass and parameter gradients against oracle/mpnn.py (FP64, the same
+BF16 roundings); the training step's loss against the oracle's energy loss;
+flexible CG with Jacobi against the oracle's flexible CG; every solve judged
+by the oracle's FP64 true residual; the Jacobi fallback; and the gain of the
+trained network over the same solver without it on the training problem size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mpnn
+from paper_1911_03973_gb300 import meshgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ebe():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03973_gb300 as mod
+    return mod
+
+
+def _setup(ebe, prob):
+    h = ebe.ebe_create(prob["coords"], prob["elems"])
+    ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+    ebe.ebe_assemble(h, ebe.EBE_STORE_FP64)
+    orc = oracle.Problem(prob)
+    # the network's input dinv is the handle's own (equal to the oracle's to
+    # rounding, checked in test_gpu_parity.py)
+    d = torch.empty(orc.n_n, dtype=torch.float64, device=DEV)
+    ebe.ebe_jacobi_diag(h, d)
+    dinv = 1.0 / d.cpu().numpy()
+    dinv[prob["dirichlet"]] = 0.0
+    return h, orc, dinv, mpnn.mesh_graph(orc.n_n, prob["elems"])
+
+
+@pytest.fixture(scope="module")
+def small(ebe):
+    prob = meshgen.config_square_jitter(65, nu=1.0, seed=2)      # 4225 nodes: 33 tiles of 128, ragged
+    h, orc, dinv, graph = _setup(ebe, prob)
+    yield prob, h, orc, dinv, graph
+    ebe.ebe_destroy(h)
+
+
+def _theta(seed, scale=0.3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = rng.normal(0, scale, mpnn.n_params())
+    return t.astype(np.float32).astype(np.float64)     # the GPU keeps FP32 masters
+
+
+def _r(orc, seed):
+    return orc.residual(orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, seed)))
+
+
+def test_zero_decoder_is_the_jacobi_step(ebe, small):
+    prob, h, orc, dinv, graph = small
+    net = ebe.ebe_mpnn_create(0)                    # library initial weights: zero decoder
+    r = _r(orc, 1)
+    rd = torch.tensor(r, dtype=torch.float64, device=DEV)
+    zd = torch.empty_like(rd)
+    ebe.ebe_mpnn_apply(net, h, rd, zd)
+    np.testing.assert_array_equal(zd.cpu().numpy(), dinv * r)
+
+
+def test_forward_matches_oracle(ebe, small):
+    prob, h, orc, dinv, graph = small
+    theta = _theta(3)
+    net = ebe.ebe_mpnn_create(0, theta)
+    np.testing.assert_array_equal(ebe.ebe_mpnn_get_params(net), theta)
+    r = _r(orc, 2)
+    rd = torch.tensor(r, dtype=torch.float64, device=DEV)
+    zd = torch.empty_like(rd)
+    ebe.ebe_mpnn_apply(net, h, rd, zd)
+    z = zd.cpu().numpy()
+    zo, _ = mpnn.forward(theta, r, dinv, graph, exact=False)
+    zj = dinv * r
+    corr_err = np.linalg.norm((z - zj) - (zo - zj)) / np.linalg.norm(zo - zj)
+    assert corr_err <= 2e-3, corr_err
+    assert np.all(z[prob["dirichlet"]] == 0.0)
+
+
+def test_gradient_matches_oracle(ebe, small):
+    """Per parameter block, the GPU gradient (FP32 sums) against the oracle's
+    (FP64) for the same BF16-rounded forward, at a training sample: r the
+    residual of x0 = 0, e = x* - x0 (x* from the oracle's PCG) and dL/dz of
+    the energy loss.  The two forwards round a few of their ~10^6 BF16 values
+    differently (FP32 vs FP64 sums before the rounding), so agreement is
+    judged per block by the relative difference and the cosine."""
+    prob, h, orc, dinv, graph = small
+    theta = _theta(4, scale=0.1)
+    net = ebe.ebe_mpnn_create(0, theta)
+    xs, _ = orc.pcg(rtol=1e-12)
+    x0 = orc.with_dirichlet(np.zeros(orc.n_n))
+    r = orc.residual(x0)
+    e = xs - x0
+    zo, cache = mpnn.forward(theta, r, dinv, graph, exact=False)
+    _, gz = mpnn.energy_loss(orc.apply, zo, e)
+    g = ebe.ebe_mpnn_grad(net, h, torch.tensor(r, dtype=torch.float64, device=DEV),
+                          torch.tensor(gz, dtype=torch.float64, device=DEV))
+    go = mpnn.backward(theta, cache, gz)
+    sizes = [64, 32] + [2048, 32] * 4 + [32, 1]
+    names = ["W_in", "b_in"] + [f"{x}{l}" for l in range(4) for x in ("W", "b")] + ["w_out", "b_out"]
+    o, stats = 0, {}
+    for name, size in zip(names, sizes):
+        a, b = g[o:o + size], go[o:o + size]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
+        stats[name] = (round(float(rel), 5), round(cos, 6))
+        o += size
+    text = "; ".join(f"{k} {v[0]} {v[1]}" for k, v in stats.items())
+    assert all(rel <= 1e-2 and cos >= 0.9999 for rel, cos in stats.values()), text
+
+
+def test_training_step_loss_matches_oracle_and_decreases(ebe, small):
+    prob, h, orc, dinv, graph = small
+    net = ebe.ebe_mpnn_create(0)
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 6))
+    xs = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 7) * 0.1)
+    r = orc.residual(x)
+    e = xs - x
+    e[prob["dirichlet"]] = 0.0
+    rd = torch.tensor(r, dtype=torch.float64, device=DEV)
+    ed = torch.tensor(e, dtype=torch.float64, device=DEV)
+    loss0 = ebe.ebe_mpnn_train_step(net, h, rd, ed, 1e-3)
+    ref, _ = mpnn.energy_loss(orc.apply, dinv * r, e)        # initial network = Jacobi step
+    assert abs(loss0 - ref) <= 1e-10 * max(1.0, ref)
+    losses = [ebe.ebe_mpnn_train_step(net, h, rd, ed, 1e-3) for _ in range(30)]
+    assert losses[-1] < 0.9 * loss0, (loss0, losses[-5:])
+
+
+def test_fcg_jacobi_matches_oracle(ebe, small):
+    prob, h, orc, dinv, graph = small
+    x = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve_learned(h, None, x, rtol=1e-8)
+    assert info["status"] == "EBE_OK" and not info["fell_back"]
+    assert orc.rel_residual(x.cpu().numpy()) <= 1e-8
+    x0 = orc.with_dirichlet(np.zeros(orc.n_n))
+    _, it = mpnn.fcg(orc.apply, orc.residual(x0), x0, lambda v: dinv * v, rtol=1e-8)
+    assert abs(info["iterations"] - it) <= max(2, 0.02 * it), (info["iterations"], it)
+
+
+def test_fallback_to_jacobi(ebe, small):
+    prob, h, orc, dinv, graph = small
+    bad = np.full(mpnn.n_params(), 50.0)                   # wildly wrong corrections
+    net = ebe.ebe_mpnn_create(0, bad)
+    x = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve_learned(h, net, x, rtol=1e-8, stall_updates=2)
+    assert info["status"] == "EBE_OK" and info["fell_back"], info
+    assert orc.rel_residual(x.cpu().numpy()) <= 1e-8
+
+
+def test_trained_network_beats_jacobi_on_the_training_size(ebe):
+    """Config 5 recipe at reduced scale: train on 129^2 jittered squares
+    (random Fourier f, nu ~ U[0,10]), test on an unseen problem of that size."""
+    from paper_1911_03973_gb300 import learned
+    n = 129
+    handles, samples = [], []
+    for seed in range(4):
+        prob = learned.training_problem(n, 100 + seed)
+        h = ebe.ebe_create(prob["coords"], prob["elems"])
+        ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+        ebe.ebe_assemble(h, ebe.EBE_STORE_FP64)
+        handles.append(h)
+        for r, e in learned.harvest(ebe, torch, h, prob["coords"].shape[0], 12, DEV):
+            samples.append((h, r, e))
+    net = ebe.ebe_mpnn_create(0)
+    losses = learned.train(ebe, net, samples, steps=600, lr=3e-3, seed=1)
+    assert np.mean(losses[-48:]) < np.mean(losses[:48])
+    prob = learned.training_problem(n, 999)
+    h, orc, dinv, graph = _setup(ebe, prob)
+    xj = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    ij = ebe.ebe_solve_learned(h, None, xj, rtol=1e-8)
+    xl = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    il = ebe.ebe_solve_learned(h, net, xl, rtol=1e-8)
+    assert il["status"] == "EBE_OK" and ij["status"] == "EBE_OK"
+    assert orc.rel_residual(xl.cpu().numpy()) <= 1e-8
+    assert not il["fell_back"]
+    assert il["iterations"] < ij["iterations"], (il, ij)

@@ -26,6 +26,10 @@ in [17, 513] nodes, seed 4) solved by the batched persistent solver in mixed
 precision with an autotuned launch shape, against the same problems solved
 one by one with ebe_solve (plain FP64 and mixed) and the batched FP64 solve.
 
+"learned" (with --learned): the message-passing preconditioner trained on
+257^2 squares and deployed in flexible CG on 1025^2 and 2049^2, against
+flexible CG with Jacobi and Jacobi-PCG (plain FP64 and mixed).
+
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
 sample of the same workload.
 """
@@ -63,7 +67,9 @@ def parse():
     ap.add_argument("--variants", action="store_true", help="also time the comparison scatters")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload (256 independent squares)")
     ap.add_argument("--batch-problems", type=int, default=256)
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "batch"], default=None,
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned preconditioner (257^2) and deploy it (1025^2, 2049^2)")
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -288,6 +294,96 @@ def run_batch(args, dev, stream, profile=False):
     }
 
 
+# ----------------------------------------------------------------------------- learned preconditioner
+def run_learned(args, dev, stream, profile=False):
+    """Train the message-passing preconditioner on 257^2 jittered squares
+    (random Fourier f, nu ~ U[0, 10]; 4 problems x 12 residual/error pairs
+    from Jacobi-PCG, 1500 Adam steps), then solve unseen 1025^2 and 2049^2
+    problems of the same kind with flexible CG + network, flexible CG +
+    Jacobi, plain FP64 Jacobi-PCG and mixed-precision Jacobi-PCG."""
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    from paper_1911_03973_gb300 import learned
+
+    def setup(n, seed):
+        p = learned.training_problem(n, seed)
+        h = ebe.ebe_create(p["coords"], p["elems"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem(h, p["nu"], p["f"], p["dirichlet"], p["g"], p["neumann"])
+        ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        return p, h
+
+    with torch.cuda.stream(stream):
+        if profile:
+            # three network applications on 1025^2 with seeded non-zero weights
+            rng = np.random.Generator(np.random.PCG64(4))
+            net = ebe.ebe_mpnn_create(dev.index, rng.normal(0, 0.1, ebe.ebe_mpnn_n_params()))
+            p, h = setup(1025, 999)
+            r = torch.rand(p["coords"].shape[0], dtype=torch.float64, device=dev)
+            z = torch.empty_like(r)
+            for _ in range(3):
+                ebe.ebe_mpnn_apply(net, h, r, z)
+            torch.cuda.synchronize()
+            return None
+        t0 = time.perf_counter()
+        samples, keep = [], []
+        for seed in range(4):
+            p, h = setup(257, 100 + seed)
+            keep.append(h)
+            for r, e in learned.harvest(ebe, torch, h, p["coords"].shape[0], 12, dev):
+                samples.append((h, r, e))
+        t_harvest = time.perf_counter() - t0
+        net = ebe.ebe_mpnn_create(dev.index)
+        t0 = time.perf_counter()
+        losses = learned.train(ebe, net, samples, steps=1500, lr=3e-3, seed=1)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        out = {"train": {"problems": "4 x 257^2 jittered, random Fourier f, nu ~ U[0,10]", "samples": len(samples),
+                         "steps": 1500, "harvest_s": round(t_harvest, 1), "train_s": round(t_train, 2),
+                         "loss_first64": round(float(np.mean(losses[:64])), 4),
+                         "loss_last64": round(float(np.mean(losses[-64:])), 4)}}
+        for n in (1025, 2049):
+            p, h = setup(n, 999)
+            nn = p["coords"].shape[0]
+
+            def timed(fn):
+                x = torch.zeros(nn, dtype=torch.float64, device=dev)
+                torch.cuda.synchronize()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                info = fn(x)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                return info, ev0.elapsed_time(ev1)
+
+            ij, tj = timed(lambda x: ebe.ebe_solve_learned(h, None, x, rtol=args.rtol))
+            il, tl = timed(lambda x: ebe.ebe_solve_learned(h, net, x, rtol=args.rtol))
+            ip, tp = timed(lambda x: ebe.ebe_solve(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_FP64))
+            im, tm = timed(lambda x: ebe.ebe_solve(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED))
+            r = torch.rand(nn, dtype=torch.float64, device=dev)
+            z = torch.empty_like(r)
+            ebe.ebe_mpnn_apply(net, h, r, z)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(10):
+                ebe.ebe_mpnn_apply(net, h, r, z)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out[f"square{n}"] = {
+                "learned_fcg": {"ms": round(tl, 1), "iterations": il["iterations"], "fell_back": il["fell_back"],
+                                "status": il["status"]},
+                "jacobi_fcg": {"ms": round(tj, 1), "iterations": ij["iterations"]},
+                "plain_fp64_pcg": {"ms": round(tp, 1), "iterations": ip["iterations"]},
+                "mixed_pcg": {"ms": round(tm, 1), "iterations": im["iterations"]},
+                "network_apply_ms": round(ev0.elapsed_time(ev1) / 10, 3)}
+            ebe.ebe_destroy(h)
+        for h in keep:
+            ebe.ebe_destroy(h)
+        ebe.ebe_mpnn_destroy(net)
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -311,6 +407,9 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     if args.profile_kernel == "batch":
         run_batch(args, dev, stream, profile=True)
+        return None
+    if args.profile_kernel == "mpnn":
+        run_learned(args, dev, stream, profile=True)
         return None
     prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
     n_n, dim = prob["coords"].shape
@@ -459,6 +558,7 @@ def run_ours(args):
     batched = None
     if not args.no_batch:
         batched = run_batch(args, dev, stream)
+    learned_res = run_learned(args, dev, stream) if args.learned else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -505,6 +605,8 @@ def run_ours(args):
     }
     if batched:
         line["batched"] = batched
+    if learned_res:
+        line["learned"] = learned_res
     if variants:
         line["residual_variants_fp64"] = variants
     print(json.dumps(line), flush=True)

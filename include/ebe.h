@@ -422,9 +422,9 @@ ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev
  * alpha = p.r / p.q) with z = B(r) from net, or the Jacobi step with net NULL,
  * FP64 vectors and element matrices, stopping on the FP64 true relative
  * residual as ebe_solve.  With a network the solve falls back to Jacobi from
- * the current iterate on a breakdown, when the residual stops decreasing
- * (64 chunks without halving) or when the true residual stalls
- * (stall_updates checks); *fell_back (may be NULL) reports it.  opts:
+ * the current iterate on a breakdown, when the residual norm does not halve
+ * within 16 chunks, or when the true residual stalls (stall_updates checks);
+ * *fell_back (may be NULL) reports it.  opts:
  * rtol, maxit, chunk (iterations between host checks), stall_updates.
  * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
 ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x_dev, const ebe_solve_opts* opts,

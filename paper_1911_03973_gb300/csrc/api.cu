@@ -1740,9 +1740,11 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             if (sh.reason == kRunning) {
                 if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
                 if (use_net) {
-                    // the learned step must keep reducing the residual
-                    if (!(sh.rr < 0.5 * best_rr)) {
-                        if (++flat_chunks >= 64) TRY(fallback());
+                    // the learned step must keep reducing the residual: at least
+                    // a halving every 16 chunks (Jacobi-CG halves it about every
+                    // 0.1 sqrt(n_n) iterations on the 2D model problems)
+                    if (!(sh.rr < 0.25 * best_rr)) {
+                        if (++flat_chunks >= 16) TRY(fallback());
                     } else {
                         best_rr = sh.rr;
                         flat_chunks = 0;

@@ -91,15 +91,30 @@ __device__ __forceinline__ void decide(Scalars* sc, double rz, double rr) {
 }
 
 // ------------------------------------------------------------------ FP64
-// The node loops visit this thread's nodes in grid-stride order, four at a
-// time: the loads of four nodes are issued before any of them is used, so
-// that each thread keeps several memory requests in flight.  All four kernels
-// of a CG iteration use programmatic dependent launch: pdl_trigger lets the
-// next kernel start launching, pdl_wait orders the reads after the previous
-// kernel.
+// The update and direction kernels contain pdl_trigger / pdl_wait
+// (programmatic dependent launch; no-ops unless launched with it).
+
+// Four consecutive nodes per vector access (16-byte loads and stores: float4,
+// or two double2); every array is a library buffer (cudaMalloc, 256-byte
+// aligned), grid-stride over the groups (the direction kernels take two
+// groups per step); the n mod 4 tail nodes go one per thread.  Per-thread
+// sums run in node order.
+struct D4 {
+    double v[4];
+};
+__device__ __forceinline__ D4 ld4(const double* p, int64_t g) {
+    const double2 a = reinterpret_cast<const double2*>(p)[2 * g], b = reinterpret_cast<const double2*>(p)[2 * g + 1];
+    return D4{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(double* p, int64_t g, const D4& d) {
+    reinterpret_cast<double2*>(p)[2 * g] = make_double2(d.v[0], d.v[1]);
+    reinterpret_cast<double2*>(p)[2 * g + 1] = make_double2(d.v[2], d.v[3]);
+}
+__device__ __forceinline__ float4 ldf4(const float* p, int64_t g) { return reinterpret_cast<const float4*>(p)[g]; }
+__device__ __forceinline__ float at(const float4& f, int u) { return u == 0 ? f.x : u == 1 ? f.y : u == 2 ? f.z : f.w; }
 
 // x += alpha p;  r -= alpha q;  z = dinv r;  sums r.z, r.r (all FP64).
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
            const double* __restrict__ q, const double* __restrict__ dinv, double* __restrict__ part,
            Scalars* __restrict__ sc) {
@@ -109,26 +124,22 @@ k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, doub
     if (sc->done) return;
     const double al = sc->alpha;
     double rz = 0.0, rr = 0.0;
-    const int64_t st = int64_t(gridDim.x) * NT;
-    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
-    for (; i + 3 * st < n; i += 4 * st) {
-        double pv[4], qv[4], xv[4], rv[4], dv[4];
+    const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
+    for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += st) {
+        const D4 pv = ld4(p, g), qv = ld4(q, g), xv = ld4(x, g), rv = ld4(r, g), dv = ld4(dinv, g);
+        D4 xo, ro;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            pv[u] = p[j]; qv[u] = q[j]; xv[u] = x[j]; rv[u] = r[j]; dv[u] = dinv[j];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            x[j] = fmadd(al, pv[u], xv[u]);
-            const double ri = fmadd(-al, qv[u], rv[u]);
-            r[j] = ri;
-            rz = fmadd(ri, dv[u] * ri, rz);
+            xo.v[u] = fmadd(al, pv.v[u], xv.v[u]);
+            const double ri = fmadd(-al, qv.v[u], rv.v[u]);
+            ro.v[u] = ri;
+            rz = fmadd(ri, dv.v[u] * ri, rz);
             rr = fmadd(ri, ri, rr);
         }
+        st4(x, g, xo);
+        st4(r, g, ro);
     }
-    for (; i < n; i += st) {
+    for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
         x[i] = fmadd(al, p[i], x[i]);
         const double ri = fmadd(-al, q[i], r[i]);
         r[i] = ri;
@@ -139,29 +150,37 @@ k_update64(int64_t n, double* __restrict__ x, const double* __restrict__ p, doub
 }
 
 // p = dinv r + beta p  (init: p = dinv r), FP64.
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_direction64(int64_t n, double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ dinv,
               int init, const Scalars* __restrict__ sc) {
     pdl_trigger();
     pdl_wait();
     if (sc->done) return;
     const double be = init ? 0.0 : sc->beta;
-    const int64_t st = int64_t(gridDim.x) * NT;
-    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
-    for (; i + 3 * st < n; i += 4 * st) {
-        double rv[4], dv[4], pv[4];
+    const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
+    for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += 2 * st) {
+        const bool two = g + st < n4;
+        D4 rv[2], dv[2], pv[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            rv[u] = r[j]; dv[u] = dinv[j]; pv[u] = init ? 0.0 : p[j];
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            const int64_t k = g + h * st;
+            rv[h] = ld4(r, k); dv[h] = ld4(dinv, k);
+            if (!init) pv[h] = ld4(p, k);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const double zi = dv[u] * rv[u];
-            p[i + u * st] = init ? zi : fmadd(be, pv[u], zi);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            D4 po;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double zi = dv[h].v[u] * rv[h].v[u];
+                po.v[u] = init ? zi : fmadd(be, pv[h].v[u], zi);
+            }
+            st4(p, g + h * st, po);
         }
     }
-    for (; i < n; i += st) {
+    for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
         const double zi = dinv[i] * r[i];
         p[i] = init ? zi : fmadd(be, p[i], zi);
     }
@@ -170,7 +189,7 @@ k_direction64(int64_t n, double* __restrict__ p, const double* __restrict__ r, c
 // ------------------------------------------------------------------ mixed
 // x += alpha p and r -= alpha q in FP64 (p, q FP32); z = dinv32 * (float) r;
 // sums r.z, r.r per thread in compensated FP32.
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, double* __restrict__ r,
                const float* __restrict__ q, const float* __restrict__ dinv, double* __restrict__ part,
                Scalars* __restrict__ sc) {
@@ -180,28 +199,24 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
     if (sc->done) return;
     const double al = sc->alpha;
     CompSum rz, rr;
-    const int64_t st = int64_t(gridDim.x) * NT;
-    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
-    for (; i + 3 * st < n; i += 4 * st) {
-        float pv[4], qv[4], dv[4];
-        double xv[4], rv[4];
+    const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
+    for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += st) {
+        const float4 pv = ldf4(p, g), qv = ldf4(q, g), dv = ldf4(dinv, g);
+        const D4 xv = ld4(x, g), rv = ld4(r, g);
+        D4 xo, ro;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            pv[u] = p[j]; qv[u] = q[j]; dv[u] = dinv[j]; xv[u] = x[j]; rv[u] = r[j];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            x[j] = fmadd(al, f2d(pv[u]), xv[u]);
-            const double ri = fmadd(-al, f2d(qv[u]), rv[u]);
-            r[j] = ri;
+            xo.v[u] = fmadd(al, f2d(at(pv, u)), xv.v[u]);
+            const double ri = fmadd(-al, f2d(at(qv, u)), rv.v[u]);
+            ro.v[u] = ri;
             const float rf = d2f(ri);
-            rz.add(rf * (dv[u] * rf));
+            rz.add(rf * (at(dv, u) * rf));
             rr.add(rf * rf);
         }
+        st4(x, g, xo);
+        st4(r, g, ro);
     }
-    for (; i < n; i += st) {
+    for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
         x[i] = fmadd(al, f2d(p[i]), x[i]);
         const double ri = fmadd(-al, f2d(q[i]), r[i]);
         r[i] = ri;
@@ -214,30 +229,38 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
 }
 
 // p = dinv32 * (float) r + beta p  (init: p = dinv32 * (float) r), FP32.
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r, const float* __restrict__ dinv,
                   int init, const Scalars* __restrict__ sc) {
     pdl_trigger();
     pdl_wait();
     if (sc->done) return;
     const float be = init ? 0.0f : float(sc->beta);
-    const int64_t st = int64_t(gridDim.x) * NT;
-    int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x;
-    for (; i + 3 * st < n; i += 4 * st) {
-        double rv[4];
-        float dv[4], pv[4];
+    const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
+    for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += 2 * st) {
+        const bool two = g + st < n4;
+        D4 rv[2];
+        float4 dv[2], pv[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t j = i + u * st;
-            rv[u] = r[j]; dv[u] = dinv[j]; pv[u] = init ? 0.0f : p[j];
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            const int64_t k = g + h * st;
+            rv[h] = ld4(r, k); dv[h] = ldf4(dinv, k);
+            pv[h] = init ? make_float4(0.f, 0.f, 0.f, 0.f) : ldf4(p, k);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float zi = dv[u] * d2f(rv[u]);
-            p[i + u * st] = init ? zi : __fmaf_rn(be, pv[u], zi);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float zi = at(dv[h], u) * d2f(rv[h].v[u]);
+                o[u] = init ? zi : __fmaf_rn(be, at(pv[h], u), zi);
+            }
+            reinterpret_cast<float4*>(p)[g + h * st] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
-    for (; i < n; i += st) {
+    for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
         const float zi = dinv[i] * d2f(r[i]);
         p[i] = init ? zi : __fmaf_rn(be, p[i], zi);
     }

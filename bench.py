@@ -176,6 +176,20 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_over_ranks(dist, device, seconds_or_ms, nbytes):
+    """Whole-job figures of N replicas (one rank per GPU, each running the full
+    workload): the slowest rank's time and the bytes of all ranks.  dist is
+    torch.distributed (any backend) or None for a single process."""
+    if dist is None:
+        return seconds_or_ms, nbytes
+    import torch
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([float(nbytes)], dtype=torch.float64, device=device)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(b.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -467,13 +481,7 @@ def run_ours(args):
         ms_total = e0.elapsed_time(e1)
         launches = ebe.ebe_get_stats(h)["kernel_launches"] - l0
         bytes_total = sum(step_bytes(m, i, True) for i in infos)
-        if dist:
-            t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_total = float(t.item())
-            bt = torch.tensor([bytes_total], dtype=torch.float64, device=dev)
-            dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-            bytes_total = float(bt.item())
+        ms_total, bytes_total = reduce_over_ranks(dist, dev, ms_total, bytes_total)
         ms_step = ms_total / args.steps
         value = bytes_total / (ms_total / 1e3) / 1e9
 
@@ -542,14 +550,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             ebytes += step_bytes(m, info, True)
-        e2e_s = sum(times)
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-            bt = torch.tensor([float(ebytes)], dtype=torch.float64, device=dev)
-            dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-            ebytes = float(bt.item())
+        e2e_s, ebytes = reduce_over_ranks(dist, dev, sum(times), float(ebytes))
         e2e = {"value": round(ebytes / e2e_s / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_s / args.e2e_steps, 2),
                "includes": "ebe_create (host partition build) + ebe_set_problem + ebe_assemble + "

@@ -173,11 +173,14 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p, bool have, int next_p
     if (!have && tid == 0) issue_patch_copies<T, NB>(bd, smem, p);
     for (int k = tid; k <= m.n_col; k += NT) co[k] = __ldg(pd.col_ptr + m.col_off + k);
     const int32_t* pn = pd.pnode + m.node_off;
-    for (int l = tid; l < m.n_nodes; l += NT) {
-        const int32_t gr = __ldg(pn + l);
-        Gs[l] = gr;
-        xs[l] = ld_l2(pv + (gr & kNodeMask));
-        acc[l] = T(0);
+    // two nodes per thread per round: both table loads, then both value loads, in flight
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        const int la = l0 + tid, lb = l0 + NT + tid;
+        const int32_t ga = la < m.n_nodes ? __ldg(pn + la) : 0, gb = lb < m.n_nodes ? __ldg(pn + lb) : 0;
+        const T xa = la < m.n_nodes ? ld_l2(pv + (ga & kNodeMask)) : T(0);
+        const T xb = lb < m.n_nodes ? ld_l2(pv + (gb & kNodeMask)) : T(0);
+        if (la < m.n_nodes) { Gs[la] = ga; xs[la] = xa; acc[la] = T(0); }
+        if (lb < m.n_nodes) { Gs[lb] = gb; xs[lb] = xb; acc[lb] = T(0); }
     }
     // *flag (the CTA's "broken" word) stays 1 from here on if the copies are lost:
     // this CTA does no more patch work and the next grid barrier ends the launch
@@ -274,13 +277,15 @@ __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
     __syncthreads();
     for (int k = tid; k <= m.n_col; k += NT) co[k] = __ldg(pd.col_ptr + m.col_off + k);
     const int32_t* pn = pd.pnode + m.node_off;
-    for (int l = tid; l < m.n_nodes; l += NT) {
-        const int32_t gr = __ldg(pn + l);
-        const int g = gr & kNodeMask;
-        Gs[l] = gr;
-        xs[l] = ld_l2(bd.x + g);
-        bs[l] = l < m.n_owned ? __ldg(bd.b + g) : 0.0;
-        acc[l] = 0.0;
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        const int la = l0 + tid, lb = l0 + NT + tid;
+        const int32_t ga = la < m.n_nodes ? __ldg(pn + la) : 0, gb = lb < m.n_nodes ? __ldg(pn + lb) : 0;
+        const double xa = la < m.n_nodes ? ld_l2(bd.x + (ga & kNodeMask)) : 0.0;
+        const double xb = lb < m.n_nodes ? ld_l2(bd.x + (gb & kNodeMask)) : 0.0;
+        const double ba = la < m.n_owned ? __ldg(bd.b + (ga & kNodeMask)) : 0.0;
+        const double bb = lb < m.n_owned ? __ldg(bd.b + (gb & kNodeMask)) : 0.0;
+        if (la < m.n_nodes) { Gs[la] = ga; xs[la] = xa; bs[la] = ba; acc[la] = 0.0; }
+        if (lb < m.n_nodes) { Gs[lb] = gb; xs[lb] = xb; bs[lb] = bb; acc[lb] = 0.0; }
     }
     __syncthreads();
     for (int cc = 0; cc < m.n_col; ++cc) {

@@ -322,6 +322,143 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
     }
 }
 
+// FP64 variant: the element matrices are read straight from global memory
+// (coalesced slot-major runs) inside the colour rounds, products folded into
+// the node sums.  GB300 runs FP64 at 1/64 of the FP32 rate, so this pass is
+// bound by FP64 issue rather than by bytes; without the 72 KB (triangles) or
+// 128 KB (tetrahedra) matrix tile in shared memory, up to eight CTAs share an
+// SM and hide the latency of the dependent FMA chains.
+struct Patch64Smem {
+    uint32_t red, co, G, xs, bs, acc, total;
+};
+__host__ __device__ constexpr Patch64Smem patch64_layout(int max_nodes) {
+    Patch64Smem s{};
+    const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
+    s.red = 0;
+    s.co = 32 * 8;
+    s.G = (s.co + (kMaxColours + 1) * 4 + 15) / 16 * 16;
+    s.xs = (s.G + gcap * 4 + 15) / 16 * 16;
+    s.bs = s.xs + gcap * 8;
+    s.acc = s.bs + gcap * 8;
+    s.total = (s.acc + gcap * 8 + 127) / 128 * 128;
+    return s;
+}
+
+template <int NB, int MODE>
+__global__ void __launch_bounds__(kPatchThreads, 4)
+k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restrict__ x, const double* __restrict__ b,
+           double* __restrict__ out, double* __restrict__ halo, double* __restrict__ part,
+           const int32_t* __restrict__ stop) {
+    constexpr int NT = kPatchThreads;
+    constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Patch64Smem L = patch64_layout(pd.max_nodes);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    int* co = reinterpret_cast<int*>(smem + L.co);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + L.G);
+    double* xs = reinterpret_cast<double*>(smem + L.xs);
+    double* bs = reinterpret_cast<double*>(smem + L.bs);
+    double* acc = reinterpret_cast<double*>(smem + L.acc);
+
+    pdl_trigger();
+    const int p = blockIdx.x;
+    const PatchMeta m = pd.meta[p];
+    const int tid = threadIdx.x;
+    const int64_t ns = pd.n_slots;
+    const int64_t slot0 = int64_t(p) * kPatch;
+    for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
+    // this thread's slots: local node ids (constant data, before the wait)
+    int ln[kEPT][NB];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) ln[k][i] = ok ? int(__ldg(pd.lconn + i * ns + slot0 + s)) : 0;
+    }
+    pdl_wait();
+    if (stop != nullptr && *stop) return;
+    const int32_t* pn = pd.pnode + m.node_off;
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        const int la = l0 + tid, lb = l0 + NT + tid;
+        const int32_t ga = la < m.n_nodes ? __ldg(pn + la) : 0, gb = lb < m.n_nodes ? __ldg(pn + lb) : 0;
+        const double xa = la < m.n_nodes ? __ldg(x + (ga & kNodeMask)) : 0.0;
+        const double xb = lb < m.n_nodes ? __ldg(x + (gb & kNodeMask)) : 0.0;
+        const double ba = (kRes && la < m.n_owned) ? __ldg(b + (ga & kNodeMask)) : 0.0;
+        const double bb = (kRes && lb < m.n_owned) ? __ldg(b + (gb & kNodeMask)) : 0.0;
+        if (la < m.n_nodes) { Gs[la] = ga; xs[la] = xa; acc[la] = 0.0; if (kRes) bs[la] = ba; }
+        if (lb < m.n_nodes) { Gs[lb] = gb; xs[lb] = xb; acc[lb] = 0.0; if (kRes) bs[lb] = bb; }
+    }
+    __syncthreads();
+    for (int c = 0; c < m.n_col; ++c) {
+        const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            if (s >= lo && s < hi) {
+                double a[NB * NB];
+#pragma unroll
+                for (int t = 0; t < NB * NB; ++t) a[t] = __ldg(A + t * ns + slot0 + s);
+                double xe[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) xe[j] = xs[ln[k][j]];
+#pragma unroll
+                for (int r = 0; r < NB; ++r) {
+                    double v = acc[ln[k][r]];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) v = fmadd(a[r * NB + j], xe[j], v);
+                    acc[ln[k][r]] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    DotAcc<double> dot;
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        const int32_t graw = Gs[l];
+        const int g = graw & kNodeMask;
+        const bool dir = graw < 0;
+        const double v = acc[l];
+        if (l < m.n_owned) {
+            const double o = kRes ? (dir ? 0.0 : bs[l] - v) : (dir ? 0.0 : v);
+            out[g] = o;
+            if (MODE == kResidualNorm) dot.add(o, o);
+            if (MODE == kApplyDot) dot.add(xs[l], o);
+        } else {
+            halo[m.halo_off + (l - m.n_owned)] = v;
+        }
+    }
+    if (MODE == kResidualNorm || MODE == kApplyDot) {
+        const double dsum = block_sum<NT>(dot.value(), red);
+        if (tid == 0) part[p] = dsum;
+    }
+}
+
+template <int NB, int MODE>
+cudaError_t run_patch64(const PlanDev& pd, const double* A, const double* x, const double* b, double* out, double* halo,
+                        double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev,
+                        bool pdl) {
+    const size_t sm = patch64_layout(pd.max_nodes).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto kern = k_patch64d<NB, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (pdl) {
+        e = launch_pdl(kern, dim3(pd.n_patches), dim3(kPatchThreads), sm, st, pd, A, x, b, out, halo, part, stop);
+        if (e != cudaSuccess) return e;
+    } else {
+        kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, x, b, out, halo, part, stop);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    k_fixup<double, MODE><<<fix_grid(pd.n_shared), kFixThreads, 0, st>>>(pd, x, b, out, halo, part, stop, sc);
+    if (ev) cudaEventRecord(ev[2], st);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
 template <typename T, int NB, int MODE>
 cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
                       const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev, bool pdl) {
@@ -350,6 +487,16 @@ template <typename T, int NB>
 cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, const T* b, T* out, T* halo,
                            double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches,
                            cudaEvent_t* ev, bool pdl) {
+    if constexpr (sizeof(T) == 8) {
+        switch (mode) {
+            case kResidual: return run_patch64<NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kResidualNorm:
+                return run_patch64<NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kApply: return run_patch64<NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kApplyDot: return run_patch64<NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (mode) {
         case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
         case kResidualNorm:

@@ -47,21 +47,54 @@ uint64_t spread3(uint64_t v) {
     return v;
 }
 
-// LSD radix sort of 64-bit values, 16-bit digits; stable.
-void radix_sort_u64(std::vector<uint64_t>& a) {
+// Run f(t, begin, end) on `threads` host threads over [0, n) in contiguous blocks.
+template <typename F>
+void parallel_blocks(int64_t n, int threads, F f) {
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / 65536 + 1)));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(f, t, n * t / nt, n * (t + 1) / nt);
+    f(0, 0, n / nt);
+    for (auto& th : pool) th.join();
+}
+
+// Stable LSD radix sort of 64-bit values by their bits [lo_bit, 64) (the
+// bits below keep their input order), 10-bit digits, the histogram and the
+// scatter of each pass split over host threads in contiguous blocks.
+void radix_sort_u64(std::vector<uint64_t>& a, int lo_bit, int threads) {
+    constexpr int kBits = 10, kBuckets = 1 << kBits;
+    const int64_t n = int64_t(a.size());
     std::vector<uint64_t> tmp(a.size());
-    std::vector<int64_t> count(1 << 16);
-    uint64_t hi = 0;
-    for (uint64_t v : a) hi |= v;
-    for (int shift = 0; shift < 64; shift += 16) {
-        if (((hi >> shift) & 0xffffull) == 0) continue;   // digit is zero everywhere
+    uint64_t any = 0;
+    for (uint64_t v : a) any |= v;
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / 65536 + 1)));
+    std::vector<int64_t> count(size_t(nt) * kBuckets);
+    for (int shift = lo_bit; shift < 64; shift += kBits) {
+        const uint64_t mask = (shift + kBits >= 64) ? (~0ull >> shift) : uint64_t(kBuckets - 1);
+        if (((any >> shift) & mask) == 0) continue;        // digit is zero everywhere
         std::fill(count.begin(), count.end(), 0);
-        for (uint64_t v : a) ++count[(v >> shift) & 0xffff];
-        int64_t s = 0;
-        for (auto& c : count) { int64_t t = c; c = s; s += t; }
-        for (uint64_t v : a) tmp[count[(v >> shift) & 0xffff]++] = v;
+        parallel_blocks(n, nt, [&](int t, int64_t b, int64_t e) {
+            int64_t* c = count.data() + size_t(t) * kBuckets;
+            for (int64_t i = b; i < e; ++i) ++c[(a[i] >> shift) & mask];
+        });
+        int64_t sum = 0;                                    // bucket-major, then block order: stable
+        for (int d = 0; d < kBuckets; ++d)
+            for (int t = 0; t < nt; ++t) {
+                int64_t& c = count[size_t(t) * kBuckets + d];
+                const int64_t v = c;
+                c = sum;
+                sum += v;
+            }
+        parallel_blocks(n, nt, [&](int t, int64_t b, int64_t e) {
+            int64_t* c = count.data() + size_t(t) * kBuckets;
+            for (int64_t i = b; i < e; ++i) tmp[c[(a[i] >> shift) & mask]++] = a[i];
+        });
         a.swap(tmp);
     }
+}
+
+int host_threads() {
+    const unsigned h = std::thread::hardware_concurrency();
+    return int(std::max(1u, std::min(16u, h)));
 }
 
 int bits_for(uint64_t n) {  // smallest b with n <= 2^b
@@ -111,22 +144,27 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     const int kbits_axis = std::min((64 - ebits) / dim, dim == 2 ? 32 : 21);
     const double qmax = double((uint64_t(1) << kbits_axis) - 1);
     std::vector<uint64_t> keys(n_e);
-    for (int64_t e = 0; e < n_e; ++e) {
-        const int32_t* v = m.elems + e * nb;
-        uint64_t q[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-            double c = 0;
-            for (int i = 0; i < nb; ++i) c += m.coords[int64_t(v[i]) * dim + d];
-            c /= nb;
-            double span = hi[d] - lo[d];
-            double t = span > 0 ? (c - lo[d]) / span : 0.0;
-            q[d] = uint64_t(std::min(qmax, std::max(0.0, std::floor(t * qmax + 0.5))));
+    const int threads = host_threads();
+    parallel_blocks(n_e, threads, [&](int, int64_t e0, int64_t e1) {
+        for (int64_t e = e0; e < e1; ++e) {
+            const int32_t* v = m.elems + e * nb;
+            uint64_t q[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) {
+                double c = 0;
+                for (int i = 0; i < nb; ++i) c += m.coords[int64_t(v[i]) * dim + d];
+                c /= nb;
+                double span = hi[d] - lo[d];
+                double t = span > 0 ? (c - lo[d]) / span : 0.0;
+                q[d] = uint64_t(std::min(qmax, std::max(0.0, std::floor(t * qmax + 0.5))));
+            }
+            uint64_t key = dim == 2 ? (spread2(q[0]) | (spread2(q[1]) << 1))
+                                    : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
+            keys[e] = (key << ebits) | uint64_t(e);
         }
-        uint64_t key = dim == 2 ? (spread2(q[0]) | (spread2(q[1]) << 1))
-                                : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
-        keys[e] = (key << ebits) | uint64_t(e);
-    }
-    radix_sort_u64(keys);
+    });
+    // the low ebits hold the element id, already ascending: a stable sort by
+    // the Morton bits alone gives the order of the full keys
+    radix_sort_u64(keys, ebits, threads);
     const uint64_t emask = ebits >= 64 ? ~0ull : ((uint64_t(1) << ebits) - 1);
 
     // ---- patches

@@ -538,23 +538,33 @@ def run_ours(args):
         h2d = hc.nbytes + he.nbytes + hf.nbytes + hd.nbytes + hg.nbytes + hn.nbytes + hx.nbytes
         d2h = hx.nbytes
         times, ebytes = [], 0
+        parts = {"create": 0.0, "set_problem": 0.0, "assemble": 0.0, "solve_host": 0.0, "destroy": 0.0}
         for _ in range(args.e2e_steps):
             hx[:] = 0.0
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h2 = ebe.ebe_create(hc, he, device=dev.index)
+            t1 = time.perf_counter()
             ebe.ebe_set_problem(h2, prob["nu"], hf, hd, hg, hn)
+            t2 = time.perf_counter()
             ebe.ebe_assemble(h2, ebe.EBE_STORE_MIXED)
+            t3 = time.perf_counter()
             info = ebe.ebe_solve_host(h2, hx, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED)
+            t4 = time.perf_counter()
             ebe.ebe_destroy(h2)
             torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
+            t5 = time.perf_counter()
+            times.append(t5 - t0)
+            for k, a, b in (("create", t0, t1), ("set_problem", t1, t2), ("assemble", t2, t3), ("solve_host", t3, t4),
+                            ("destroy", t4, t5)):
+                parts[k] += (b - a) * 1e3 / args.e2e_steps
             ebytes += step_bytes(m, info, True)
         e2e_s, ebytes = reduce_over_ranks(dist, dev, sum(times), float(ebytes))
         e2e = {"value": round(ebytes / e2e_s / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_s / args.e2e_steps, 2),
                "includes": "ebe_create (host partition build) + ebe_set_problem + ebe_assemble + "
-                           "ebe_solve_host + ebe_destroy"}
+                           "ebe_solve_host + ebe_destroy",
+               "ms_per_call": {k: round(v, 1) for k, v in parts.items()}}
 
     batched = None
     if not args.no_batch:

@@ -47,10 +47,11 @@ uint64_t spread3(uint64_t v) {
     return v;
 }
 
-// Run f(t, begin, end) on `threads` host threads over [0, n) in contiguous blocks.
+// Run f(t, begin, end) on `threads` host threads over [0, n) in contiguous
+// blocks of at least `grain` items.
 template <typename F>
-void parallel_blocks(int64_t n, int threads, F f) {
-    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / 65536 + 1)));
+void parallel_blocks(int64_t n, int threads, F f, int64_t grain = 65536) {
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / grain + 1)));
     std::vector<std::thread> pool;
     for (int t = 1; t < nt; ++t) pool.emplace_back(f, t, n * t / nt, n * (t + 1) / nt);
     f(0, 0, n / nt);
@@ -167,93 +168,146 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     radix_sort_u64(keys, ebits, threads);
     const uint64_t emask = ebits >= 64 ? ~0ull : ((uint64_t(1) << ebits) - 1);
 
-    // ---- patches
+    // ---- patches, built independently on host threads (scratch per thread:
+    // an open-addressing table from global node id to local index), then
+    // concatenated in patch order
     P.n_patches = (n_e + kPatch - 1) / kPatch;
     P.n_slots = P.n_patches * kPatch;
     P.slot_elem.assign(P.n_slots, -1);
     P.lconn.assign(size_t(nb) * P.n_slots, 0);
     P.meta.resize(P.n_patches);
-    P.pnode.reserve(size_t(n_e) * 2);
-    P.col_ptr.reserve(size_t(P.n_patches) * 12);
 
-    std::vector<int32_t> mark(n_n, -1), local(n_n, 0), in_patch(n_n, 0);
-    std::vector<int32_t> el(kPatch), lnodes, first_touch;
-    std::vector<uint64_t> used;  // per local node: colours of its elements so far
-    std::vector<int> colour(kPatch);
-    std::vector<int32_t> halo_node;  // halo slot -> global node
-    halo_node.reserve(size_t(n_n));
-    int64_t halo_count = 0;
-
-    for (int64_t p = 0; p < P.n_patches; ++p) {
-        const int64_t e0 = p * kPatch;
-        const int n_el = int(std::min<int64_t>(kPatch, n_e - e0));
-        for (int s = 0; s < n_el; ++s) el[s] = int32_t(keys[e0 + s] & emask);
-        // local nodes in first-touch order
-        first_touch.clear();
-        for (int s = 0; s < n_el; ++s) {
-            const int32_t* v = m.elems + int64_t(el[s]) * nb;
-            for (int i = 0; i < nb; ++i) {
-                int32_t g = v[i];
-                if (mark[g] != int32_t(p)) { mark[g] = int32_t(p); in_patch[g] = 0; first_touch.push_back(g); }
-                ++in_patch[g];
-            }
-        }
-        // owned first, then shared, each in first-touch order
-        lnodes.clear();
-        int n_owned = 0;
-        for (int32_t g : first_touch) if (in_patch[g] == inc[g]) { lnodes.push_back(g); ++n_owned; }
-        for (int32_t g : first_touch) if (in_patch[g] != inc[g]) lnodes.push_back(g);
-        const int n_nodes = int(lnodes.size());
-        if (n_nodes > 65535) { err = "patch with more than 65535 nodes"; return EBE_INVALID_ARG; }
-        for (int l = 0; l < n_nodes; ++l) local[lnodes[l]] = l;
-        // greedy colouring in Morton order
-        used.assign(n_nodes, 0);
-        int n_col = 0;
-        for (int s = 0; s < n_el; ++s) {
-            const int32_t* v = m.elems + int64_t(el[s]) * nb;
-            uint64_t busy = 0;
-            for (int i = 0; i < nb; ++i) busy |= used[local[v[i]]];
-            if (busy == ~0ull) { err = "patch needs more than 64 colours"; return EBE_INVALID_ARG; }
-            int c = 0;
-            while (busy & (1ull << c)) ++c;
-            colour[s] = c;
-            n_col = std::max(n_col, c + 1);
-            for (int i = 0; i < nb; ++i) used[local[v[i]]] |= (1ull << c);
-        }
-        // slots: elements grouped by colour, Morton order within a colour
-        PatchMeta& mt = P.meta[p];
-        mt.node_off = int32_t(P.pnode.size());
-        mt.n_nodes = n_nodes;
-        mt.n_owned = n_owned;
-        mt.halo_off = int32_t(halo_count);
-        mt.n_el = n_el;
-        mt.col_off = int32_t(P.col_ptr.size());
-        mt.n_col = n_col;
-        mt.pad = 0;
-        int slot = 0;
-        for (int c = 0; c < n_col; ++c) {
-            P.col_ptr.push_back(slot);
+    struct PatchOut {
+        std::vector<int32_t> lnodes;    // local nodes (owned first), padded to a multiple of 4
+        std::vector<int32_t> col_ptr;   // n_col + 1 slot offsets
+        int n_nodes = 0, n_owned = 0, n_col = 0;
+        int status = EBE_OK;
+        const char* msg = nullptr;
+    };
+    std::vector<PatchOut> outs(size_t(P.n_patches));
+    parallel_blocks(P.n_patches, threads, [&](int, int64_t p0, int64_t p1) {
+        constexpr int kTable = 1 << 13;   // twice the 4 * kPatch local nodes a patch can have
+        static_assert(kTable >= 8 * kPatch, "hash table too small");
+        std::vector<int32_t> tkey(kTable, -1), tval(kTable), tcnt(kTable);
+        std::vector<int32_t> el(kPatch), first_touch;
+        std::vector<uint32_t> filled;   // table slots in use, cleared slot by slot after each patch
+        std::vector<uint64_t> used;
+        std::vector<int> colour(kPatch);
+        auto slot_of = [&](int32_t g) {
+            uint32_t hsh = (uint32_t(g) * 2654435761u) >> 19;   // 13 bits
+            while (tkey[hsh] != g && tkey[hsh] != -1) hsh = (hsh + 1) & (kTable - 1);
+            return hsh;
+        };
+        for (int64_t p = p0; p < p1; ++p) {
+            PatchOut& out = outs[size_t(p)];
+            const int64_t e0 = p * kPatch;
+            const int n_el = int(std::min<int64_t>(kPatch, n_e - e0));
+            for (int s = 0; s < n_el; ++s) el[s] = int32_t(keys[e0 + s] & emask);
+            // local nodes in first-touch order, with their counts in the patch
+            first_touch.clear();
             for (int s = 0; s < n_el; ++s) {
-                if (colour[s] != c) continue;
-                const int64_t gs = e0 + slot;
-                P.slot_elem[gs] = el[s];
                 const int32_t* v = m.elems + int64_t(el[s]) * nb;
-                for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(local[v[i]]);
-                ++slot;
+                for (int i = 0; i < nb; ++i) {
+                    const uint32_t t = slot_of(v[i]);
+                    if (tkey[t] == -1) { tkey[t] = v[i]; tcnt[t] = 0; first_touch.push_back(v[i]); filled.push_back(t); }
+                    ++tcnt[t];
+                }
             }
+            // owned first, then shared, each in first-touch order
+            std::vector<int32_t>& lnodes = out.lnodes;
+            int n_owned = 0;
+            for (int32_t g : first_touch) if (tcnt[slot_of(g)] == inc[g]) { lnodes.push_back(g); ++n_owned; }
+            for (int32_t g : first_touch) if (tcnt[slot_of(g)] != inc[g]) lnodes.push_back(g);
+            const int n_nodes = int(lnodes.size());
+            out.n_nodes = n_nodes;
+            out.n_owned = n_owned;
+            // (clearing by key would cut probe chains of keys not yet cleared)
+            auto reset = [&]() { for (uint32_t t : filled) tkey[t] = -1; filled.clear(); };
+            if (n_nodes > 65535) {
+                out.status = EBE_INVALID_ARG;
+                out.msg = "patch with more than 65535 nodes";
+                reset();
+                return;
+            }
+            for (int l = 0; l < n_nodes; ++l) tval[slot_of(lnodes[l])] = l;
+            auto local = [&](int32_t g) { return tval[slot_of(g)]; };
+            // greedy colouring in Morton order
+            used.assign(n_nodes, 0);
+            int n_col = 0;
+            for (int s = 0; s < n_el; ++s) {
+                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                uint64_t busy = 0;
+                for (int i = 0; i < nb; ++i) busy |= used[local(v[i])];
+                if (busy == ~0ull) {
+                    out.status = EBE_INVALID_ARG;
+                    out.msg = "patch needs more than 64 colours";
+                    reset();
+                    return;
+                }
+                int c = 0;
+                while (busy & (1ull << c)) ++c;
+                colour[s] = c;
+                n_col = std::max(n_col, c + 1);
+                for (int i = 0; i < nb; ++i) used[local(v[i])] |= (1ull << c);
+            }
+            out.n_col = n_col;
+            // slots: elements grouped by colour, Morton order within a colour
+            int slot = 0;
+            for (int c = 0; c < n_col; ++c) {
+                out.col_ptr.push_back(slot);
+                for (int s = 0; s < n_el; ++s) {
+                    if (colour[s] != c) continue;
+                    const int64_t gs = e0 + slot;
+                    P.slot_elem[gs] = el[s];
+                    const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                    for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(local(v[i]));
+                    ++slot;
+                }
+            }
+            out.col_ptr.push_back(slot);
+            // each table starts on a 16-byte boundary (bulk copies need it)
+            while (lnodes.size() % 4 != 0) lnodes.push_back(lnodes[0]);
+            reset();
         }
-        P.col_ptr.push_back(slot);
-        for (int32_t g : lnodes) P.pnode.push_back(g);
-        // each table starts on a 16-byte boundary (bulk copies need it)
-        while (P.pnode.size() % 4 != 0) P.pnode.push_back(lnodes[0]);
-        for (int l = n_owned; l < n_nodes; ++l) halo_node.push_back(lnodes[l]);
-        halo_count += n_nodes - n_owned;
-        P.max_nodes = std::max(P.max_nodes, n_nodes);
-        P.max_col = std::max(P.max_col, n_col);
-        if (int64_t(P.pnode.size()) > int64_t(kNodeMask) || halo_count > int64_t(kNodeMask)) {
-            err = "partition tables exceed 2^31 entries"; return EBE_INVALID_ARG;
+    }, 16);
+    // offsets in patch order; the first failing patch reports
+    int64_t n_pnode = 0, n_colptr = 0, halo_count = 0;
+    for (int64_t p = 0; p < P.n_patches; ++p) {
+        const PatchOut& o = outs[size_t(p)];
+        if (o.status != EBE_OK) { err = o.msg; return o.status; }
+        PatchMeta& mt = P.meta[p];
+        mt.node_off = int32_t(n_pnode);
+        mt.n_nodes = o.n_nodes;
+        mt.n_owned = o.n_owned;
+        mt.halo_off = int32_t(halo_count);
+        mt.n_el = int32_t(std::min<int64_t>(kPatch, n_e - p * kPatch));
+        mt.col_off = int32_t(n_colptr);
+        mt.n_col = o.n_col;
+        mt.pad = 0;
+        n_pnode += int64_t(o.lnodes.size());
+        n_colptr += int64_t(o.col_ptr.size());
+        halo_count += o.n_nodes - o.n_owned;
+        P.max_nodes = std::max(P.max_nodes, o.n_nodes);
+        P.max_col = std::max(P.max_col, o.n_col);
+        if (n_pnode > int64_t(kNodeMask) || halo_count > int64_t(kNodeMask)) {
+            err = "partition tables exceed 2^31 entries";
+            return EBE_INVALID_ARG;
         }
     }
+    P.pnode.resize(size_t(n_pnode));
+    P.col_ptr.resize(size_t(n_colptr));
+    std::vector<int32_t> halo_node(static_cast<size_t>(halo_count));   // halo slot -> global node
+    parallel_blocks(P.n_patches, threads, [&](int, int64_t p0, int64_t p1) {
+        for (int64_t p = p0; p < p1; ++p) {
+            const PatchOut& o = outs[size_t(p)];
+            const PatchMeta& mt = P.meta[p];
+            std::copy(o.lnodes.begin(), o.lnodes.end(), P.pnode.begin() + mt.node_off);
+            std::copy(o.col_ptr.begin(), o.col_ptr.end(), P.col_ptr.begin() + mt.col_off);
+            std::copy(o.lnodes.begin() + o.n_owned, o.lnodes.begin() + o.n_nodes, halo_node.begin() + mt.halo_off);
+        }
+    }, 64);
+    outs.clear();
+    outs.shrink_to_fit();
     P.n_halo = halo_count;
 
     // ---- shared nodes: CSR of halo slots in patch order (slots are numbered

@@ -14,8 +14,8 @@ solver).  The mesh partition (built once per mesh, like the paper's index
 arrays) and the inputs are resident on the device before the timed region.
 
 value = algorithmic bytes of the step (every kernel's minimum traffic: each
-element matrix, connectivity index and node vector entry counted once per
-pass) / step time, in GB/s; the plain FP64 Jacobi-PCG of the same problem is
+distinct element matrix entry, connectivity index and node vector entry
+counted once per pass) / step time, in GB/s; the plain FP64 Jacobi-PCG of the same problem is
 timed beside it ("plain_fp64").  The roofline object is the FP32 operator
 application (patch kernel + halo fix-up) timed per launch with CUDA events on
 its stream.  e2e repeats the step through the C ABI from pinned host buffers:
@@ -78,20 +78,23 @@ def parse():
 def bytes_model(dim: int, n_n: int, n_e: int):
     """Algorithmic bytes of each pass (each entry counted once per pass).
 
-    Element: n_b^2 matrix entries + n_b int32 connectivity indices.
+    Element: the n_b(n_b+1)/2 distinct entries of the symmetric A_e (all the
+    information it holds, and what the library stores) + n_b int32
+    connectivity indices.
     Node vectors: every vector read or written by the pass, once.
     """
     nb = dim + 1
+    na = nb * (nb + 1) // 2
     conn = 4 * nb * n_e
     m = {}
     # element matrices + load vector + Jacobi diagonal: coords (dim f64) + f (f64) in,
     # A64 + A32 out, b, d, dinv (f64) + b32, dinv32 (f32) out
-    m["assemble_mixed"] = conn + n_n * 8 * (dim + 1) + n_e * nb * nb * (8 + 4) + n_n * (3 * 8 + 2 * 4)
-    m["assemble_fp64"] = conn + n_n * 8 * (dim + 1) + n_e * nb * nb * 8 + n_n * 3 * 8
-    m["residual64"] = conn + n_e * nb * nb * 8 + n_n * 3 * 8          # x, b in; r out
-    m["residual32"] = conn + n_e * nb * nb * 4 + n_n * 3 * 4
-    m["apply64"] = conn + n_e * nb * nb * 8 + n_n * 2 * 8             # p in; q out
-    m["apply32"] = conn + n_e * nb * nb * 4 + n_n * 2 * 4
+    m["assemble_mixed"] = conn + n_n * 8 * (dim + 1) + n_e * na * (8 + 4) + n_n * (3 * 8 + 2 * 4)
+    m["assemble_fp64"] = conn + n_n * 8 * (dim + 1) + n_e * na * 8 + n_n * 3 * 8
+    m["residual64"] = conn + n_e * na * 8 + n_n * 3 * 8          # x, b in; r out
+    m["residual32"] = conn + n_e * na * 4 + n_n * 3 * 4
+    m["apply64"] = conn + n_e * na * 8 + n_n * 2 * 8             # p in; q out
+    m["apply32"] = conn + n_e * na * 4 + n_n * 2 * 4
     # update (x, p, r, q, dinv in; x, r out) + direction (r, dinv, p in; p out)
     m["vec64"] = n_n * 8 * (7 + 4)
     m["vec_mixed"] = n_n * ((8 + 4 + 8 + 4 + 4) + (8 + 8) + (8 + 4 + 4) + 4)   # x, r FP64; p, q, dinv FP32
@@ -594,7 +597,7 @@ def run_ours(args):
         "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n, "n_elements": n_e,
                    "n_b": dim + 1, "solver": "Jacobi-PCG, FP32 A_e/vectors, FP64 reliable updates",
                    "rtol": args.rtol, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) ** 2 * 12) / 1e6),
+                   "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) * (dim + 2) // 2 * 12) / 1e6),
                    "value_def": "algorithmic bytes of the step / step time"},
         "pcg": {"ms_to_1e-8": round(ms_step, 2), "iterations": info0["iterations"],
                 "true_residuals": info0["true_residuals"], "rel_residual": info0["rel_residual"],

@@ -192,8 +192,10 @@ ebe_status ebe_set_problem(ebe_handle* h, double nu, const double* f_nodal,
  * Eq. matrices_K_M, A_e = K_e + nu M_e (Sec. 2), the assembled load vector
  * b = sum_e C_e^T M_e f_e and the inverse Jacobi diagonal
  * dinv = 1 / sum_e C_e^T diag(A_e) (0 on Dirichlet nodes).  store:
- * EBE_STORE_FP64 or EBE_STORE_MIXED.  Enqueued on the handle's stream; the
- * degenerate-element check synchronises it.
+ * EBE_STORE_FP64 or EBE_STORE_MIXED.  A_e is symmetric, so the handle keeps
+ * its n_b(n_b+1)/2 distinct entries per element (6 for triangles, 10 for
+ * tetrahedra; FP64, plus FP32 for MIXED).  Enqueued on the handle's stream;
+ * the degenerate-element check synchronises it.
  * Errors: EBE_NOT_READY, EBE_DEGENERATE_ELEMENT, EBE_CUDA_ERROR, EBE_OOM. */
 ebe_status ebe_assemble(ebe_handle* h, int32_t store);
 
@@ -204,7 +206,7 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store);
 ebe_status ebe_element_matrices(ebe_handle* h, double* K_dev, double* M_dev);
 
 /* Copy the element matrices A_e held by the handle to a device buffer in the
- * same layout.  dtype EBE_F64 (double*) or EBE_F32 (float*, MIXED storage; the
+ * same layout (full n_b x n_b, both triangles written).  dtype EBE_F64 (double*) or EBE_F32 (float*, MIXED storage; the
  * stored difference form: diagonal entries hold the row sums s_i).
  * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
 ebe_status ebe_get_local_matrices(ebe_handle* h, void* A_dev, int32_t dtype);

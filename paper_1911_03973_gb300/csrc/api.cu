@@ -494,7 +494,7 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
     TRY(check_ready(h, false));
     if (store != EBE_STORE_FP64 && store != EBE_STORE_MIXED) return ebe_status(fail(h, EBE_INVALID_ARG, "bad store"));
     Scope scp(h);
-    const int64_t n_n = h->plan.n_n, nbb = int64_t(h->pd.nb) * h->pd.nb;
+    const int64_t n_n = h->plan.n_n, nbb = sym_count(h->pd.nb);
     TRY(dalloc(h, &h->A64, nbb * h->pd.n_slots, true));
     TRY(dalloc(h, &h->b, n_n));
     TRY(dalloc(h, &h->d, n_n));
@@ -683,7 +683,7 @@ ebe_status ebe_residual_variant(ebe_handle* h, const double* x, double* r, int32
             h->n_gcol = nc;
             int32_t* order_d = nullptr;
             TRY(upload(h, &order_d, order.data(), int64_t(order.size())));
-            TRY(dalloc(h, &h->Acol, int64_t(P.nb) * P.nb * P.n_e));
+            TRY(dalloc(h, &h->Acol, int64_t(sym_count(P.nb)) * P.n_e));
             TRY(dalloc(h, &h->gcol, int64_t(P.nb) * P.n_e));
             CK(launch_permute_slots(P.nb, P.n_slots, P.n_e, order_d, h->A64, h->gconn, h->Acol, h->gcol, h->st, &l),
                "permute");

@@ -32,7 +32,7 @@ __global__ void k_permute(int nb, int64_t n_slots, int64_t n, const int32_t* __r
     const int64_t k = int64_t(blockIdx.x) * NT + threadIdx.x;
     if (k >= n) return;
     const int64_t s = order[k];
-    for (int t = 0; t < nb * nb; ++t) Ao[t * n + k] = A[t * n_slots + s];
+    for (int t = 0; t < sym_count(nb); ++t) Ao[t * n + k] = A[t * n_slots + s];
     for (int i = 0; i < nb; ++i) go[i * n + k] = gconn[i * n_slots + s];
 }
 
@@ -49,7 +49,7 @@ __global__ void k_colour_pass(int64_t lo, int64_t hi, int64_t n, const double* _
     for (int i = 0; i < NB; ++i) {
         double v = r[g[i]];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(Ac + (i * NB + j) * n + k), xe[j], v);
+        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(Ac + sym_index(NB, i, j) * n + k), xe[j], v);
         r[g[i]] = v;
     }
 }
@@ -68,7 +68,7 @@ __global__ void k_atomic_pass(const PlanDev pd, const double* __restrict__ A, co
     for (int i = 0; i < NB; ++i) {
         double v = 0.0;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(A + (i * NB + j) * ns + s), xe[j], v);
+        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(A + sym_index(NB, i, j) * ns + s), xe[j], v);
         atomicAdd(r + g[i], v);
     }
 }
@@ -86,7 +86,7 @@ __global__ void k_element_products(const PlanDev pd, const double* __restrict__ 
     for (int i = 0; i < NB; ++i) {
         double v = 0.0;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(A + (i * NB + j) * ns + s), xe[j], v);
+        for (int j = 0; j < NB; ++j) v = __fma_rn(__ldcs(A + sym_index(NB, i, j) * ns + s), xe[j], v);
         Y[i * ns + s] = v;
     }
 }

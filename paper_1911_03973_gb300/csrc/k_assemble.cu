@@ -77,6 +77,7 @@ __device__ __forceinline__ double p1_element(const double (&v)[NB][NB - 1], doub
 }
 
 // Element matrices of every slot, A_e = K_e + nu M_e stored FP64 (and FP32),
+// packed symmetric (sym_index),
 // with the load vector b = sum_e C_e^T M_e f_e and d = sum_e C_e^T diag(A_e)
 // accumulated per node like the residual (colour order, halo for shared).
 template <int NB>
@@ -136,10 +137,10 @@ k_assemble(const PlanDev pd, const double* __restrict__ coords, const double* __
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
                 const double aij = K[i][j] + nu * (i == j ? md : mo);
-                if (ok) {
-                    A64[(i * NB + j) * ns + slot0 + s] = aij;
+                if (ok && i <= j) {   // packed symmetric storage
+                    A64[sym_index(NB, i, j) * ns + slot0 + s] = aij;
                     // FP32 copy in difference form: row sums on the diagonal slots
-                    if (A32 != nullptr) A32[(i * NB + j) * ns + slot0 + s] = float(i == j ? rowsum : aij);
+                    if (A32 != nullptr) A32[sym_index(NB, i, j) * ns + slot0 + s] = float(i == j ? rowsum : aij);
                 }
                 if (i == j) di[k][i] = aij;
             }
@@ -238,7 +239,7 @@ __global__ void k_export_A(const PlanDev pd, const T* __restrict__ A, T* __restr
     if (e < 0) return;
     const int nb = pd.nb;
     for (int i = 0; i < nb; ++i)
-        for (int j = 0; j < nb; ++j) out[int64_t(e) * nb * nb + j * nb + i] = A[(i * nb + j) * pd.n_slots + s];
+        for (int j = 0; j < nb; ++j) out[int64_t(e) * nb * nb + j * nb + i] = A[sym_index(nb, i, j) * pd.n_slots + s];
 }
 
 __global__ void k_mark(int32_t* __restrict__ ids, int64_t n, const uint8_t* __restrict__ mask) {

@@ -89,7 +89,7 @@ __host__ __device__ constexpr BatchSmem batch_layout(int max_nodes, int n_prob) 
     s.list = up(s.mode + uint32_t(n_prob), 16);      // live problems
     s.pre = s.list + uint32_t(n_prob) * 4;           // prefix sums: patches, fix-up items, tiles [3][n_prob + 1]
     s.A = up(s.pre + 3u * uint32_t(n_prob + 1) * 4, 128);
-    s.L = s.A + uint32_t(NB * NB * kPatch * sizeof(T));
+    s.L = s.A + uint32_t(sym_count(NB) * kPatch * sizeof(T));
     s.G = s.L + uint32_t(NB * kPatch * 2);
     s.xs = up(s.G + gcap * 4, 16);
     s.acc = up(s.xs + gcap * uint32_t(sizeof(T)), 16);
@@ -127,9 +127,9 @@ __device__ __forceinline__ void issue_patch_copies(const BatchDev& bd, unsigned 
     const int64_t slot0 = int64_t(p) * kPatch;
     const uint32_t mbar = tma::smem_addr(smem + Lo.bar);
     const uint64_t pol = tma::policy_evict_first();
-    tma::mbar_expect_tx(mbar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
+    tma::mbar_expect_tx(mbar, uint32_t(sym_count(NB) * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
 #pragma unroll
-    for (int t = 0; t < NB * NB; ++t)
+    for (int t = 0; t < sym_count(NB); ++t)
         tma::bulk_load(tma::smem_addr(smem + Lo.A + t * kPatch * sizeof(T)), A + t * ns + slot0,
                        uint32_t(kPatch * sizeof(T)), mbar, pol);
 #pragma unroll
@@ -208,14 +208,14 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p, bool have, int next_p
         for (int r = 0; r < NB; ++r) {
             T v;
             if constexpr (sizeof(T) == 4) {
-                v = ok ? As[(r * NB + r) * kPatch + s] * xe[r] : T(0);
+                v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[r] : T(0);
 #pragma unroll
                 for (int j = 0; j < NB; ++j)
-                    if (j != r) v = ok ? fmadd(As[(r * NB + j) * kPatch + s], xe[j] - xe[r], v) : v;
+                    if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[j] - xe[r], v) : v;
             } else {
                 v = T(0);
 #pragma unroll
-                for (int j = 0; j < NB; ++j) v = ok ? fmadd(As[(r * NB + j) * kPatch + s], xe[j], v) : v;
+                for (int j = 0; j < NB; ++j) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[j], v) : v;
             }
             y[k][r] = v;
         }
@@ -298,7 +298,7 @@ __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
             for (int r = 0; r < NB; ++r) {
                 double v = acc[ln[r]];
 #pragma unroll
-                for (int j = 0; j < NB; ++j) v = fmadd(__ldg(bd.A64 + (r * NB + j) * ns + slot0 + s), xs[ln[j]], v);
+                for (int j = 0; j < NB; ++j) v = fmadd(__ldg(bd.A64 + sym_index(NB, r, j) * ns + slot0 + s), xs[ln[j]], v);
                 acc[ln[r]] = v;
             }
         }

@@ -4,16 +4,15 @@
 // patch and several CTAs share an SM, so that one CTA's copies overlap
 // another's arithmetic:
 //   * the TMA engine bulk-copies the patch's element matrices (structure of
-//     arrays: entry t of the patch's 1024 slots is one contiguous run) and
+//     arrays: packed symmetric entry t of the patch's 1024 slots is one
+//     contiguous run, n_b(n_b+1)/2 runs) and
 //     16-bit local connectivity into shared memory, evict-first in L2; while
 //     they are in flight the threads gather the patch's node table, x and b
 //     at the patch nodes -- the restriction x_e = R_e x of Algorithm 1,
 //     shared by neighbouring elements;
 //   * the threads add A_e x_e into per-node shared-memory sums colour by
 //     colour: within a colour no two elements share a node, so there are no
-//     atomics and the order of the additions is fixed (bitwise reproducible).
-//     The product is folded into the sum (sum = fma(a_ij, x_j, sum)), so the
-//     FP64 pipe does exactly n_b^2 FMAs per element;
+//     atomics and the order of the additions is fixed (bitwise reproducible);
 //   * they write the result of every owned node (all of its elements are in
 //     this patch) and the partial sum of every shared node to its halo slot.
 // The fix-up pass adds the halo partials of each shared node in patch order.
@@ -51,7 +50,7 @@ using tma::policy_evict_first;
 using tma::smem_addr;
 
 // Shared-memory layout of a patch pass.  One patch per CTA: its element
-// matrices (n_b^2 runs of 1024 values) and local connectivity (n_b runs) come
+// matrices (n_b(n_b+1)/2 runs of 1024 values) and local connectivity (n_b runs) come
 // in by TMA bulk copies; the node table, x and b at the patch nodes by plain
 // loads issued while the bulk copies are in flight.
 struct PatchSmem {
@@ -66,7 +65,7 @@ __host__ __device__ constexpr PatchSmem patch_layout(int max_nodes) {
     s.red = 16;                                         // 32 doubles
     s.co = s.red + 32 * 8;                              // kMaxColours + 1 ints
     s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
-    s.L = s.A + uint32_t(NB * NB * kPatch * sizeof(T));
+    s.L = s.A + uint32_t(sym_count(NB) * kPatch * sizeof(T));
     s.G = s.L + uint32_t(NB * kPatch * 2);
     s.xs = s.G + gcap * 4;
     s.bs = (s.xs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
@@ -88,6 +87,7 @@ template <typename T, int NB, int MODE>
 __global__ void __launch_bounds__(kPatchThreads)
 k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
         T* __restrict__ out, T* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
+    static_assert(sizeof(T) == 4, "FP64 patch passes use k_patch64d");
     constexpr int NT = kPatchThreads;
     constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -117,9 +117,9 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     if (tid == 0) {
         mbar_init(bar, 1);
         const uint64_t pol = policy_evict_first();
-        mbar_expect_tx(bar, uint32_t(NB * NB * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
+        mbar_expect_tx(bar, uint32_t(sym_count(NB) * kPatch * sizeof(T)) + uint32_t(NB * kPatch * 2));
 #pragma unroll
-        for (int t = 0; t < NB * NB; ++t)
+        for (int t = 0; t < sym_count(NB); ++t)
             bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * sizeof(T)), bar, pol);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
@@ -179,59 +179,36 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
             xe[k][i] = xs[ln[k][i]];
         }
     }
-    if constexpr (sizeof(T) == 8) {
-        // FP64: the product is folded into the node sum inside the colour
-        // rounds (acc = fma(a_rj, x_j, acc)), the minimum of n_b^2 FP64 FMAs
-        // per element -- the FP64 pipe, not DRAM, bounds this pass
-        for (int c = 0; c < m.n_col; ++c) {
-            const int lo = co[c], hi = co[c + 1];
+    // FP32: every thread forms the products of its slots at once, then the
+    // colour rounds only add them into the node sums (short rounds).
+    // Difference form: the diagonal slot holds the row sum s_r,
+    // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
+    // difference is exact in FP32 and no accuracy is lost to cancellation.
+    T y[kEPT][NB];
 #pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                const int s = tid + k * NT;
-                if (s >= lo && s < hi) {
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
 #pragma unroll
-                    for (int r = 0; r < NB; ++r) {
-                        T v = acc[ln[k][r]];
+        for (int r = 0; r < NB; ++r) {
+            T v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[k][r] : T(0);
 #pragma unroll
-                        for (int j = 0; j < NB; ++j) v = fmadd(As[(r * NB + j) * kPatch + s], xe[k][j], v);
-                        acc[ln[k][r]] = v;
-                    }
-                }
-            }
-            __syncthreads();
+            for (int j = 0; j < NB; ++j)
+                if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
+            y[k][r] = v;
         }
-    } else {
-        // FP32: every thread forms the products of its slots at once, then the
-        // colour rounds only add them into the node sums (short rounds).
-        // Difference form: the diagonal slot holds the row sum s_r,
-        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
-        // difference is exact in FP32 and no accuracy is lost to cancellation.
-        T y[kEPT][NB];
+    }
+    for (int c = 0; c < m.n_col; ++c) {
+        const int lo = co[c], hi = co[c + 1];
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
             const int s = tid + k * NT;
-            const bool ok = s < m.n_el;
+            if (s >= lo && s < hi) {
 #pragma unroll
-            for (int r = 0; r < NB; ++r) {
-                T v = ok ? As[(r * NB + r) * kPatch + s] * xe[k][r] : T(0);
-#pragma unroll
-                for (int j = 0; j < NB; ++j)
-                    if (j != r) v = ok ? fmadd(As[(r * NB + j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
-                y[k][r] = v;
+                for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
             }
         }
-        for (int c = 0; c < m.n_col; ++c) {
-            const int lo = co[c], hi = co[c + 1];
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                const int s = tid + k * NT;
-                if (s >= lo && s < hi) {
-#pragma unroll
-                    for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
-                }
-            }
-            __syncthreads();
-        }
+        __syncthreads();
     }
 
     // owned nodes: final value; shared nodes: halo partial
@@ -345,7 +322,7 @@ __host__ __device__ constexpr Patch64Smem patch64_layout(int max_nodes) {
 }
 
 template <int NB, int MODE>
-__global__ void __launch_bounds__(kPatchThreads, 4)
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 4 : 3)
 k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restrict__ x, const double* __restrict__ b,
            double* __restrict__ out, double* __restrict__ halo, double* __restrict__ part,
            const int32_t* __restrict__ stop) {
@@ -396,9 +373,9 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
         for (int k = 0; k < kEPT; ++k) {
             const int s = tid + k * NT;
             if (s >= lo && s < hi) {
-                double a[NB * NB];
+                double a[sym_count(NB)];
 #pragma unroll
-                for (int t = 0; t < NB * NB; ++t) a[t] = __ldg(A + t * ns + slot0 + s);
+                for (int t = 0; t < sym_count(NB); ++t) a[t] = __ldg(A + t * ns + slot0 + s);
                 double xe[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) xe[j] = xs[ln[k][j]];
@@ -406,7 +383,7 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
                 for (int r = 0; r < NB; ++r) {
                     double v = acc[ln[k][r]];
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) v = fmadd(a[r * NB + j], xe[j], v);
+                    for (int j = 0; j < NB; ++j) v = fmadd(a[sym_index(NB, r, j)], xe[j], v);
                     acc[ln[k][r]] = v;
                 }
             }
@@ -496,14 +473,15 @@ cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, 
             case kApplyDot: return run_patch64<NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
             default: return cudaErrorInvalidValue;
         }
-    }
-    switch (mode) {
-        case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
-        case kResidualNorm:
-            return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
-        case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
-        case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
-        default: return cudaErrorInvalidValue;
+    } else {
+        switch (mode) {
+            case kResidual: return run_patch<T, NB, kResidual>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kResidualNorm:
+                return run_patch<T, NB, kResidualNorm>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kApply: return run_patch<T, NB, kApply>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            case kApplyDot: return run_patch<T, NB, kApplyDot>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+            default: return cudaErrorInvalidValue;
+        }
     }
 }
 

@@ -30,6 +30,16 @@ struct PlanDev {
     int num_sms = 1;                    // persistent grid size of the patch pass
 };
 
+// Element matrices are symmetric (K_e and M_e of Eq. matrices_K_M; the
+// closed forms give a_ij and a_ji from the same products, so they are equal
+// bit for bit) and are stored packed: sym_count(nb) slot-major runs of
+// n_slots values, the nb diagonal entries first, then the pairs i < j in the
+// order (0,1), (0,2), (1,2), (0,3), (1,3), (2,3).
+__host__ __device__ constexpr int sym_count(int nb) { return nb * (nb + 1) / 2; }
+__host__ __device__ constexpr int sym_index(int nb, int i, int j) {
+    return i == j ? i : nb + (i < j ? j * (j - 1) / 2 + i : i * (i - 1) / 2 + j);
+}
+
 // What a patch pass produces at the nodes.
 enum PatchMode : int {
     kResidual = 0,      // out = mask(b - A x)

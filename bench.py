@@ -97,9 +97,9 @@ def bytes_model(dim: int, n_n: int, n_e: int):
     m["apply32"] = conn + n_e * na * 4 + n_n * 2 * 4
     # update (x, p, r, q, dinv in; x, r out) + direction (r, dinv, p in; p out)
     m["vec64"] = n_n * 8 * (7 + 4)
-    m["vec_mixed"] = n_n * ((8 + 4 + 8 + 4 + 4) + (8 + 8) + (8 + 4 + 4) + 4)   # x, r FP64; p, q, dinv FP32
-    # after a true residual: r.z and r.r (r, dinv in), then a direction step
-    m["restart_mixed"] = n_n * ((8 + 4) + (8 + 4 + 4 + 4))
+    m["vec_mixed"] = n_n * ((8 + 4 + 4 + 4 + 4) + (8 + 4) + (4 + 4 + 4) + 4)   # x FP64; r, p, q, dinv FP32
+    # after a true residual: r.z and r.r (r64, dinv in; r32 out), then a direction step
+    m["restart_mixed"] = n_n * ((8 + 4 + 4) + (4 + 4 + 4 + 4))
     m["restart64"] = n_n * ((8 + 8) + (8 + 8 + 8 + 8))
     return m
 
@@ -595,7 +595,7 @@ def run_ours(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n, "n_elements": n_e,
-                   "n_b": dim + 1, "solver": "Jacobi-PCG, FP32 A_e/vectors, FP64 reliable updates",
+                   "n_b": dim + 1, "solver": "Jacobi-PCG, FP32 A_e/r/p/q, FP64 x, FP64 residual replacement",
                    "rtol": args.rtol, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) * (dim + 2) // 2 * 12) / 1e6),
                    "value_def": "algorithmic bytes of the step / step time"},

@@ -69,7 +69,7 @@ struct ebe_handle {
 
     // solver vectors
     double *x64w = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
-    float *p32 = nullptr, *q32 = nullptr;
+    float *p32 = nullptr, *q32 = nullptr, *r32 = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_chunk[2] = {0, 0};
     int graph_nodes[2] = {0, 0};
@@ -703,9 +703,10 @@ ebe_status ebe_residual_variant(ebe_handle* h, const double* x, double* r, int32
 namespace {
 
 struct SolveBufs {
-    int dt;        // type of A, p, q: 0 = FP64, 1 = FP32
+    int dt;        // type of A, p, q and the recurrence residual r: 0 = FP64, 1 = FP32
     void* p;
     void* q;
+    void* r;       // recurrence residual (r64 itself for FP64)
     const void* A;
     const void* dinv;  // FP64 (plain) or FP32 (mixed) inverse Jacobi diagonal
     void* halo;
@@ -715,22 +716,22 @@ SolveBufs bufs_for(ebe_handle* h, bool mixed) {
     SolveBufs s;
     s.dt = mixed ? 1 : 0;
     if (mixed) {
-        s.p = h->p32; s.q = h->q32; s.A = h->A32; s.dinv = h->dinv32; s.halo = h->halo32;
+        s.p = h->p32; s.q = h->q32; s.r = h->r32; s.A = h->A32; s.dinv = h->dinv32; s.halo = h->halo32;
     } else {
-        s.p = h->p64; s.q = h->q64; s.A = h->A64; s.dinv = h->dinv; s.halo = h->halo64;
+        s.p = h->p64; s.q = h->q64; s.r = h->r64; s.A = h->A64; s.dinv = h->dinv; s.halo = h->halo64;
     }
     return s;
 }
 
 // One CG iteration: q = mask(A p) and p.q (alpha), update (stop test), direction.
-// x, r and dinv are FP64 in both precisions.
+// x is FP64 in both precisions.
 int enqueue_iteration(ebe_handle* h, const SolveBufs& s, int* l) {
     const int64_t n = h->plan.n_n;
     CK(launch_patch_pass(h->pd, s.dt, kApplyDot, s.A, s.p, nullptr, s.q, s.halo, h->part_patch, &h->sc->done, h->sc,
                          h->st, l, nullptr, true),
        "apply");
-    CK(launch_update(s.dt, n, h->x64w, s.p, h->r64, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
-    CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 0, h->sc, h->st, l), "direction");
+    CK(launch_update(s.dt, n, h->x64w, s.p, s.r, s.q, s.dinv, h->part_vec, h->sc, h->st, l), "update");
+    CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, l), "direction");
     return EBE_OK;
 }
 
@@ -765,13 +766,14 @@ int true_residual(ebe_handle* h, double& rr) {
     return EBE_OK;
 }
 
-// Jacobi-PCG.  The solution x, the residual r and z = dinv r are FP64 in both
-// precisions.  EBE_PREC_MIXED keeps the search direction p, q = A p and the
-// element matrices in FP32 (difference form), so the operator pass streams
-// half the bytes; its FP32 rounding makes the recurrence residual drift from
-// the true one, so whenever the recurrence residual has dropped by `delta`
-// since the last FP64 true residual, r is replaced by a fresh FP64 true
-// residual (FP64 element matrices) and CG continues with the same direction.
+// Jacobi-PCG.  The solution x is FP64 in both precisions.  EBE_PREC_MIXED
+// keeps the recurrence residual r, z = dinv r, the search direction p,
+// q = A p and the element matrices in FP32 (difference form), so the passes
+// stream about half the bytes and the FP64 pipe only updates x; FP32
+// rounding makes the recurrence residual drift from the true one, so
+// whenever the recurrence residual has dropped by `delta` since the last
+// FP64 true residual, r is replaced by a fresh FP64 true residual (FP64
+// element matrices) and CG continues with the same direction.
 int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
     const auto t0 = std::chrono::steady_clock::now();
     const bool mixed = o.precision == EBE_PREC_MIXED;
@@ -784,6 +786,7 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
     if (mixed) {
         TRY(dalloc(h, &h->p32, n));
         TRY(dalloc(h, &h->q32, n));
+        TRY(dalloc(h, &h->r32, n));
         TRY(dalloc(h, &h->halo32, nh));
     } else {
         TRY(dalloc(h, &h->p64, n));
@@ -813,8 +816,8 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
         // dropped by delta, and a margin at the end for the drift.
         const double fin = mixed ? 0.7 * target : target;
         l = 0;
-        CK(launch_restart(s.dt, n, h->r64, s.dinv, 1, h->part_vec, h->sc, h->st, &l), "restart");
-        CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 1, h->sc, h->st, &l), "direction");
+        CK(launch_restart(s.dt, n, h->r64, s.dinv, 1, h->part_vec, h->sc, h->st, &l, h->r32), "restart");
+        CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 1, h->sc, h->st, &l), "direction");
         double thr = mixed ? std::max(o.delta * r0, fin) : fin;
         CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
         add_launches(h, l);
@@ -851,8 +854,8 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
             // residual replacement: r64 already holds the FP64 true residual;
             // continue CG from it with the same direction
             l = 0;
-            CK(launch_restart(s.dt, n, h->r64, s.dinv, 0, h->part_vec, h->sc, h->st, &l), "restart");
-            CK(launch_direction(s.dt, n, s.p, h->r64, s.dinv, 0, h->sc, h->st, &l), "direction");
+            CK(launch_restart(s.dt, n, h->r64, s.dinv, 0, h->part_vec, h->sc, h->st, &l, h->r32), "restart");
+            CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 0, h->sc, h->st, &l), "direction");
             thr = mixed ? std::max(o.delta * std::sqrt(rr), fin) : fin;
             CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
             add_launches(h, l);
@@ -1069,6 +1072,7 @@ int batch_buffers(ebe_handle* h, bool mixed) {
     if (mixed) {
         TRY(dalloc(h, &h->p32, n));
         TRY(dalloc(h, &h->q32, n));
+        TRY(dalloc(h, &h->r32, n));
         TRY(dalloc(h, &h->halo32, nh));
     } else {
         TRY(dalloc(h, &h->p64, n));
@@ -1092,6 +1096,7 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.dinv = mixed ? static_cast<const void*>(h->dinv32) : h->dinv;
     bd.x = h->x64w;
     bd.r = h->r64;
+    bd.rin = mixed ? static_cast<void*>(h->r32) : h->r64;
     bd.p = mixed ? static_cast<void*>(h->p32) : h->p64;
     bd.q = mixed ? static_cast<void*>(h->q32) : h->q64;
     bd.halo = mixed ? static_cast<void*>(h->halo32) : h->halo64;

@@ -489,6 +489,7 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
     const T* dinv = static_cast<const T*>(bd.dinv);
     double* x = bd.x;
     double* r = bd.r;
+    T* ri_v = static_cast<T*>(bd.rin);   // recurrence residual (FP32 when mixed)
     double a = 0.0, b = 0.0;
     const BatchProblem* P = bd.prob + it.k;
     if (md == kBNormal) {
@@ -496,33 +497,33 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
         const int brk = ld_l2(&P->bd);
         if (!brk) {
             if constexpr (MIXED) {
+                // x += alpha p in FP64; r -= alpha q and z = dinv r in FP32
+                const float alf = d2f(al);
                 CompSum rz, rr;
                 int i = it.lo + tid;
                 for (; i + 3 * NT < it.hi; i += 4 * NT) {
-                    float pq[4], qq[4], dv[4];
-                    double xv[4], rv[4];
+                    float pq[4], qq[4], dv[4], rv[4];
+                    double xv[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = i + u * NT;
                         pq[u] = ld_l2(pv + j); qq[u] = ld_l2(q + j); dv[u] = __ldg(dinv + j);
-                        xv[u] = ld_l2(x + j); rv[u] = ld_l2(r + j);
+                        xv[u] = ld_l2(x + j); rv[u] = ld_l2(ri_v + j);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = i + u * NT;
                         x[j] = fmadd(al, f2d(pq[u]), xv[u]);
-                        const double ri = fmadd(-al, f2d(qq[u]), rv[u]);
-                        r[j] = ri;
-                        const float rf = d2f(ri);
+                        const float rf = __fmaf_rn(-alf, qq[u], rv[u]);
+                        ri_v[j] = rf;
                         rz.add(rf * (dv[u] * rf));
                         rr.add(rf * rf);
                     }
                 }
                 for (; i < it.hi; i += NT) {
                     x[i] = fmadd(al, f2d(ld_l2(pv + i)), ld_l2(x + i));
-                    const double ri = fmadd(-al, f2d(ld_l2(q + i)), ld_l2(r + i));
-                    r[i] = ri;
-                    const float rf = d2f(ri);
+                    const float rf = __fmaf_rn(-alf, ld_l2(q + i), ld_l2(ri_v + i));
+                    ri_v[i] = rf;
                     rz.add(rf * (__ldg(dinv + i) * rf));
                     rr.add(rf * rf);
                 }
@@ -558,11 +559,13 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
             }
         }
     } else {
-        // after a replacement: the sums of the restart, z formed as in the update
+        // after a replacement: the sums of the restart, z formed as in the
+        // update; mixed: the FP32 recurrence residual restarts from the true one
         if constexpr (MIXED) {
             CompSum rz, rr;
             for (int i = it.lo + tid; i < it.hi; i += NT) {
                 const float rf = d2f(ld_l2(r + i));
+                ri_v[i] = rf;
                 rz.add(rf * (__ldg(dinv + i) * rf));
                 rr.add(rf * rf);
             }
@@ -606,11 +609,10 @@ __device__ __forceinline__ void direction_item(Ctx& c, int ti) {
     const T be = T(ld_l2(&P->beta));
     T* pv = static_cast<T*>(bd.p);
     const T* dinv = static_cast<const T*>(bd.dinv);
-    const double* r = bd.r;
+    const T* r = static_cast<const T*>(bd.rin);
     int i = it.lo + int(threadIdx.x);
     for (; i + 3 * NT < it.hi; i += 4 * NT) {
-        double rv[4];
-        T dv[4], pq[4];
+        T rv[4], dv[4], pq[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = i + u * NT;
@@ -618,16 +620,12 @@ __device__ __forceinline__ void direction_item(Ctx& c, int ti) {
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            T zi;
-            if constexpr (sizeof(T) == 4) zi = dv[u] * d2f(rv[u]);
-            else zi = dv[u] * rv[u];
+            const T zi = dv[u] * rv[u];
             pv[i + u * NT] = init ? zi : fmadd(be, pq[u], zi);
         }
     }
     for (; i < it.hi; i += NT) {
-        T zi;
-        if constexpr (sizeof(T) == 4) zi = __ldg(dinv + i) * d2f(ld_l2(r + i));
-        else zi = __ldg(dinv + i) * ld_l2(r + i);
+        const T zi = __ldg(dinv + i) * ld_l2(r + i);
         pv[i] = init ? zi : fmadd(be, ld_l2(pv + i), zi);
     }
 }

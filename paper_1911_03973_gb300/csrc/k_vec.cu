@@ -8,11 +8,13 @@
 // last block also takes the iteration's scalar decisions (beta, stop) so that
 // the host never reads anything inside a graph chunk.
 //
-// GB300 runs FP64 at 1/64 of the FP32 rate, so the mixed-precision kernels
-// keep only what needs FP64 in FP64: the solution x and the residual r (the
-// two recurrences whose rounding would make the recurrence residual drift).
-// z = dinv r, the direction p and q = A p are FP32; the per-thread dot sums
-// use compensated FP32 (Neumaier) before the FP64 block reduction.
+// GB300 runs FP64 at 1/64 of the FP32 rate (two FP64 operations per SM and
+// clock), so the mixed-precision kernels keep only the solution x in FP64:
+// FP32 rounding of x would reach the residual amplified by the condition
+// number.  The recurrence residual r, z = dinv r, the direction p and q = A p
+// are FP32 (r's own rounding drift is not amplified and is removed at every
+// replacement by the FP64 true residual); the per-thread dot sums use
+// compensated FP32 (Neumaier) before the FP64 block reduction.
 #include <cstdint>
 #include <tuple>
 
@@ -187,10 +189,11 @@ k_direction64(int64_t n, double* __restrict__ p, const double* __restrict__ r, c
 }
 
 // ------------------------------------------------------------------ mixed
-// x += alpha p and r -= alpha q in FP64 (p, q FP32); z = dinv32 * (float) r;
-// sums r.z, r.r per thread in compensated FP32.
+// x += alpha p in FP64 (p FP32); r -= alpha q, z = dinv r in FP32; sums r.z,
+// r.r per thread in compensated FP32.  Two FP64 operations per node (the
+// widening of p and the FMA).
 __global__ void __launch_bounds__(NT, 4)
-k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, double* __restrict__ r,
+k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, float* __restrict__ r,
                const float* __restrict__ q, const float* __restrict__ dinv, double* __restrict__ part,
                Scalars* __restrict__ sc) {
     __shared__ double red[64];
@@ -198,29 +201,29 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
     pdl_wait();
     if (sc->done) return;
     const double al = sc->alpha;
+    const float alf = d2f(al);
     CompSum rz, rr;
     const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
     for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += st) {
-        const float4 pv = ldf4(p, g), qv = ldf4(q, g), dv = ldf4(dinv, g);
-        const D4 xv = ld4(x, g), rv = ld4(r, g);
-        D4 xo, ro;
+        const float4 pv = ldf4(p, g), qv = ldf4(q, g), dv = ldf4(dinv, g), rv = ldf4(r, g);
+        const D4 xv = ld4(x, g);
+        D4 xo;
+        float ro[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             xo.v[u] = fmadd(al, f2d(at(pv, u)), xv.v[u]);
-            const double ri = fmadd(-al, f2d(at(qv, u)), rv.v[u]);
-            ro.v[u] = ri;
-            const float rf = d2f(ri);
+            const float rf = __fmaf_rn(-alf, at(qv, u), at(rv, u));
+            ro[u] = rf;
             rz.add(rf * (at(dv, u) * rf));
             rr.add(rf * rf);
         }
         st4(x, g, xo);
-        st4(r, g, ro);
+        reinterpret_cast<float4*>(r)[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
     }
     for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
         x[i] = fmadd(al, f2d(p[i]), x[i]);
-        const double ri = fmadd(-al, f2d(q[i]), r[i]);
-        r[i] = ri;
-        const float rf = d2f(ri);
+        const float rf = __fmaf_rn(-alf, q[i], r[i]);
+        r[i] = rf;
         rz.add(rf * (dinv[i] * rf));
         rr.add(rf * rf);
     }
@@ -228,9 +231,9 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, d
     if (grid_sum2(a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) decide(sc, a, b);
 }
 
-// p = dinv32 * (float) r + beta p  (init: p = dinv32 * (float) r), FP32.
+// p = dinv r + beta p  (init: p = dinv r), FP32.
 __global__ void __launch_bounds__(NT, 4)
-k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r, const float* __restrict__ dinv,
+k_direction_mixed(int64_t n, float* __restrict__ p, const float* __restrict__ r, const float* __restrict__ dinv,
                   int init, const Scalars* __restrict__ sc) {
     pdl_trigger();
     pdl_wait();
@@ -239,13 +242,12 @@ k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r
     const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
     for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += 2 * st) {
         const bool two = g + st < n4;
-        D4 rv[2];
-        float4 dv[2], pv[2];
+        float4 rv[2], dv[2], pv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (h == 1 && !two) break;
             const int64_t k = g + h * st;
-            rv[h] = ld4(r, k); dv[h] = ldf4(dinv, k);
+            rv[h] = ldf4(r, k); dv[h] = ldf4(dinv, k);
             pv[h] = init ? make_float4(0.f, 0.f, 0.f, 0.f) : ldf4(p, k);
         }
 #pragma unroll
@@ -254,25 +256,26 @@ k_direction_mixed(int64_t n, float* __restrict__ p, const double* __restrict__ r
             float o[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float zi = at(dv[h], u) * d2f(rv[h].v[u]);
+                const float zi = at(dv[h], u) * at(rv[h], u);
                 o[u] = init ? zi : __fmaf_rn(be, at(pv[h], u), zi);
             }
             reinterpret_cast<float4*>(p)[g + h * st] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
     for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += st) {
-        const float zi = dinv[i] * d2f(r[i]);
+        const float zi = dinv[i] * r[i];
         p[i] = init ? zi : __fmaf_rn(be, p[i], zi);
     }
 }
 
 // After a true-residual replacement: sums r.z, r.r with z as the update
 // kernel of the same precision forms it; beta = r.z / rho, rho = r.z
-// (init: rho = r.z, beta = 0).
+// (init: rho = r.z, beta = 0).  Mixed: also r32 = (float) r, the start of
+// the FP32 recurrence residual.
 template <bool MIXED>
 __global__ void __launch_bounds__(NT)
 k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv_v, int init,
-          double* __restrict__ part, Scalars* __restrict__ sc) {
+          double* __restrict__ part, Scalars* __restrict__ sc, float* __restrict__ r32) {
     __shared__ double red[64];
     double a, b;
     if (MIXED) {
@@ -280,6 +283,7 @@ k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv
         CompSum rz, rr;
         for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
             const float rf = d2f(r[i]);
+            if (r32 != nullptr) r32[i] = rf;
             rz.add(rf * (dinv[i] * rf));
             rr.add(rf * rf);
         }
@@ -362,7 +366,7 @@ cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, co
                 : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
     } else {
         auto kern = k_update_mixed;
-        auto args = std::make_tuple(n, static_cast<double*>(x), static_cast<const float*>(p), static_cast<double*>(r),
+        auto args = std::make_tuple(n, static_cast<double*>(x), static_cast<const float*>(p), static_cast<float*>(r),
                                     static_cast<const float*>(q), static_cast<const float*>(dinv), part, sc);
         e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
                 : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
@@ -382,7 +386,7 @@ cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const vo
                 : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
     } else {
         auto kern = k_direction_mixed;
-        auto args = std::make_tuple(n, static_cast<float*>(p), static_cast<const double*>(r),
+        auto args = std::make_tuple(n, static_cast<float*>(p), static_cast<const float*>(r),
                                     static_cast<const float*>(dinv), init, static_cast<const Scalars*>(sc));
         e = pdl ? std::apply([&](auto... a) { return launch_pdl(kern, dim3(vec_grid(n)), dim3(NT), 0, st, a...); }, args)
                 : (std::apply([&](auto... a) { kern<<<vec_grid(n), NT, 0, st>>>(a...); }, args), cudaGetLastError());
@@ -392,9 +396,9 @@ cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const vo
 }
 
 cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part, Scalars* sc,
-                           cudaStream_t st, int* launches) {
-    if (vt == 0) k_restart<false><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
-    else k_restart<true><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc);
+                           cudaStream_t st, int* launches, float* r32) {
+    if (vt == 0) k_restart<false><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc, nullptr);
+    else k_restart<true><<<vec_grid(n), NT, 0, st>>>(n, r, dinv, init, part, sc, r32);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -127,17 +127,18 @@ cudaError_t launch_mark_dirichlet(const PlanDev& pd, int32_t* pnode, int64_t n_p
 cudaError_t launch_set_dirichlet(double* x, const int32_t* nd, const double* g, int64_t n_d,
                                  cudaStream_t st, int* launches);
 // x += alpha p; r -= alpha q; sums r.(dinv r), r.r; stop test (last block).
-// vt 0: x, r, dinv, p, q FP64.  vt 1: x, r FP64; p, q, dinv FP32.
+// vt 0: x, r, dinv, p, q FP64.  vt 1: x FP64; r, p, q, dinv FP32.
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q,
                           const void* dinv, double* part, Scalars* sc, cudaStream_t st, int* launches,
                           bool pdl = false);
-// p = dinv r + beta p  (init: p = dinv r); vt as launch_update.
+// p = dinv r + beta p  (init: p = dinv r); vt as launch_update (r FP32 for vt 1).
 cudaError_t launch_direction(int vt, int64_t n, void* p, const void* r, const void* dinv, int init,
                              Scalars* sc, cudaStream_t st, int* launches, bool pdl = false);
 // After a residual replacement: sums r.(dinv r) and r.r; beta = rz/rho, rho = rz
-// (init: rho = rz, beta = 0).  FP64 r; dinv FP64 (vt 0) or FP32 (vt 1).
+// (init: rho = rz, beta = 0).  FP64 r; dinv FP64 (vt 0) or FP32 (vt 1); for
+// vt 1, r32 (if not NULL) receives (float) r.
 cudaError_t launch_restart(int vt, int64_t n, const double* r, const void* dinv, int init, double* part,
-                           Scalars* sc, cudaStream_t st, int* launches);
+                           Scalars* sc, cudaStream_t st, int* launches, float* r32 = nullptr);
 // thr2 >= 0: new stop threshold; maxit >= 0: new cap; reset_iter: iter = 0.
 // Always clears done / reason.
 cudaError_t launch_control(Scalars* sc, double thr2, int64_t maxit, int reset_iter, cudaStream_t st, int* launches);
@@ -205,7 +206,8 @@ struct BatchDev {
     const double* b = nullptr;             // FP64 load vector
     const void* dinv = nullptr;            // inverse Jacobi diagonal, inner type
     double* x = nullptr;
-    double* r = nullptr;
+    double* r = nullptr;                   // FP64 true residual
+    void* rin = nullptr;                   // recurrence residual, inner type (r itself for FP64)
     void* p = nullptr;                     // direction, inner type
     void* q = nullptr;                     // A p, inner type
     void* halo = nullptr;                  // halo partials, inner type

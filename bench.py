@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--learned", action="store_true",
                     help="also train the learned preconditioner (257^2) and deploy it (1025^2, 2049^2)")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "batch", "mpnn"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -444,6 +444,11 @@ def run_ours(args):
             q32 = torch.empty_like(p32)
             x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
             r64 = torch.empty_like(x64)
+            if args.profile_kernel == "vec":
+                # three mixed-precision CG iterations, launched one by one
+                ebe.ebe_solve(h, x, rtol=1e-300, maxit=3, precision=ebe.EBE_PREC_MIXED, chunk=1, use_graph=False)
+                torch.cuda.synchronize()
+                return None
             for _ in range(3):
                 if args.profile_kernel == "apply32":
                     ebe.ebe_apply(h, p32, q32)

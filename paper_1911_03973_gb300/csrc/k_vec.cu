@@ -350,9 +350,21 @@ __global__ void k_control(Scalars* sc, double thr2, int64_t maxit, int reset_ite
 
 }  // namespace
 
+// One wave of CTAs: the update and direction kernels hold 64 registers per
+// thread (4 CTAs of 256 threads per SM), and a second wave would only add a
+// tail and more block partials.  Capped at the 1216 partials the reductions
+// have room for.
 int vec_grid(int64_t n) {
-    int64_t g = (n + NT - 1) / NT;
-    return int(g < 1 ? 1 : (g > 1216 ? 1216 : g));
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1)
+            sms = 152;
+        cap = sms * 4 > 1216 ? 1216 : sms * 4;
+    }
+    const int64_t g = (n + NT - 1) / NT;
+    return int(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 cudaError_t launch_update(int vt, int64_t n, void* x, const void* p, void* r, const void* q, const void* dinv,

@@ -193,6 +193,9 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
         std::vector<uint32_t> filled;   // table slots in use, cleared slot by slot after each patch
         std::vector<uint64_t> used;
         std::vector<int> colour(kPatch);
+        std::vector<int> order, gidx, first_set, set_list, set_fill, perm, bank, visit;
+        std::vector<int32_t> renum;
+        std::vector<uint32_t> set_used;
         auto slot_of = [&](int32_t g) {
             uint32_t hsh = (uint32_t(g) * 2654435761u) >> 19;   // 13 bits
             while (tkey[hsh] != g && tkey[hsh] != -1) hsh = (hsh + 1) & (kTable - 1);
@@ -252,19 +255,101 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             }
             out.n_col = n_col;
             // slots: elements grouped by colour, Morton order within a colour
-            int slot = 0;
+            order.clear();
             for (int c = 0; c < n_col; ++c) {
-                out.col_ptr.push_back(slot);
-                for (int s = 0; s < n_el; ++s) {
-                    if (colour[s] != c) continue;
-                    const int64_t gs = e0 + slot;
-                    P.slot_elem[gs] = el[s];
-                    const int32_t* v = m.elems + int64_t(el[s]) * nb;
-                    for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(local(v[i]));
-                    ++slot;
-                }
+                out.col_ptr.push_back(int32_t(order.size()));
+                for (int s = 0; s < n_el; ++s)
+                    if (colour[s] == c) order.push_back(s);
             }
-            out.col_ptr.push_back(slot);
+            out.col_ptr.push_back(int32_t(order.size()));
+            // Local numbering for the shared-memory banks.  The patch kernel
+            // gives 32 consecutive slots to a warp; in a colour round its
+            // lanes read-modify-write the node sums of vertex r of their
+            // elements, and they gather x the same way.  Those 32 nodes are
+            // distinct, and the accesses take one shared-memory cycle when
+            // their local ids are distinct modulo 32 (the bank), more
+            // otherwise.  Greedily, in order of first appearance, each node
+            // takes a bank that none of its access sets (warp group x colour
+            // x vertex) holds yet, among the banks with free ids in its block
+            // (owned or shared); the ids then follow the banks.  Sums are taken
+            // in colour order whatever the numbering, so results do not change.
+            {
+                const int ns = int(order.size());
+                gidx.assign(ns, 0);
+                int n_grp = 0;
+                for (int q = 0; q < ns; ++q) {
+                    if (q > 0 && (q % 32 == 0 || colour[order[q]] != colour[order[q - 1]])) ++n_grp;
+                    gidx[q] = n_grp;
+                }
+                ++n_grp;
+                const int n_set = n_grp * nb;
+                // node -> access sets (CSR)
+                first_set.assign(n_nodes + 1, 0);
+                for (int q = 0; q < ns; ++q) {
+                    const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
+                    for (int i = 0; i < nb; ++i) ++first_set[local(v[i]) + 1];
+                }
+                for (int l = 0; l < n_nodes; ++l) first_set[l + 1] += first_set[l];
+                set_list.assign(first_set[n_nodes], 0);
+                set_fill.assign(first_set.begin(), first_set.end() - 1);
+                visit.clear();
+                for (int q = 0; q < ns; ++q) {
+                    const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
+                    for (int i = 0; i < nb; ++i) {
+                        const int l = local(v[i]);
+                        if (set_fill[l] == first_set[l]) visit.push_back(l);   // first appearance
+                        set_list[set_fill[l]++] = gidx[q] * nb + i;
+                    }
+                }
+                set_used.assign(n_set, 0u);
+                int cap[2][32] = {};
+                for (int l = 0; l < n_nodes; ++l) ++cap[l < n_owned ? 0 : 1][l % 32];
+                bank.assign(n_nodes, 0);
+                for (int l : visit) {
+                    const int blk = l < n_owned ? 0 : 1;
+                    uint32_t busy = 0;
+                    for (int k = first_set[l]; k < first_set[l + 1]; ++k) busy |= set_used[set_list[k]];
+                    uint32_t open = 0;
+                    for (int b = 0; b < 32; ++b) open |= (cap[blk][b] > 0 ? 1u : 0u) << b;
+                    int best;
+                    if (open & ~busy) {
+                        best = __builtin_ctz(open & ~busy);
+                    } else {   // every open bank conflicts somewhere: fewest conflicting sets
+                        int cost[32] = {};
+                        for (int k = first_set[l]; k < first_set[l + 1]; ++k)
+                            for (uint32_t u = set_used[set_list[k]]; u; u &= u - 1) ++cost[__builtin_ctz(u)];
+                        best = -1;
+                        for (uint32_t u = open; u; u &= u - 1) {
+                            const int b = __builtin_ctz(u);
+                            if (best < 0 || cost[b] < cost[best]) best = b;
+                        }
+                    }
+                    bank[l] = best;
+                    --cap[blk][best];
+                    for (int k = first_set[l]; k < first_set[l + 1]; ++k) set_used[set_list[k]] |= 1u << best;
+                }
+                // ids by bank, in each block in order of first appearance
+                int next[2][32];
+                for (int b = 0; b < 32; ++b) {
+                    next[0][b] = b;
+                    next[1][b] = n_owned + ((b - n_owned % 32) % 32 + 32) % 32;
+                }
+                perm.assign(n_nodes, 0);
+                for (int l : visit) {
+                    const int blk = l < n_owned ? 0 : 1;
+                    perm[l] = next[blk][bank[l]];
+                    next[blk][bank[l]] += 32;
+                }
+                renum.resize(n_nodes);
+                for (int l = 0; l < n_nodes; ++l) renum[perm[l]] = lnodes[l];
+                for (int l = 0; l < n_nodes; ++l) lnodes[l] = renum[l];
+            }
+            for (int q = 0; q < int(order.size()); ++q) {
+                const int64_t gs = e0 + q;
+                P.slot_elem[gs] = el[order[q]];
+                const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
+                for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(perm[local(v[i])]);
+            }
             // each table starts on a 16-byte boundary (bulk copies need it)
             while (lnodes.size() % 4 != 0) lnodes.push_back(lnodes[0]);
             reset();

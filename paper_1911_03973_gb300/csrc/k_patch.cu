@@ -299,12 +299,12 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
     }
 }
 
-// FP64 variant: the element matrices are read straight from global memory
-// (coalesced slot-major runs) inside the colour rounds, products folded into
-// the node sums.  GB300 runs FP64 at 1/64 of the FP32 rate, so this pass is
-// bound by FP64 issue rather than by bytes; without the 72 KB (triangles) or
-// 128 KB (tetrahedra) matrix tile in shared memory, up to eight CTAs share an
-// SM and hide the latency of the dependent FMA chains.
+// FP64 variant: each thread reads the element matrices of its slots straight
+// from global memory (coalesced slot-major runs) and forms their products
+// A_e x_e; the colour rounds then add them into the node sums.  GB300 runs
+// FP64 at 1/64 of the FP32 rate, so this pass is bound by FP64 issue rather
+// than by bytes; without a matrix tile in shared memory four CTAs (three for
+// tetrahedra) share an SM and hide the latency of the FMA chains.
 struct Patch64Smem {
     uint32_t red, co, G, xs, bs, acc, total;
 };
@@ -367,25 +367,35 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
         if (lb < m.n_nodes) { Gs[lb] = gb; xs[lb] = xb; acc[lb] = 0.0; if (kRes) bs[lb] = bb; }
     }
     __syncthreads();
+    // products of all slots first, while every thread is busy (a colour round
+    // keeps about one thread in eight at work); the rounds only add them
+    double y[kEPT][NB];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
+        double a[sym_count(NB)];
+#pragma unroll
+        for (int t = 0; t < sym_count(NB); ++t) a[t] = ok ? __ldg(A + t * ns + slot0 + s) : 0.0;
+        double xe[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) xe[j] = xs[ln[k][j]];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            double v = a[sym_index(NB, r, 0)] * xe[0];
+#pragma unroll
+            for (int j = 1; j < NB; ++j) v = fmadd(a[sym_index(NB, r, j)], xe[j], v);
+            y[k][r] = v;
+        }
+    }
     for (int c = 0; c < m.n_col; ++c) {
         const int lo = co[c], hi = co[c + 1];
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
             const int s = tid + k * NT;
             if (s >= lo && s < hi) {
-                double a[sym_count(NB)];
 #pragma unroll
-                for (int t = 0; t < sym_count(NB); ++t) a[t] = __ldg(A + t * ns + slot0 + s);
-                double xe[NB];
-#pragma unroll
-                for (int j = 0; j < NB; ++j) xe[j] = xs[ln[k][j]];
-#pragma unroll
-                for (int r = 0; r < NB; ++r) {
-                    double v = acc[ln[k][r]];
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) v = fmadd(a[sym_index(NB, r, j)], xe[j], v);
-                    acc[ln[k][r]] = v;
-                }
+                for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
             }
         }
         __syncthreads();

@@ -602,12 +602,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n, "n_elements": n_e,
-                   "n_b": dim + 1, "solver": "Jacobi-PCG, FP32 A_e/r/p/q, FP64 x, FP64 residual replacement",
-                   "rtol": args.rtol, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) * (dim + 2) // 2 * 12) / 1e6),
-                   "value_def": "algorithmic bytes of the step / step time"},
-        "pcg": {"ms_to_1e-8": round(ms_step, 2), "iterations": info0["iterations"],
+        "config": workload_config(args, n_n, n_e, dim, world),
+        "pcg": {"solver": "Jacobi-PCG, FP32 A_e/r/p/q, FP64 x, FP64 residual replacement",
+                "ms_to_1e-8": round(ms_step, 2), "iterations": info0["iterations"],
                 "true_residuals": info0["true_residuals"], "rel_residual": info0["rel_residual"],
                 "plain_fp64_ms": round(ms_plain, 2) if ms_plain else None,
                 "plain_fp64_iterations": pinfo[-1]["iterations"] if pinfo else None,
@@ -655,6 +652,14 @@ def oracle_sample(prob, m, iters=10):
                       f"iterations ({info['residual_evals']} Algorithm-1 residuals), single thread"}
 
 
+def workload_config(args, n_n: int, n_e: int, dim: int, world: int) -> dict:
+    """The workload both arms report (the same dict for the same arguments)."""
+    return {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n, "n_elements": n_e,
+            "n_b": dim + 1, "rtol": args.rtol, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (A_e FP64 + FP32 = %.0f MB)" % ((n_e * (dim + 1) * (dim + 2) // 2 * 12) / 1e6),
+            "value_def": "algorithmic bytes of the step / step time"}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     world, rank, _ = dist_env()
@@ -674,8 +679,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"square{args.n}_jitter0.2_nu{args.nu:g}_tri", "n_nodes": n_n,
-                       "n_elements": int(prob["elems"].shape[0])},
+            "config": workload_config(args, n_n, int(prob["elems"].shape[0]), dim, world),
             "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": samples[0]["sample"]},
             "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

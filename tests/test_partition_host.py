@@ -68,3 +68,35 @@ def test_validation_errors_without_gpu(ebe):
     with pytest.raises(ebe.EbeError) as ei:       # ebe_create validates before touching a device
         ebe.ebe_create(c, np.array([[0, 1, 99]], np.int32))
     assert ei.value.status == 2
+
+
+def _bank_wavefronts(P, group=32, banks=32):
+    """Shared-memory cycles of the colour rounds' node-sum accesses, as the FP32
+    patch kernel issues them: 32 consecutive slots per warp, one access per
+    element vertex, split by colour; a cycle per distinct address in the most
+    loaded bank.  Returns (cycles, the one-cycle-per-access minimum)."""
+    K = P["patch_elems"]
+    cycles = ideal = 0
+    for p, (node_off, n_nodes, n_owned, halo_off, n_el, col_off, n_col, _) in enumerate(P["patch_meta"]):
+        co = P["col_ptr"][col_off:col_off + n_col + 1]
+        colour = np.repeat(np.arange(n_col), np.diff(co))
+        loc = P["lconn"][:, p * K:p * K + n_el].astype(np.int64)
+        for g0 in range(0, n_el, group):
+            sl = slice(g0, min(g0 + group, n_el))
+            for c in np.unique(colour[sl]):
+                sel = colour[sl] == c
+                for i in range(loc.shape[0]):
+                    b = np.bincount(loc[i, sl][sel] % banks, minlength=banks)
+                    cycles += int(b.max())
+                    ideal += 1
+    return cycles, ideal
+
+
+def test_local_numbering_spreads_banks(ebe):
+    # local node ids are chosen per patch so that a warp's accesses fall in
+    # distinct shared-memory banks where possible; numbering nodes in first-touch
+    # order instead costs about 2.7x the minimum on this mesh
+    c, e = meshgen.square_tri(257)
+    c = meshgen.jitter_interior(c, 1 / 256, 0.2, seed=2)
+    cycles, ideal = _bank_wavefronts(ebe.ebe_partition_export(c, e))
+    assert cycles <= 2.1 * ideal, (cycles, ideal)

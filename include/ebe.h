@@ -74,12 +74,12 @@ enum {
 enum {
     EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG                                          */
     EBE_PREC_MIXED = 1    /* the operator pass runs on FP32 A_e (difference form) with the
-                             search direction p, q = A p and z = dinv r in FP32; the
-                             solution x and the residual r stay FP64; dot products add
-                             per thread in compensated FP32 and across threads in FP64;
-                             r is replaced by the FP64 true residual (FP64 A_e) whenever
-                             the recurrence residual has dropped by the factor `delta`
-                             since the last replacement (needs EBE_STORE_MIXED)        */
+                             search direction p, q = A p, the recurrence residual r and
+                             z = dinv r in FP32; the solution x stays FP64; dot products
+                             add per thread in compensated FP32 and across threads in
+                             FP64; r is replaced by the FP64 true residual (FP64 A_e)
+                             whenever the recurrence residual has dropped by the factor
+                             `delta` since the last replacement (needs EBE_STORE_MIXED) */
 };
 
 /* Scatter strategies of the residual (ebe_residual_variant). */

@@ -24,8 +24,8 @@
 // CTA i mod gridDim, so the live work is spread evenly however many problems
 // have finished.
 // The per-problem decisions follow the single-problem solver: mixed
-// precision keeps x and r in FP64 and replaces the recurrence residual by
-// the FP64 true residual whenever it has dropped by delta; a problem is done
+// precision keeps x in FP64 and the recurrence residual in FP32, and replaces
+// it by the FP64 true residual whenever it has dropped by delta; a problem is done
 // when its true relative residual reaches rtol.  Problems that are done cost
 // nothing but a shared-memory lookup per item.  Every sum is taken in a fixed
 // order, so a solve is bitwise reproducible (for any launch shape with the

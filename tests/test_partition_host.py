@@ -68,6 +68,18 @@ def test_validation_errors_without_gpu(ebe):
     with pytest.raises(ebe.EbeError) as ei:       # ebe_create validates before touching a device
         ebe.ebe_create(c, np.array([[0, 1, 99]], np.int32))
     assert ei.value.status == 2
+    with pytest.raises(ebe.EbeError) as ei:       # an empty mesh has nothing to partition
+        ebe.ebe_partition_export(c, np.zeros((0, 3), np.int32))
+    assert ei.value.status == 1
+
+
+def test_single_element_mesh(ebe):
+    # one triangle: one patch of one slot, every node owned, no halo
+    c = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    e = np.array([[0, 1, 2]], np.int32)
+    P = ebe.ebe_partition_export(c, e)
+    check_partition(P, c, e)
+    assert P["n_patches"] == 1 and P["n_shared"] == 0 and P["patch_meta"][0][2] == 3
 
 
 def _bank_wavefronts(P, group=32, banks=32):

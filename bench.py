@@ -314,6 +314,57 @@ def run_batch(args, dev, stream, profile=False):
 
 
 # ----------------------------------------------------------------------------- learned preconditioner
+def run_paper_experiment(dev, stream):
+    """The paper's own timed experiment (Sec. 3), as context: the 1025^2 square,
+    nu = 0, f = 1, u = 1 on the boundary; the element matrix arrays K_e, M_e and
+    124 iterations of Richardson and of the three-level Chebyshev method with
+    the spectral bounds of the structured mesh.  The paper quotes about 5 s per
+    array and about 50 s per method in MATLAB on hardware it does not name."""
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    from paper_1911_03973_gb300 import meshgen
+    n = 1025
+    prob = meshgen.config_square_f1(n, nu=0.0, g_value=1.0)
+    n_n, n_e, nb = prob["coords"].shape[0], prob["elems"].shape[0], prob["elems"].shape[1]
+    lam1 = 8.0 * math.sin(math.pi / (2 * (n - 1))) ** 2          # bounds of the stencil spectrum
+    lam2 = 8.0 * math.sin((n - 2) * math.pi / (2 * (n - 1))) ** 2
+    out = {"workload": "square1025_f1_nu0_u1 (Sec. 3 experiment)", "n_nodes": n_n, "n_elements": n_e,
+           "paper_matlab_s": {"K_e_array": 5.0, "M_e_array": 5.0, "124_iterations_per_method": 50.0}}
+    with torch.cuda.stream(stream):
+        h = ebe.ebe_create(prob["coords"], prob["elems"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+        K = torch.empty(n_e * nb * nb, dtype=torch.float64, device=dev)
+        M = torch.empty_like(K)
+        x = torch.zeros(n_n, dtype=torch.float64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+        def timed(fn, reps=3):
+            fn()
+            best = None
+            for _ in range(reps):
+                ev[0].record(stream)
+                fn()
+                ev[1].record(stream)
+                ev[1].synchronize()
+                t = ev[0].elapsed_time(ev[1])
+                best = t if best is None else min(best, t)
+            return round(best, 3)
+        out["K_e_M_e_arrays_ms"] = timed(lambda: ebe.ebe_element_matrices(h, K, M))
+        out["assemble_fp64_ms"] = timed(lambda: ebe.ebe_assemble(h, ebe.EBE_STORE_FP64))
+
+        def rich():
+            x.zero_()
+            ebe.ebe_richardson(h, x, 124, 2.0 / (lam1 + lam2))
+
+        def cheb3():
+            x.zero_()
+            ebe.ebe_chebyshev3(h, x, 124, lam1, lam2)
+        out["richardson_124_ms"] = timed(rich)
+        out["chebyshev3_124_ms"] = timed(cheb3)
+        ebe.ebe_destroy(h)
+    return out
+
+
 def run_learned(args, dev, stream, profile=False):
     """Train the message-passing preconditioner on 257^2 jittered squares
     (random Fourier f, nu ~ U[0, 10]; 4 problems x 12 residual/error pairs
@@ -581,6 +632,7 @@ def run_ours(args):
     if not args.no_batch:
         batched = run_batch(args, dev, stream)
     learned_res = run_learned(args, dev, stream) if args.learned else None
+    paper_exp = run_paper_experiment(dev, stream) if rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -631,6 +683,8 @@ def run_ours(args):
         line["learned"] = learned_res
     if variants:
         line["residual_variants_fp64"] = variants
+    if paper_exp:
+        line["paper_experiment"] = paper_exp
     print(json.dumps(line), flush=True)
     return line
 

@@ -27,6 +27,12 @@ in [17, 513] nodes, seed 4) solved by the batched persistent solver in mixed
 precision with an autotuned launch shape, against the same problems solved
 one by one with ebe_solve (plain FP64 and mixed) and the batched FP64 solve.
 
+"cube129" (skip with --no-cube): the 3D configuration, 129^3 nodes in 6 Kuhn
+tetrahedra per cell, mixed-precision and plain FP64 solves to 1e-8 and the
+operator rooflines.  "paper_experiment": the paper's own timed experiment
+(Sec. 3, the 1025^2 square: element arrays and 124 Richardson / Chebyshev
+iterations), beside the MATLAB times the paper quotes, as context.
+
 "learned" (with --learned): the message-passing preconditioner trained on
 257^2 squares and deployed in flexible CG on 1025^2 and 2049^2, against
 flexible CG with Jacobi and Jacobi-PCG (plain FP64 and mixed).
@@ -68,6 +74,7 @@ def parse():
     ap.add_argument("--variants", action="store_true", help="also time the comparison scatters")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload (256 independent squares)")
     ap.add_argument("--batch-problems", type=int, default=256)
+    ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
     ap.add_argument("--learned", action="store_true",
                     help="also train the learned preconditioner (257^2) and deploy it (1025^2, 2049^2)")
     ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "batch", "mpnn"], default=None,
@@ -314,6 +321,60 @@ def run_batch(args, dev, stream, profile=False):
 
 
 # ----------------------------------------------------------------------------- learned preconditioner
+def run_cube(args, dev, stream):
+    """The 3D configuration: the unit cube with 129^3 nodes, 6 Kuhn tetrahedra per
+    cell (12,582,912 elements), nu = 0.5, f = 1 + 0.1 N(0,1) per node (seed 3),
+    Dirichlet 0 on z = 0: mixed-precision and plain FP64 Jacobi-PCG to 1e-8
+    (CUDA events around ebe_solve, element matrices assembled beforehand) and
+    the per-launch times of the FP32 operator and the FP64 residual."""
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    from paper_1911_03973_gb300 import meshgen
+    prob = meshgen.config_cube_noise(129, nu=0.5, seed=3)
+    n_n, dim = prob["coords"].shape
+    n_e = prob["elems"].shape[0]
+    m = bytes_model(dim, n_n, n_e)
+    out = {"workload": "cube129_kuhn_nu0.5_noise0.1_tet", "n_nodes": n_n, "n_elements": n_e, "n_b": dim + 1}
+    with torch.cuda.stream(stream):
+        h = ebe.ebe_create(prob["coords"], prob["elems"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+        ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        x = torch.zeros(n_n, dtype=torch.float64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for key, prec in (("mixed", ebe.EBE_PREC_MIXED), ("plain_fp64", ebe.EBE_PREC_FP64)):
+            times = []
+            for rep_ in range(3):
+                x.zero_()
+                ev[0].record(stream)
+                info = ebe.ebe_solve(h, x, rtol=args.rtol, precision=prec)
+                ev[1].record(stream)
+                ev[1].synchronize()
+                if info["status"] != "EBE_OK":
+                    raise RuntimeError(f"cube solve failed: {info}")
+                if rep_ > 0:
+                    times.append(ev[0].elapsed_time(ev[1]))
+            out[key] = {"ms_to_1e-8": round(min(times), 2), "iterations": info["iterations"],
+                        "true_residuals": info["true_residuals"], "rel_residual": info["rel_residual"]}
+        out["speedup_vs_plain"] = round(out["plain_fp64"]["ms_to_1e-8"] / out["mixed"]["ms_to_1e-8"], 3)
+        p32 = torch.rand(n_n, dtype=torch.float32, device=dev)
+        q32 = torch.empty_like(p32)
+        x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
+        r64 = torch.empty_like(x64)
+        ebe.ebe_time_operator(h, p32, q32, True, 5)
+        a32 = ebe.ebe_time_operator(h, p32, q32, True, 20)
+        ebe.ebe_time_operator(h, x64, r64, False, 5)
+        r64t = ebe.ebe_time_operator(h, x64, r64, False, 20)
+        peak = peaks()[0]
+        g32 = m["apply32"] / (sum(a32) / 1e3) / 1e9
+        g64 = m["residual64"] / (sum(r64t) / 1e3) / 1e9
+        out["apply32"] = {"ms_per_launch": [round(a32[0], 5), round(a32[1], 5)], "bytes_per_launch": m["apply32"],
+                          "gbs": round(g32, 1), "frac": round(g32 / peak, 4)}
+        out["residual64"] = {"ms_per_launch": [round(r64t[0], 5), round(r64t[1], 5)],
+                             "bytes_per_launch": m["residual64"], "gbs": round(g64, 1), "frac": round(g64 / peak, 4)}
+        ebe.ebe_destroy(h)
+    return out
+
+
 def run_paper_experiment(dev, stream):
     """The paper's own timed experiment (Sec. 3), as context: the 1025^2 square,
     nu = 0, f = 1, u = 1 on the boundary; the element matrix arrays K_e, M_e and
@@ -633,6 +694,7 @@ def run_ours(args):
         batched = run_batch(args, dev, stream)
     learned_res = run_learned(args, dev, stream) if args.learned else None
     paper_exp = run_paper_experiment(dev, stream) if rank == 0 else None
+    cube = run_cube(args, dev, stream) if rank == 0 and not args.no_cube else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -683,6 +745,8 @@ def run_ours(args):
         line["learned"] = learned_res
     if variants:
         line["residual_variants_fp64"] = variants
+    if cube:
+        line["cube129"] = cube
     if paper_exp:
         line["paper_experiment"] = paper_exp
     print(json.dumps(line), flush=True)

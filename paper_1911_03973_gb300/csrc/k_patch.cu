@@ -13,6 +13,8 @@
 //   * the threads add A_e x_e into per-node shared-memory sums colour by
 //     colour: within a colour no two elements share a node, so there are no
 //     atomics and the order of the additions is fixed (bitwise reproducible);
+//     meshes with many colours per patch (tetrahedra) give each warp its own
+//     copy of the sums instead, merged in warp order after one barrier;
 //   * they write the result of every owned node (all of its elements are in
 //     this patch) and the partial sum of every shared node to its halo slot.
 // The fix-up pass adds the halo partials of each shared node in patch order.
@@ -56,7 +58,8 @@ using tma::smem_addr;
 struct PatchSmem {
     uint32_t bar, flag, red, co, A, L, G, xs, bs, acc, total;
 };
-template <typename T, int NB>
+constexpr int kWarpCopies = 8;   // node-sum copies of the per-warp scheme (one per warp)
+template <typename T, int NB, bool WARPS>
 __host__ __device__ constexpr PatchSmem patch_layout(int max_nodes) {
     PatchSmem s{};
     const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
@@ -70,11 +73,15 @@ __host__ __device__ constexpr PatchSmem patch_layout(int max_nodes) {
     s.xs = s.G + gcap * 4;
     s.bs = (s.xs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
     s.acc = (s.bs + gcap * uint32_t(sizeof(T)) + 15) / 16 * 16;
-    s.total = (s.acc + gcap * uint32_t(sizeof(T)) + 127) / 128 * 128;
+    s.total = (s.acc + (WARPS ? kWarpCopies : 1) * gcap * uint32_t(sizeof(T)) + 127) / 128 * 128;
     return s;
 }
 
 constexpr int kPatchThreads = 256;
+static_assert(kPatchThreads / 32 == kWarpCopies, "one node-sum copy per warp");
+// Meshes whose patches need more colours than this add their element
+// products through per-warp copies of the node sums instead of colour rounds.
+constexpr int kWarpSchemeColours = 16;
 constexpr int kEPT = kPatch / kPatchThreads;     // elements owned by a thread
 
 // One patch per CTA, several CTAs per SM so that one CTA's copies overlap
@@ -83,7 +90,7 @@ constexpr int kEPT = kPatch / kPatchThreads;     // elements owned by a thread
 // tid + 256 k and keeps their local node ids and x values in registers, so a
 // colour round only reads the element matrix entries from shared memory and
 // updates the node sums.
-template <typename T, int NB, int MODE>
+template <typename T, int NB, int MODE, bool WARPS>
 __global__ void __launch_bounds__(kPatchThreads)
 k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
         T* __restrict__ out, T* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
@@ -91,7 +98,7 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     constexpr int NT = kPatchThreads;
     constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
     extern __shared__ __align__(128) unsigned char smem[];
-    const PatchSmem L = patch_layout<T, NB>(pd.max_nodes);
+    const PatchSmem L = patch_layout<T, NB, WARPS>(pd.max_nodes);
     volatile int* flag = reinterpret_cast<volatile int*>(smem + L.flag);
     double* red = reinterpret_cast<double*>(smem + L.red);
     int* co = reinterpret_cast<int*>(smem + L.co);
@@ -154,7 +161,7 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
             if (l < m.n_nodes) {
                 Gs[l] = gr[u];
                 xs[l] = xv[u];
-                acc[l] = T(0);
+                if (!WARPS) acc[l] = T(0);
                 if (kRes) bs[l] = bv[u];
             }
         }
@@ -166,49 +173,94 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     while (!mbar_try_wait(bar, 0)) {
     }                                             // completed already: acquire for this thread
 
-    // my slots: local node ids and x values in registers
-    int ln[kEPT][NB];
-    T xe[kEPT][NB];
+    if constexpr (WARPS) {
+        // Many colours (tetrahedra: about 30 per patch) would mean as many
+        // block barriers with little work between them.  Instead warp w adds
+        // the elements of colours w, w + 8, ... into its own copy of the node
+        // sums (a colour's elements share no node; a warp sync separates its
+        // colours); after one barrier the node value is the sum of the 8 copies
+        // in warp order (a fixed order: bitwise reproducible).
+        const int gcap = (pd.max_nodes + 3) / 4 * 4;
+        const int warp = tid >> 5, lane = tid & 31;
+        T* accw = acc + warp * gcap;
+        for (int l = lane; l < m.n_nodes; l += 32) accw[l] = T(0);
+        __syncwarp();
+        for (int c = warp; c < m.n_col; c += kWarpCopies) {
+            const int lo = co[c], hi = co[c + 1];
+            for (int s = lo + lane; s < hi; s += 32) {
+                int ln[NB];
+                T xe[NB];
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int s = tid + k * NT;
-        const bool ok = s < m.n_el;
+                for (int i = 0; i < NB; ++i) {
+                    ln[i] = int(Ls[i * kPatch + s]);
+                    xe[i] = xs[ln[i]];
+                }
+                // difference form: the diagonal slot holds the row sum s_r,
+                // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r)
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            ln[k][i] = ok ? int(Ls[i * kPatch + s]) : 0;
-            xe[k][i] = xs[ln[k][i]];
+                for (int r = 0; r < NB; ++r) {
+                    T v = As[sym_index(NB, r, r) * kPatch + s] * xe[r];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j != r) v = fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[j] - xe[r], v);
+                    accw[ln[r]] += v;
+                }
+            }
+            __syncwarp();
         }
-    }
-    // FP32: every thread forms the products of its slots at once, then the
-    // colour rounds only add them into the node sums (short rounds).
-    // Difference form: the diagonal slot holds the row sum s_r,
-    // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
-    // difference is exact in FP32 and no accuracy is lost to cancellation.
-    T y[kEPT][NB];
+        __syncthreads();
+        for (int l = tid; l < m.n_nodes; l += NT) {
+            T v = acc[l];
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int s = tid + k * NT;
-        const bool ok = s < m.n_el;
-#pragma unroll
-        for (int r = 0; r < NB; ++r) {
-            T v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[k][r] : T(0);
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
-            y[k][r] = v;
+            for (int w = 1; w < kWarpCopies; ++w) v += acc[w * gcap + l];
+            acc[l] = v;
         }
-    }
-    for (int c = 0; c < m.n_col; ++c) {
-        const int lo = co[c], hi = co[c + 1];
+        __syncthreads();
+    } else {
+        // my slots: local node ids and x values in registers
+        int ln[kEPT][NB];
+        T xe[kEPT][NB];
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
             const int s = tid + k * NT;
-            if (s >= lo && s < hi) {
+            const bool ok = s < m.n_el;
 #pragma unroll
-                for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
+            for (int i = 0; i < NB; ++i) {
+                ln[k][i] = ok ? int(Ls[i * kPatch + s]) : 0;
+                xe[k][i] = xs[ln[k][i]];
             }
         }
-        __syncthreads();
+        // FP32: every thread forms the products of its slots at once, then the
+        // colour rounds only add them into the node sums (short rounds).
+        // Difference form: the diagonal slot holds the row sum s_r,
+        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
+        // difference is exact in FP32 and no accuracy is lost to cancellation.
+        T y[kEPT][NB];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            const bool ok = s < m.n_el;
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                T v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[k][r] : T(0);
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
+                y[k][r] = v;
+            }
+        }
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
+                }
+            }
+            __syncthreads();
+        }
     }
 
     // owned nodes: final value; shared nodes: halo partial
@@ -446,12 +498,13 @@ cudaError_t run_patch64(const PlanDev& pd, const double* A, const double* x, con
     return cudaGetLastError();
 }
 
-template <typename T, int NB, int MODE>
-cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
-                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev, bool pdl) {
-    const size_t sm = patch_layout<T, NB>(pd.max_nodes).total;
+template <typename T, int NB, int MODE, bool WARPS>
+cudaError_t run_patch_as(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
+                         const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev,
+                         bool pdl) {
+    const size_t sm = patch_layout<T, NB, WARPS>(pd.max_nodes).total;
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;   // a patch does not fit in shared memory
-    auto kern = k_patch<T, NB, MODE>;
+    auto kern = k_patch<T, NB, MODE, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], st);
@@ -468,6 +521,17 @@ cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* 
     if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();
+}
+
+// Colour rounds for meshes with few colours per patch (triangles: 8; measured
+// 66.5 against 75.5 us per 2049^2 application), per-warp node-sum copies for
+// many (Kuhn tetrahedra: about 30; 142 against 205 us per 129^3 application).
+template <typename T, int NB, int MODE>
+cudaError_t run_patch(const PlanDev& pd, const T* A, const T* x, const T* b, T* out, T* halo, double* part,
+                      const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev, bool pdl) {
+    if (pd.max_col > kWarpSchemeColours)
+        return run_patch_as<T, NB, MODE, true>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
+    return run_patch_as<T, NB, MODE, false>(pd, A, x, b, out, halo, part, stop, sc, st, launches, ev, pdl);
 }
 
 template <typename T, int NB>

@@ -18,6 +18,13 @@ constexpr int kPatch = 1024;
 constexpr uint32_t kDirichletBit = 0x80000000u;
 constexpr int32_t kNodeMask = 0x7fffffff;
 constexpr int kMaxColours = 64;
+// Meshes whose patches need more colours than this (tetrahedra) have the FP32
+// patch pass add element products through per-warp copies of the node sums:
+// a warp walks each of its colours from the colour's first slot, 32 slots at a
+// time.  With fewer colours it runs colour rounds, a warp holding 32
+// consecutive slots counted from the patch's first slot.  The planner numbers
+// local nodes for the shared-memory banks of the same access groups.
+constexpr int kWarpSchemeColours = 16;
 
 // Per-patch metadata (32 bytes).
 struct PatchMeta {

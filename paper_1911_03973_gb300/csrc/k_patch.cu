@@ -79,9 +79,7 @@ __host__ __device__ constexpr PatchSmem patch_layout(int max_nodes) {
 
 constexpr int kPatchThreads = 256;
 static_assert(kPatchThreads / 32 == kWarpCopies, "one node-sum copy per warp");
-// Meshes whose patches need more colours than this add their element
-// products through per-warp copies of the node sums instead of colour rounds.
-constexpr int kWarpSchemeColours = 16;
+
 constexpr int kEPT = kPatch / kPatchThreads;     // elements owned by a thread
 
 // One patch per CTA, several CTAs per SM so that one CTA's copies overlap

@@ -277,8 +277,11 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                 const int ns = int(order.size());
                 gidx.assign(ns, 0);
                 int n_grp = 0;
-                for (int q = 0; q < ns; ++q) {
-                    if (q > 0 && (q % 32 == 0 || colour[order[q]] != colour[order[q - 1]])) ++n_grp;
+                const bool per_warp = n_col > kWarpSchemeColours;   // groups as the kernel's warps walk them
+                for (int q = 0, c0 = 0; q < ns; ++q) {
+                    const bool new_colour = q > 0 && colour[order[q]] != colour[order[q - 1]];
+                    if (new_colour) c0 = q;
+                    if (q > 0 && (new_colour || (per_warp ? (q - c0) % 32 == 0 : q % 32 == 0))) ++n_grp;
                     gidx[q] = n_grp;
                 }
                 ++n_grp;

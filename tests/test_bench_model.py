@@ -1,0 +1,35 @@
+"""The benchmark's algorithmic byte model, pinned to hand counts (no GPU).
+
+Per pass, each of the n_b^2 entries of the element arrays, each int32
+connectivity index and each node-vector entry read or written counts once.
+"""
+import bench
+
+
+def test_square_2049_bytes():
+    n_n, n_e = 2049 * 2049, 2 * 2048 * 2048          # 4,198,401 nodes, 8,388,608 triangles
+    m = bench.bytes_model(2, n_n, n_e)
+    # FP64 residual: 9 x 8 B + 3 x 4 B per triangle; x, b in and r out, 8 B each
+    assert m["residual64"] == n_e * (72 + 12) + n_n * 24 == 805_404_696
+    # FP32 operator: 9 x 4 B + 3 x 4 B per triangle; p in, q out
+    assert m["apply32"] == n_e * (36 + 12) + n_n * 8 == 436_240_392
+    stored = bench.bytes_model(2, n_n, n_e, stored=True)
+    assert stored["apply32"] == n_e * (24 + 12) + n_n * 8 == 335_577_096
+    assert stored["residual64"] == n_e * (48 + 12) + n_n * 24
+
+
+def test_cube_129_bytes():
+    n_n, n_e = 129 ** 3, 6 * 128 ** 3                  # 2,146,689 nodes, 12,582,912 tetrahedra
+    m = bench.bytes_model(3, n_n, n_e)
+    assert m["residual32"] == n_e * (64 + 16) + n_n * 12   # about 1,032 MB
+    assert abs(m["residual32"] / 1e6 - 1032.4) < 0.1
+    assert m["residual64"] == n_e * (128 + 16) + n_n * 24
+    stored = bench.bytes_model(3, n_n, n_e, stored=True)
+    assert stored["apply32"] == n_e * (40 + 16) + n_n * 8
+
+
+def test_mixed_iteration_node_bytes():
+    # one mixed CG iteration's node work: update reads x (8), p, r, q, dinv (4 each)
+    # and writes x (8), r (4); direction reads r, dinv, p and writes p (4 each)
+    m = bench.bytes_model(2, 1000, 1)
+    assert m["vec_mixed"] == 1000 * (8 + 16 + 12 + 12 + 4)

@@ -15,6 +15,7 @@
 // are FP32 (r's own rounding drift is not amplified and is removed at every
 // replacement by the FP64 true residual); the per-thread dot sums use
 // compensated FP32 (Neumaier) before the FP64 block reduction.
+#include <atomic>
 #include <cstdint>
 #include <tuple>
 
@@ -355,13 +356,16 @@ __global__ void k_control(Scalars* sc, double thr2, int64_t maxit, int reset_ite
 // tail and more block partials.  Capped at the 1216 partials the reductions
 // have room for.
 int vec_grid(int64_t n) {
-    static int cap = 0;
+    constexpr int kDevices = 64;
+    static std::atomic<int> caps[kDevices];   // per device, 0 = not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int cap = dev < kDevices ? caps[dev].load(std::memory_order_relaxed) : 0;
     if (cap == 0) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms < 1)
-            sms = 152;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
         cap = sms * 4 > 1216 ? 1216 : sms * 4;
+        if (dev < kDevices) caps[dev].store(cap, std::memory_order_relaxed);
     }
     const int64_t g = (n + NT - 1) / NT;
     return int(g < 1 ? 1 : (g > cap ? cap : g));

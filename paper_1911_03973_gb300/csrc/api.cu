@@ -287,6 +287,7 @@ static int create_device(ebe_handle* h, const double* coords_host) {
     pd.n_slots = P.n_slots;
     pd.n_patches = int(P.n_patches);
     pd.n_shared = int(P.sh_node.size());
+    pd.n_halo = P.n_halo;
     pd.max_nodes = P.max_nodes;
     pd.max_col = P.max_col;
     int32_t* col_ptr = nullptr;

@@ -16,6 +16,7 @@ struct PlanDev {
     int64_t n_slots = 0;
     int n_patches = 0;
     int n_shared = 0;
+    int64_t n_halo = 0;                 // halo slots (sh_ptr[n_shared])
     int max_nodes = 0;
     int max_col = 0;
     const PatchMeta* meta = nullptr;
@@ -90,7 +91,11 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 // Fixed grid of the node-vector kernels for n nodes (deterministic partials).
 int vec_grid(int64_t n);
-int fix_grid(int n_shared);
+// Fix-up grid: `rows` shared rows per thread at a time (1 or 2).
+int fix_grid(int n_shared, int rows = 1);
+// Rows per fix-up thread for this partition: 2 (their loads interleaved) when
+// a shared node has at most 2.5 halo slots on average, else 1.
+int fix_rows(const PlanDev& pd);
 constexpr int kVecThreads = 256;
 
 // ---- patch passes (k_patch.cu) -------------------------------------------

@@ -23,3 +23,30 @@ def test_c_program_uses_the_abi():
         out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
         assert out.returncode == 0, out.stderr
         assert out.stdout.strip() == "ok"
+
+
+@pytest.mark.gpu
+def test_c_program_solves_through_the_abi():
+    # create / set_problem / assemble / solve_host from C, judged by the oracle
+    import numpy as np
+
+    import oracle
+    from paper_1911_03973_gb300 import build, meshgen
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lib = build.build()
+    oracle.build()
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "solve_host")
+        xbin = os.path.join(d, "x.bin")
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c", "solve_host.c"), lib, "-o", exe,
+                        "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+        out = subprocess.run([exe, xbin], capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stdout + out.stderr
+        lines = out.stdout.split("\n")
+        assert lines[0].startswith("fp64 EBE_OK") and lines[1].startswith("mixed EBE_OK"), out.stdout
+        xs = np.fromfile(xbin, dtype=np.float64).reshape(2, -1)
+    orc = oracle.Problem(meshgen.config_square_f1(33, nu=1.0))
+    for x in xs:
+        assert orc.rel_residual(x) <= 1e-8

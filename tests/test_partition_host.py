@@ -112,3 +112,29 @@ def test_local_numbering_spreads_banks(ebe):
     c = meshgen.jitter_interior(c, 1 / 256, 0.2, seed=2)
     cycles, ideal = _bank_wavefronts(ebe.ebe_partition_export(c, e))
     assert cycles <= 2.1 * ideal, (cycles, ideal)
+
+
+def test_random_meshes_partition_and_replay(ebe):
+    # random sizes (ragged last patches), jitter, node and element orders, in 2D
+    # (few colours per patch) and 3D (many colours): every invariant, and the
+    # replayed patch pass against the oracle's Algorithm 1
+    rng = np.random.Generator(np.random.PCG64(2024))
+    for trial in range(12):
+        tri = trial % 3 != 2
+        n = int(rng.integers(3, 60)) if tri else int(rng.integers(3, 12))
+        if tri:
+            c, e = meshgen.square_tri(n)
+            c = meshgen.jitter_interior(c, 1.0 / (n - 1), 0.2, seed=int(rng.integers(1 << 30)))
+        else:
+            c, e = meshgen.cube_tet(n)
+        c, e, _, _ = meshgen.permute_nodes(c, e, [], seed=int(rng.integers(1 << 30)))
+        e = e[rng.permutation(e.shape[0])]
+        P = ebe.ebe_partition_export(c, e)
+        check_partition(P, c, e)
+        prob = {"coords": c, "elems": e, "nu": 0.5, "f": np.ones(c.shape[0]),
+                "dirichlet": np.array([0], np.int32), "g": np.zeros(1), "neumann": np.zeros(0, np.int32)}
+        orc = oracle.Problem(prob)
+        x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, trial))
+        r = replay_patch_residual(P, e, orc.A, orc.rhs(), x, prob["dirichlet"])
+        ref = orc.residual(x)
+        assert np.linalg.norm(r - ref) <= 1e-12 * max(np.linalg.norm(ref), 1e-300), (trial, n, tri)

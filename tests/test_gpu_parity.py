@@ -244,3 +244,39 @@ def test_errors_reported_not_raised_on_device(ebe):
         ebe.ebe_residual(h2, torch.zeros(n, dtype=torch.float64, device=DEV),
                          torch.zeros(n, dtype=torch.float64, device=DEV))
     assert ei.value.status == 10
+
+
+def test_random_meshes_residuals_match_oracle(ebe):
+    # random sizes, jitter, node and element orders; triangles use colour rounds,
+    # tetrahedra (many colours per patch) the per-warp node sums in FP32
+    rng = np.random.Generator(np.random.PCG64(77))
+    for trial in range(6):
+        tri = trial % 2 == 0
+        n = int(rng.integers(3, 80)) if tri else int(rng.integers(3, 14))
+        if tri:
+            c, e = meshgen.square_tri(n)
+            c = meshgen.jitter_interior(c, 1.0 / (n - 1), 0.2, seed=int(rng.integers(1 << 30)))
+        else:
+            c, e = meshgen.cube_tet(n)
+        c, e, _, _ = meshgen.permute_nodes(c, e, [], seed=int(rng.integers(1 << 30)))
+        e = np.ascontiguousarray(e[rng.permutation(e.shape[0])])
+        nd = np.unique(rng.integers(0, c.shape[0], size=max(1, c.shape[0] // 20))).astype(np.int32)
+        prob = {"coords": c, "elems": e, "nu": float(rng.uniform(0.0, 2.0)), "f": rng.normal(size=c.shape[0]),
+                "dirichlet": nd, "g": rng.normal(size=nd.size), "neumann": np.zeros(0, np.int32)}
+        orc = oracle.Problem(prob)
+        h = _setup(ebe, prob)
+        x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 100 + trial))
+        xd = _t(x)
+        rd = torch.empty_like(xd)
+        ebe.ebe_residual(h, xd, rd)
+        orc32 = oracle.Problem(prob, A_override=fp32_difference_form(orc.A))
+        x32 = x.astype(np.float32)
+        rd32 = torch.empty(orc.n_n, dtype=torch.float32, device=DEV)
+        ebe.ebe_residual(h, _t(x32, torch.float32), rd32)
+        torch.cuda.synchronize()
+        ref = orc.residual(x)
+        assert np.linalg.norm(rd.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref), (trial, n, tri)
+        ref32 = orc32.residual(x32.astype(np.float64))
+        r32 = rd32.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(r32 - ref32) <= 1e-5 * np.linalg.norm(ref32), (trial, n, tri)
+        ebe.ebe_destroy(h)

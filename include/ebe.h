@@ -248,9 +248,13 @@ ebe_status ebe_residual_variant(ebe_handle* h, const double* x_dev, double* r_de
 
 /* Jacobi-PCG on A x = b with x(nd) = g, stopping when the FP64 true relative
  * residual |mask(b - A x)| / |mask(b - A x0)| <= rtol (x0 = the given x with
- * x(nd) = g).  x_dev: device [n_n] double, in: x0, out: solution.  opts NULL =
- * defaults.  info may be NULL.  Synchronises the stream once at the end.
- * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
+ * x(nd) = g).  The true residual is evaluated (FP64 element matrices) each
+ * time the recurrence residual reaches rtol |r0| (and, for EBE_PREC_MIXED, at
+ * every replacement); for EBE_PREC_MIXED a failed check at that final
+ * threshold tightens it by the factor 0.7.  x_dev: device [n_n] double, in: x0, out:
+ * solution.  opts NULL = defaults.  info may be NULL.  Synchronises the
+ * stream once at the end.  Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN,
+ * EBE_STALL or an error. */
 ebe_status ebe_solve(ebe_handle* h, double* x_dev, const ebe_solve_opts* opts, ebe_solve_info* info);
 
 /* ebe_solve with a HOST x (host [n_n] double, in: x0, out: solution); the

@@ -811,11 +811,15 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
     if (!std::isfinite(r0)) status = EBE_BREAKDOWN;
     if (r0 > 0.0 && std::isfinite(r0)) {
         const double target = o.rtol * r0;
-        // plain FP64: the recurrence residual tracks the true one, so the true
-        // residual is checked once the recurrence reaches rtol (a textbook
-        // stopping test).  Mixed: a replacement whenever the recurrence has
-        // dropped by delta, and a margin at the end for the drift.
-        const double fin = mixed ? 0.7 * target : target;
+        // The true residual is checked once the recurrence residual reaches
+        // rtol (a textbook stopping test); mixed precision also replaces r
+        // whenever the recurrence has dropped by delta.  In mixed precision a
+        // failed check at the final threshold (the FP32 recurrence drifted
+        // below the true residual) tightens that threshold by kFinalMargin;
+        // the 2-norm residual of CG falls in steps, so a fixed margin below
+        // rtol from the start would cost whole steps of iterations.  The
+        // FP64 recurrence tracks the true residual, and its threshold stays.
+        double fin = target;
         l = 0;
         CK(launch_restart(s.dt, n, h->r64, s.dinv, 1, h->part_vec, h->sc, h->st, &l, h->r32), "restart");
         CK(launch_direction(s.dt, n, s.p, s.r, s.dinv, 1, h->sc, h->st, &l), "direction");
@@ -852,6 +856,7 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
             if (sh.reason == kMaxit) { status = EBE_MAXIT; break; }
             if (rel < 0.9 * best) { best = rel; no_progress = 0; }
             else if (++no_progress >= o.stall_updates) { status = EBE_STALL; break; }
+            if (mixed && sh.reason == kTrigger && thr <= fin) fin *= kFinalMargin;
             // residual replacement: r64 already holds the FP64 true residual;
             // continue CG from it with the same direction
             l = 0;
@@ -1113,7 +1118,7 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.phase_ns = h->bphase;
     bd.rtol = o.rtol;
     bd.delta = o.delta;
-    bd.margin = 0.7;
+    bd.margin = kFinalMargin;
     bd.maxit = o.maxit;
     bd.stall_updates = o.stall_updates;
     bd.iter_budget = budget;

@@ -442,7 +442,8 @@ __device__ __forceinline__ void decide(const BatchDev& bd, int k, int md, double
         P->rho = rz;
         P->beta = 0.0;
         P->dir_init = 1;
-        const double fin = (MIXED ? bd.margin : 1.0) * bd.rtol * r0;
+        const double fin = bd.rtol * r0;
+        P->fin = fin;
         const double thr = MIXED ? fmax(bd.delta * r0, fin) : fin;
         P->thr2 = thr * thr;
         P->mode = kBNormal;
@@ -462,12 +463,18 @@ __device__ __forceinline__ void decide(const BatchDev& bd, int k, int md, double
         P->no_progress = np;
         if (np >= bd.stall_updates) { finish(EBE_STALL); return; }
     }
+    // mixed precision: a failed check at the final threshold tightens it
+    // (the FP32 recurrence residual drifted below the true one)
+    double fin = P->fin;
+    if (MIXED && P->thr2 <= fin * fin) {
+        fin *= bd.margin;
+        P->fin = fin;
+    }
     // residual replacement: continue CG from the true residual, same direction
     const double rho = P->rho;
     P->beta = rho != 0.0 ? rz / rho : 0.0;
     P->rho = rz;
     P->dir_init = 0;
-    const double fin = (MIXED ? bd.margin : 1.0) * bd.rtol * P->r0;
     const double thr = MIXED ? fmax(bd.delta * sqrt(rrt), fin) : fin;
     P->thr2 = thr * thr;
     P->mode = kBNormal;

@@ -52,6 +52,11 @@ enum PatchMode : int {
 // Why a solver graph stopped (Scalars::reason).
 enum StopReason : int { kRunning = 0, kTrigger = 1, kBreakdown = 2, kMaxit = 3 };
 
+// Factor by which a mixed-precision solver's final recurrence threshold
+// (first rtol |r0|) tightens after an FP64 true-residual check at that
+// threshold has failed.
+constexpr double kFinalMargin = 0.7;
+
 // Solver scalars, kept on the device between kernels of an iteration.
 struct Scalars {
     double rho;      // r.z of the current direction
@@ -172,6 +177,7 @@ struct BatchProblem {
     double rrt;        // last true-residual r.r
     double rel;        // last true relative residual
     double best;       // best true relative residual so far (stall test)
+    double fin;        // final recurrence threshold: rtol r0 (mixed: times bd.margin per failed check at it)
     int64_t iter;      // CG iterations done
     int32_t mode;      // BatchMode
     int32_t status;    // ebe_status once done
@@ -226,7 +232,7 @@ struct BatchDev {
     int32_t* live = nullptr;               // problems not done
     int64_t* loops = nullptr;              // iterations (of any kind) run by the persistent kernel
     unsigned long long* phase_ns = nullptr;   // [4] time of the phases P, F, U, D (barrier to barrier, CTA 0)
-    double rtol = 1e-8, delta = 0.1, margin = 0.7;
+    double rtol = 1e-8, delta = 0.1, margin = kFinalMargin;
     int64_t maxit = 0;
     int32_t stall_updates = 8;
     int64_t iter_budget = 0;               // loop iterations of one launch

@@ -23,6 +23,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ebe_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A prebuilt copy of the library may be named here instead (the oracle's own
+# tests load copies of ebe_oracle.c with planted mistakes this way).
+_LIB_OVERRIDE = os.environ.get("EBE_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -46,8 +49,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            lib = ctypes.CDLL(_LIB_OVERRIDE or build())
             lib.orc_element_matrices.restype = ctypes.c_int
             lib.orc_element_matrices.argtypes = [ctypes.c_int, _I64, _I64, _F64P, _I32P, _F64P, _F64P, _F64P, _I64P]
             lib.orc_local_system.restype = None

@@ -1,0 +1,116 @@
+"""Planted mistakes in the oracle are caught by its pins (CPU only).
+
+Each mutant is ``oracle/ebe_oracle.c`` with one plausible mistake -- a dropped
+term or factor, a wrong sign, a wrong index, a wrong constant, a step left
+out -- compiled into a library of its own.  The pin tests
+(``tests/test_oracle_pins.py``) then run against it in a subprocess and must
+fail; the unmodified source, compiled the same way, must pass them.  The
+mistakes are planted in copies under pytest's temporary directory; the
+oracle itself is never changed.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ebe_oracle.c")
+
+# (name, exact text in ebe_oracle.c, replacement); each text occurs once.
+MUTANTS = [
+    # element matrices, Eq. matrices_K_M
+    ("K_e without the element measure", "Ke[i + nb * j] = vol * s;", "Ke[i + nb * j] = s;"),
+    ("K_e with a wrong gradient index", "s += g[i * dim + d] * g[j * dim + d];", "s += g[i * dim + d] * g[i * dim + d];"),
+    ("M_e with a wrong quadrature weight", "Me[i + nb * j] = vol / nq * m;", "Me[i + nb * j] = vol / (nq + 1) * m;"),
+    ("M_e by the vertex rule (lumped)", "qp[q][i] = (i == q) ? 0.0 : 0.5;", "qp[q][i] = (i == q) ? 1.0 : 0.0;"),
+    ("M_e with a wrong 3D quadrature point",
+     "double a = (5.0 + 3.0 * sqrt(5.0)) / 20.0, b = (5.0 - sqrt(5.0)) / 20.0;",
+     "double a = (5.0 + 3.0 * sqrt(5.0)) / 20.0, b = (5.0 - sqrt(3.0)) / 20.0;"),
+    ("Gauss-Jordan elimination with a wrong sign", "for (int c = 0; c < 2 * nb; ++c) V[k][c] -= fac * V[col][c];",
+     "for (int c = 0; c < 2 * nb; ++c) V[k][c] += fac * V[col][c];"),
+    ("tetrahedron volume without 1/3!", "double fact = (dim == 2) ? 2.0 : 6.0;", "double fact = (dim == 2) ? 2.0 : 2.0;"),
+    ("gradients read from the wrong half of inv(V)", "grad[i * dim + d] = V[1 + d][nb + i];",
+     "grad[i * dim + d] = V[1 + d][i];"),
+    # local systems, Sec. 2
+    ("A_e = K_e - nu M_e", "Ae[t] = Ke[t] + nu * Me[t];", "Ae[t] = Ke[t] - nu * Me[t];"),
+    ("b_e with a wrong node index", "s += Me[i + nb * j] * f_nodal[elems[e * nb + j]];",
+     "s += Me[i + nb * j] * f_nodal[elems[e * nb + i]];"),
+    # Algorithm 1
+    ("local residual with a wrong sign", "re[i] = (be ? be[e * nb + i] : 0.0) - s;", "re[i] = (be ? be[e * nb + i] : 0.0) + s;"),
+    ("local product with a wrong index", "for (int j = 0; j < nb; ++j) s += Ae[i + nb * j] * xe[j];\n            re[i]",
+     "for (int j = 0; j < nb; ++j) s += Ae[i + nb * j] * xe[i];\n            re[i]"),
+    ("assembly overwrites instead of adding", "for (int i = 0; i < nb; ++i) r[idx[i]] += re[i];",
+     "for (int i = 0; i < nb; ++i) r[idx[i]] = re[i];"),
+    ("residual without r(nd) = 0", "    zero_rows(r, nd, n_d);\n}", "}"),
+    ("operator with a wrong sign", "            y[idx[i]] += s;", "            y[idx[i]] -= s;"),
+    ("operator without the Dirichlet mask", "    zero_rows(y, nd, n_d);\n}", "}"),
+    ("load assembly overwrites", "for (int i = 0; i < nb; ++i) b[elems[e * nb + i]] += be[e * nb + i];",
+     "for (int i = 0; i < nb; ++i) b[elems[e * nb + i]] = be[e * nb + i];"),
+    ("Jacobi diagonal takes the first column", "d[elems[e * nb + i]] += A[(int64_t)nb * nb * e + i + nb * i];",
+     "d[elems[e * nb + i]] += A[(int64_t)nb * nb * e + i];"),
+    ("dense assembly onto the diagonal", "dense[(int64_t)idx[i] * n_n + idx[j]] += Ae[i + nb * j];",
+     "dense[(int64_t)idx[i] * n_n + idx[i]] += Ae[i + nb * j];"),
+    # Jacobi-PCG
+    ("PCG beta inverted", "double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    ("PCG residual update with a wrong sign", "x[i] += alpha * p[i]; r[i] -= alpha * q[i];",
+     "x[i] += alpha * p[i]; r[i] += alpha * q[i];"),
+    ("PCG without the Jacobi preconditioner in the loop",
+     "for (int64_t i = 0; i < n_n; ++i) z[i] = dinv[i] * r[i];\n        double rho_new",
+     "for (int64_t i = 0; i < n_n; ++i) z[i] = r[i];\n        double rho_new"),
+    ("PCG step length halved", "double alpha = rho / pq;", "double alpha = 0.5 * rho / pq;"),
+    ("PCG direction without the previous direction", "p[i] = z[i] + beta * p[i];", "p[i] = z[i];"),
+    ("relative residual measured on x0", "double num = sqrt(dot(n_n, r, r));", "double num = den;"),
+    # stationary iterations
+    ("Richardson step with a wrong sign", "for (int64_t i = 0; i < n_n; ++i) x[i] += omega * r[i];",
+     "for (int64_t i = 0; i < n_n; ++i) x[i] -= omega * r[i];"),
+    ("two-level Chebyshev multiplies by the root", "for (int64_t i = 0; i < n_n; ++i) x[i] += r[i] / a;",
+     "for (int64_t i = 0; i < n_n; ++i) x[i] += r[i] * a;"),
+    ("two-level Chebyshev always takes the first root", "double a = alphas[k % N];", "double a = alphas[0];"),
+    ("three-level first step as printed, 2/(l2-l1)", "x[i] += 2.0 / (l1 + l2) * r[i];", "x[i] += 2.0 / (l2 - l1) * r[i];"),
+    ("recurrence of Eq. recrCk with a wrong sign", "double ratio_next = 2.0 * s - rho;", "double ratio_next = 2.0 * s + rho;"),
+    ("three-level residual factor 2 instead of 4",
+     "x[i] = xk + c_km1_over_c_kp1 * (xk - xprev[i]) + 4.0 / (l2 - l1) * c_k_over_c_kp1 * r[i];",
+     "x[i] = xk + c_km1_over_c_kp1 * (xk - xprev[i]) + 2.0 / (l2 - l1) * c_k_over_c_kp1 * r[i];"),
+    ("three-level ratio not advanced", "rho = c_k_over_c_kp1;", "rho = rho;"),
+    ("C_1 inverted", "double rho = 1.0 / s;", "double rho = s;"),
+    # discrete L2 error
+    ("mass norm with a wrong index", "s += err[idx[i]] * Me[i + nb * j] * err[idx[j]];",
+     "s += err[idx[i]] * Me[i + nb * j] * err[idx[i]];"),
+    ("mass norm squared", "return sqrt(s);\n}", "return s;\n}"),
+]
+
+
+def _compile(src_text, out_dir, name):
+    c = os.path.join(out_dir, name + ".c")
+    so = os.path.join(out_dir, name + ".so")
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", c, "-o", so, "-lm"], check=True)
+    return so
+
+
+def _run_pins(lib):
+    env = dict(os.environ, EBE_ORACLE_LIB=lib)
+    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+                           "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
+                          timeout=600)
+
+
+def _source():
+    with open(SRC) as f:
+        return f.read()
+
+
+def test_unmodified_copy_passes_the_pins(tmp_path):
+    res = _run_pins(_compile(_source(), str(tmp_path), "control"))
+    assert res.returncode == 0, res.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    src = _source()
+    assert src.count(old) == 1, name
+    res = _run_pins(_compile(src.replace(old, new), str(tmp_path), "mutant"))
+    assert res.returncode == 1, (name, res.stdout[-2000:])   # 1: some pin failed (not a crash or a usage error)

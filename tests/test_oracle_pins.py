@@ -314,6 +314,63 @@ def test_pcg_reports_maxit():
     assert info["status"] == "maxit" and info["iterations"] == 3
 
 
+def test_jacobi_pcg_is_invariant_under_diagonal_scaling():
+    """Jacobi-PCG on S A S y = S b (S a positive diagonal) produces the iterates
+    y_k = S^-1 x_k of Jacobi-PCG on A x = b: the preconditioner diag(SAS)^-1
+    absorbs S.  Plain CG or any other fixed preconditioner does not."""
+    prob = meshgen.config_square_jitter(9, nu=0.5, seed=5)
+    n_n = prob["coords"].shape[0]
+    nd = prob["dirichlet"]
+    prob["f"] = np.zeros(n_n)                                     # b = 0: the lifted g drives the solve
+    prob["g"] = 1.0 + 0.5 * np.sin(7.0 * np.arange(nd.shape[0]))
+    s = np.exp(np.random.default_rng(11).uniform(-1.0, 1.0, n_n))
+    p = oracle.Problem(prob)
+    e = prob["elems"]
+    As = p.A * s[e][:, :, None] * s[e][:, None, :]               # S_e A_e S_e
+    probs = dict(prob, g=prob["g"] / s[nd])
+    ps = oracle.Problem(probs, A_override=As)
+    for k in (1, 2, 5, 12):
+        x, info = p.pcg(rtol=1e-300, maxit=k)
+        y, infos = ps.pcg(rtol=1e-300, maxit=k)
+        assert info["status"] == infos["status"] == "maxit"
+        np.testing.assert_allclose(s * y, x, rtol=1e-11, atol=1e-13)
+
+
+def test_relative_residual_along_the_segment_to_the_solution():
+    """x_t = x0 + t (x* - x0) has b - A x_t = (1 - t)(b - A x0) when A x* = b,
+    so its relative residual is |1 - t|."""
+    prob = meshgen.config_square_jitter(9, nu=1.0, seed=6)
+    p = oracle.Problem(prob)
+    A, b = p.dense("A"), p.dense("M") @ prob["f"]
+    nd = prob["dirichlet"]
+    free = np.setdiff1d(np.arange(p.n_n), nd)
+    xs = p.with_dirichlet(np.zeros(p.n_n))                        # x* by a dense solve on the free block
+    xs[free] = np.linalg.solve(A[np.ix_(free, free)], b[free] - A[np.ix_(free, nd)] @ xs[nd])
+    x0 = p.with_dirichlet(np.zeros(p.n_n))
+    for t in (0.0, 0.25, 0.5, 1.5):
+        assert p.rel_residual(x0 + t * (xs - x0)) == pytest.approx(abs(1.0 - t), abs=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_norm_of_a_linear_function_is_its_l2_norm(dim):
+    """A linear u is its own P1 interpolant and M integrates products of P1
+    functions exactly, so sqrt(u^T M u) = ||u||_L2 over the unit square/cube:
+    int (a.x + c)^2 = |a|^2/3 + (sum_{i<j} a_i a_j)/2 + c sum(a) + c^2."""
+    if dim == 2:
+        c, e = meshgen.square_tri(9)
+        c = meshgen.jitter_interior(c, 1.0 / 8, 0.2, seed=7)
+        a = np.array([1.0, -0.3])
+    else:
+        c, e = meshgen.cube_tet(5)
+        a = np.array([1.0, -0.3, 0.6])
+    c0 = 0.2
+    u = c @ a + c0
+    pairs = sum(a[i] * a[j] for i in range(dim) for j in range(i + 1, dim))
+    exact = a @ a / 3.0 + pairs / 2.0 + c0 * a.sum() + c0 ** 2
+    p = _prob(c, e)
+    assert p.mass_norm(u) == pytest.approx(math.sqrt(exact), rel=1e-13)
+
+
 # ---------------------------------------------------------------- Sec. 2 iterations
 def _small_paper_problem(n=9):
     prob = meshgen.config_square_f1(n, nu=0.0, g_value=1.0)

@@ -4,7 +4,8 @@ The network is the library's own definition (the paper leaves the
 preconditioner slot of its solver loops open, Sec. 2); these tests pin the
 oracle to things other than itself: central finite differences of its loss
 (a dropped term, wrong sign or transposed operand in backward() fails them),
-the homogeneity and Jacobi limit that the definition implies, the mesh graph
+the homogeneity in r, the scaling with the Jacobi diagonal and the Jacobi
+limit that the definition implies, the mesh graph
 of the two-element mesh of Fig. 1 by hand, hand-computed BF16 roundings, and
 flexible CG with a fixed SPD preconditioner reducing to textbook PCG.
 """
@@ -64,6 +65,19 @@ def test_homogeneous_of_degree_one():
     for a in (1e-6, 3.0, 1e5):
         za, _ = mpnn.forward(theta, a * r, dinv, graph, exact=True)
         np.testing.assert_allclose(za, a * z1, rtol=1e-12, atol=1e-300)
+
+
+def test_scales_with_the_jacobi_diagonal():
+    """Both input features are scale-free and the output is zj + rms(zj) o, so
+    B(r; c dinv) = c B(r; dinv) for every c > 0."""
+    prob, orc, dinv, graph = _small()
+    rng = np.random.Generator(np.random.PCG64(8))
+    theta = rng.normal(0, 0.3, mpnn.n_params())
+    r = orc.residual(orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 5)))
+    z1, _ = mpnn.forward(theta, r, dinv, graph, exact=True)
+    for c in (1e-4, 0.37, 50.0):
+        zc, _ = mpnn.forward(theta, r, c * dinv, graph, exact=True)
+        np.testing.assert_allclose(zc, c * z1, rtol=1e-12, atol=1e-300)
 
 
 def test_backward_matches_finite_differences():

@@ -5,8 +5,10 @@ term or factor, a wrong sign, a wrong index, a wrong constant, a step left
 out -- compiled into a library of its own.  The pin tests
 (``tests/test_oracle_pins.py``) then run against it in a subprocess and must
 fail; the unmodified source, compiled the same way, must pass them.  The
-mistakes are planted in copies under pytest's temporary directory; the
-oracle itself is never changed.
+learned-preconditioner oracle ``oracle/mpnn.py`` is treated the same way: a
+mutated copy is imported in place of the module before its pins
+(``tests/test_mpnn_oracle.py``) run.  The mistakes are planted in copies
+under pytest's temporary directory; the oracle itself is never changed.
 """
 import os
 import subprocess
@@ -16,6 +18,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ebe_oracle.c")
+MPNN_SRC = os.path.join(ROOT, "oracle", "mpnn.py")
 
 # (name, exact text in ebe_oracle.c, replacement); each text occurs once.
 MUTANTS = [
@@ -114,3 +117,73 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
     assert src.count(old) == 1, name
     res = _run_pins(_compile(src.replace(old, new), str(tmp_path), "mutant"))
     assert res.returncode == 1, (name, res.stdout[-2000:])   # 1: some pin failed (not a crash or a usage error)
+
+
+# (name, exact text in mpnn.py, replacement); each text occurs once.
+MPNN_MUTANTS = [
+    ("graph keeps self loops", "keep = a != b", "keep = a == a"),
+    ("neighbour sum instead of mean", "return sums / deg[:, None]", "return sums"),
+    ("transposed mean without 1/deg", "np.add.at(out, idx, g[rows] / deg[rows, None])", "np.add.at(out, idx, g[rows])"),
+    ("message with a wrong sign", "a = _mean_nbr(graph, h) - h", "a = _mean_nbr(graph, h) + h"),
+    ("layer without the skip connection", "h = rd(h + np.maximum(v, 0.0))", "h = rd(np.maximum(v, 0.0))"),
+    ("output without the Jacobi term", "z = np.where(free, zj + sz * o, 0.0)", "z = np.where(free, sz * o, 0.0)"),
+    ("output scaled by rms(r)", "z = np.where(free, zj + sz * o, 0.0)", "z = np.where(free, zj + s * o, 0.0)"),
+    ("second feature scaled by rms(r)", "x = np.stack([r / s, zj / sz], 1)", "x = np.stack([r / s, zj / s], 1)"),
+    ("Dirichlet rows not zeroed", "z = np.where(free, zj + sz * o, 0.0)", "z = zj + sz * o"),
+    ("backward ignores the relu gate", "gv = gh * (cache[\"vs\"][l] > 0.0)", "gv = gh"),
+    ("backward drops the -h of the message", "gh = gh + gu[:, :H] - ga + _mean_nbr_T(graph, ga)",
+     "gh = gh + gu[:, :H] + _mean_nbr_T(graph, ga)"),
+    ("backward drops the skip connection", "gh = gh + gu[:, :H] - ga + _mean_nbr_T(graph, ga)",
+     "gh = gu[:, :H] - ga + _mean_nbr_T(graph, ga)"),
+    ("backward uses the transposed input weights", "g[\"W_in\"] = gh.T @ cache[\"x\"]",
+     "g[\"W_in\"] = (cache[\"x\"].T @ gh).T[:, ::-1]"),
+    ("loss gradient without the factor 2", "return float(w @ Aw) / eAe, -2.0 * Aw / eAe",
+     "return float(w @ Aw) / eAe, -1.0 * Aw / eAe"),
+    ("BF16 rounds half up", "bias = 0x7FFF + ((bits >> 16) & 1)", "bias = 0x8000"),
+    ("BF16 truncates", "out = ((bits + bias) & 0xFFFF0000).astype(np.uint32)", "out = (bits & 0xFFFF0000).astype(np.uint32)"),
+    ("FCG direction with a wrong sign", "p = z - (z @ q) / (p @ q) * p", "p = z + (z @ q) / (p @ q) * p"),
+    ("FCG step from p.p", "al = (p @ r) / (p @ q)", "al = (p @ p) / (p @ q)"),
+]
+
+_MPNN_DRIVER = (
+    "import importlib.util, sys\n"
+    "spec = importlib.util.spec_from_file_location('oracle.mpnn', sys.argv[1])\n"
+    "mod = importlib.util.module_from_spec(spec)\n"
+    "sys.modules['oracle.mpnn'] = mod\n"
+    "spec.loader.exec_module(mod)\n"
+    "import oracle\n"
+    "oracle.mpnn = mod\n"
+    "import pytest\n"
+    "sys.exit(pytest.main([sys.argv[2], '-x', '-q', '-p', 'no:cacheprovider', '-m', 'not gpu']))\n"
+)
+
+
+def _run_mpnn_pins(path):
+    env = dict(os.environ)
+    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    return subprocess.run([sys.executable, "-c", _MPNN_DRIVER, path, os.path.join(ROOT, "tests", "test_mpnn_oracle.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _mpnn_source():
+    with open(MPNN_SRC) as f:
+        return f.read()
+
+
+def test_unmodified_mpnn_copy_passes_the_pins(tmp_path):
+    path = os.path.join(str(tmp_path), "mpnn_copy.py")
+    with open(path, "w") as f:
+        f.write(_mpnn_source())
+    res = _run_mpnn_pins(path)
+    assert res.returncode == 0, res.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MPNN_MUTANTS, ids=[m[0] for m in MPNN_MUTANTS])
+def test_planted_mpnn_mistake_is_caught(tmp_path, name, old, new):
+    src = _mpnn_source()
+    assert src.count(old) == 1, name
+    path = os.path.join(str(tmp_path), "mpnn_mutant.py")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    res = _run_mpnn_pins(path)
+    assert res.returncode == 1, (name, res.stdout[-2000:])

@@ -3,7 +3,11 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "ebe.h"
@@ -39,18 +43,43 @@ struct PatchMeta {
 };
 
 // Host-side element partition, built once per mesh.
+// A std::vector whose resize() leaves new elements of trivial types
+// uninitialised: the partition's large tables are written in full by host
+// threads, so the first touch of their pages happens there, in parallel,
+// instead of in a serial zero fill.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <typename U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <typename U>
+    void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <typename U, typename... A>
+    void construct(U* p, A&&... a) {
+        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <typename T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
+
 struct HostPlan {
     int dim = 0, nb = 0;
     int64_t n_n = 0, n_e = 0;
     int64_t n_patches = 0, n_slots = 0;
-    std::vector<int32_t> slot_elem;   // [n_slots] caller's element id of each slot, -1 = padding
-    std::vector<uint16_t> lconn;      // [nb][n_slots] local node id of vertex i of each slot
-    std::vector<PatchMeta> meta;      // [n_patches]
-    std::vector<int32_t> pnode;       // local-node tables of all patches (global node ids)
-    std::vector<int32_t> col_ptr;     // colour offsets (n_col + 1 per patch), slot-relative
-    std::vector<int32_t> sh_node;     // [n_shared] nodes touched by >= 2 patches
-    std::vector<int32_t> sh_ptr;      // [n_shared + 1] CSR into sh_slot
-    std::vector<int32_t> sh_slot;     // [n_halo] halo slots of each shared node, patch order
+    HostVec<int32_t> slot_elem;   // [n_slots] caller's element id of each slot, -1 = padding
+    HostVec<uint16_t> lconn;      // [nb][n_slots] local node id of vertex i of each slot
+    HostVec<PatchMeta> meta;      // [n_patches]
+    HostVec<int32_t> pnode;       // local-node tables of all patches (global node ids)
+    HostVec<int32_t> col_ptr;     // colour offsets (n_col + 1 per patch), slot-relative
+    HostVec<int32_t> sh_node;     // [n_shared] nodes touched by >= 2 patches
+    HostVec<int32_t> sh_ptr;      // [n_shared + 1] CSR into sh_slot
+    HostVec<int32_t> sh_slot;     // [n_halo] halo slots of each shared node, patch order
     int64_t n_halo = 0;
     int max_nodes = 0;
     int max_col = 0;

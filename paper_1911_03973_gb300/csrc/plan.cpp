@@ -58,13 +58,25 @@ void parallel_blocks(int64_t n, int threads, F f, int64_t grain = 65536) {
     for (auto& th : pool) th.join();
 }
 
+// Lowest i in [0, n) with bad(i), or n if none: each host thread scans a
+// contiguous block up to its first failure; the lowest block result wins.
+template <typename F>
+int64_t first_failing(int64_t n, int threads, F bad) {
+    std::vector<int64_t> first(size_t(std::max(threads, 1)), n);
+    parallel_blocks(n, threads, [&](int t, int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i)
+            if (bad(i)) { first[size_t(t)] = i; return; }
+    });
+    return *std::min_element(first.begin(), first.end());
+}
+
 // Stable LSD radix sort of 64-bit values by their bits [lo_bit, 64) (the
 // bits below keep their input order), 10-bit digits, the histogram and the
 // scatter of each pass split over host threads in contiguous blocks.
-void radix_sort_u64(std::vector<uint64_t>& a, int lo_bit, int threads) {
+void radix_sort_u64(HostVec<uint64_t>& a, int lo_bit, int threads) {
     constexpr int kBits = 10, kBuckets = 1 << kBits;
     const int64_t n = int64_t(a.size());
-    std::vector<uint64_t> tmp(a.size());
+    HostVec<uint64_t> tmp(a.size());   // every entry is written by each pass's scatter
     uint64_t any = 0;
     for (uint64_t v : a) any |= v;
     const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / 65536 + 1)));
@@ -117,35 +129,68 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     P = HostPlan();
     P.dim = dim; P.nb = nb; P.n_n = n_n; P.n_e = n_e;
 
-    // ---- validation: ids in range, distinct within an element, finite coords
-    for (int64_t k = 0; k < n_n * dim; ++k)
-        if (!std::isfinite(m.coords[k])) { err = "non-finite coordinate at node " + std::to_string(k / dim); return EBE_INVALID_ARG; }
-    std::vector<int32_t> inc(n_n, 0);  // elements per node
-    for (int64_t e = 0; e < n_e; ++e) {
+    // ---- validation: finite coords, ids in range, distinct within an element,
+    // every node in some element.  Each check runs over host threads in
+    // blocks; the lowest failing index is reported, as a serial scan would.
+    const int threads = host_threads();
+    {
+        const int64_t nc = n_n * dim;
+        const int64_t bad = first_failing(nc, threads, [&](int64_t k) { return !std::isfinite(m.coords[k]); });
+        if (bad < nc) { err = "non-finite coordinate at node " + std::to_string(bad / dim); return EBE_INVALID_ARG; }
+    }
+    auto element_fault = [&](int64_t e) {
         const int32_t* v = m.elems + e * nb;
         for (int i = 0; i < nb; ++i) {
+            if (v[i] < 0 || v[i] >= n_n) return true;
+            for (int j = 0; j < i; ++j) if (v[j] == v[i]) return true;
+        }
+        return false;
+    };
+    const int64_t bad_e = first_failing(n_e, threads, element_fault);
+    if (bad_e < n_e) {
+        const int32_t* v = m.elems + bad_e * nb;
+        for (int i = 0; i < nb; ++i) {
             if (v[i] < 0 || v[i] >= n_n) {
-                err = "element " + std::to_string(e) + " has node id " + std::to_string(v[i]) + " outside [0, n_n)";
+                err = "element " + std::to_string(bad_e) + " has node id " + std::to_string(v[i]) + " outside [0, n_n)";
                 return EBE_INDEX_RANGE;
             }
             for (int j = 0; j < i; ++j)
-                if (v[j] == v[i]) { err = "element " + std::to_string(e) + " repeats node " + std::to_string(v[i]); return EBE_INDEX_RANGE; }
-            ++inc[v[i]];
+                if (v[j] == v[i]) { err = "element " + std::to_string(bad_e) + " repeats node " + std::to_string(v[i]); return EBE_INDEX_RANGE; }
         }
     }
-    for (int64_t g = 0; g < n_n; ++g)
-        if (inc[g] == 0) { err = "node " + std::to_string(g) + " belongs to no element"; return EBE_INVALID_ARG; }
+    HostVec<int32_t> inc(n_n);  // elements per node (ids are valid now)
+    parallel_blocks(n_n, threads, [&](int, int64_t g0, int64_t g1) { std::fill(inc.begin() + g0, inc.begin() + g1, 0); });
+    parallel_blocks(n_e * nb, threads, [&](int, int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) __atomic_fetch_add(&inc[m.elems[k]], 1, __ATOMIC_RELAXED);
+    });
+    {
+        const int64_t bad = first_failing(n_n, threads, [&](int64_t g) { return inc[g] == 0; });
+        if (bad < n_n) { err = "node " + std::to_string(bad) + " belongs to no element"; return EBE_INVALID_ARG; }
+    }
 
     // ---- Morton order of element centroids
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) { lo[d] = std::numeric_limits<double>::max(); hi[d] = -lo[d]; }
-    for (int64_t k = 0; k < n_n; ++k)
-        for (int d = 0; d < dim; ++d) { lo[d] = std::min(lo[d], m.coords[k * dim + d]); hi[d] = std::max(hi[d], m.coords[k * dim + d]); }
+    {
+        // per-thread bounds, then combined (min and max are exact in any order)
+        std::vector<double> tb(size_t(threads) * 6);
+        for (int t = 0; t < threads; ++t)
+            for (int d = 0; d < 3; ++d) { tb[t * 6 + d] = lo[d]; tb[t * 6 + 3 + d] = hi[d]; }
+        parallel_blocks(n_n, threads, [&](int t, int64_t k0, int64_t k1) {
+            double* b = tb.data() + size_t(t) * 6;
+            for (int64_t k = k0; k < k1; ++k)
+                for (int d = 0; d < dim; ++d) {
+                    b[d] = std::min(b[d], m.coords[k * dim + d]);
+                    b[3 + d] = std::max(b[3 + d], m.coords[k * dim + d]);
+                }
+        });
+        for (int t = 0; t < threads; ++t)
+            for (int d = 0; d < dim; ++d) { lo[d] = std::min(lo[d], tb[t * 6 + d]); hi[d] = std::max(hi[d], tb[t * 6 + 3 + d]); }
+    }
     const int ebits = bits_for(uint64_t(n_e));
     const int kbits_axis = std::min((64 - ebits) / dim, dim == 2 ? 32 : 21);
     const double qmax = double((uint64_t(1) << kbits_axis) - 1);
-    std::vector<uint64_t> keys(n_e);
-    const int threads = host_threads();
+    HostVec<uint64_t> keys(n_e);
     parallel_blocks(n_e, threads, [&](int, int64_t e0, int64_t e1) {
         for (int64_t e = e0; e < e1; ++e) {
             const int32_t* v = m.elems + e * nb;
@@ -173,8 +218,14 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     // concatenated in patch order
     P.n_patches = (n_e + kPatch - 1) / kPatch;
     P.n_slots = P.n_patches * kPatch;
-    P.slot_elem.assign(P.n_slots, -1);
-    P.lconn.assign(size_t(nb) * P.n_slots, 0);
+    // slots of elements are written by their patch below; the padding slots
+    // of the last patch are element -1 with local ids 0
+    P.slot_elem.resize(size_t(P.n_slots));
+    P.lconn.resize(size_t(nb) * P.n_slots);
+    for (int64_t s = n_e; s < P.n_slots; ++s) {
+        P.slot_elem[s] = -1;
+        for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + s] = 0;
+    }
     P.meta.resize(P.n_patches);
 
     struct PatchOut {
@@ -190,6 +241,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
         static_assert(kTable >= 8 * kPatch, "hash table too small");
         std::vector<int32_t> tkey(kTable, -1), tval(kTable), tcnt(kTable);
         std::vector<int32_t> el(kPatch), first_touch;
+        std::vector<int> lid(size_t(kPatch) * 4);
         std::vector<uint32_t> filled;   // table slots in use, cleared slot by slot after each patch
         std::vector<uint64_t> used;
         std::vector<int> colour(kPatch);
@@ -233,14 +285,18 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                 return;
             }
             for (int l = 0; l < n_nodes; ++l) tval[slot_of(lnodes[l])] = l;
-            auto local = [&](int32_t g) { return tval[slot_of(g)]; };
+            // local ids of the patch's elements, looked up once: lid[s * nb + i]
+            for (int s = 0; s < n_el; ++s) {
+                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                for (int i = 0; i < nb; ++i) lid[s * nb + i] = tval[slot_of(v[i])];
+            }
             // greedy colouring in Morton order
             used.assign(n_nodes, 0);
             int n_col = 0;
             for (int s = 0; s < n_el; ++s) {
-                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                const int* v = lid.data() + s * nb;
                 uint64_t busy = 0;
-                for (int i = 0; i < nb; ++i) busy |= used[local(v[i])];
+                for (int i = 0; i < nb; ++i) busy |= used[v[i]];
                 if (busy == ~0ull) {
                     out.status = EBE_INVALID_ARG;
                     out.msg = "patch needs more than 64 colours";
@@ -251,7 +307,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                 while (busy & (1ull << c)) ++c;
                 colour[s] = c;
                 n_col = std::max(n_col, c + 1);
-                for (int i = 0; i < nb; ++i) used[local(v[i])] |= (1ull << c);
+                for (int i = 0; i < nb; ++i) used[v[i]] |= (1ull << c);
             }
             out.n_col = n_col;
             // slots: elements grouped by colour, Morton order within a colour
@@ -289,17 +345,17 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                 // node -> access sets (CSR)
                 first_set.assign(n_nodes + 1, 0);
                 for (int q = 0; q < ns; ++q) {
-                    const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
-                    for (int i = 0; i < nb; ++i) ++first_set[local(v[i]) + 1];
+                    const int* v = lid.data() + order[q] * nb;
+                    for (int i = 0; i < nb; ++i) ++first_set[v[i] + 1];
                 }
                 for (int l = 0; l < n_nodes; ++l) first_set[l + 1] += first_set[l];
                 set_list.assign(first_set[n_nodes], 0);
                 set_fill.assign(first_set.begin(), first_set.end() - 1);
                 visit.clear();
                 for (int q = 0; q < ns; ++q) {
-                    const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
+                    const int* v = lid.data() + order[q] * nb;
                     for (int i = 0; i < nb; ++i) {
-                        const int l = local(v[i]);
+                        const int l = v[i];
                         if (set_fill[l] == first_set[l]) visit.push_back(l);   // first appearance
                         set_list[set_fill[l]++] = gidx[q] * nb + i;
                     }
@@ -350,8 +406,8 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             for (int q = 0; q < int(order.size()); ++q) {
                 const int64_t gs = e0 + q;
                 P.slot_elem[gs] = el[order[q]];
-                const int32_t* v = m.elems + int64_t(el[order[q]]) * nb;
-                for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(perm[local(v[i])]);
+                const int* v = lid.data() + order[q] * nb;
+                for (int i = 0; i < nb; ++i) P.lconn[size_t(i) * P.n_slots + gs] = uint16_t(perm[v[i]]);
             }
             // each table starts on a 16-byte boundary (bulk copies need it)
             while (lnodes.size() % 4 != 0) lnodes.push_back(lnodes[0]);
@@ -384,7 +440,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     }
     P.pnode.resize(size_t(n_pnode));
     P.col_ptr.resize(size_t(n_colptr));
-    std::vector<int32_t> halo_node(static_cast<size_t>(halo_count));   // halo slot -> global node
+    HostVec<int32_t> halo_node(static_cast<size_t>(halo_count));   // halo slot -> global node
     parallel_blocks(P.n_patches, threads, [&](int, int64_t p0, int64_t p1) {
         for (int64_t p = p0; p < p1; ++p) {
             const PatchOut& o = outs[size_t(p)];
@@ -400,15 +456,34 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
 
     // ---- shared nodes: CSR of halo slots in patch order (slots are numbered
     // patch by patch, so ascending slot order is ascending patch order)
-    std::vector<int32_t> cnt(n_n, 0);
-    for (int32_t g : halo_node) ++cnt[g];
-    std::vector<int32_t> node_row(n_n, -1);
-    int64_t n_shared = 0;
-    for (int64_t g = 0; g < n_n; ++g) if (cnt[g] > 0) node_row[g] = int32_t(n_shared++);
+    HostVec<int32_t> cnt(n_n);
+    parallel_blocks(n_n, threads, [&](int, int64_t g0, int64_t g1) { std::fill(cnt.begin() + g0, cnt.begin() + g1, 0); });
+    parallel_blocks(halo_count, threads, [&](int, int64_t s0, int64_t s1) {
+        for (int64_t s = s0; s < s1; ++s) __atomic_fetch_add(&cnt[halo_node[s]], 1, __ATOMIC_RELAXED);
+    });
+    // rows of the shared nodes in ascending node order: per-block counts, then
+    // each block numbers its nodes from its prefix
+    HostVec<int32_t> node_row(n_n);   // written for every shared node, read only there
+    std::vector<int64_t> blk_rows(size_t(threads) + 1, 0);
+    parallel_blocks(n_n, threads, [&](int t, int64_t g0, int64_t g1) {
+        int64_t c = 0;
+        for (int64_t g = g0; g < g1; ++g) c += cnt[g] > 0;
+        blk_rows[size_t(t) + 1] = c;
+    });
+    for (int t = 0; t < threads; ++t) blk_rows[size_t(t) + 1] += blk_rows[size_t(t)];
+    const int64_t n_shared = blk_rows[size_t(threads)];
     P.sh_node.resize(n_shared);
     P.sh_ptr.assign(n_shared + 1, 0);
-    for (int64_t g = 0; g < n_n; ++g)
-        if (cnt[g] > 0) { P.sh_node[node_row[g]] = int32_t(g); P.sh_ptr[node_row[g] + 1] = cnt[g]; }
+    parallel_blocks(n_n, threads, [&](int t, int64_t g0, int64_t g1) {
+        int64_t row = blk_rows[size_t(t)];
+        for (int64_t g = g0; g < g1; ++g)
+            if (cnt[g] > 0) {
+                node_row[g] = int32_t(row);
+                P.sh_node[row] = int32_t(g);
+                P.sh_ptr[row + 1] = cnt[g];
+                ++row;
+            }
+    });
     for (int64_t k = 0; k < n_shared; ++k) P.sh_ptr[k + 1] += P.sh_ptr[k];
     P.sh_slot.resize(halo_count);
     std::vector<int32_t> fill(P.sh_ptr.begin(), P.sh_ptr.end() - 1);

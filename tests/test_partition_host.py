@@ -138,3 +138,32 @@ def test_random_meshes_partition_and_replay(ebe):
         r = replay_patch_residual(P, e, orc.A, orc.rhs(), x, prob["dirichlet"])
         ref = orc.residual(x)
         assert np.linalg.norm(r - ref) <= 1e-12 * max(np.linalg.norm(ref), 1e-300), (trial, n, tri)
+
+
+def test_validation_reports_the_first_failure_on_a_large_mesh(ebe):
+    # 2 * 400^2 = 320,000 elements: the checks run over several host threads,
+    # and each must still name the lowest failing element or node
+    c, e = meshgen.square_tri(401)
+    n_e = e.shape[0]
+    for bad_at, value, word in ((250_000, -5, "outside"), (300_000, None, "repeats")):
+        eb = e.copy()
+        later = n_e - 7
+        for k in (later, bad_at):                  # a later fault too: the earlier one is reported
+            if value is None:
+                eb[k, 2] = eb[k, 0]
+            else:
+                eb[k, 1] = value
+        with pytest.raises(ebe.EbeError) as ei:
+            ebe.ebe_partition_export(c, eb)
+        assert ei.value.status == 2 and f"element {bad_at} " in str(ei.value) and word in str(ei.value), str(ei.value)
+    cb = c.copy()
+    cb[150_000, 1] = np.inf
+    cb[20_000, 0] = np.nan
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_partition_export(cb, e)
+    assert ei.value.status == 1 and "node 20000" in str(ei.value), str(ei.value)
+    # nodes 100,000 and 160,000 in no element: drop every element touching them
+    touch = np.isin(e, [100_000, 160_000]).any(axis=1)
+    with pytest.raises(ebe.EbeError) as ei:
+        ebe.ebe_partition_export(c, e[~touch])
+    assert ei.value.status == 1 and "node 100000 " in str(ei.value), str(ei.value)

@@ -242,6 +242,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
         std::vector<int32_t> tkey(kTable, -1), tval(kTable), tcnt(kTable);
         std::vector<int32_t> el(kPatch), first_touch;
         std::vector<int> lid(size_t(kPatch) * 4);
+        std::vector<int32_t> gv(size_t(kPatch) * 4);
         std::vector<uint32_t> filled;   // table slots in use, cleared slot by slot after each patch
         std::vector<uint64_t> used;
         std::vector<int> colour(kPatch);
@@ -257,11 +258,16 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             PatchOut& out = outs[size_t(p)];
             const int64_t e0 = p * kPatch;
             const int n_el = int(std::min<int64_t>(kPatch, n_e - e0));
-            for (int s = 0; s < n_el; ++s) el[s] = int32_t(keys[e0 + s] & emask);
+            // the patch's elements and their global node ids, gathered once
+            for (int s = 0; s < n_el; ++s) {
+                el[s] = int32_t(keys[e0 + s] & emask);
+                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                for (int i = 0; i < nb; ++i) gv[s * nb + i] = v[i];
+            }
             // local nodes in first-touch order, with their counts in the patch
             first_touch.clear();
             for (int s = 0; s < n_el; ++s) {
-                const int32_t* v = m.elems + int64_t(el[s]) * nb;
+                const int32_t* v = gv.data() + s * nb;
                 for (int i = 0; i < nb; ++i) {
                     const uint32_t t = slot_of(v[i]);
                     if (tkey[t] == -1) { tkey[t] = v[i]; tcnt[t] = 0; first_touch.push_back(v[i]); filled.push_back(t); }
@@ -286,10 +292,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             }
             for (int l = 0; l < n_nodes; ++l) tval[slot_of(lnodes[l])] = l;
             // local ids of the patch's elements, looked up once: lid[s * nb + i]
-            for (int s = 0; s < n_el; ++s) {
-                const int32_t* v = m.elems + int64_t(el[s]) * nb;
-                for (int i = 0; i < nb; ++i) lid[s * nb + i] = tval[slot_of(v[i])];
-            }
+            for (int s = 0; s < n_el * nb; ++s) lid[s] = tval[slot_of(gv[s])];
             // greedy colouring in Morton order
             used.assign(n_nodes, 0);
             int n_col = 0;

@@ -113,6 +113,20 @@ def bytes_model(dim: int, n_n: int, n_e: int, stored: bool = False):
     return m
 
 
+def fp64_alu_model(nb: int, n_n: int, n_e: int, sms: int, mhz):
+    """FP64-pipe ceiling of one FP64 residual (patch pass + fix-up).
+
+    Operations on the FP64 pipe: the n_b x n_b local product (n_b^2 multiply
+    or fused multiply-add instructions) and the n_b additions into the node
+    sums per element, then r = b - sum and the r.r accumulation per node.
+    GB300 issues two FP64 operations per SM and clock (1.25 TFLOP/s nominal
+    counts an FMA as two flops).  Returns None when the clock is unknown."""
+    if not mhz or not sms:
+        return None
+    ops = n_e * (nb * nb + nb) + 2 * n_n
+    return {"ops_per_launch": int(ops), "peak_gops": round(2.0 * sms * float(mhz) * 1e6 / 1e9, 1)}
+
+
 def step_bytes(m, info, mixed: bool):
     it, tr = info["iterations"], info["true_residuals"]
     if mixed:
@@ -649,6 +663,11 @@ def run_ours(args):
     peak, peak_kind = peaks()
     ach = m["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9
     ach64 = m["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9
+    alu64 = fp64_alu_model(dim + 1, n_n, n_e, torch.cuda.get_device_properties(dev).multi_processor_count,
+                           clk.get("sm_mhz") or clk.get("sm_max_mhz"))
+    if alu64 is not None:
+        alu64["achieved_gops"] = round(alu64["ops_per_launch"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9, 1)
+        alu64["frac"] = round(alu64["achieved_gops"] / alu64["peak_gops"], 4)
     trf = traffic_record("apply32")
 
     # e2e: the user's whole call sequence from pinned host buffers
@@ -733,7 +752,8 @@ def run_ours(args):
         "residual_fp64": {"gbs": round(ach64, 1), "frac": round(ach64 / peak, 4),
                           "ms_per_launch": [round(ms_patch64, 5), round(ms_fix64, 5)],
                           "bytes_per_launch": m["residual64"],
-                          "stored_gbs": round(m_stored["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9, 1)},
+                          "stored_gbs": round(m_stored["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9, 1),
+                          "fp64_pipe": alu64},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,

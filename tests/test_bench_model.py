@@ -33,3 +33,16 @@ def test_mixed_iteration_node_bytes():
     # and writes x (8), r (4); direction reads r, dinv, p and writes p (4 each)
     m = bench.bytes_model(2, 1000, 1)
     assert m["vec_mixed"] == 1000 * (8 + 16 + 12 + 12 + 4)
+
+
+def test_fp64_pipe_model():
+    # FP64 residual on 2049^2 triangles: 9 products + 3 node additions per
+    # triangle, r = b - sum and r.r per node; 2 FP64 operations per SM and clock
+    n_n, n_e = 2049 * 2049, 2 * 2048 * 2048
+    a = bench.fp64_alu_model(3, n_n, n_e, 152, 2070.0)
+    assert a["ops_per_launch"] == 12 * n_e + 2 * n_n == 109_060_098
+    assert a["peak_gops"] == 629.3                       # 2 x 152 x 2.07 GHz
+    t = bench.fp64_alu_model(4, 129 ** 3, 6 * 128 ** 3, 152, 2070.0)
+    assert t["ops_per_launch"] == 20 * 6 * 128 ** 3 + 2 * 129 ** 3
+    assert bench.fp64_alu_model(3, n_n, n_e, 152, None) is None
+    assert bench.fp64_alu_model(3, n_n, n_e, 0, 2070.0) is None

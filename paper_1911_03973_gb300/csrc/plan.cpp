@@ -10,9 +10,14 @@
 //      whose elements lie in the patch is "owned", the others are "shared";
 //   3. inside a patch the elements are greedily coloured so that no two
 //      elements of one colour share a node, and stored colour by colour;
-//   4. every shared local node gets a halo slot; for every shared node the
+//   4. the local node ids of a patch are chosen so that the 32 nodes one
+//      warp touches in a colour round fall in distinct shared-memory banks
+//      where possible (owned ids first, then shared);
+//   5. every shared local node gets a halo slot; for every shared node the
 //      halo slots are listed in patch order (a CSR), which fixes the order in
 //      which its partial sums are added.
+// Validation, Morton keys, the sort, the patches and the halo CSR run on up to
+// 16 host threads; the result does not depend on the thread count.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -156,6 +156,9 @@ typedef struct {
 /* Validate the mesh on the host, copy it to the device and build the element
  * partition (patches, local connectivity, halo lists).  Sec. 1 / Sec. 2: the
  * connectivity plays the role of C_e and R_e, which are never stored.
+ * The partition is built on up to 16 host threads (32 problems at a time for
+ * a batch); the environment variable EBE_HOST_THREADS (an integer >= 1) caps
+ * them.  The partition does not depend on the thread count.
  * Errors: EBE_INVALID_ARG, EBE_INDEX_RANGE, EBE_CUDA_ERROR, EBE_OOM.
  * On error *h is NULL. */
 ebe_status ebe_create(ebe_handle** h, const ebe_mesh* mesh, const ebe_create_opts* opts,

@@ -355,7 +355,7 @@ static int create_batch_impl(ebe_handle* h, const ebe_mesh* meshes, int n_prob, 
         if (!meshes[k].coords || !meshes[k].elems)
             return fail(h, EBE_INVALID_ARG, "problem " + std::to_string(k) + ": coords and elems must be non-NULL");
     std::string err;
-    const int threads = int(std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+    const int threads = host_threads(32);
     int s = build_batch_plan(meshes, n_prob, threads, h->plan, h->lay, err);
     if (s != EBE_OK) return fail(h, s, err);
     h->n_prob = n_prob;
@@ -1387,7 +1387,7 @@ ebe_status ebe_partition_export_batch(const ebe_mesh* meshes, int32_t n_problems
     HostPlan P;
     BatchLayout L;
     std::string err;
-    const int threads = int(std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+    const int threads = host_threads(32);
     int s = build_batch_plan(meshes, n_problems, threads, P, L, err);
     if (s != EBE_OK) { g_create_error = err; return ebe_status(s); }
     export_plan(P, sz, slot_elem, lconn, patch_meta, pnode, col_ptr, sh_node, sh_ptr, sh_slot);

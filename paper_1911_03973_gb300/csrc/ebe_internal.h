@@ -85,6 +85,10 @@ struct HostPlan {
     int max_col = 0;
 };
 
+// Host threads for the partition build: EBE_HOST_THREADS if set (>= 1),
+// else the hardware's, at most `cap`.
+int host_threads(int cap);
+
 // Validate the mesh and build the partition.  Returns an ebe_status.
 int build_plan(const ebe_mesh& m, HostPlan& plan, std::string& err);
 

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <thread>
@@ -110,10 +111,18 @@ void radix_sort_u64(HostVec<uint64_t>& a, int lo_bit, int threads) {
     }
 }
 
-int host_threads() {
+}  // namespace
+
+int host_threads(int cap) {
+    if (const char* env = std::getenv("EBE_HOST_THREADS")) {   // a user's cap, 1..64
+        const int v = std::atoi(env);
+        if (v >= 1) return std::min(v, std::min(cap, 64));
+    }
     const unsigned h = std::thread::hardware_concurrency();
-    return int(std::max(1u, std::min(16u, h)));
+    return int(std::max(1u, std::min(unsigned(cap), h)));
 }
+
+namespace {
 
 int bits_for(uint64_t n) {  // smallest b with n <= 2^b
     int b = 0;
@@ -137,7 +146,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
     // ---- validation: finite coords, ids in range, distinct within an element,
     // every node in some element.  Each check runs over host threads in
     // blocks; the lowest failing index is reported, as a serial scan would.
-    const int threads = host_threads();
+    const int threads = host_threads(16);
     {
         const int64_t nc = n_n * dim;
         const int64_t bad = first_failing(nc, threads, [&](int64_t k) { return !std::isfinite(m.coords[k]); });

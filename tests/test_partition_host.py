@@ -167,3 +167,35 @@ def test_validation_reports_the_first_failure_on_a_large_mesh(ebe):
     with pytest.raises(ebe.EbeError) as ei:
         ebe.ebe_partition_export(c, e[~touch])
     assert ei.value.status == 1 and "node 100000 " in str(ei.value), str(ei.value)
+
+
+def test_partition_does_not_depend_on_the_host_thread_count():
+    # the same meshes partitioned on 1 and on 8 host threads (EBE_HOST_THREADS),
+    # each in a process of its own: every table is byte-identical
+    import hashlib
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import hashlib, numpy as np, paper_1911_03973_gb300 as ebe\n"
+        "from paper_1911_03973_gb300 import meshgen\n"
+        "p = meshgen.config_square_jitter(513, nu=1.0, seed=2)\n"
+        "c, e = meshgen.cube_tet(31)\n"
+        "c, e, _, _ = meshgen.permute_nodes(c, e, [], seed=6)\n"
+        "e = e[np.random.default_rng(7).permutation(e.shape[0])]\n"
+        "for cc, ee in ((p['coords'], p['elems']), (c, e)):\n"
+        "    P = ebe.ebe_partition_export(cc, ee)\n"
+        "    h = hashlib.sha256()\n"
+        "    for k in sorted(P):\n"
+        "        h.update(k.encode()); h.update(np.ascontiguousarray(np.asarray(P[k])).tobytes())\n"
+        "    print(h.hexdigest())\n")
+    out = []
+    for t in ("1", "8"):
+        env = dict(os.environ, EBE_HOST_THREADS=t)
+        env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+        res = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert res.returncode == 0, res.stderr[-2000:]
+        out.append(res.stdout.split())
+    assert len(out[0]) == 2 and out[0] == out[1], out

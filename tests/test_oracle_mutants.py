@@ -7,7 +7,9 @@ out -- compiled into a library of its own.  The pin tests
 fail; the unmodified source, compiled the same way, must pass them.  The
 learned-preconditioner oracle ``oracle/mpnn.py`` is treated the same way: a
 mutated copy is imported in place of the module before its pins
-(``tests/test_mpnn_oracle.py``) run.  The mistakes are planted in copies
+(``tests/test_mpnn_oracle.py``) run; so is the Python layer of the oracle
+(``oracle/__init__.py``: wrappers, Dirichlet lift, Chebyshev roots), as a
+mutated copy of the whole package placed first on the import path.  The mistakes are planted in copies
 under pytest's temporary directory; the oracle itself is never changed.
 """
 import os
@@ -187,3 +189,65 @@ def test_planted_mpnn_mistake_is_caught(tmp_path, name, old, new):
         f.write(src.replace(old, new))
     res = _run_mpnn_pins(path)
     assert res.returncode == 1, (name, res.stdout[-2000:])
+
+
+# (name, exact text in oracle/__init__.py, replacement); each text occurs once.
+PKG_MUTANTS = [
+    ("Dirichlet values not carried by the iterate", "x[self.nd] = self.g", "x[self.nd] = 0.0"),
+    ("default x0 of the relative residual without g", "x0 = self.with_dirichlet(np.zeros(self.n_n))",
+     "x0 = np.zeros(self.n_n)"),
+    ("PCG ignores the given x0", "x = self.with_dirichlet(np.zeros(self.n_n) if x0 is None else x0)",
+     "x = self.with_dirichlet(np.zeros(self.n_n))"),
+    ("PCG status codes swapped", '{0: "converged", 1: "maxit", 2: "breakdown"}', '{0: "maxit", 1: "converged", 2: "breakdown"}'),
+    ("PCG info fields swapped", '"iterations": int(info[0]), "rel_residual": float(info[1]),',
+     '"iterations": int(info[1]), "rel_residual": float(info[0]),'),
+    ("dense K and M swapped", 'src = {"A": self._Ab, "K": self._Kb, "M": self._Mb}[which]',
+     'src = {"A": self._Ab, "K": self._Mb, "M": self._Kb}[which]'),
+    ("nu ignored", 'self.nu = float(prob["nu"])', "self.nu = 1.0"),
+    ("Chebyshev roots: centre and half-width swapped", "d, c = 0.5 * (lam1 + lam2), 0.5 * (lam2 - lam1)",
+     "d, c = 0.5 * (lam2 - lam1), 0.5 * (lam1 + lam2)"),
+    ("Chebyshev roots at the wrong angles", "math.cos(math.pi * (k + 0.5) / N)", "math.cos(math.pi * (k + 1.0) / N)"),
+]
+
+
+def _copy_package(dst_root, text):
+    import shutil
+    pkg = os.path.join(dst_root, "oracle")
+    os.makedirs(pkg)
+    for name in ("ebe_oracle.c", "mpnn.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", name), os.path.join(pkg, name))
+    with open(os.path.join(pkg, "__init__.py"), "w") as f:
+        f.write(text)
+
+
+def _run_pins_with_package(dst_root):
+    env = dict(os.environ)
+    env.pop("EBE_ORACLE_LIB", None)
+    env["PYTHONPATH"] = dst_root + os.pathsep + ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    # run from the copy's directory: `python -c` puts the working directory
+    # first on the import path; exit code 3 if the copy was not the one imported
+    code = ("import sys, oracle, pytest\n"
+            "if not oracle.__file__.startswith(sys.argv[1]): sys.exit(3)\n"
+            "sys.exit(pytest.main([sys.argv[2], '-x', '-q', '-p', 'no:cacheprovider', '-m', 'not gpu']))\n")
+    return subprocess.run([sys.executable, "-c", code, dst_root, os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          cwd=dst_root, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _package_source():
+    with open(os.path.join(ROOT, "oracle", "__init__.py")) as f:
+        return f.read()
+
+
+def test_unmodified_package_copy_passes_the_pins(tmp_path):
+    _copy_package(str(tmp_path), _package_source())
+    res = _run_pins_with_package(str(tmp_path))
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", PKG_MUTANTS, ids=[m[0] for m in PKG_MUTANTS])
+def test_planted_package_mistake_is_caught(tmp_path, name, old, new):
+    src = _package_source()
+    assert src.count(old) == 1, name
+    _copy_package(str(tmp_path), src.replace(old, new))
+    res = _run_pins_with_package(str(tmp_path))
+    assert res.returncode == 1, (name, res.stdout[-2000:], res.stderr[-2000:])

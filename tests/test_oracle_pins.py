@@ -336,10 +336,15 @@ def test_jacobi_pcg_is_invariant_under_diagonal_scaling():
         np.testing.assert_allclose(s * y, x, rtol=1e-11, atol=1e-13)
 
 
-def test_relative_residual_along_the_segment_to_the_solution():
+@pytest.mark.parametrize("case", ["jitter_g0", "lifted_g1"])
+def test_relative_residual_along_the_segment_to_the_solution(case):
     """x_t = x0 + t (x* - x0) has b - A x_t = (1 - t)(b - A x0) when A x* = b,
-    so its relative residual is |1 - t|."""
-    prob = meshgen.config_square_jitter(9, nu=1.0, seed=6)
+    so its relative residual is |1 - t| (x0: the zero iterate carrying g, the
+    default; Sec. 3's u = 1 on the boundary makes g nonzero)."""
+    if case == "jitter_g0":
+        prob = meshgen.config_square_jitter(9, nu=1.0, seed=6)
+    else:
+        prob = meshgen.config_square_f1(9, nu=0.0, g_value=1.0)
     p = oracle.Problem(prob)
     A, b = p.dense("A"), p.dense("M") @ prob["f"]
     nd = prob["dirichlet"]
@@ -349,6 +354,27 @@ def test_relative_residual_along_the_segment_to_the_solution():
     x0 = p.with_dirichlet(np.zeros(p.n_n))
     for t in (0.0, 0.25, 0.5, 1.5):
         assert p.rel_residual(x0 + t * (xs - x0)) == pytest.approx(abs(1.0 - t), abs=1e-12)
+
+
+def test_pcg_from_one_eigenvector_away_takes_one_step():
+    """On the SW-NE square with nu = 0 and Dirichlet 0 on the whole boundary the
+    masked K is the 5-point Laplacian times 1 (diagonal 4), so Jacobi-PCG is CG
+    and sin(pi x) sin(2 pi y) at the nodes is an eigenvector: started at
+    x* + 0.3 v, one step lands on x*."""
+    n = 17
+    prob = meshgen.config_square_f1(n, nu=0.0)
+    p = oracle.Problem(prob)
+    A, b = p.dense("A"), p.dense("M") @ prob["f"]
+    nd = prob["dirichlet"]
+    free = np.setdiff1d(np.arange(p.n_n), nd)
+    xs = np.zeros(p.n_n)
+    xs[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
+    xy = prob["coords"]
+    v = np.sin(np.pi * xy[:, 0]) * np.sin(2 * np.pi * xy[:, 1])
+    v[nd] = 0.0
+    x, info = p.pcg(x0=xs + 0.3 * v, rtol=1e-10)
+    assert info["status"] == "converged" and info["iterations"] == 1, info
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-12 * np.abs(xs).max())
 
 
 @pytest.mark.parametrize("dim", [2, 3])

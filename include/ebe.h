@@ -31,6 +31,13 @@
  *   rows of a residual or an operator application are set to zero, as in the
  *   paper's listings (r(nd) = 0 after every residual, Sec. 2.1).
  * - A handle is not thread-safe: one host thread at a time per handle.
+ *
+ * Call sequence: ebe_create (mesh) -> ebe_set_problem (nu, f, boundary sets)
+ * -> ebe_assemble (element matrices, b, Jacobi diagonal) -> any number of
+ * ebe_residual / ebe_apply / ebe_solve / ebe_richardson / ebe_chebyshev* ->
+ * ebe_destroy.  ebe_set_problem may be called again (then ebe_assemble
+ * again); batches use ebe_create_batch / ebe_set_problem_batch /
+ * ebe_solve_batch in the same order.
  */
 #ifndef EBE_H
 #define EBE_H

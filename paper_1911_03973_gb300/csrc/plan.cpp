@@ -111,6 +111,58 @@ void radix_sort_u64(HostVec<uint64_t>& a, int lo_bit, int threads) {
     }
 }
 
+// Ascending sort of distinct 64-bit values: one bucket pass on the 12 highest
+// occupied bits (histogram and scatter split over host threads in contiguous
+// blocks), then every bucket sorted on its own by the threads, in cache.
+// Distinct values have one sorted order, so the result equals any other
+// sort's.  Buckets above 2^20 values (a strongly clustered input) fall back
+// to the LSD radix sort of the whole array.
+void sort_distinct_u64(HostVec<uint64_t>& a, int threads) {
+    constexpr int kBits = 12, kBuckets = 1 << kBits;
+    constexpr int64_t kMaxBucket = int64_t(1) << 20;
+    const int64_t n = int64_t(a.size());
+    if (n < 2) return;
+    uint64_t any = 0;
+    for (uint64_t v : a) any |= v;
+    if (any == 0) return;
+    const int hb = 63 - __builtin_clzll(any);
+    const int shift = std::max(0, hb + 1 - kBits);
+    const int nt = int(std::max<int64_t>(1, std::min<int64_t>(threads, n / 65536 + 1)));
+    std::vector<int64_t> count(size_t(nt) * kBuckets, 0);
+    parallel_blocks(n, nt, [&](int t, int64_t b, int64_t e) {
+        int64_t* c = count.data() + size_t(t) * kBuckets;
+        for (int64_t i = b; i < e; ++i) ++c[a[i] >> shift];
+    });
+    std::vector<int64_t> start(kBuckets + 1, 0);
+    int64_t sum = 0, biggest = 0;
+    for (int d = 0; d < kBuckets; ++d) {
+        start[d] = sum;
+        for (int t = 0; t < nt; ++t) {
+            int64_t& c = count[size_t(t) * kBuckets + d];
+            const int64_t v = c;
+            c = sum;
+            sum += v;
+        }
+        biggest = std::max(biggest, sum - start[d]);
+    }
+    start[kBuckets] = sum;
+    if (biggest > kMaxBucket) { radix_sort_u64(a, 0, threads); return; }
+    HostVec<uint64_t> tmp(a.size());   // every entry is written by the scatter
+    parallel_blocks(n, nt, [&](int t, int64_t b, int64_t e) {
+        int64_t* c = count.data() + size_t(t) * kBuckets;
+        for (int64_t i = b; i < e; ++i) tmp[c[a[i] >> shift]++] = a[i];
+    });
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int d = next++; d < kBuckets; d = next++) std::sort(tmp.begin() + start[d], tmp.begin() + start[d + 1]);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+    a.swap(tmp);
+}
+
 }  // namespace
 
 int host_threads(int cap) {
@@ -222,9 +274,9 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             keys[e] = (key << ebits) | uint64_t(e);
         }
     });
-    // the low ebits hold the element id, already ascending: a stable sort by
-    // the Morton bits alone gives the order of the full keys
-    radix_sort_u64(keys, ebits, threads);
+    // the low ebits hold the element id, so the keys are distinct and their
+    // sorted order is the Morton order with ties kept in element order
+    sort_distinct_u64(keys, threads);
     const uint64_t emask = ebits >= 64 ? ~0ull : ((uint64_t(1) << ebits) - 1);
 
     // ---- patches, built independently on host threads (scratch per thread:

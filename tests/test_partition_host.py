@@ -199,3 +199,17 @@ def test_partition_does_not_depend_on_the_host_thread_count():
         assert res.returncode == 0, res.stderr[-2000:]
         out.append(res.stdout.split())
     assert len(out[0]) == 2 and out[0] == out[1], out
+
+
+def test_clustered_mesh_partition(ebe):
+    # 1.2 M small triangles in a corner of a bounding box stretched by one
+    # large triangle: almost every Morton key shares its 12 highest bits, so
+    # the key sort takes its fallback (a bucket above 2^20 keys); the
+    # partition must still satisfy every invariant
+    c, e = meshgen.square_tri(776)
+    c = c * 1e-3
+    n0 = c.shape[0]
+    c = np.vstack([c, [[10.0, 0.0], [0.0, 10.0], [10.0, 10.0]]])
+    e = np.vstack([e, [[n0, n0 + 2, n0 + 1]]]).astype(np.int32)
+    P = ebe.ebe_partition_export(c, e)
+    check_partition(P, c, e)

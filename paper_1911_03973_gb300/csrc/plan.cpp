@@ -432,28 +432,43 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                 set_used.assign(n_set, 0u);
                 int cap[2][32] = {};
                 for (int l = 0; l < n_nodes; ++l) ++cap[l < n_owned ? 0 : 1][l % 32];
+                uint32_t open_banks[2] = {0u, 0u};   // bit b: bank b still has a free id in the block
+                for (int blk = 0; blk < 2; ++blk)
+                    for (int b = 0; b < 32; ++b) open_banks[blk] |= (cap[blk][b] > 0 ? 1u : 0u) << b;
                 bank.assign(n_nodes, 0);
                 for (int l : visit) {
                     const int blk = l < n_owned ? 0 : 1;
                     uint32_t busy = 0;
                     for (int k = first_set[l]; k < first_set[l + 1]; ++k) busy |= set_used[set_list[k]];
-                    uint32_t open = 0;
-                    for (int b = 0; b < 32; ++b) open |= (cap[blk][b] > 0 ? 1u : 0u) << b;
+                    const uint32_t open = open_banks[blk];
                     int best;
                     if (open & ~busy) {
                         best = __builtin_ctz(open & ~busy);
-                    } else {   // every open bank conflicts somewhere: fewest conflicting sets
-                        int cost[32] = {};
-                        for (int k = first_set[l]; k < first_set[l + 1]; ++k)
-                            for (uint32_t u = set_used[set_list[k]]; u; u &= u - 1) ++cost[__builtin_ctz(u)];
-                        best = -1;
-                        for (uint32_t u = open; u; u &= u - 1) {
-                            const int b = __builtin_ctz(u);
-                            if (best < 0 || cost[b] < cost[best]) best = b;
+                    } else {   // every open bank conflicts somewhere: fewest conflicting sets, lowest bank on ties
+                        // the 32 banks' counts as bit planes (plane j holds bit j of every count),
+                        // each set added with a ripple carry
+                        uint32_t plane[32];
+                        int np = 0;
+                        for (int k = first_set[l]; k < first_set[l + 1]; ++k) {
+                            uint32_t carry = set_used[set_list[k]];
+                            for (int j = 0; carry != 0; ++j) {
+                                if (j == np) plane[np++] = 0u;
+                                const uint32_t t = plane[j] & carry;
+                                plane[j] ^= carry;
+                                carry = t;
+                            }
                         }
+                        // the open banks of least count: from the highest plane down, keep those
+                        // with a zero bit whenever any has one
+                        uint32_t cand = open;
+                        for (int j = np - 1; j >= 0; --j) {
+                            const uint32_t z = cand & ~plane[j];
+                            if (z) cand = z;
+                        }
+                        best = __builtin_ctz(cand);
                     }
                     bank[l] = best;
-                    --cap[blk][best];
+                    if (--cap[blk][best] == 0) open_banks[blk] &= ~(1u << best);
                     for (int k = first_set[l]; k < first_set[l + 1]; ++k) set_used[set_list[k]] |= 1u << best;
                 }
                 // ids by bank, in each block in order of first appearance

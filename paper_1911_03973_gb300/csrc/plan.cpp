@@ -312,7 +312,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
         std::vector<uint32_t> filled;   // table slots in use, cleared slot by slot after each patch
         std::vector<uint64_t> used;
         std::vector<int> colour(kPatch);
-        std::vector<int> order, gidx, first_set, set_list, set_fill, perm, bank, visit;
+        std::vector<int> cstart, order, gidx, first_set, set_list, set_fill, perm, bank, visit;
         std::vector<int32_t> renum;
         std::vector<uint32_t> set_used;
         auto slot_of = [&](int32_t g) {
@@ -380,13 +380,13 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
             }
             out.n_col = n_col;
             // slots: elements grouped by colour, Morton order within a colour
-            order.clear();
-            for (int c = 0; c < n_col; ++c) {
-                out.col_ptr.push_back(int32_t(order.size()));
-                for (int s = 0; s < n_el; ++s)
-                    if (colour[s] == c) order.push_back(s);
-            }
-            out.col_ptr.push_back(int32_t(order.size()));
+            // (a counting sort by colour: stable, so Morton order is kept)
+            cstart.assign(n_col + 1, 0);
+            for (int s = 0; s < n_el; ++s) ++cstart[colour[s] + 1];
+            for (int c = 0; c < n_col; ++c) cstart[c + 1] += cstart[c];
+            out.col_ptr.assign(cstart.begin(), cstart.end());
+            order.resize(n_el);
+            for (int s = 0; s < n_el; ++s) order[cstart[colour[s]]++] = s;
             // Local numbering for the shared-memory banks.  The patch kernel
             // gives 32 consecutive slots to a warp; in a colour round its
             // lanes read-modify-write the node sums of vertex r of their

@@ -372,8 +372,7 @@ int build_plan(const ebe_mesh& m, HostPlan& P, std::string& err) {
                     reset();
                     return;
                 }
-                int c = 0;
-                while (busy & (1ull << c)) ++c;
+                const int c = __builtin_ctzll(~busy);   // lowest free colour (busy != ~0 here)
                 colour[s] = c;
                 n_col = std::max(n_col, c + 1);
                 for (int i = 0; i < nb; ++i) used[v[i]] |= (1ull << c);

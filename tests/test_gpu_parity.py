@@ -246,6 +246,38 @@ def test_errors_reported_not_raised_on_device(ebe):
     assert ei.value.status == 10
 
 
+def test_set_problem_rejects_bad_data_on_the_host(ebe):
+    # nu < 0 or not finite, f or g not finite, a Dirichlet node listed twice
+    # or out of range, a node in both boundary sets: each is refused before any
+    # device work, and the handle then takes a valid problem and solves it
+    c, e = meshgen.square_tri(5)
+    n = c.shape[0]
+    nd = meshgen.square_boundary_nodes(5)
+    f = np.ones(n)
+    h = ebe.ebe_create(c, e)
+    cases = [
+        (dict(nu=-1.0), 1),
+        (dict(nu=float("nan")), 1),
+        (dict(f=np.where(np.arange(n) == 7, np.nan, 1.0)), 1),
+        (dict(g=np.where(np.arange(nd.size) == 0, np.inf, 0.0)), 1),
+        (dict(dirichlet=np.concatenate([nd, nd[:1]])), 1),
+        (dict(dirichlet=np.array([0, n], np.int32)), 2),
+        (dict(neumann=nd[:2]), 1),
+    ]
+    for change, status in cases:
+        a = dict(nu=1.0, f=f, dirichlet=nd, g=None, neumann=None)
+        a.update(change)
+        with pytest.raises(ebe.EbeError) as ei:
+            ebe.ebe_set_problem(h, a["nu"], a["f"], a["dirichlet"], a["g"], a["neumann"])
+        assert ei.value.status == status, (change, str(ei.value))
+    ebe.ebe_set_problem(h, 1.0, f, nd)
+    ebe.ebe_assemble(h)
+    x = torch.zeros(n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve(h, x, rtol=1e-8)
+    assert info["status"] == "EBE_OK", info
+    ebe.ebe_destroy(h)
+
+
 def test_random_meshes_residuals_match_oracle(ebe):
     # random sizes, jitter, node and element orders; triangles use colour rounds,
     # tetrahedra (many colours per patch) the per-warp node sums in FP32

@@ -12,6 +12,7 @@ mutated copy is imported in place of the module before its pins
 mutated copy of the whole package placed first on the import path.  The mistakes are planted in copies
 under pytest's temporary directory; the oracle itself is never changed.
 """
+import concurrent.futures as cf
 import os
 import subprocess
 import sys
@@ -86,6 +87,14 @@ MUTANTS = [
 ]
 
 
+def _env(**extra):
+    """The subprocesses' environment: the repository on the import path and one
+    BLAS thread each (several pin runs go at once)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", **extra)
+    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    return env
+
+
 def _compile(src_text, out_dir, name):
     c = os.path.join(out_dir, name + ".c")
     so = os.path.join(out_dir, name + ".so")
@@ -96,8 +105,7 @@ def _compile(src_text, out_dir, name):
 
 
 def _run_pins(lib):
-    env = dict(os.environ, EBE_ORACLE_LIB=lib)
-    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    env = _env(EBE_ORACLE_LIB=lib)
     return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
                            "-p", "no:cacheprovider", "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
                           timeout=600)
@@ -113,11 +121,14 @@ def test_unmodified_copy_passes_the_pins(tmp_path):
     assert res.returncode == 0, res.stdout[-2000:]
 
 
+def _run_c_mutant(d, old, new):
+    return _run_pins(_compile(_source().replace(old, new), d, "mutant"))
+
+
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_is_caught(tmp_path, name, old, new):
-    src = _source()
-    assert src.count(old) == 1, name
-    res = _run_pins(_compile(src.replace(old, new), str(tmp_path), "mutant"))
+def test_planted_mistake_is_caught(mutant_runs, name, old, new):
+    assert _source().count(old) == 1, name
+    res = mutant_runs[("c", name)]
     assert res.returncode == 1, (name, res.stdout[-2000:])   # 1: some pin failed (not a crash or a usage error)
 
 
@@ -161,8 +172,7 @@ _MPNN_DRIVER = (
 
 
 def _run_mpnn_pins(path):
-    env = dict(os.environ)
-    env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    env = _env()
     return subprocess.run([sys.executable, "-c", _MPNN_DRIVER, path, os.path.join(ROOT, "tests", "test_mpnn_oracle.py")],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
@@ -180,14 +190,17 @@ def test_unmodified_mpnn_copy_passes_the_pins(tmp_path):
     assert res.returncode == 0, res.stdout[-2000:]
 
 
-@pytest.mark.parametrize("name,old,new", MPNN_MUTANTS, ids=[m[0] for m in MPNN_MUTANTS])
-def test_planted_mpnn_mistake_is_caught(tmp_path, name, old, new):
-    src = _mpnn_source()
-    assert src.count(old) == 1, name
-    path = os.path.join(str(tmp_path), "mpnn_mutant.py")
+def _run_mpnn_mutant(d, old, new):
+    path = os.path.join(d, "mpnn_mutant.py")
     with open(path, "w") as f:
-        f.write(src.replace(old, new))
-    res = _run_mpnn_pins(path)
+        f.write(_mpnn_source().replace(old, new))
+    return _run_mpnn_pins(path)
+
+
+@pytest.mark.parametrize("name,old,new", MPNN_MUTANTS, ids=[m[0] for m in MPNN_MUTANTS])
+def test_planted_mpnn_mistake_is_caught(mutant_runs, name, old, new):
+    assert _mpnn_source().count(old) == 1, name
+    res = mutant_runs[("mpnn", name)]
     assert res.returncode == 1, (name, res.stdout[-2000:])
 
 
@@ -221,9 +234,9 @@ def _copy_package(dst_root, text):
 
 
 def _run_pins_with_package(dst_root):
-    env = dict(os.environ)
+    env = _env()
     env.pop("EBE_ORACLE_LIB", None)
-    env["PYTHONPATH"] = dst_root + os.pathsep + ROOT + os.pathsep + env.get("PYTHONPATH", "")
+    env["PYTHONPATH"] = dst_root + os.pathsep + env["PYTHONPATH"]
     # run from the copy's directory: `python -c` puts the working directory
     # first on the import path; exit code 3 if the copy was not the one imported
     code = ("import sys, oracle, pytest\n"
@@ -244,10 +257,26 @@ def test_unmodified_package_copy_passes_the_pins(tmp_path):
     assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
 
 
+def _run_pkg_mutant(d, old, new):
+    _copy_package(d, _package_source().replace(old, new))
+    return _run_pins_with_package(d)
+
+
 @pytest.mark.parametrize("name,old,new", PKG_MUTANTS, ids=[m[0] for m in PKG_MUTANTS])
-def test_planted_package_mistake_is_caught(tmp_path, name, old, new):
-    src = _package_source()
-    assert src.count(old) == 1, name
-    _copy_package(str(tmp_path), src.replace(old, new))
-    res = _run_pins_with_package(str(tmp_path))
+def test_planted_package_mistake_is_caught(mutant_runs, name, old, new):
+    assert _package_source().count(old) == 1, name
+    res = mutant_runs[("pkg", name)]
     assert res.returncode == 1, (name, res.stdout[-2000:], res.stderr[-2000:])
+
+
+@pytest.fixture(scope="module")
+def mutant_runs(tmp_path_factory):
+    """Every mutant's pin run, each in its own directory and process, several
+    at a time on a thread pool; keyed by (kind, name)."""
+    jobs = ([("c", m, _run_c_mutant) for m in MUTANTS] + [("mpnn", m, _run_mpnn_mutant) for m in MPNN_MUTANTS]
+            + [("pkg", m, _run_pkg_mutant) for m in PKG_MUTANTS])
+    assert len({(kind, m[0]) for kind, m, _ in jobs}) == len(jobs), "mutant names must be unique"
+    dirs = [str(tmp_path_factory.mktemp("mutant")) for _ in jobs]
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+        futs = {(kind, m[0]): ex.submit(fn, d, m[1], m[2]) for (kind, m, fn), d in zip(jobs, dirs)}
+        return {key: f.result() for key, f in futs.items()}

@@ -33,9 +33,18 @@ operator rooflines.  "paper_experiment": the paper's own timed experiment
 (Sec. 3, the 1025^2 square: element arrays and 124 Richardson / Chebyshev
 iterations), beside the MATLAB times the paper quotes, as context.
 
-"learned" (with --learned): the message-passing preconditioner trained on
-257^2 squares and deployed in flexible CG on 1025^2 and 2049^2, against
+"nu0" (skip with --no-nu0): the same 2049^2 workload with nu = 0, mixed and
+plain FP64.  "square33" (skip with --no-small): the 33^2 square (2048
+triangles, nu = 1, f = 1, Dirichlet 0), time to solution and per iteration.
+"residual_variants_fp64" (skip with --no-variants): the FP64 residual with the
+patch scatter against the node-centric, colour-by-colour and atomic ones.
+
+"learned" (skip with --no-learned): the message-passing preconditioner trained
+on 257^2 squares and deployed in flexible CG on 1025^2 and 2049^2, against
 flexible CG with Jacobi and Jacobi-PCG (plain FP64 and mixed).
+
+"summary", the line's last key, repeats every number of the metric in short
+form: PCG time to 1e-8, mixed against plain FP64, per workload.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
 sample of the same workload.
@@ -71,12 +80,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", action="store_true", help="also time the comparison scatters")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the comparison scatters")
+    ap.add_argument("--no-nu0", action="store_true", help="skip the nu = 0 leg of the 2049^2 workload")
+    ap.add_argument("--no-small", action="store_true", help="skip the 33^2 workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload (256 independent squares)")
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
-    ap.add_argument("--learned", action="store_true",
-                    help="also train the learned preconditioner (257^2) and deploy it (1025^2, 2049^2)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training the learned preconditioner (257^2) and deploying it (1025^2, 2049^2)")
     ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
@@ -389,6 +400,50 @@ def run_cube(args, dev, stream):
     return out
 
 
+def _timed_solve(ebe, torch, h, x, stream, reps, **kw):
+    """Best of `reps` timed ebe_solve calls from x0 = 0 (CUDA events on the
+    handle's stream, one untimed call first); returns (ms, info)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    x.zero_()
+    ebe.ebe_solve(h, x, **kw)
+    best, info = None, None
+    for _ in range(reps):
+        x.zero_()
+        ev[0].record(stream)
+        i = ebe.ebe_solve(h, x, **kw)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if i["status"] != "EBE_OK":
+            raise RuntimeError(f"solve failed: {i}")
+        t = ev[0].elapsed_time(ev[1])
+        if best is None or t < best:
+            best, info = t, i
+    return best, info
+
+
+def run_pcg_leg(args, dev, stream, prob, reps=1):
+    """Mixed-precision and plain FP64 Jacobi-PCG to FP64 rel. residual rtol on
+    one problem, element matrices assembled beforehand (both stored):
+    CUDA-event times of ebe_solve, iterations, speed-up of mixed over plain."""
+    import torch
+    import paper_1911_03973_gb300 as ebe
+    n_n = prob["coords"].shape[0]
+    with torch.cuda.stream(stream):
+        h = ebe.ebe_create(prob["coords"], prob["elems"], device=dev.index, stream=stream.cuda_stream)
+        ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+        ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        x = torch.zeros(n_n, dtype=torch.float64, device=dev)
+        out = {}
+        for key, prec in (("mixed", ebe.EBE_PREC_MIXED), ("plain_fp64", ebe.EBE_PREC_FP64)):
+            ms, info = _timed_solve(ebe, torch, h, x, stream, reps, rtol=args.rtol, precision=prec)
+            out[key] = {"ms_to_1e-8": round(ms, 3), "iterations": info["iterations"],
+                        "true_residuals": info["true_residuals"], "rel_residual": info["rel_residual"],
+                        "us_per_iteration": round(1e3 * ms / max(info["iterations"], 1), 2)}
+        out["speedup_vs_plain"] = round(out["plain_fp64"]["ms_to_1e-8"] / out["mixed"]["ms_to_1e-8"], 3)
+        ebe.ebe_destroy(h)
+    return out
+
+
 def run_paper_experiment(dev, stream):
     """The paper's own timed experiment (Sec. 3), as context: the 1025^2 square,
     nu = 0, f = 1, u = 1 on the boundary; the element matrix arrays K_e, M_e and
@@ -431,10 +486,15 @@ def run_paper_experiment(dev, stream):
             x.zero_()
             ebe.ebe_richardson(h, x, 124, 2.0 / (lam1 + lam2))
 
+        def cheb2():
+            x.zero_()
+            ebe.ebe_chebyshev2_bounds(h, x, 124, lam1, lam2, 32)
+
         def cheb3():
             x.zero_()
             ebe.ebe_chebyshev3(h, x, 124, lam1, lam2)
         out["richardson_124_ms"] = timed(rich)
+        out["chebyshev2_N32_124_ms"] = timed(cheb2)
         out["chebyshev3_124_ms"] = timed(cheb3)
         ebe.ebe_destroy(h)
     return out
@@ -645,7 +705,7 @@ def run_ours(args):
         r64 = torch.empty_like(x64)
         ms_patch64, ms_fix64 = ebe.ebe_time_operator(h, x64, r64, apply=False, reps=20)
         variants = None
-        if args.variants:
+        if not args.no_variants:
             variants = {}
             for name in ("PATCH", "COLOUR", "NODE", "ATOMIC"):
                 code = getattr(ebe, f"EBE_SCATTER_{name}")
@@ -708,10 +768,18 @@ def run_ours(args):
                            "ebe_solve_host + ebe_destroy",
                "ms_per_call": {k: round(v, 1) for k, v in parts.items()}}
 
+    nu0 = None
+    if rank == 0 and not args.no_nu0:
+        nu0 = run_pcg_leg(args, dev, stream, meshgen.config_square_jitter(args.n, nu=0.0, seed=2))
+        nu0 = {"workload": f"square{args.n}_jitter0.2_nu0_tri", **nu0}
+    small = None
+    if rank == 0 and not args.no_small:
+        small = run_pcg_leg(args, dev, stream, meshgen.config_square_f1(33, nu=1.0), reps=5)
+        small = {"workload": "square33_f1_nu1_dirichlet0 (2048 triangles)", **small}
     batched = None
     if not args.no_batch:
         batched = run_batch(args, dev, stream)
-    learned_res = run_learned(args, dev, stream) if args.learned else None
+    learned_res = run_learned(args, dev, stream) if rank == 0 and not args.no_learned else None
     paper_exp = run_paper_experiment(dev, stream) if rank == 0 else None
     cube = run_cube(args, dev, stream) if rank == 0 and not args.no_cube else None
 
@@ -759,6 +827,10 @@ def run_ours(args):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if nu0:
+        line["nu0"] = nu0
+    if small:
+        line["square33"] = small
     if batched:
         line["batched"] = batched
     if learned_res:
@@ -769,8 +841,48 @@ def run_ours(args):
         line["cube129"] = cube
     if paper_exp:
         line["paper_experiment"] = paper_exp
+    line["summary"] = summary_block(line, ms_plain, pinfo, peak)
     print(json.dumps(line), flush=True)
     return line
+
+
+def summary_block(line, ms_plain, pinfo, peak):
+    """Every number of the metric in a few hundred characters, as the line's
+    last key: PCG time to 1e-8, mixed against plain FP64, per workload, the
+    operators' HBM fractions and the comparison scatters."""
+    pc = line["pcg"]
+    r = line["roofline"]
+    s = {"sq2049_nu1": {"mixed_ms": pc["ms_to_1e-8"], "it": pc["iterations"],
+                        "plain_ms": round(ms_plain, 1) if ms_plain else None,
+                        "plain_it": pinfo[-1]["iterations"] if pinfo else None, "x": pc["speedup_vs_plain"]}}
+    for key, name in (("nu0", "sq2049_nu0"), ("square33", "sq33"), ("cube129", "cube129")):
+        v = line.get(key)
+        if v:
+            s[name] = {"mixed_ms": v["mixed"]["ms_to_1e-8"], "it": v["mixed"]["iterations"],
+                       "plain_ms": v["plain_fp64"]["ms_to_1e-8"], "plain_it": v["plain_fp64"]["iterations"],
+                       "x": v["speedup_vs_plain"]}
+    if "sq33" in s:
+        s["sq33"].update({"us_per_it": line["square33"]["mixed"]["us_per_iteration"],
+                          "plain_us_per_it": line["square33"]["plain_fp64"]["us_per_iteration"]})
+    b = line.get("batched")
+    if b:
+        s["batch256"] = {"mixed_ms": b["ms_to_1e-8"], "batched_fp64_ms": b["batched_fp64_ms"],
+                         "seq_fp64_ms": b["sequential_fp64_ms"], "x_vs_seq_fp64": b["speedup_vs_sequential_fp64"],
+                         "gbs": b["gbs"], "frac": round(b["gbs"] / peak, 3)}
+    lr = line.get("learned")
+    if lr:
+        s["learned"] = {k: {"fcg_net_ms": v["learned_fcg"]["ms"], "net_it": v["learned_fcg"]["iterations"],
+                            "fell_back": v["learned_fcg"]["fell_back"], "plain_pcg_ms": v["plain_fp64_pcg"]["ms"],
+                            "ratio_to_plain": round(v["learned_fcg"]["ms"] / v["plain_fp64_pcg"]["ms"], 3)}
+                        for k, v in lr.items() if k.startswith("square")}
+    s["hbm_frac"] = {"apply32": r["frac"], "residual64": line["residual_fp64"]["frac"]}
+    c = line.get("cube129")
+    if c:
+        s["hbm_frac"].update({"cube_apply32": c["apply32"]["frac"], "cube_residual64": c["residual64"]["frac"]})
+    v = line.get("residual_variants_fp64")
+    if v:
+        s["scatter_fp64_ms"] = {k: x["ms"] for k, x in v.items()}
+    return s
 
 
 def oracle_sample(prob, m, iters=10):

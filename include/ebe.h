@@ -284,6 +284,15 @@ ebe_status ebe_richardson(ebe_handle* h, double* x_dev, int64_t iters, double om
  * the roots of the shifted and scaled Chebyshev polynomial in the order the
  * caller chooses. */
 ebe_status ebe_chebyshev2(ebe_handle* h, double* x_dev, int64_t iters, const double* alphas, int64_t N);
+/* Eq. Czebyshev2lev in the paper's form: the library builds the N roots of
+ * the shifted and scaled Chebyshev polynomial P_N for the spectrum bounds
+ * 0 < lam1 < lam2 (Sec. 2.2), alpha_k = (lam1 + lam2)/2 + (lam2 - lam1)/2
+ * cos(pi (k + 1/2) / N), k = 0..N-1, and cycles through them in that order
+ * (the order of the paper's listing; with N = 32 on the Sec. 3 problem the
+ * partial products of a cycle amplify rounding errors, the instability the
+ * paper reports).  Errors: EBE_INVALID_ARG (bounds, 1 <= N <= 2^20), and as
+ * ebe_chebyshev2. */
+ebe_status ebe_chebyshev2_bounds(ebe_handle* h, double* x_dev, int64_t iters, double lam1, double lam2, int64_t N);
 /* Eq. Czebyshev3lev (the three-term recurrence with the scaling factors of
  * Eq. recrCk) for spectrum bounds 0 < lam1 < lam2, evaluated in the
  * equivalent direction form p = r + beta p, x += alpha p. */
@@ -325,6 +334,10 @@ typedef struct {
     int32_t ctas_per_sm;     /* CTAs per SM of the persistent kernel; 0 = as many as fit */
     int32_t tile_nodes;      /* nodes per work item of the vector phases: 1024, 2048 or 4096;
                                 0 = 2048                                                 */
+    int64_t barrier_ns;      /* bound of one grid-barrier wait in nanoseconds, 0 = 2 s.  A
+                                wait that runs out ends the launch: ebe_solve_batch returns
+                                EBE_CUDA_ERROR, the solution is invalid, and the handle
+                                stays usable for the next call                           */
 } ebe_batch_config;
 
 typedef struct {
@@ -362,7 +375,7 @@ ebe_status ebe_solve_batch_host(ebe_handle* h, double* x_host, const ebe_solve_o
 
 /* Set the launch shape of ebe_solve_batch for both precisions (NULL: back to
  * the defaults).  Errors: EBE_INVALID_ARG (tile_nodes not 0/1024/2048/4096,
- * ctas_per_sm outside [0, 8]); a ctas_per_sm that does not fit on an SM for
+ * ctas_per_sm outside [0, 8], barrier_ns < 0); a ctas_per_sm that does not fit on an SM for
  * the precision of a later ebe_solve_batch makes that call fail with
  * EBE_INVALID_ARG. */
 ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg);
@@ -448,18 +461,23 @@ ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x_dev, const 
 
 /* ---------------------------------------------------------------- allocation-free residual */
 
-/* ebe_residual (FP64) for callers that must not allocate device memory during
- * the call -- for instance code running while a stream is being captured into
- * a CUDA graph, where cudaMalloc is not allowed, or a process whose device
- * memory is owned by another allocator.  ebe_residual allocates its scratch
- * on first use; this call takes it from a fixed device array compiled into
- * the library (32 MiB: 4,194,304 doubles, held on every device that loads the
- * library until the process exits) and calls no allocator.  The paper has no
- * counterpart: this is an interface feature of the library.
+/* ebe_residual (FP64) for callers that cannot call cudaMalloc when they need
+ * a residual: a process whose device memory is handed out by another
+ * allocator (a framework's caching allocator, or a fixed pool that owns the
+ * whole device), or a real-time loop that must not take the allocator's
+ * locks or risk the implicit device synchronisation of cudaMalloc.
+ * ebe_residual allocates its scratch on first use; this call takes it from a
+ * fixed device array compiled into the library (32 MiB: 4,194,304 doubles,
+ * held on every device that loads the library until the process exits) and
+ * calls no allocator.  The paper has no counterpart: this is an interface
+ * feature of the library.
  * x_dev, r_dev: device [n_n] double (caller-owned), as for ebe_residual.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the array, so calls
- * whose kernels overlap on the GPU (several streams or handles at once) race.
+ * The first call on a device looks up the array's device address and keeps it
+ * for the life of the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) invalidates every handle on the
+ * device and that address: do not call the library on a device after
+ * resetting it.  All calls share the array, so calls whose kernels overlap on
+ * the GPU (several streams or handles at once) race.
  * Errors: EBE_NOT_READY, EBE_INVALID_ARG (also when the mesh needs more than
  * 4,194,304 halo slots, see ebe_stats.n_halo), EBE_CUDA_ERROR. */
 ebe_status ebe_residual_noalloc(ebe_handle* h, const double* x_dev, double* r_dev);

@@ -258,6 +258,11 @@ class Problem:
                                 iters, _p(alphas, _F64P), alphas.shape[0])
         return x
 
+    def chebyshev2_bounds(self, x0, iters, lam1, lam2, N):
+        """Eq. Czebyshev2lev with the roots of P_N for the bounds lam1 < lam2,
+        taken in the order of chebyshev_roots (the paper's listing)."""
+        return self.chebyshev2(x0, iters, chebyshev_roots(lam1, lam2, N))
+
     def chebyshev3(self, x0, iters, lam1, lam2):
         """Eq. Czebyshev3lev with the scaling factors of Eq. recrCk."""
         x = _f64(x0).copy()

@@ -335,9 +335,10 @@ def ebe_solve_batch_host(h: Handle, x, rtol=None, maxit=None, precision=None, de
     return _batch_result(h, infos, summary)
 
 
-def ebe_set_batch_config(h: Handle, ctas_per_sm: int = 0, tile_nodes: int = 0) -> None:
-    """Launch shape of ebe_solve_batch (0 = default for either field)."""
-    c = _abi.ebe_batch_config(int(ctas_per_sm), int(tile_nodes))
+def ebe_set_batch_config(h: Handle, ctas_per_sm: int = 0, tile_nodes: int = 0, barrier_ns: int = 0) -> None:
+    """Launch shape of ebe_solve_batch and the bound of its grid-barrier waits
+    (0 = default for every field)."""
+    c = _abi.ebe_batch_config(int(ctas_per_sm), int(tile_nodes), int(barrier_ns))
     _check(h, _lib().ebe_set_batch_config(h.ptr, ctypes.byref(c)))
 
 
@@ -454,7 +455,8 @@ def ebe_solve_learned(h: Handle, net, x, rtol=None, maxit=None, chunk=None, stal
 def ebe_residual_noalloc(h: Handle, x, r) -> None:
     """ebe_residual_noalloc: FP64 residual without any device allocation in the
     call (scratch from a fixed device array in the library), for callers that
-    cannot allocate, e.g. inside a CUDA-graph capture."""
+    cannot call cudaMalloc (device memory owned by another allocator, or a
+    loop that must not take the allocator's locks)."""
     _check(h, _lib().ebe_residual_noalloc(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), _dev(r, EBE_F64, h.n_n, "r")))
 
 
@@ -468,6 +470,13 @@ def ebe_chebyshev2(h: Handle, x, iters: int, alphas) -> None:
     a = _host_f64(alphas)
     _check(h, _lib().ebe_chebyshev2(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters),
                                     a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size))
+
+
+def ebe_chebyshev2_bounds(h: Handle, x, iters: int, lam1: float, lam2: float, N: int) -> None:
+    """Eq. Czebyshev2lev with the N roots of P_N built by the library from the
+    spectrum bounds lam1 < lam2, in the order of the paper's listing."""
+    _check(h, _lib().ebe_chebyshev2_bounds(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), int(iters), float(lam1), float(lam2),
+                                           int(N)))
 
 
 def ebe_chebyshev3(h: Handle, x, iters: int, lam1: float, lam2: float) -> None:

@@ -72,7 +72,7 @@ class ebe_partition_sizes(ctypes.Structure):
 
 
 class ebe_batch_config(ctypes.Structure):
-    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("tile_nodes", ctypes.c_int32)]
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("tile_nodes", ctypes.c_int32), ("barrier_ns", ctypes.c_int64)]
 
 
 class ebe_batch_info(ctypes.Structure):
@@ -132,6 +132,8 @@ SIGNATURES = [
     ("ebe_residual_noalloc", ctypes.c_int, [_H, _VP, _VP]),
     ("ebe_richardson", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double]),
     ("ebe_chebyshev2", ctypes.c_int, [_H, _VP, ctypes.c_int64, _F64P, ctypes.c_int64]),
+    ("ebe_chebyshev2_bounds", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int64]),
     ("ebe_chebyshev3", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double]),
     ("ebe_get_stats", ctypes.c_int, [_H, ctypes.POINTER(ebe_stats)]),
     ("ebe_partition_export", ctypes.c_int, [ctypes.POINTER(ebe_mesh), ctypes.POINTER(ebe_partition_sizes),

@@ -93,7 +93,7 @@ struct ebe_handle {
     int64_t* bloops = nullptr;
     unsigned long long* bphase = nullptr;   // [4] phase times of the persistent kernel
     int64_t* bcount_host = nullptr;      // pinned: loops, live, phase times [4]
-    ebe_batch_config bcfg[2] = {{0, 0}, {0, 0}};   // launch shape per precision (FP64, mixed)
+    ebe_batch_config bcfg[2] = {{0, 0, 0}, {0, 0, 0}};   // launch shape per precision (FP64, mixed)
     cudaGraphExec_t bgraph = nullptr;
     std::vector<double> bgraph_key;
 
@@ -184,12 +184,25 @@ void leave(ebe_handle* h) {
     }
 }
 
+// Makes `device` current for the lifetime of the guard and gives the caller
+// back the device that was current before, so that a host program driving
+// several GPUs keeps its own current device across library calls.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+        if (prev != device) cudaSetDevice(device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 struct Scope {
     ebe_handle* h;
-    explicit Scope(ebe_handle* hh) : h(hh) {
-        cudaSetDevice(h->device);
-        enter(h);
-    }
+    DeviceGuard dev;
+    explicit Scope(ebe_handle* hh) : h(hh), dev(hh->device) { enter(h); }
     ~Scope() { leave(h); }
 };
 
@@ -205,12 +218,19 @@ int check_ready(ebe_handle* h, bool need_assembled) {
     return EBE_OK;
 }
 
-// Reads the device error word on the handle's stream (synchronises it).
+// Reads the device error word on the handle's stream (synchronises it).  A
+// wait that gave up is reported once: the word is cleared again, so the
+// handle can run the next call (the results of this one are invalid).
 int check_device(ebe_handle* h) {
     int32_t e = 0;
     CK(cudaMemcpyAsync(&e, h->dev_err, sizeof(e), cudaMemcpyDeviceToHost, h->st), "read device flag");
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
-    if (e != 0) return fail(h, EBE_CUDA_ERROR, "a device-side wait timed out (bulk copy did not complete)");
+    if (e != 0) {
+        CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int32_t), h->st), "clear device flag");
+        CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+        return fail(h, EBE_CUDA_ERROR, e == 2 ? "a grid-wide barrier wait of the batched solver timed out"
+                                              : "a device-side wait timed out (bulk copy did not complete)");
+    }
     return EBE_OK;
 }
 
@@ -255,7 +275,7 @@ void ebe_solve_opts_default(ebe_solve_opts* o) {
 
 void ebe_destroy(ebe_handle* h) {
     if (!h) return;
-    cudaSetDevice(h->device);
+    DeviceGuard dev(h->device);
     if (h->st) cudaStreamSynchronize(h->st);
     for (int k = 0; k < 2; ++k)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
@@ -275,7 +295,7 @@ static int create_device(ebe_handle* h, const double* coords_host) {
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
     if (h->device < 0 || h->device >= ndev) return fail(h, EBE_INVALID_ARG, "no such CUDA device");
-    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    DeviceGuard dev(h->device);
     CK(cudaDeviceGetAttribute(&h->pd.num_sms, cudaDevAttrMultiProcessorCount, h->device), "cudaDeviceGetAttribute");
     if (h->own_stream) CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "cudaStreamCreate");
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
@@ -969,6 +989,21 @@ ebe_status ebe_chebyshev2(ebe_handle* h, double* x, int64_t iters, const double*
     return ebe_status(stationary_impl(h, x, iters, 1, alphas, N));
 }
 
+// The roots of P_N (Sec. 2.2) for the spectrum bounds lam1 < lam2, in the
+// order the paper's two-level listing cycles through them:
+// alpha_k = (lam1 + lam2)/2 + (lam2 - lam1)/2 cos(pi (k + 1/2) / N),
+// k = 0..N-1, largest first.  The order matters in floating point: it decides
+// how far the partial products of (I - A / alpha_k) grow within a cycle.
+ebe_status ebe_chebyshev2_bounds(ebe_handle* h, double* x, int64_t iters, double lam1, double lam2, int64_t N) {
+    if (!h) return EBE_INVALID_ARG;
+    if (!(lam1 > 0.0 && lam2 > lam1 && std::isfinite(lam2)) || N < 1 || N > (int64_t(1) << 20))
+        return ebe_status(fail(h, EBE_INVALID_ARG, "need 0 < lam1 < lam2 and 1 <= N <= 2^20"));
+    const double d = 0.5 * (lam1 + lam2), c = 0.5 * (lam2 - lam1);
+    std::vector<double> alphas(static_cast<size_t>(N));
+    for (int64_t k = 0; k < N; ++k) alphas[size_t(k)] = d + c * std::cos(M_PI * (double(k) + 0.5) / double(N));
+    return ebe_status(stationary_impl(h, x, iters, 1, alphas.data(), N));
+}
+
 ebe_status ebe_chebyshev3(ebe_handle* h, double* x, int64_t iters, double lam1, double lam2) {
     const double prm[2] = {lam1, lam2};
     return ebe_status(stationary_impl(h, x, iters, 2, prm, 2));
@@ -1169,7 +1204,8 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     // one launch runs up to maxit CG steps plus the true residuals of every
     // problem; a launch that ends with problems left is followed by another
     const int64_t budget = o.maxit + 65536;
-    const BatchDev bd = make_batch_dev(h, mixed, ti, o, budget);
+    BatchDev bd = make_batch_dev(h, mixed, ti, o, budget);
+    if (cfg.barrier_ns > 0) bd.barrier_ns = uint64_t(cfg.barrier_ns);
     int ctas = 0;
     TRY(resolve_shape(h, bd, mixed, cfg, ctas));
     const int64_t n = h->plan.n_n;
@@ -1178,7 +1214,7 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     int l = 0;
     if (o.use_graph) {
         const std::vector<double> key = {double(mixed), double(ctas), double(tile), o.rtol, o.delta, double(o.maxit),
-                                         double(o.stall_updates)};
+                                         double(o.stall_updates), double(bd.barrier_ns)};
         if (!h->bgraph || h->bgraph_key != key) {
             if (h->bgraph) { cudaGraphExecDestroy(h->bgraph); h->bgraph = nullptr; }
             cudaGraph_t g = nullptr;
@@ -1235,6 +1271,7 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
         summary->solve_ms = ms;
         summary->config.ctas_per_sm = ctas;
         summary->config.tile_nodes = tile;
+        summary->config.barrier_ns = int64_t(bd.barrier_ns);
         for (int ph = 0; ph < 4; ++ph) summary->phase_ms[ph] = double(h->bcount_host[2 + ph]) * 1e-6;
     }
     if (status != EBE_OK)
@@ -1271,9 +1308,11 @@ ebe_status ebe_solve_batch_host(ebe_handle* h, double* x, const ebe_solve_opts* 
 
 ebe_status ebe_set_batch_config(ebe_handle* h, const ebe_batch_config* cfg) {
     if (!h) return EBE_INVALID_ARG;
-    if (!cfg) { h->bcfg[0] = h->bcfg[1] = ebe_batch_config{0, 0}; return EBE_OK; }
-    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8 || (cfg->tile_nodes != 0 && tile_index(cfg->tile_nodes) < 0))
-        return ebe_status(fail(h, EBE_INVALID_ARG, "ctas_per_sm must be in [0, 8], tile_nodes 0, 1024, 2048 or 4096"));
+    if (!cfg) { h->bcfg[0] = h->bcfg[1] = ebe_batch_config{0, 0, 0}; return EBE_OK; }
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8 || (cfg->tile_nodes != 0 && tile_index(cfg->tile_nodes) < 0) ||
+        cfg->barrier_ns < 0)
+        return ebe_status(fail(h, EBE_INVALID_ARG,
+                               "ctas_per_sm must be in [0, 8], tile_nodes 0, 1024, 2048 or 4096, barrier_ns >= 0"));
     h->bcfg[0] = h->bcfg[1] = *cfg;
     return EBE_OK;
 }
@@ -1318,7 +1357,7 @@ ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_b
                 float t = 0.f;
                 cudaEventElapsedTime(&t, ev[0], ev[1]);
                 const double per = loops > 0 ? double(t) / double(std::max<int64_t>(done_loops, 1)) : double(t);
-                cands.push_back({ebe_batch_config{c, kTileSizes[ti]}, per});
+                cands.push_back({ebe_batch_config{c, kTileSizes[ti], h->bcfg[mixed ? 1 : 0].barrier_ns}, per});
             }
         }
     }
@@ -1519,6 +1558,7 @@ int net_bind(ebe_mpnn* m, ebe_handle* h, bool train) {
     if (!m || !h) return EBE_INVALID_ARG;
     if (m->device != h->device) return fail(h, EBE_INVALID_ARG, "network and handle are on different devices");
     TRY(check_ready(h, true));
+    DeviceGuard dev(h->device);
     TRY(ensure_mesh_graph(h));
     const int s = net_buffers(m, h->plan.n_n, train);
     if (s != EBE_OK) return fail(h, s, "network buffers: " + m->msg);
@@ -1553,7 +1593,13 @@ ebe_status ebe_mpnn_create(ebe_mpnn** out, int32_t device, const double* theta) 
         ebe_mpnn_destroy(m);
         return ebe_status(s);
     };
-    if (cudaSetDevice(device) != cudaSuccess) { m->msg = "no such CUDA device"; return bail(EBE_INVALID_ARG); }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        m->msg = "no such CUDA device";
+        return bail(EBE_INVALID_ARG);
+    }
+    DeviceGuard dev(device);
     MpnnDev& d = m->md;
     int s = EBE_OK;
     if ((s = malloc_net(m, &d.theta, kMpnnParams)) || (s = malloc_net(m, &d.adam_m, kMpnnParams, true)) ||
@@ -1571,7 +1617,7 @@ ebe_status ebe_mpnn_create(ebe_mpnn** out, int32_t device, const double* theta) 
 
 void ebe_mpnn_destroy(ebe_mpnn* m) {
     if (!m) return;
-    cudaSetDevice(m->device);
+    DeviceGuard dev(m->device);
     cudaDeviceSynchronize();
     for (void* p : m->allocs) cudaFree(p);
     delete m;
@@ -1597,7 +1643,7 @@ ebe_status ebe_mpnn_set_params(ebe_mpnn* m, const double* theta) {
             for (int k = 0; k < 2 * kMpnnHidden * kMpnnHidden; ++k)
                 t[kMpnnW0 + l * kMpnnLayerParams + k] = float(uni() / std::sqrt(2.0 * kMpnnHidden));
     }
-    cudaSetDevice(m->device);
+    DeviceGuard dev(m->device);
     if (cudaMemcpy(m->md.theta, t.data(), sizeof(float) * kMpnnParams, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(m->md.adam_m, 0, sizeof(float) * kMpnnParams) != cudaSuccess ||
         cudaMemset(m->md.adam_v, 0, sizeof(float) * kMpnnParams) != cudaSuccess)
@@ -1611,7 +1657,7 @@ ebe_status ebe_mpnn_set_params(ebe_mpnn* m, const double* theta) {
 ebe_status ebe_mpnn_get_params(const ebe_mpnn* m, double* theta) {
     if (!m || !theta) return EBE_INVALID_ARG;
     std::vector<float> t(kMpnnParams);
-    cudaSetDevice(m->device);
+    DeviceGuard dev(m->device);
     if (cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemcpy(t.data(), m->md.theta, sizeof(float) * kMpnnParams, cudaMemcpyDeviceToHost) != cudaSuccess)
         return EBE_CUDA_ERROR;
@@ -1831,7 +1877,7 @@ ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
     s->device_error = 0;
     if (h->dev_err) {
         int32_t e = 0;
-        cudaSetDevice(h->device);
+        DeviceGuard dev(h->device);
         if (cudaMemcpyAsync(&e, h->dev_err, sizeof(e), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
             cudaStreamSynchronize(h->st) != cudaSuccess)
             return EBE_CUDA_ERROR;
@@ -1843,11 +1889,11 @@ ebe_status ebe_get_stats(const ebe_handle* h, ebe_stats* s) {
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free residual
-// Some callers cannot allocate device memory at the point where they need a
-// residual: code running while a stream is being captured into a CUDA graph
-// (cudaMalloc is not allowed there), a process whose device memory is owned
-// by another allocator, or a real-time loop that must not take the
-// allocator's locks.  ebe_residual allocates its halo scratch on first use;
+// Some callers cannot call cudaMalloc at the point where they need a
+// residual: a process whose device memory is handed out by another allocator
+// (a framework's caching allocator or a fixed pool that owns the device), or
+// a real-time loop that must not take the allocator's locks or risk the
+// implicit device synchronisation of cudaMalloc.  ebe_residual allocates its halo scratch on first use;
 // ebe_residual_noalloc takes it from a fixed file-scope device array
 // instead: kNoAllocHaloMax doubles (32 MiB), present on every device that
 // loads the library for the life of the process.  Every call shares the
@@ -1864,14 +1910,13 @@ std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the handle's device (in host code
-// the array's name is only a stand-in).  Looked up once per device, with that
-// device current.
+// the array's name is only a stand-in).  Looked up once per device; the
+// caller has made the handle's device current.
 int noalloc_scratch(ebe_handle* h, double** out) {
     if (h->device < 0 || h->device >= kNoAllocMaxDevices) return fail(h, EBE_INVALID_ARG, "device ordinal too large");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_addr[h->device]) {
         void* p = nullptr;
-        CK(cudaSetDevice(h->device), "cudaSetDevice");
         CK(cudaGetSymbolAddress(&p, g_noalloc_halo), "cudaGetSymbolAddress");
         g_noalloc_addr[h->device] = p;
     }
@@ -1888,9 +1933,9 @@ extern "C" ebe_status ebe_residual_noalloc(ebe_handle* h, const double* x, doubl
         return ebe_status(fail(h, EBE_INVALID_ARG,
                                "mesh needs " + std::to_string(h->plan.n_halo) + " halo slots; ebe_residual_noalloc holds " +
                                    std::to_string(kNoAllocHaloMax) + " (use ebe_residual)"));
+    Scope scp(h);
     double* halo = nullptr;
     TRY(noalloc_scratch(h, &halo));
-    Scope scp(h);
     int l = 0;
     CK(launch_patch_pass(h->pd, 0, kResidual, h->A64, x, h->b, r, halo, h->part_patch, nullptr, h->sc, h->st, &l),
        "patch pass");

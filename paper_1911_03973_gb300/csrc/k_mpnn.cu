@@ -257,8 +257,13 @@ __global__ void __launch_bounds__(128) k_mpnn_layer(int64_t n, const int32_t* __
         }
         if (tid == 0 && !tma::mbar_wait_bounded(mbar, phase, err)) sflag = 1;
         __syncthreads();
+        if (sflag) {                        // uniform: the accumulator did not arrive in time
+            // the committed MMA may still be writing TMEM: wait once more
+            // (bounded) before the accumulator is freed below
+            if (tid == 0) tma::mbar_wait_bounded(mbar, phase, nullptr);
+            break;
+        }
         phase ^= 1u;
-        if (sflag) break;                   // uniform: the accumulator never arrived
         while (!tma::mbar_try_wait(mbar, phase ^ 1u)) {
         }
         tc_fence_after();

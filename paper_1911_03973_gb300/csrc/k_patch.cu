@@ -167,7 +167,10 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     // one thread waits (bounded) for the bulk copies and shares the outcome
     if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
     __syncthreads();
-    if (*flag == 0) return;
+    if (*flag == 0) {                             // error flag set: give the copies a last
+        if (tid == 0) mbar_wait_bounded(bar, 0, nullptr);   // bounded chance to land, then leave
+        return;
+    }
     while (!mbar_try_wait(bar, 0)) {
     }                                             // completed already: acquire for this thread
 

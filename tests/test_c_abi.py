@@ -1,5 +1,6 @@
 """The C ABI from a C program (no GPU): tests/c/abi_host.c is compiled with gcc
 as C99 against include/ebe.h, linked with libebe.so and run."""
+import ctypes
 import os
 import shutil
 import subprocess
@@ -50,3 +51,34 @@ def test_c_program_solves_through_the_abi():
     orc = oracle.Problem(meshgen.config_square_f1(33, nu=1.0))
     for x in xs:
         assert orc.rel_residual(x) <= 1e-8
+
+
+def test_binding_struct_layouts_match_the_c_compiler():
+    # every struct of include/ebe.h: size and field offsets from gcc against ctypes
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1911_03973_gb300 import _abi
+    fields = {
+        "ebe_mesh": ["dim", "n_b", "n_n", "n_e", "coords", "elems"],
+        "ebe_create_opts": ["device", "patch_elems"],
+        "ebe_solve_opts": ["rtol", "maxit", "precision", "chunk", "delta", "stall_updates", "use_graph"],
+        "ebe_solve_info": ["status", "iterations", "true_residuals", "rel_residual", "r0_norm", "solve_ms"],
+        "ebe_stats": ["kernel_launches", "device_error"],
+        "ebe_batch_config": ["ctas_per_sm", "tile_nodes", "barrier_ns"],
+        "ebe_batch_info": ["loops", "launches", "n_converged", "solve_ms", "config", "phase_ms"],
+        "ebe_partition_sizes": ["n_patches", "patch_elems"],
+    }
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "layout")
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c", "layout.c"), "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=60, check=True).stdout
+    seen = set()
+    for line in out.strip().split("\n"):
+        name, size, *offs = line.split()
+        cls = getattr(_abi, name)
+        assert ctypes.sizeof(cls) == int(size), name
+        for f, off in zip(fields[name], offs):
+            assert getattr(cls, f).offset == int(off), (name, f)
+        seen.add(name)
+    assert seen == set(fields)

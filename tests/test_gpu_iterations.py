@@ -42,7 +42,7 @@ def _close(a, b, tol):
     return np.abs(a - b).max() <= tol * max(1.0, np.abs(b).max())
 
 
-@pytest.mark.parametrize("method", ["richardson", "cheb2_N8", "cheb3"])
+@pytest.mark.parametrize("method", ["richardson", "cheb2_N8", "cheb2_given_roots", "cheb3"])
 def test_paper_experiment_iterations_match_oracle(ebe, method):
     n = 33
     prob = meshgen.config_square_f1(n, nu=0.0, g_value=1.0)     # Sec. 3 setting
@@ -55,13 +55,53 @@ def test_paper_experiment_iterations_match_oracle(ebe, method):
         ebe.ebe_richardson(h, xd, 124, 2.0 / (l1 + l2))
         ref = orc.richardson(orc.with_dirichlet(x0), 124, 2.0 / (l1 + l2))
     elif method == "cheb2_N8":
-        roots = oracle.chebyshev_roots(l1, l2, 8)
+        # the library builds the roots of P_8 itself (Sec. 2.2), as the oracle does
+        ebe.ebe_chebyshev2_bounds(h, xd, 40, l1, l2, 8)
+        ref = orc.chebyshev2_bounds(orc.with_dirichlet(x0), 40, l1, l2, 8)
+    elif method == "cheb2_given_roots":
+        # the explicit-roots call with a caller's order (ascending, not the listing's)
+        roots = np.sort(0.5 * (l1 + l2) + 0.5 * (l2 - l1) * np.cos(math.pi * (np.arange(8) + 0.5) / 8))
         ebe.ebe_chebyshev2(h, xd, 40, roots)
         ref = orc.chebyshev2(orc.with_dirichlet(x0), 40, roots)
     else:
         ebe.ebe_chebyshev3(h, xd, 124, l1, l2)
         ref = orc.chebyshev3(orc.with_dirichlet(x0), 124, l1, l2)
     assert _close(xd.cpu().numpy(), ref, 1e-10)
+
+
+def test_two_level_N32_instability_of_the_paper_experiment(ebe):
+    """Sec. 3: 33^2 nodes, nu = 0, u = 1 on the boundary, f = 1, 124 steps.
+    The two-level method with N = 32 (roots built by the library, in the
+    listing's order) against the oracle's iterate; in this order the partial
+    products of a cycle amplify rounding errors by about 1e7 (a 1e-16 change
+    of x0 moves the oracle's iterate by 4.5e-3 at k = 32 and 6.6e-10 at
+    k = 124), so the GPU and the oracle, which add in different orders, are
+    compared at 1e-6 after 124 steps.  The instability the paper reports shows
+    as the two-level iterate at k = N differing from the three-level one,
+    equal to it in exact arithmetic (Eq. Cheberror1), and as its error after
+    124 steps staying far above the three-level method's."""
+    n = 33
+    prob = meshgen.config_square_f1(n, nu=0.0, g_value=1.0)
+    orc = oracle.Problem(prob)
+    l1, l2 = _bounds(n)
+    h = _setup(ebe, prob)
+    x0 = orc.with_dirichlet(np.zeros(orc.n_n))
+    u, _ = orc.pcg(rtol=1e-13)
+
+    def run(fn, iters):
+        xd = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+        fn(xd, iters)
+        return xd.cpu().numpy()
+    x2 = run(lambda xd, k: ebe.ebe_chebyshev2_bounds(h, xd, k, l1, l2, 32), 124)
+    ref = orc.chebyshev2_bounds(x0, 124, l1, l2, 32)
+    assert _close(x2, ref, 1e-6)
+    x3 = run(lambda xd, k: ebe.ebe_chebyshev3(h, xd, k, l1, l2), 124)
+    e0 = np.abs(x0 - u).max()
+    e2, e3 = np.abs(x2 - u).max() / e0, np.abs(x3 - u).max() / e0
+    assert e3 < 1e-4 and e2 > 10 * e3
+    x2N = run(lambda xd, k: ebe.ebe_chebyshev2_bounds(h, xd, k, l1, l2, 32), 32)
+    x3N = run(lambda xd, k: ebe.ebe_chebyshev3(h, xd, k, l1, l2), 32)
+    assert np.abs(x2N - x3N).max() > 1e-6 * np.abs(x3N).max()
 
 
 def test_iterations_on_jittered_tets(ebe):
@@ -83,3 +123,7 @@ def test_iteration_argument_errors(ebe):
         ebe.ebe_chebyshev3(h, xd, 5, 2.0, 1.0)
     with pytest.raises(ebe.EbeError):
         ebe.ebe_chebyshev2(h, xd, 5, np.array([1.0, 0.0]))
+    with pytest.raises(ebe.EbeError):
+        ebe.ebe_chebyshev2_bounds(h, xd, 5, 1.0, 2.0, 0)
+    with pytest.raises(ebe.EbeError):
+        ebe.ebe_chebyshev2_bounds(h, xd, 5, 0.0, 2.0, 8)

@@ -437,7 +437,7 @@ def test_chebyshev2_error_is_P_N():
     p = oracle.Problem(prob)
     u, _ = p.pcg(rtol=1e-13)
     x0 = p.with_dirichlet(np.zeros(p.n_n))
-    xN = p.chebyshev2(x0, N, oracle.chebyshev_roots(l1, l2, N))
+    xN = p.chebyshev2_bounds(x0, N, l1, l2, N)
     free = np.setdiff1d(np.arange(p.n_n), prob["dirichlet"])
     Aff = p.dense("A")[np.ix_(free, free)]
     w, V = np.linalg.eigh(Aff)
@@ -454,7 +454,7 @@ def test_chebyshev2_equals_chebyshev3_at_N(N):
     prob, l1, l2 = _small_paper_problem(9)
     p = oracle.Problem(prob)
     x0 = p.with_dirichlet(np.zeros(p.n_n))
-    x2 = p.chebyshev2(x0, N, oracle.chebyshev_roots(l1, l2, N))
+    x2 = p.chebyshev2_bounds(x0, N, l1, l2, N)
     x3 = p.chebyshev3(x0, N, l1, l2)
     np.testing.assert_allclose(x2, x3, atol=1e-11 * max(1.0, np.abs(x2).max()))
 

@@ -1,9 +1,10 @@
-"""ebe_residual_noalloc: the residual for callers that cannot allocate device
-memory (for example code running inside a CUDA-graph capture, where
-cudaMalloc is not allowed).  Its scratch lives in a fixed device array in the
-library, so its result must equal ebe_residual's on two calls in a row (the
-second call finds the previous call's data in the shared array).  Collected
-last so that a failure here leaves every other test already run."""
+"""ebe_residual_noalloc: the residual for callers that cannot call cudaMalloc
+(a process whose device memory is handed out by another allocator, or a
+real-time loop that must not take the allocator's locks).  Its scratch lives
+in a fixed device array in the library, so its result must equal
+ebe_residual's on two calls in a row (the second call finds the previous
+call's data in the shared array).  Collected last so that a failure here
+leaves every other test already run."""
 import numpy as np
 import pytest
 

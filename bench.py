@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the learned preconditioner (257^2) and deploying it (1025^2, 2049^2)")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "batch", "mpnn"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "cg", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -634,7 +634,13 @@ def run_ours(args):
             x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
             r64 = torch.empty_like(x64)
             if args.profile_kernel == "vec":
-                # three mixed-precision CG iterations, launched one by one
+                # three textbook mixed-precision CG iterations, launched one by one
+                ebe.ebe_solve(h, x, rtol=1e-300, maxit=3, precision=ebe.EBE_PREC_MIXED_TEXTBOOK, chunk=1,
+                              use_graph=False)
+                torch.cuda.synchronize()
+                return None
+            if args.profile_kernel == "cg":
+                # four single-sync passes (fresh pass + three iterations), launched one by one
                 ebe.ebe_solve(h, x, rtol=1e-300, maxit=3, precision=ebe.EBE_PREC_MIXED, chunk=1, use_graph=False)
                 torch.cuda.synchronize()
                 return None
@@ -695,6 +701,12 @@ def run_ours(args):
             ep1.record(stream)
             torch.cuda.synchronize()
             ms_plain = ep0.elapsed_time(ep1) / args.plain_steps
+        # the same mixed-precision arithmetic in the textbook four-launch iteration
+        ms_text, tinfo = None, None
+        if args.plain_steps > 0:
+            ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+            ms_text, tinfo = _timed_solve(ebe, torch, h, x, stream, 1, rtol=args.rtol,
+                                          precision=ebe.EBE_PREC_MIXED_TEXTBOOK)
 
         # roofline: FP32 operator application, per-launch events on its stream
         ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
@@ -809,7 +821,9 @@ def run_ours(args):
                 "true_residuals": info0["true_residuals"], "rel_residual": info0["rel_residual"],
                 "plain_fp64_ms": round(ms_plain, 2) if ms_plain else None,
                 "plain_fp64_iterations": pinfo[-1]["iterations"] if pinfo else None,
-                "speedup_vs_plain": round(ms_plain / ms_step, 3) if ms_plain else None},
+                "speedup_vs_plain": round(ms_plain / ms_step, 3) if ms_plain else None,
+                "textbook_mixed_ms": round(ms_text, 2) if ms_text else None,
+                "textbook_mixed_iterations": tinfo["iterations"] if tinfo else None},
         "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4), "traffic": trf,
                      "kernel": "FP32 operator application: patch pass + halo fix-up",
@@ -854,7 +868,8 @@ def summary_block(line, ms_plain, pinfo, peak):
     r = line["roofline"]
     s = {"sq2049_nu1": {"mixed_ms": pc["ms_to_1e-8"], "it": pc["iterations"],
                         "plain_ms": round(ms_plain, 1) if ms_plain else None,
-                        "plain_it": pinfo[-1]["iterations"] if pinfo else None, "x": pc["speedup_vs_plain"]}}
+                        "plain_it": pinfo[-1]["iterations"] if pinfo else None, "x": pc["speedup_vs_plain"],
+                        "textbook_mixed_ms": pc["textbook_mixed_ms"]}}
     for key, name in (("nu0", "sq2049_nu0"), ("square33", "sq33"), ("cube129", "cube129")):
         v = line.get(key)
         if v:

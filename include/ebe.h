@@ -79,14 +79,23 @@ enum {
 
 /* Solver precision for ebe_solve. */
 enum {
-    EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG                                          */
-    EBE_PREC_MIXED = 1    /* the operator pass runs on FP32 A_e (difference form) with the
+    EBE_PREC_FP64 = 0,    /* plain FP64 Jacobi-PCG (textbook: four launches per iteration) */
+    EBE_PREC_MIXED = 1,   /* the operator pass runs on FP32 A_e (difference form) with the
                              search direction p, q = A p, the recurrence residual r and
                              z = dinv r in FP32; the solution x stays FP64; dot products
                              add per thread in compensated FP32 and across threads in
                              FP64; r is replaced by the FP64 true residual (FP64 A_e)
                              whenever the recurrence residual has dropped by the factor
-                             `delta` since the last replacement (needs EBE_STORE_MIXED) */
+                             `delta` since the last replacement (needs EBE_STORE_MIXED).
+                             One iteration is two launches with one grid-wide reduction:
+                             the x and r updates and the new direction are formed where
+                             the operator pass gathers its operand, and the next r.z
+                             comes from r'.(dinv r') = r.z - 2 alpha q.z + alpha^2
+                             q.(dinv q) (the same iterates as the textbook form in exact
+                             arithmetic)                                              */
+    EBE_PREC_MIXED_TEXTBOOK = 2   /* EBE_PREC_MIXED arithmetic in the textbook four-launch
+                             iteration (operator, update, direction; two reductions), for
+                             comparison; ebe_solve only                               */
 };
 
 /* Scatter strategies of the residual (ebe_residual_variant). */
@@ -259,8 +268,8 @@ ebe_status ebe_residual_variant(ebe_handle* h, const double* x_dev, double* r_de
 /* Jacobi-PCG on A x = b with x(nd) = g, stopping when the FP64 true relative
  * residual |mask(b - A x)| / |mask(b - A x0)| <= rtol (x0 = the given x with
  * x(nd) = g).  The true residual is evaluated (FP64 element matrices) each
- * time the recurrence residual reaches rtol |r0| (and, for EBE_PREC_MIXED, at
- * every replacement); for EBE_PREC_MIXED a failed check at that final
+ * time the recurrence residual reaches rtol |r0| (and, in mixed precision, at
+ * every replacement); in mixed precision a failed check at that final
  * threshold tightens it by the factor 0.7.  x_dev: device [n_n] double, in: x0, out:
  * solution.  opts NULL = defaults.  info may be NULL.  Synchronises the
  * stream once at the end.  Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN,

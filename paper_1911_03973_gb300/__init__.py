@@ -15,8 +15,10 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (EBE_F32, EBE_F64, EBE_PREC_FP64, EBE_PREC_MIXED, EBE_SCATTER_ATOMIC,  # noqa: F401
-                   EBE_SCATTER_COLOUR, EBE_SCATTER_NODE, EBE_SCATTER_PATCH, EBE_STORE_FP64, EBE_STORE_MIXED)
+from ._abi import (EBE_BREAKDOWN, EBE_CUDA_ERROR, EBE_DEGENERATE_ELEMENT, EBE_F32, EBE_F64,  # noqa: F401
+                   EBE_INDEX_RANGE, EBE_INVALID_ARG, EBE_MAXIT, EBE_NOT_READY, EBE_OK, EBE_OOM, EBE_PREC_FP64,
+                   EBE_PREC_MIXED, EBE_PREC_MIXED_TEXTBOOK, EBE_SCATTER_ATOMIC, EBE_SCATTER_COLOUR, EBE_SCATTER_NODE, EBE_SCATTER_PATCH,
+                   EBE_SINGULAR, EBE_STALL, EBE_STORE_FP64, EBE_STORE_MIXED)
 
 SOLVER_OUTCOMES = (_abi.EBE_OK, _abi.EBE_MAXIT, _abi.EBE_BREAKDOWN, _abi.EBE_STALL)
 

@@ -31,6 +31,7 @@ EBE_STORE_FP64 = 0
 EBE_STORE_MIXED = 1
 EBE_PREC_FP64 = 0
 EBE_PREC_MIXED = 1
+EBE_PREC_MIXED_TEXTBOOK = 2
 EBE_SCATTER_PATCH = 0
 EBE_SCATTER_COLOUR = 1
 EBE_SCATTER_NODE = 2

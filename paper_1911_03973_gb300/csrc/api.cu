@@ -74,6 +74,20 @@ struct ebe_handle {
     int graph_chunk[2] = {0, 0};
     int graph_nodes[2] = {0, 0};
 
+    // solver numbering of the single-sync mixed solver (see create_device)
+    PlanDev pd_int;                 // pd with the node tables in the solver numbering
+    int64_t n_int = 0;              // nodes of the solver numbering (with padding)
+    int32_t* int_of_user = nullptr; // [n_n] solver number of each node
+    int32_t* pnode_int = nullptr;
+    int32_t* sh_node_int = nullptr;
+    bool int_ready = false;         // bi, dinvi32 built from the current assembly
+    double *xi = nullptr, *ri64 = nullptr, *bi = nullptr;
+    float *dinvi32 = nullptr, *ri32 = nullptr, *qi32 = nullptr, *pi32[2] = {nullptr, nullptr};
+    double* part5 = nullptr;
+    cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};   // chunk of passes per starting direction buffer
+    int cg_chunk = 0;
+    int cg_nodes = 0;
+
     // batches (ebe_create makes a batch of one)
     int n_prob = 1;
     BatchLayout lay;
@@ -277,8 +291,10 @@ void ebe_destroy(ebe_handle* h) {
     if (!h) return;
     DeviceGuard dev(h->device);
     if (h->st) cudaStreamSynchronize(h->st);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        if (h->cg_graph[k]) cudaGraphExecDestroy(h->cg_graph[k]);
+    }
     if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
     for (void* p : h->allocs) cudaFree(p);
     if (h->sc_host) cudaFreeHost(h->sc_host);
@@ -334,12 +350,52 @@ static int create_device(ebe_handle* h, const double* coords_host) {
     pd.sh_ptr = sh_ptr;
     pd.sh_slot = sh_slot;
     pd.slot_elem = slot_elem;
+    // Solver numbering for the single-sync mixed solver: the owned nodes of
+    // each patch as one contiguous run in patch order (each run padded to a
+    // multiple of 4 nodes), then the shared nodes in the order of the fix-up
+    // rows.  The patch pass then reads and writes its owned nodes' vector
+    // entries with coalesced accesses and the fix-up its shared rows.
+    {
+        const int64_t np = P.n_patches, nsh = int64_t(P.sh_node.size());
+        std::vector<int32_t> own_off(size_t(np) + 1);
+        int64_t off = 0;
+        for (int64_t p = 0; p < np; ++p) {
+            own_off[size_t(p)] = int32_t(off);
+            off += (P.meta[size_t(p)].n_owned + 3) / 4 * 4;
+        }
+        own_off[size_t(np)] = int32_t(off);
+        h->n_int = (off + nsh + 3) / 4 * 4;
+        if (h->n_int >= (int64_t(1) << 31)) return fail(h, EBE_INVALID_ARG, "mesh too large for the solver numbering");
+        std::vector<int32_t> iou(static_cast<size_t>(P.n_n), -1), pint(P.pnode.size()), shint(static_cast<size_t>(nsh));
+        for (int64_t p = 0; p < np; ++p) {
+            const PatchMeta& m = P.meta[size_t(p)];
+            for (int l = 0; l < m.n_owned; ++l) iou[size_t(P.pnode[size_t(m.node_off + l)] & kNodeMask)] = own_off[size_t(p)] + l;
+        }
+        for (int64_t k = 0; k < nsh; ++k) {
+            shint[size_t(k)] = int32_t(off + k);
+            iou[size_t(P.sh_node[size_t(k)] & kNodeMask)] = int32_t(off + k);
+        }
+        for (size_t i = 0; i < pint.size(); ++i) pint[i] = iou[size_t(P.pnode[i] & kNodeMask)];
+        int32_t* own_off_d = nullptr;
+        TRY(upload(h, &own_off_d, own_off.data(), int64_t(own_off.size())));
+        TRY(upload(h, &h->int_of_user, iou.data(), int64_t(iou.size())));
+        TRY(upload(h, &h->pnode_int, pint.data(), int64_t(pint.size())));
+        TRY(upload(h, &h->sh_node_int, shint.data(), int64_t(shint.size())));
+        h->pd_int = pd;
+        h->pd_int.pnode = h->pnode_int;
+        h->pd_int.sh_node = h->sh_node_int;
+        h->pd_int.own_off = own_off_d;
+        h->pd_int.sh_base = int32_t(off);
+        CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");   // the host tables go away
+    }
     TRY(dalloc(h, &h->part_patch, P.n_patches + 1216));
     TRY(dalloc(h, &h->part_vec, 3 * 1216));   // up to three partial sums per block
     TRY(dalloc(h, &h->sc, 1, true));
     TRY(dalloc(h, &h->bad, 1));
     TRY(dalloc(h, &h->dev_err, 1, true));
     pd.err = h->dev_err;
+    h->pd_int.err = h->dev_err;
+    h->pd_int.num_sms = pd.num_sms;
     CK(cudaMallocHost(&h->sc_host, sizeof(Scalars)), "cudaMallocHost");
     std::memset(h->sc_host, 0, sizeof(Scalars));
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");  // host arrays may go away now
@@ -488,6 +544,8 @@ static int set_problem_impl(ebe_handle* h, const double* nu, const double* f_nod
     }
     int l = 0;
     CK(launch_mark_dirichlet(h->pd, h->pnode, h->n_pnode, h->sh_node, h->dmask, h->st, &l), "mark Dirichlet");
+    CK(launch_copy_dirichlet_bit(h->pnode_int, h->pnode, h->n_pnode, h->st, &l), "mark Dirichlet");
+    CK(launch_copy_dirichlet_bit(h->sh_node_int, h->sh_node, h->pd.n_shared, h->st, &l), "mark Dirichlet");
     add_launches(h, l);
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
     h->nu = nu[0];
@@ -542,6 +600,7 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
     }
     h->store = store;
     h->assembled = true;
+    h->int_ready = false;
     return EBE_OK;
 }
 
@@ -787,7 +846,9 @@ int true_residual(ebe_handle* h, double& rr) {
     return EBE_OK;
 }
 
-// Jacobi-PCG.  The solution x is FP64 in both precisions.  EBE_PREC_MIXED
+// Jacobi-PCG in the textbook form (four launches per iteration: operator
+// pass, fix-up, update, direction).  The solution x is FP64 in both
+// precisions.  EBE_PREC_MIXED_TEXTBOOK
 // keeps the recurrence residual r, z = dinv r, the search direction p,
 // q = A p and the element matrices in FP32 (difference form), so the passes
 // stream about half the bytes and the FP64 pipe only updates x; FP32
@@ -797,8 +858,8 @@ int true_residual(ebe_handle* h, double& rr) {
 // element matrices) and CG continues with the same direction.
 int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
     const auto t0 = std::chrono::steady_clock::now();
-    const bool mixed = o.precision == EBE_PREC_MIXED;
-    if (mixed && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
+    const bool mixed = o.precision == EBE_PREC_MIXED_TEXTBOOK;
+    if (mixed && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "mixed precision needs ebe_assemble(EBE_STORE_MIXED)");
     const int64_t n = h->plan.n_n;
     const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
     TRY(dalloc(h, &h->x64w, n));
@@ -904,6 +965,180 @@ int solve_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o
     return status;
 }
 
+// ------------------------------------------------ single-synchronisation mixed solver
+// Jacobi-PCG with the search direction, q = A p, the recurrence residual and
+// the FP32 element matrices as in the textbook mixed solver, but one
+// iteration is one launch_cg_pass (patch pass + fix-up): the x, r updates and
+// the new direction are formed where the next operator pass gathers its
+// operand, and beta comes from the expansion of r'.(dinv r') in sums that
+// pass forms, so each iteration has one grid-wide reduction.  Vectors live
+// in the solver numbering (owned nodes of a patch contiguous); x is permuted
+// in and out once per solve.  The direction alternates between two buffers
+// (a pass reads one and writes the other), so that after a residual
+// replacement CG continues from the previous direction exactly as the
+// textbook solver does.
+
+// b and dinv in the solver numbering, once per assembly.
+int ensure_solver_vectors(ebe_handle* h) {
+    const int64_t n = h->plan.n_n, ni = h->n_int;
+    TRY(dalloc(h, &h->bi, ni, true));
+    TRY(dalloc(h, &h->dinvi32, ni, true));
+    if (h->int_ready) return EBE_OK;
+    int l = 0;
+    CK(launch_permute(0, 1, n, h->int_of_user, h->b, h->bi, h->st, &l), "b to the solver numbering");
+    CK(launch_permute(1, 1, n, h->int_of_user, h->dinv32, h->dinvi32, h->st, &l), "dinv to the solver numbering");
+    add_launches(h, l);
+    h->int_ready = true;
+    return EBE_OK;
+}
+
+int ensure_cg_graphs(ebe_handle* h, int chunk) {
+    if (h->cg_graph[0] && h->cg_graph[1] && h->cg_chunk == chunk) return EBE_OK;
+    for (int k = 0; k < 2; ++k)
+        if (h->cg_graph[k]) { cudaGraphExecDestroy(h->cg_graph[k]); h->cg_graph[k] = nullptr; }
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        int l = 0;
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < chunk && e == cudaSuccess; ++it)
+            e = launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[(par + it) & 1], h->pi32[(par + it + 1) & 1],
+                               h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st, &l, true);
+        cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "single-sync pass"); }
+        if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->cg_graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { h->cg_graph[par] = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+        h->cg_nodes = l;
+    }
+    h->cg_chunk = chunk;
+    return EBE_OK;
+}
+
+// r = mask(b - A64 x) in the solver numbering and its squared norm.
+int true_residual_int(ebe_handle* h, double& rr) {
+    int l = 0;
+    CK(launch_patch_pass(h->pd_int, 0, kResidualNorm, h->A64, h->xi, h->bi, h->ri64, h->halo64, h->part_patch, nullptr,
+                         h->sc, h->st, &l), "true residual");
+    add_launches(h, l);
+    TRY(sync_scalars(h));
+    rr = h->sc_host->rrt;
+    return EBE_OK;
+}
+
+int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
+    const int64_t n = h->plan.n_n, ni = h->n_int;
+    const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
+    TRY(dalloc(h, &h->x64w, n));
+    TRY(dalloc(h, &h->xi, ni));
+    TRY(dalloc(h, &h->ri64, ni, true));       // padding entries stay zero
+    TRY(dalloc(h, &h->ri32, ni));
+    TRY(dalloc(h, &h->qi32, ni));
+    TRY(dalloc(h, &h->pi32[0], ni));
+    TRY(dalloc(h, &h->pi32[1], ni));
+    TRY(dalloc(h, &h->halo64, nh));
+    TRY(dalloc(h, &h->halo32, nh));
+    TRY(dalloc(h, &h->part5, 5 * (int64_t(h->pd.n_patches) + kFixGridMax)));
+    TRY(ensure_solver_vectors(h));
+    int l = 0;
+    CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x0");
+    CK(launch_set_dirichlet(h->x64w, h->nd, h->g, h->n_d, h->st, &l), "x(nd) = g");
+    CK(cudaMemsetAsync(h->xi, 0, sizeof(double) * size_t(ni), h->st), "memset");
+    CK(launch_permute(0, 1, n, h->int_of_user, h->x64w, h->xi, h->st, &l), "x0 to the solver numbering");
+    CK(launch_control(h->sc, 0.0, o.maxit, 1, h->st, &l), "control");
+    add_launches(h, l);
+    double rr = 0.0;
+    TRY(true_residual_int(h, rr));
+    info.true_residuals = 1;
+    const double r0 = std::sqrt(rr);
+    info.r0_norm = r0;
+    info.iterations = 0;
+    info.rel_residual = r0 > 0.0 ? 1.0 : 0.0;
+    int status = EBE_OK;
+    if (!std::isfinite(r0)) status = EBE_BREAKDOWN;
+    if (r0 > 0.0 && std::isfinite(r0)) {
+        const double target = o.rtol * r0;
+        double fin = target;
+        l = 0;
+        CK(cudaMemsetAsync(h->pi32[0], 0, sizeof(float) * size_t(ni), h->st), "memset");
+        CK(cudaMemsetAsync(h->pi32[1], 0, sizeof(float) * size_t(ni), h->st), "memset");
+        CK(cudaMemsetAsync(h->qi32, 0, sizeof(float) * size_t(ni), h->st), "memset");
+        CK(launch_restart(1, ni, h->ri64, h->dinvi32, 1, h->part_vec, h->sc, h->st, &l, h->ri32), "restart");
+        CK(launch_cg_arm(h->sc, h->st, &l), "arm");
+        double thr = std::max(o.delta * r0, fin);
+        CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
+        add_launches(h, l);
+        if (o.use_graph) TRY(ensure_cg_graphs(h, o.chunk));
+        int par = 0;                   // buffer of the current direction (read by the next pass)
+        int64_t passes = h->sc_host->passes;
+        double best = 1.0;
+        int no_progress = 0;
+        for (;;) {
+            if (o.use_graph) {
+                CK(cudaGraphLaunch(h->cg_graph[par], h->st), "cudaGraphLaunch");
+                add_launches(h, h->cg_nodes);
+            } else {
+                l = 0;
+                for (int it = 0; it < o.chunk; ++it)
+                    CK(launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[(par + it) & 1],
+                                      h->pi32[(par + it + 1) & 1], h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st,
+                                      &l, false), "single-sync pass");
+                add_launches(h, l);
+            }
+            const int64_t before = info.iterations;
+            TRY(sync_scalars(h));
+            const Scalars sh = *h->sc_host;
+            par = int((par + (sh.passes - passes)) & 1);
+            passes = sh.passes;
+            info.iterations = sh.iter;
+            if (sh.reason == kRunning) {
+                if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
+                continue;
+            }
+            if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
+            TRY(true_residual_int(h, rr));
+            info.true_residuals += 1;
+            const double rel = std::sqrt(rr) / r0;
+            info.rel_residual = rel;
+            if (!std::isfinite(rel)) { status = EBE_BREAKDOWN; break; }
+            if (rel <= o.rtol) { status = EBE_OK; break; }
+            if (sh.reason == kMaxit) { status = EBE_MAXIT; break; }
+            if (rel < 0.9 * best) { best = rel; no_progress = 0; }
+            else if (++no_progress >= o.stall_updates) { status = EBE_STALL; break; }
+            if (sh.reason == kTrigger && thr <= fin) fin *= kFinalMargin;
+            // residual replacement: continue CG from the FP64 true residual with
+            // the direction that preceded the triggering pass (the pass that
+            // triggered formed the next direction in the other buffer)
+            par ^= 1;
+            l = 0;
+            CK(launch_restart(1, ni, h->ri64, h->dinvi32, 0, h->part_vec, h->sc, h->st, &l, h->ri32), "restart");
+            CK(launch_cg_arm(h->sc, h->st, &l), "arm");
+            thr = std::max(o.delta * std::sqrt(rr), fin);
+            CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
+            add_launches(h, l);
+        }
+        if (status == EBE_BREAKDOWN && true_residual_int(h, rr) == EBE_OK) info.rel_residual = std::sqrt(rr) / r0;
+    }
+    l = 0;
+    CK(launch_permute(0, 0, n, h->int_of_user, h->xi, h->x64w, h->st, &l), "x to the caller's numbering");
+    add_launches(h, l);
+    CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    info.status = status;
+    info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (status != EBE_OK) {
+        const char* why = status == EBE_MAXIT ? "maxit reached" : status == EBE_STALL ? "true residual stalled"
+                                                                                        : "breakdown (p.Ap <= 0 or non-finite)";
+        h->err = std::string("solve stopped: ") + why;
+    }
+    return status;
+}
+
 int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts, ebe_solve_info* info) {
     TRY(check_ready(h, true));
     if (!x) return fail(h, EBE_INVALID_ARG, "x is NULL");
@@ -911,11 +1146,12 @@ int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts,
     ebe_solve_opts_default(&o);
     if (opts) o = *opts;
     if (!(o.rtol > 0.0) || o.maxit < 1 || o.chunk < 1 || o.chunk > 4096 || !(o.delta > 0.0 && o.delta < 1.0) ||
-        o.stall_updates < 1 || (o.precision != EBE_PREC_FP64 && o.precision != EBE_PREC_MIXED))
+        o.stall_updates < 1 ||
+        (o.precision != EBE_PREC_FP64 && o.precision != EBE_PREC_MIXED && o.precision != EBE_PREC_MIXED_TEXTBOOK))
         return fail(h, EBE_INVALID_ARG, "bad solve options");
     ebe_solve_info local{};
     Scope scp(h);
-    int s = solve_impl(h, x, host, o, local);
+    int s = o.precision == EBE_PREC_MIXED ? solve_cg1_impl(h, x, host, o, local) : solve_impl(h, x, host, o, local);
     if (info) *info = local;
     return s;
 }

@@ -18,6 +18,7 @@
 //   * they write the result of every owned node (all of its elements are in
 //     this patch) and the partial sum of every shared node to its halo slot.
 // The fix-up pass adds the halo partials of each shared node in patch order.
+#include <algorithm>
 #include <cstdint>
 
 #include "device_util.cuh"
@@ -81,6 +82,109 @@ constexpr int kPatchThreads = 256;
 static_assert(kPatchThreads / 32 == kWarpCopies, "one node-sum copy per warp");
 
 constexpr int kEPT = kPatch / kPatchThreads;     // elements owned by a thread
+
+// The element products A_e x_e of one patch added into the per-node sums acc
+// (shared memory) in a fixed order: colour rounds for few colours per patch,
+// per-warp copies merged in warp order for many.  xs holds the operand at
+// the patch nodes; with colour rounds the caller has zeroed acc[0, n_nodes)
+// and synchronised the CTA.  On return acc[l] is node l's sum and the CTA is
+// synchronised.
+template <typename T, int NB, bool WARPS>
+__device__ __forceinline__ void patch_sums(const PatchMeta& m, int max_nodes, const T* __restrict__ As,
+                                           const uint16_t* __restrict__ Ls, const T* __restrict__ xs,
+                                           T* __restrict__ acc, const int* __restrict__ co, int tid) {
+    constexpr int NT = kPatchThreads;
+    if constexpr (WARPS) {
+        // Many colours (tetrahedra: about 30 per patch) would mean as many
+        // block barriers with little work between them.  Instead warp w adds
+        // the elements of colours w, w + 8, ... into its own copy of the node
+        // sums (a colour's elements share no node; a warp sync separates its
+        // colours); after one barrier the node value is the sum of the 8 copies
+        // in warp order (a fixed order: bitwise reproducible).
+        const int gcap = (max_nodes + 3) / 4 * 4;
+        const int warp = tid >> 5, lane = tid & 31;
+        T* accw = acc + warp * gcap;
+        for (int l = lane; l < m.n_nodes; l += 32) accw[l] = T(0);
+        __syncwarp();
+        for (int c = warp; c < m.n_col; c += kWarpCopies) {
+            const int lo = co[c], hi = co[c + 1];
+            for (int s = lo + lane; s < hi; s += 32) {
+                int ln[NB];
+                T xe[NB];
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    ln[i] = int(Ls[i * kPatch + s]);
+                    xe[i] = xs[ln[i]];
+                }
+                // difference form: the diagonal slot holds the row sum s_r,
+                // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r)
+#pragma unroll
+                for (int r = 0; r < NB; ++r) {
+                    T v = As[sym_index(NB, r, r) * kPatch + s] * xe[r];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j != r) v = fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[j] - xe[r], v);
+                    accw[ln[r]] += v;
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int l = tid; l < m.n_nodes; l += NT) {
+            T v = acc[l];
+#pragma unroll
+            for (int w = 1; w < kWarpCopies; ++w) v += acc[w * gcap + l];
+            acc[l] = v;
+        }
+        __syncthreads();
+    } else {
+        // my slots: local node ids and x values in registers
+        int ln[kEPT][NB];
+        T xe[kEPT][NB];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            const bool ok = s < m.n_el;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                ln[k][i] = ok ? int(Ls[i * kPatch + s]) : 0;
+                xe[k][i] = xs[ln[k][i]];
+            }
+        }
+        // FP32: every thread forms the products of its slots at once, then the
+        // colour rounds only add them into the node sums (short rounds).
+        // Difference form: the diagonal slot holds the row sum s_r,
+        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
+        // difference is exact in FP32 and no accuracy is lost to cancellation.
+        T y[kEPT][NB];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            const bool ok = s < m.n_el;
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                T v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[k][r] : T(0);
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
+                y[k][r] = v;
+            }
+        }
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+}
 
 // One patch per CTA, several CTAs per SM so that one CTA's copies overlap
 // another's arithmetic.  Thread 0 starts the bulk copies; meanwhile all
@@ -174,95 +278,7 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
     while (!mbar_try_wait(bar, 0)) {
     }                                             // completed already: acquire for this thread
 
-    if constexpr (WARPS) {
-        // Many colours (tetrahedra: about 30 per patch) would mean as many
-        // block barriers with little work between them.  Instead warp w adds
-        // the elements of colours w, w + 8, ... into its own copy of the node
-        // sums (a colour's elements share no node; a warp sync separates its
-        // colours); after one barrier the node value is the sum of the 8 copies
-        // in warp order (a fixed order: bitwise reproducible).
-        const int gcap = (pd.max_nodes + 3) / 4 * 4;
-        const int warp = tid >> 5, lane = tid & 31;
-        T* accw = acc + warp * gcap;
-        for (int l = lane; l < m.n_nodes; l += 32) accw[l] = T(0);
-        __syncwarp();
-        for (int c = warp; c < m.n_col; c += kWarpCopies) {
-            const int lo = co[c], hi = co[c + 1];
-            for (int s = lo + lane; s < hi; s += 32) {
-                int ln[NB];
-                T xe[NB];
-#pragma unroll
-                for (int i = 0; i < NB; ++i) {
-                    ln[i] = int(Ls[i * kPatch + s]);
-                    xe[i] = xs[ln[i]];
-                }
-                // difference form: the diagonal slot holds the row sum s_r,
-                // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r)
-#pragma unroll
-                for (int r = 0; r < NB; ++r) {
-                    T v = As[sym_index(NB, r, r) * kPatch + s] * xe[r];
-#pragma unroll
-                    for (int j = 0; j < NB; ++j)
-                        if (j != r) v = fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[j] - xe[r], v);
-                    accw[ln[r]] += v;
-                }
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int l = tid; l < m.n_nodes; l += NT) {
-            T v = acc[l];
-#pragma unroll
-            for (int w = 1; w < kWarpCopies; ++w) v += acc[w * gcap + l];
-            acc[l] = v;
-        }
-        __syncthreads();
-    } else {
-        // my slots: local node ids and x values in registers
-        int ln[kEPT][NB];
-        T xe[kEPT][NB];
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) {
-            const int s = tid + k * NT;
-            const bool ok = s < m.n_el;
-#pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                ln[k][i] = ok ? int(Ls[i * kPatch + s]) : 0;
-                xe[k][i] = xs[ln[k][i]];
-            }
-        }
-        // FP32: every thread forms the products of its slots at once, then the
-        // colour rounds only add them into the node sums (short rounds).
-        // Difference form: the diagonal slot holds the row sum s_r,
-        // y_r = s_r x_r + sum_{j != r} a_rj (x_j - x_r); for a smooth x the
-        // difference is exact in FP32 and no accuracy is lost to cancellation.
-        T y[kEPT][NB];
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) {
-            const int s = tid + k * NT;
-            const bool ok = s < m.n_el;
-#pragma unroll
-            for (int r = 0; r < NB; ++r) {
-                T v = ok ? As[sym_index(NB, r, r) * kPatch + s] * xe[k][r] : T(0);
-#pragma unroll
-                for (int j = 0; j < NB; ++j)
-                    if (j != r) v = ok ? fmadd(As[sym_index(NB, r, j) * kPatch + s], xe[k][j] - xe[k][r], v) : v;
-                y[k][r] = v;
-            }
-        }
-        for (int c = 0; c < m.n_col; ++c) {
-            const int lo = co[c], hi = co[c + 1];
-#pragma unroll
-            for (int k = 0; k < kEPT; ++k) {
-                const int s = tid + k * NT;
-                if (s >= lo && s < hi) {
-#pragma unroll
-                    for (int r = 0; r < NB; ++r) acc[ln[k][r]] += y[k][r];
-                }
-            }
-            __syncthreads();
-        }
-    }
+    patch_sums<T, NB, WARPS>(m, pd.max_nodes, As, Ls, xs, acc, co, tid);
 
     // owned nodes: final value; shared nodes: halo partial
     DotAcc<T> dot;
@@ -588,17 +604,416 @@ cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, 
     }
 }
 
+
+// ---------------------------------------------------------------- single-sync CG pass
+// One Jacobi-PCG iteration in two launches (see launch_cg_pass): the node
+// work of the textbook update and direction steps is done where the operator
+// pass gathers its operand, and the next step's r.z comes from the expansion
+// r'.(dinv r') = r.z - 2 alpha q.z + alpha^2 q.(dinv q) of the sums the pass
+// forms anyway, so one grid-wide reduction per iteration remains.  Vectors are
+// in the solver numbering: a patch's owned nodes are one contiguous run
+// (coalesced loads and stores, no node-table reads), shared nodes are read
+// through the node table and updated by the fix-up, which owns them.
+
+constexpr int kCgSums = 5;   // r.z, r.r, p.q, q.z, q.(dinv q)
+
+struct CgSmem {
+    uint32_t bar, flag, red, co, A, L, xs, zs, ds, acc, total;
+};
+template <int NB, bool WARPS>
+__host__ __device__ constexpr CgSmem cg_layout(int max_nodes) {
+    CgSmem s{};
+    const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
+    s.bar = 0;                                          // u64 mbarrier
+    s.flag = 8;                                         // int
+    s.red = 16;                                         // kCgSums x 8 doubles
+    s.co = s.red + kCgSums * 8 * 8;                     // kMaxColours + 1 ints
+    s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
+    s.L = s.A + uint32_t(sym_count(NB) * kPatch * 4);
+    s.xs = s.L + uint32_t(NB * kPatch * 2);             // p_new at the patch nodes
+    s.zs = s.xs + gcap * 4;                             // z at the owned nodes
+    s.ds = s.zs + gcap * 4;                             // dinv at the owned nodes
+    s.acc = s.ds + gcap * 4;
+    s.total = (s.acc + (WARPS ? kWarpCopies : 1) * gcap * 4 + 127) / 128 * 128;
+    return s;
+}
+
+// kCgSums block sums in a fixed order (warp butterflies, then warp 0 over the
+// per-warp sums); valid in thread 0.  red: kCgSums x 8 doubles.
+__device__ __forceinline__ void block_sums5(double (&v)[kCgSums], double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) red[k * 8 + w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) v[k] = lane < int(blockDim.x >> 5) ? red[k * 8 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < kCgSums; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+}
+
+// The node step of one iteration at one node, as the textbook update and
+// direction kernels compute it: r' = r - alpha q (FP32), z = dinv r',
+// p' = z + beta p (FP32), x' = x + alpha p (FP64, p widened exactly).
+struct CgNode {
+    float rn, z, pn;
+};
+__device__ __forceinline__ CgNode cg_node(float r, float q, float p, float d, float alf, float bef) {
+    CgNode o;
+    o.rn = __fmaf_rn(-alf, q, r);
+    o.z = d * o.rn;
+    o.pn = __fmaf_rn(bef, p, o.z);
+    return o;
+}
+
+template <int NB, bool WARPS>
+__global__ void __launch_bounds__(kPatchThreads)
+k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r, float* __restrict__ q,
+           const float* __restrict__ p_old, float* __restrict__ p_new, const float* __restrict__ dinv,
+           double* __restrict__ x, float* __restrict__ halo, double* __restrict__ part, const Scalars* __restrict__ sc) {
+    constexpr int NT = kPatchThreads;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const CgSmem L = cg_layout<NB, WARPS>(pd.max_nodes);
+    volatile int* flag = reinterpret_cast<volatile int*>(smem + L.flag);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    int* co = reinterpret_cast<int*>(smem + L.co);
+    const float* As = reinterpret_cast<const float*>(smem + L.A);
+    const uint16_t* Ls = reinterpret_cast<const uint16_t*>(smem + L.L);
+    float* xs = reinterpret_cast<float*>(smem + L.xs);
+    float* zs = reinterpret_cast<float*>(smem + L.zs);
+    float* ds = reinterpret_cast<float*>(smem + L.ds);
+    float* acc = reinterpret_cast<float*>(smem + L.acc);
+    const uint32_t bar = smem_addr(smem + L.bar);
+
+    pdl_trigger();
+    const int p = blockIdx.x;
+    const PatchMeta m = pd.meta[p];
+    const int tid = threadIdx.x;
+    const int64_t ns = pd.n_slots;
+    const int64_t slot0 = int64_t(p) * kPatch;
+    // element matrices and connectivity are constant: copy before the wait
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        const uint64_t pol = policy_evict_first();
+        mbar_expect_tx(bar, uint32_t(sym_count(NB) * kPatch * 4) + uint32_t(NB * kPatch * 2));
+#pragma unroll
+        for (int t = 0; t < sym_count(NB); ++t)
+            bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * 4), bar, pol);
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+            bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
+    }
+    for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
+    pdl_wait();
+    if (sc->done) {                                  // uniform: the solver has stopped
+        if (tid == 0) mbar_wait_bounded(bar, 0, nullptr);
+        return;
+    }
+    const double al = sc->alpha;
+    const float alf = d2f(al), bef = float(sc->beta);
+    const int own0 = __ldg(pd.own_off + p);
+    const int32_t* pn = pd.pnode + m.node_off;
+    // node step at every patch node (owned: contiguous run, written back;
+    // shared: through the node table, written by the fix-up)
+    CompSum srz, srr;
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        int id[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            id[u] = l < m.n_owned ? own0 + l : (l < m.n_nodes ? (__ldg(pn + l) & kNodeMask) : -1);
+        }
+        float rv[2], qv[2], pv[2], dv[2];
+        double xv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            if (id[u] >= 0) {
+                rv[u] = r[id[u]];
+                qv[u] = q[id[u]];
+                pv[u] = __ldg(p_old + id[u]);
+                dv[u] = __ldg(dinv + id[u]);
+                xv[u] = l < m.n_owned ? x[id[u]] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int l = l0 + u * NT + tid;
+            if (id[u] < 0) continue;
+            const CgNode c = cg_node(rv[u], qv[u], pv[u], dv[u], alf, bef);
+            xs[l] = c.pn;
+            if (!WARPS) acc[l] = 0.0f;
+            if (l < m.n_owned) {
+                x[id[u]] = fmadd(al, f2d(pv[u]), xv[u]);
+                r[id[u]] = c.rn;
+                p_new[id[u]] = c.pn;
+                zs[l] = c.z;
+                ds[l] = dv[u];
+                srz.add(c.rn * c.z);
+                srr.add(c.rn * c.rn);
+            }
+        }
+    }
+    if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
+    __syncthreads();
+    if (*flag == 0) {
+        if (tid == 0) mbar_wait_bounded(bar, 0, nullptr);
+        return;
+    }
+    while (!mbar_try_wait(bar, 0)) {
+    }
+    patch_sums<float, NB, WARPS>(m, pd.max_nodes, As, Ls, xs, acc, co, tid);
+    // q = mask(A p_new): owned nodes final (Dirichlet rows: dinv = 0), shared
+    // nodes to their halo slots
+    CompSum spq, sqz, sqdq;
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        const float v = acc[l];
+        if (l < m.n_owned) {
+            const float d = ds[l];
+            const float qn = d == 0.0f ? 0.0f : v;
+            q[own0 + l] = qn;
+            spq.add(xs[l] * qn);
+            sqz.add(qn * zs[l]);
+            sqdq.add(qn * (d * qn));
+        } else {
+            halo[m.halo_off + (l - m.n_owned)] = v;
+        }
+    }
+    double v[kCgSums] = {srz.value(), srr.value(), spq.value(), sqz.value(), sqdq.value()};
+    block_sums5(v, red);
+    if (tid == 0) {
+        const int64_t stride = int64_t(pd.n_patches) + kFixGridMax;
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) part[k * stride + p] = v[k];
+    }
+}
+
+// Shared nodes of a single-sync pass: the node step (the fix-up owns them),
+// q from the halo partials in patch order, the sums; the last block adds all
+// partials in index order and takes the iteration's scalar decisions.
+template <int ROWS>
+__global__ void __launch_bounds__(kFixThreads)
+k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const float* __restrict__ p_old,
+           float* __restrict__ p_new, const float* __restrict__ dinv, double* __restrict__ x,
+           const float* __restrict__ halo, double* __restrict__ part, Scalars* __restrict__ sc) {
+    __shared__ double red[kCgSums * 8];
+    __shared__ bool last;
+    pdl_trigger();
+    pdl_wait();
+    if (sc->done) return;
+    const double al = sc->alpha;
+    const float alf = d2f(al), bef = float(sc->beta);
+    CompSum s5[kCgSums];
+    const int st = int(gridDim.x) * kFixThreads;
+    for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += ROWS * st) {
+        int s0[ROWS], cnt[ROWS];
+        int nmax = 0;
+        float rv[ROWS], qv[ROWS], pv[ROWS], dv[ROWS];
+        double xv[ROWS];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int kk = k + u * st;
+            const bool ok = kk < pd.n_shared;
+            s0[u] = ok ? __ldg(pd.sh_ptr + kk) : 0;
+            cnt[u] = ok ? __ldg(pd.sh_ptr + kk + 1) - s0[u] : 0;
+            nmax = cnt[u] > nmax ? cnt[u] : nmax;
+            const int id = pd.sh_base + kk;
+            rv[u] = ok ? r[id] : 0.0f;
+            qv[u] = ok ? q[id] : 0.0f;
+            pv[u] = ok ? __ldg(p_old + id) : 0.0f;
+            dv[u] = ok ? __ldg(dinv + id) : 0.0f;
+            xv[u] = ok ? x[id] : 0.0;
+        }
+        float hv[ROWS];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) hv[u] = 0.0f;
+        for (int t = 0; t < nmax; ++t)
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u)
+                if (t < cnt[u]) hv[u] += halo[__ldg(pd.sh_slot + s0[u] + t)];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int kk = k + u * st;
+            if (kk >= pd.n_shared) break;
+            const int id = pd.sh_base + kk;
+            const CgNode c = cg_node(rv[u], qv[u], pv[u], dv[u], alf, bef);
+            const float qn = dv[u] == 0.0f ? 0.0f : hv[u];
+            x[id] = fmadd(al, f2d(pv[u]), xv[u]);
+            r[id] = c.rn;
+            p_new[id] = c.pn;
+            q[id] = qn;
+            s5[0].add(c.rn * c.z);
+            s5[1].add(c.rn * c.rn);
+            s5[2].add(c.pn * qn);
+            s5[3].add(qn * c.z);
+            s5[4].add(qn * (dv[u] * qn));
+        }
+    }
+    double v[kCgSums];
+#pragma unroll
+    for (int j = 0; j < kCgSums; ++j) v[j] = s5[j].value();
+    // this block also adds a contiguous chunk of the per-patch partials
+    const int np = pd.n_patches;
+    const int64_t stride = int64_t(np) + kFixGridMax;
+    const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
+    const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
+    for (int i = int(blockIdx.x) * chunk + threadIdx.x; i < p1; i += kFixThreads)
+#pragma unroll
+        for (int j = 0; j < kCgSums; ++j) v[j] += part[j * stride + i];
+    block_sums5(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < kCgSums; ++j) part[j * stride + np + blockIdx.x] = v[j];
+        __threadfence();
+        last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < kCgSums; ++j) v[j] = 0.0;
+    for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads)
+#pragma unroll
+        for (int j = 0; j < kCgSums; ++j) v[j] += __ldcg(part + j * stride + np + i);
+    block_sums5(v, red);
+    if (threadIdx.x != 0) return;
+    sc->ctr_fix = 0;
+    const double rho = v[0], rr = v[1], pq = v[2], qz = v[3], qdq = v[4];
+    const bool fresh = sc->fresh != 0;
+    sc->fresh = 0;
+    sc->passes += 1;
+    if (!fresh) sc->iter += 1;
+    sc->rz = rho;
+    sc->rr = rr;
+    sc->pq = pq;
+    sc->qz = qz;
+    sc->qdq = qdq;
+    if (!isfinite(rho) || !isfinite(rr) || !isfinite(pq) || !isfinite(qz) || !isfinite(qdq) || rho < 0.0) {
+        sc->done = 1;
+        sc->reason = kBreakdown;
+    } else if (!fresh && rr <= sc->thr2) {
+        sc->done = 1;            // rho keeps the previous direction's r.z for the replacement
+        sc->reason = kTrigger;
+    } else if (!fresh && sc->iter >= sc->maxit) {
+        sc->done = 1;
+        sc->reason = kMaxit;
+    } else if (!(pq > 0.0)) {
+        sc->done = 1;
+        sc->reason = kBreakdown;
+    } else {
+        const double a = rho / pq;
+        const double rho_next = fmadd(a * a, qdq, fmadd(-2.0 * a, qz, rho));
+        sc->alpha = a;
+        sc->beta = rho_next > 0.0 ? rho_next / rho : 0.0;   // < 0 only through cancellation: restart the direction
+        sc->rho = rho;
+    }
+}
+
+template <int NB, bool WARPS>
+cudaError_t run_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
+                        const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
+                        int* launches, bool pdl) {
+    const size_t sm = cg_layout<NB, WARPS>(pd.max_nodes).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto kern = k_cg_patch<NB, WARPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    if (pdl) {
+        e = launch_pdl(kern, dim3(pd.n_patches), dim3(kPatchThreads), sm, st, pd, A, r, q, p_old, p_new, dinv, x, halo,
+                       part, sc);
+        if (e != cudaSuccess) return e;
+    } else {
+        kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fix_rows(pd) == 2)
+        k_cg_fixup<2><<<fix_grid(pd.n_shared, 2), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
+    else
+        k_cg_fixup<1><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+__global__ void k_cg_arm(Scalars* sc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc->alpha = 0.0;
+        sc->fresh = 1;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(int64_t n, const int32_t* __restrict__ map, const T* __restrict__ src,
+                                                 T* __restrict__ dst, int to_solver) {
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256) {
+        if (to_solver) dst[map[i]] = src[i];
+        else dst[i] = src[map[i]];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_copy_dirichlet_bit(int32_t* __restrict__ dst, const int32_t* __restrict__ src,
+                                                            int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256)
+        dst[i] = int32_t((uint32_t(dst[i]) & uint32_t(kNodeMask)) | (uint32_t(src[i]) & kDirichletBit));
+}
 }  // namespace
 
 int fix_grid(int n_shared, int rows) {
     int g = (n_shared + rows * kFixThreads - 1) / (rows * kFixThreads);
-    return g < 1 ? 1 : (g > 1216 ? 1216 : g);
+    return g < 1 ? 1 : (g > kFixGridMax ? kFixGridMax : g);
 }
 
 int fix_rows(const PlanDev& pd) {
     // 2049^2 triangles: 2.04 slots per shared node, 10.5 -> 9.0 us per fix-up with
     // two rows; 129^3 tetrahedra (more slots per node): 16.0 -> 18.5 us, one row
     return 2 * pd.n_halo <= 5 * int64_t(pd.n_shared) ? 2 : 1;
+}
+
+cudaError_t launch_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
+                           const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
+                           int* launches, bool pdl) {
+    if (pd.own_off == nullptr) return cudaErrorInvalidValue;
+    const bool warps = pd.max_col > kWarpSchemeColours;
+    if (pd.nb == 3)
+        return warps ? run_cg_pass<3, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl)
+                     : run_cg_pass<3, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl);
+    return warps ? run_cg_pass<4, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl)
+                 : run_cg_pass<4, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl);
+}
+
+cudaError_t launch_cg_arm(Scalars* sc, cudaStream_t st, int* launches) {
+    k_cg_arm<<<1, 32, 0, st>>>(sc);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(int dtype, int to_solver, int64_t n, const int32_t* map, const void* src, void* dst,
+                           cudaStream_t st, int* launches) {
+    if (n <= 0) return cudaSuccess;
+    const int g = int(std::min<int64_t>((n + 255) / 256, 4096));
+    if (dtype == 0)
+        k_permute<double><<<g, 256, 0, st>>>(n, map, static_cast<const double*>(src), static_cast<double*>(dst), to_solver);
+    else
+        k_permute<float><<<g, 256, 0, st>>>(n, map, static_cast<const float*>(src), static_cast<float*>(dst), to_solver);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_dirichlet_bit(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st, int* launches) {
+    if (n <= 0) return cudaSuccess;
+    const int g = int(std::min<int64_t>((n + 255) / 256, 4096));
+    k_copy_dirichlet_bit<<<g, 256, 0, st>>>(dst, src, n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void* A, const void* x, const void* b,

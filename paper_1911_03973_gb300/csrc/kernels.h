@@ -29,6 +29,12 @@ struct PlanDev {
     const int32_t* slot_elem = nullptr; // [n_slots], -1 = padding
     int32_t* err = nullptr;             // set to 1 when a bounded device wait gives up
     int num_sms = 1;                    // persistent grid size of the patch pass
+    // Solver numbering (set in the view of the single-sync solver only): the
+    // owned nodes of patch p are nodes own_off[p] + l, l < n_owned (one
+    // contiguous run per patch, padded to a multiple of 4), and shared row k
+    // of the fix-up is node sh_base + k.
+    const int32_t* own_off = nullptr;   // [n_patches + 1]
+    int sh_base = 0;
 };
 
 // Element matrices are symmetric (K_e and M_e of Eq. matrices_K_M; the
@@ -73,6 +79,12 @@ struct Scalars {
     int32_t reason;  // StopReason
     uint32_t ctr_fix;   // arrival counters of the last-block reductions
     uint32_t ctr_vec;
+    // single-sync iteration (launch_cg_pass)
+    double qz;       // q.z of the last pass (z = dinv r)
+    double qdq;      // q.(dinv q) of the last pass
+    int64_t passes;  // passes that ran to completion (parity of the two direction buffers)
+    int32_t fresh;   // the next pass starts from a new residual: no update, no iteration counted
+    int32_t pad;
 };
 
 // Launch with programmatic stream serialisation: the kernel may start while
@@ -96,7 +108,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 // Fixed grid of the node-vector kernels for n nodes (deterministic partials).
 int vec_grid(int64_t n);
-// Fix-up grid: `rows` shared rows per thread at a time (1 or 2).
+// Fix-up grid: `rows` shared rows per thread at a time (1 or 2), at most
+// kFixGridMax blocks.
+constexpr int kFixGridMax = 1216;
 int fix_grid(int n_shared, int rows = 1);
 // Rows per fix-up thread for this partition: 2 (their loads interleaved) when
 // a shared node has at most 2.5 halo slots on average, else 1.
@@ -116,6 +130,31 @@ cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void
                               const void* b, void* out, void* halo, double* part, const int32_t* stop,
                               Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr,
                               bool pdl = false);
+
+// ---- single-synchronisation mixed-precision CG (k_patch.cu) ---------------
+// One pass = one CG iteration in two launches (patch pass + shared-node
+// fix-up), all node vectors in the solver numbering (pd.own_off set), FP32
+// except x:
+//   r <- r - alpha q;  x <- x + alpha p_old;  z = dinv r;  p_new = z + beta p_old;
+//   q <- mask(A p_new) (FP32 difference-form element matrices A);
+//   sums r.z, r.r, p_new.q, q.z, q.(dinv q) -> the last fix-up block sets
+//   alpha = r.z / p.q, beta = rho_next / r.z with
+//   rho_next = r.z - 2 alpha q.z + alpha^2 q.(dinv q) (= r'.(dinv r') of the
+//   next residual r' = r - alpha q), counts the iteration and takes the stop
+//   decisions of the textbook update step (trigger on r.r <= thr2, maxit,
+//   breakdown).  sc->fresh: alpha = 0 and no iteration (first pass after a
+//   (re)start).  Dirichlet rows are those with dinv = 0.  part: 5 x
+//   (n_patches + fix_grid(n_shared)) doubles.
+cudaError_t launch_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
+                           const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
+                           int* launches, bool pdl = false);
+// alpha = 0, fresh = 1 (after a restart of the recurrence).
+cudaError_t launch_cg_arm(Scalars* sc, cudaStream_t st, int* launches);
+// dst[map[i]] = src[i] (to the solver numbering) or dst[i] = src[map[i]] (back), i < n.
+cudaError_t launch_permute(int dtype, int to_solver, int64_t n, const int32_t* map, const void* src, void* dst,
+                           cudaStream_t st, int* launches);
+// dst[i] = (dst[i] & node mask) | (src[i] & Dirichlet bit), i < n.
+cudaError_t launch_copy_dirichlet_bit(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st, int* launches);
 
 // ---- element data (k_assemble.cu) -----------------------------------------
 // Element matrices, load vector and Jacobi diagonal (FP64), Eq. matrices_K_M.

@@ -121,6 +121,13 @@ def bytes_model(dim: int, n_n: int, n_e: int, stored: bool = False):
     # after a true residual: r.z and r.r (r64, dinv in; r32 out), then a direction step
     m["restart_mixed"] = n_n * ((8 + 4 + 4) + (4 + 4 + 4 + 4))
     m["restart64"] = n_n * ((8 + 8) + (8 + 8 + 8 + 8))
+    # one iteration of the single-sync mixed solver (one pass): the operator's
+    # element matrices and connectivity, and per node r, q, p, dinv (4 B) and
+    # x (8 B) in, r, p, q (4 B) and x (8 B) out -- the direction the operator
+    # applies is formed in registers, not read
+    m["cg_mixed"] = conn + n_e * na * 4 + n_n * (4 * 4 + 8 + 3 * 4 + 8)
+    # restart of the single-sync recurrence: r64, dinv in, r32 out
+    m["cg_restart"] = n_n * (8 + 4 + 4)
     return m
 
 
@@ -139,10 +146,14 @@ def fp64_alu_model(nb: int, n_n: int, n_e: int, sms: int, mhz):
 
 
 def step_bytes(m, info, mixed: bool):
+    """Algorithmic bytes of one step: element matrices, then the solve as it
+    runs.  Mixed (single-sync solver): one pass per iteration plus one first
+    pass per start of the recurrence (the initial one and every replacement),
+    a restart and an FP64 true residual per check.  Plain FP64 (textbook
+    iteration): operator, update and direction per iteration."""
     it, tr = info["iterations"], info["true_residuals"]
     if mixed:
-        return (m["assemble_mixed"] + it * (m["apply32"] + m["vec_mixed"]) + tr * m["residual64"]
-                + max(tr - 1, 0) * m["restart_mixed"])
+        return (m["assemble_mixed"] + (it + tr) * m["cg_mixed"] + tr * (m["residual64"] + m["cg_restart"]))
     return m["assemble_fp64"] + it * (m["apply64"] + m["vec64"]) + tr * m["residual64"] + max(tr - 1, 0) * m["restart64"]
 
 
@@ -563,6 +574,7 @@ def run_learned(args, dev, stream, profile=False):
 
             ij, tj = timed(lambda x: ebe.ebe_solve_learned(h, None, x, rtol=args.rtol))
             il, tl = timed(lambda x: ebe.ebe_solve_learned(h, net, x, rtol=args.rtol))
+            i0, t0n = timed(lambda x: ebe.ebe_solve_learned(h, net, x, rtol=args.rtol, race_iters=0))
             ip, tp = timed(lambda x: ebe.ebe_solve(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_FP64))
             im, tm = timed(lambda x: ebe.ebe_solve(h, x, rtol=args.rtol, precision=ebe.EBE_PREC_MIXED))
             r = torch.rand(nn, dtype=torch.float64, device=dev)
@@ -577,7 +589,9 @@ def run_learned(args, dev, stream, profile=False):
             torch.cuda.synchronize()
             out[f"square{n}"] = {
                 "learned_fcg": {"ms": round(tl, 1), "iterations": il["iterations"], "fell_back": il["fell_back"],
-                                "status": il["status"]},
+                                "status": il["status"], "rule": "race of 64 Jacobi / 64 network iterations"},
+                "network_first": {"ms": round(t0n, 1), "iterations": i0["iterations"], "fell_back": i0["fell_back"],
+                                  "rule": "network from the start, fallback rules only"},
                 "jacobi_fcg": {"ms": round(tj, 1), "iterations": ij["iterations"]},
                 "plain_fp64_pcg": {"ms": round(tp, 1), "iterations": ip["iterations"]},
                 "mixed_pcg": {"ms": round(tm, 1), "iterations": im["iterations"]},
@@ -708,8 +722,11 @@ def run_ours(args):
             ms_text, tinfo = _timed_solve(ebe, torch, h, x, stream, 1, rtol=args.rtol,
                                           precision=ebe.EBE_PREC_MIXED_TEXTBOOK)
 
-        # roofline: FP32 operator application, per-launch events on its stream
+        # roofline: the solver's iteration (single-sync pass: patch + fix-up)
+        # and the plain FP32 operator application, per-launch events on the stream
         ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+        ebe.ebe_time_cg_pass(h, reps=5)
+        ms_cg = ebe.ebe_time_cg_pass(h, reps=40)
         p32 = torch.rand(n_n, dtype=torch.float32, device=dev)
         q32 = torch.empty_like(p32)
         ms_patch, ms_fix = ebe.ebe_time_operator(h, p32, q32, apply=True, reps=20)
@@ -734,6 +751,7 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     ach = m["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9
+    ach_cg = m["cg_mixed"] / ((ms_cg[0] + ms_cg[1]) / 1e3) / 1e9
     ach64 = m["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9
     alu64 = fp64_alu_model(dim + 1, n_n, n_e, torch.cuda.get_device_properties(dev).multi_processor_count,
                            clk.get("sm_mhz") or clk.get("sm_max_mhz"))
@@ -824,13 +842,17 @@ def run_ours(args):
                 "speedup_vs_plain": round(ms_plain / ms_step, 3) if ms_plain else None,
                 "textbook_mixed_ms": round(ms_text, 2) if ms_text else None,
                 "textbook_mixed_iterations": tinfo["iterations"] if tinfo else None},
-        "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(ach / peak, 4), "traffic": trf,
-                     "kernel": "FP32 operator application: patch pass + halo fix-up",
-                     "ms_per_launch": [round(ms_patch, 5), round(ms_fix, 5)],
-                     "bytes_per_launch": m["apply32"], "peak_kind": peak_kind,
-                     "stored_bytes_per_launch": m_stored["apply32"],
-                     "stored_gbs": round(m_stored["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(ach_cg, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach_cg / peak, 4), "traffic": trf,
+                     "kernel": "one iteration of the mixed solver: single-sync pass (k_cg_patch + k_cg_fixup)",
+                     "ms_per_launch": [round(ms_cg[0], 5), round(ms_cg[1], 5)],
+                     "bytes_per_launch": m["cg_mixed"], "peak_kind": peak_kind,
+                     "stored_bytes_per_launch": m_stored["cg_mixed"],
+                     "stored_gbs": round(m_stored["cg_mixed"] / ((ms_cg[0] + ms_cg[1]) / 1e3) / 1e9, 1)},
+        "apply_fp32": {"gbs": round(ach, 1), "frac": round(ach / peak, 4),
+                       "kernel": "FP32 operator application: patch pass + halo fix-up",
+                       "ms_per_launch": [round(ms_patch, 5), round(ms_fix, 5)], "bytes_per_launch": m["apply32"],
+                       "stored_gbs": round(m_stored["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9, 1)},
         "residual_fp64": {"gbs": round(ach64, 1), "frac": round(ach64 / peak, 4),
                           "ms_per_launch": [round(ms_patch64, 5), round(ms_fix64, 5)],
                           "bytes_per_launch": m["residual64"],
@@ -888,9 +910,11 @@ def summary_block(line, ms_plain, pinfo, peak):
     if lr:
         s["learned"] = {k: {"fcg_net_ms": v["learned_fcg"]["ms"], "net_it": v["learned_fcg"]["iterations"],
                             "fell_back": v["learned_fcg"]["fell_back"], "plain_pcg_ms": v["plain_fp64_pcg"]["ms"],
-                            "ratio_to_plain": round(v["learned_fcg"]["ms"] / v["plain_fp64_pcg"]["ms"], 3)}
+                            "ratio_to_plain": round(v["learned_fcg"]["ms"] / v["plain_fp64_pcg"]["ms"], 3),
+                            "net_first_ms": v["network_first"]["ms"]}
                         for k, v in lr.items() if k.startswith("square")}
-    s["hbm_frac"] = {"apply32": r["frac"], "residual64": line["residual_fp64"]["frac"]}
+    s["hbm_frac"] = {"cg_pass": r["frac"], "apply32": line["apply_fp32"]["frac"],
+                     "residual64": line["residual_fp64"]["frac"]}
     c = line.get("cube129")
     if c:
         s["hbm_frac"].update({"cube_apply32": c["apply32"]["frac"], "cube_residual64": c["residual64"]["frac"]})

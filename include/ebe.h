@@ -140,6 +140,10 @@ typedef struct {
     int32_t stall_updates;   /* true-residual checks without progress before EBE_STALL,
                                 default 8                                                */
     int32_t use_graph;       /* 1 (default): iterations run as captured CUDA graphs      */
+    int32_t race_iters;      /* ebe_solve_learned only: iterations of each leg of the race
+                                between Jacobi and the network; 0 = no race (the network
+                                from the start, with the fallback rules only); default -1
+                                = 2 chunk                                                */
 } ebe_solve_opts;
 
 typedef struct {
@@ -257,6 +261,16 @@ ebe_status ebe_apply(ebe_handle* h, const void* x_dev, void* y_dev, int32_t dtyp
  * Synchronises the stream.  Arguments and errors as ebe_residual. */
 ebe_status ebe_time_operator(ebe_handle* h, const void* x_dev, void* y_dev, int32_t dtype, int32_t apply,
                              int32_t reps, double* ms);
+
+/* Measure one iteration of the EBE_PREC_MIXED solver (the single-sync pass:
+ * patch kernel and fix-up kernel): from x0 = 0 on the handle's problem, one
+ * untimed first pass and then `reps` CG iterations without a stopping test,
+ * with CUDA events recorded on the handle's stream around each of the two
+ * kernels.  ms: host [2], receives the mean milliseconds per launch of the
+ * patch kernel and of the fix-up kernel.  Uses the solver's own work vectors
+ * (no caller data).  Needs EBE_STORE_MIXED.  Synchronises the stream.
+ * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_BREAKDOWN, EBE_CUDA_ERROR. */
+ebe_status ebe_time_cg_pass(ebe_handle* h, int32_t reps, double* ms);
 
 /* FP64 residual r = mask(b - A x) with a chosen scatter strategy
  * (EBE_SCATTER_*), for comparing them.  Builds the strategy's data on first
@@ -459,11 +473,16 @@ ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev
 /* Flexible CG (one stored direction: p = z - (z.q_prev / p_prev.q_prev) p_prev,
  * alpha = p.r / p.q) with z = B(r) from net, or the Jacobi step with net NULL,
  * FP64 vectors and element matrices, stopping on the FP64 true relative
- * residual as ebe_solve.  With a network the solve falls back to Jacobi from
- * the current iterate on a breakdown, when the residual norm does not halve
- * within 16 chunks, or when the true residual stalls (stall_updates checks);
- * *fell_back (may be NULL) reports it.  opts:
- * rtol, maxit, chunk (iterations between host checks), stall_updates.
+ * residual as ebe_solve.  With a network the solve starts with a race: from
+ * x0, race_iters iterations of Jacobi-FCG, then, again from x0, race_iters
+ * iterations with the network, each timed with CUDA events; the one with the
+ * larger reduction of the residual norm per unit time continues (so a network
+ * that is slower than Jacobi costs about its race_iters timed iterations).  The
+ * network-FCG then falls back to Jacobi from the current iterate on a
+ * breakdown, when the residual norm does not halve within 16 chunks, or when
+ * the true residual stalls (stall_updates checks); *fell_back (may be NULL)
+ * is 1 when the solution came from Jacobi.  opts:
+ * rtol, maxit, chunk (iterations between host checks), stall_updates, race_iters.
  * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
 ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x_dev, const ebe_solve_opts* opts,
                              ebe_solve_info* info, int32_t* fell_back);

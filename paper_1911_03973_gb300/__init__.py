@@ -177,6 +177,14 @@ def ebe_time_operator(h: Handle, x, y, apply: bool = True, reps: int = 20) -> tu
     return float(ms[0]), float(ms[1])
 
 
+def ebe_time_cg_pass(h: Handle, reps: int = 20) -> tuple:
+    """Mean ms per launch of (patch kernel, fix-up kernel) of one single-sync
+    mixed-precision CG iteration, CUDA events on the handle's stream."""
+    ms = (ctypes.c_double * 2)()
+    _check(h, _lib().ebe_time_cg_pass(h.ptr, int(reps), ms))
+    return float(ms[0]), float(ms[1])
+
+
 def ebe_residual_variant(h: Handle, x, r, scatter: int) -> None:
     _check(h, _lib().ebe_residual_variant(h.ptr, _dev(x, EBE_F64, h.n_n, "x"), _dev(r, EBE_F64, h.n_n, "r"),
                                           int(scatter)))
@@ -440,9 +448,12 @@ def ebe_mpnn_train_step(net: Mpnn, h: Handle, r, e, lr: float) -> float:
     return loss.value
 
 
-def ebe_solve_learned(h: Handle, net, x, rtol=None, maxit=None, chunk=None, stall_updates=None) -> dict:
+def ebe_solve_learned(h: Handle, net, x, rtol=None, maxit=None, chunk=None, stall_updates=None,
+                      race_iters=None) -> dict:
     """Flexible CG with the network (or Jacobi with net=None) on a device x; adds "fell_back"."""
     o = _opts(rtol, maxit, None, chunk, None, stall_updates, None)
+    if race_iters is not None:
+        o.race_iters = int(race_iters)
     info = _abi.ebe_solve_info()
     fb = ctypes.c_int32()
     st = _lib().ebe_solve_learned(h.ptr, net.ptr if net is not None else None, _dev(x, EBE_F64, h.n_n, "x"),

@@ -51,7 +51,7 @@ class ebe_create_opts(ctypes.Structure):
 class ebe_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("delta", ctypes.c_double), ("stall_updates", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("race_iters", ctypes.c_int32)]
 
 
 class ebe_solve_info(ctypes.Structure):
@@ -133,6 +133,7 @@ SIGNATURES = [
     ("ebe_residual_noalloc", ctypes.c_int, [_H, _VP, _VP]),
     ("ebe_richardson", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double]),
     ("ebe_chebyshev2", ctypes.c_int, [_H, _VP, ctypes.c_int64, _F64P, ctypes.c_int64]),
+    ("ebe_time_cg_pass", ctypes.c_int, [_H, ctypes.c_int32, _F64P]),
     ("ebe_chebyshev2_bounds", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int64]),
     ("ebe_chebyshev3", ctypes.c_int, [_H, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double]),

@@ -116,6 +116,7 @@ struct ebe_handle {
     int32_t* g_nbr = nullptr;
     float* g_invdeg = nullptr;
     double* z64 = nullptr;
+    double *xsave0 = nullptr, *xsave1 = nullptr;   // iterates of the learned solver's race
 
     // comparison scatters
     int32_t* gconn = nullptr;
@@ -285,6 +286,7 @@ void ebe_solve_opts_default(ebe_solve_opts* o) {
     o->delta = 0.1;
     o->stall_updates = 8;
     o->use_graph = 1;
+    o->race_iters = -1;
 }
 
 void ebe_destroy(ebe_handle* h) {
@@ -1027,8 +1029,8 @@ int true_residual_int(ebe_handle* h, double& rr) {
     return EBE_OK;
 }
 
-int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
-    const auto t0 = std::chrono::steady_clock::now();
+// Work vectors of the single-sync solver (solver numbering).
+int cg1_buffers(ebe_handle* h) {
     if (h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs ebe_assemble(EBE_STORE_MIXED)");
     const int64_t n = h->plan.n_n, ni = h->n_int;
     const int64_t nh = std::max<int64_t>(h->plan.n_halo, 1);
@@ -1042,7 +1044,28 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
     TRY(dalloc(h, &h->halo64, nh));
     TRY(dalloc(h, &h->halo32, nh));
     TRY(dalloc(h, &h->part5, 5 * (int64_t(h->pd.n_patches) + kFixGridMax)));
-    TRY(ensure_solver_vectors(h));
+    return ensure_solver_vectors(h);
+}
+
+// The recurrence started from the FP64 true residual in ri64: p = q = 0,
+// r32, r.z, beta = 0, alpha = 0 and the fresh flag (first pass: no update).
+int cg1_start(ebe_handle* h, double thr2) {
+    const int64_t ni = h->n_int;
+    int l = 0;
+    CK(cudaMemsetAsync(h->pi32[0], 0, sizeof(float) * size_t(ni), h->st), "memset");
+    CK(cudaMemsetAsync(h->pi32[1], 0, sizeof(float) * size_t(ni), h->st), "memset");
+    CK(cudaMemsetAsync(h->qi32, 0, sizeof(float) * size_t(ni), h->st), "memset");
+    CK(launch_restart(1, ni, h->ri64, h->dinvi32, 1, h->part_vec, h->sc, h->st, &l, h->ri32), "restart");
+    CK(launch_cg_arm(h->sc, h->st, &l), "arm");
+    CK(launch_control(h->sc, thr2, -1, 0, h->st, &l), "control");
+    add_launches(h, l);
+    return EBE_OK;
+}
+
+int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = h->plan.n_n, ni = h->n_int;
+    TRY(cg1_buffers(h));
     int l = 0;
     CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                        h->st), "copy x0");
@@ -1063,15 +1086,8 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
     if (r0 > 0.0 && std::isfinite(r0)) {
         const double target = o.rtol * r0;
         double fin = target;
-        l = 0;
-        CK(cudaMemsetAsync(h->pi32[0], 0, sizeof(float) * size_t(ni), h->st), "memset");
-        CK(cudaMemsetAsync(h->pi32[1], 0, sizeof(float) * size_t(ni), h->st), "memset");
-        CK(cudaMemsetAsync(h->qi32, 0, sizeof(float) * size_t(ni), h->st), "memset");
-        CK(launch_restart(1, ni, h->ri64, h->dinvi32, 1, h->part_vec, h->sc, h->st, &l, h->ri32), "restart");
-        CK(launch_cg_arm(h->sc, h->st, &l), "arm");
         double thr = std::max(o.delta * r0, fin);
-        CK(launch_control(h->sc, thr * thr, -1, 0, h->st, &l), "control");
-        add_launches(h, l);
+        TRY(cg1_start(h, thr * thr));
         if (o.use_graph) TRY(ensure_cg_graphs(h, o.chunk));
         int par = 0;                   // buffer of the current direction (read by the next pass)
         int64_t passes = h->sc_host->passes;
@@ -1157,6 +1173,55 @@ int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts,
 }
 
 }  // namespace
+
+ebe_status ebe_time_cg_pass(ebe_handle* h, int32_t reps, double* ms) {
+    TRY(check_ready(h, true));
+    if (!ms || reps < 1 || reps > 100000) return ebe_status(fail(h, EBE_INVALID_ARG, "ms must be non-NULL, 1 <= reps <= 100000"));
+    Scope scp(h);
+    TRY(cg1_buffers(h));
+    int l = 0;
+    CK(cudaMemsetAsync(h->xi, 0, sizeof(double) * size_t(h->n_int), h->st), "memset");
+    CK(launch_control(h->sc, 0.0, int64_t(1) << 62, 1, h->st, &l), "control");
+    add_launches(h, l);
+    double rr = 0.0;
+    TRY(true_residual_int(h, rr));
+    TRY(cg1_start(h, -1.0));                       // threshold 0: no stop inside the timed passes
+    std::vector<cudaEvent_t> ev(size_t(3) * size_t(reps + 1), nullptr);
+    int status = EBE_OK;
+    for (auto& e : ev) {
+        const cudaError_t c = cudaEventCreate(&e);
+        if (c != cudaSuccess && status == EBE_OK) status = cuda_fail(h, c, "cudaEventCreate");
+    }
+    l = 0;
+    for (int r = 0; r <= reps && status == EBE_OK; ++r) {   // pass 0 is the fresh (untimed) pass
+        const cudaError_t e = launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[r & 1], h->pi32[(r + 1) & 1],
+                                             h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st, &l, true,
+                                             &ev[size_t(3) * size_t(r)]);
+        if (e != cudaSuccess) status = cuda_fail(h, e, "single-sync pass");
+    }
+    add_launches(h, l);
+    double t_patch = 0.0, t_fix = 0.0;
+    if (status == EBE_OK) {
+        const cudaError_t e = cudaEventSynchronize(ev.back());
+        if (e != cudaSuccess) status = cuda_fail(h, e, "cudaEventSynchronize");
+        for (int r = 1; r <= reps && status == EBE_OK; ++r) {
+            float a = 0.f, c = 0.f;
+            cudaEventElapsedTime(&a, ev[size_t(3) * r], ev[size_t(3) * r + 1]);
+            cudaEventElapsedTime(&c, ev[size_t(3) * r + 1], ev[size_t(3) * r + 2]);
+            t_patch += a;
+            t_fix += c;
+        }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (status == EBE_OK) status = sync_scalars(h);
+    if (status == EBE_OK && h->sc_host->reason != kRunning)
+        status = fail(h, EBE_BREAKDOWN, "the timed passes stopped (breakdown)");
+    if (status != EBE_OK) return ebe_status(status);
+    ms[0] = t_patch / reps;
+    ms[1] = t_fix / reps;
+    return EBE_OK;
+}
 
 ebe_status ebe_solve(ebe_handle* h, double* x, const ebe_solve_opts* opts, ebe_solve_info* info) {
     return ebe_status(solve_entry(h, x, false, opts, info));
@@ -2012,19 +2077,90 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             add_launches(h, ll);
             return EBE_OK;
         };
-        for (;;) {
-            l = 0;
-            for (int it = 0; it < o.chunk; ++it) {
-                if (use_net) CK(launch_mpnn_forward(net->md, n, h->r64, h->dinv, h->z64, false, h->st, &l), "network");
-                else CK(launch_jacobi(n, h->r64, h->dinv, h->z64, &h->sc->done, h->st, &l), "Jacobi");
-                CK(launch_fcg_dots(n, h->z64, h->r64, h->p64, h->q64, first, h->part_vec, h->sc, h->st, &l), "FCG dots");
-                CK(launch_fcg_dir(n, h->z64, h->p64, first, h->sc, h->st, &l), "FCG direction");
+        // `iters` FCG iterations with the current preconditioner, enqueued
+        auto enqueue = [&](int iters) -> int {
+            int ll = 0;
+            for (int it = 0; it < iters; ++it) {
+                if (use_net) CK(launch_mpnn_forward(net->md, n, h->r64, h->dinv, h->z64, false, h->st, &ll), "network");
+                else CK(launch_jacobi(n, h->r64, h->dinv, h->z64, &h->sc->done, h->st, &ll), "Jacobi");
+                CK(launch_fcg_dots(n, h->z64, h->r64, h->p64, h->q64, first, h->part_vec, h->sc, h->st, &ll), "FCG dots");
+                CK(launch_fcg_dir(n, h->z64, h->p64, first, h->sc, h->st, &ll), "FCG direction");
                 CK(launch_patch_pass(h->pd, 0, kApplyDot, h->A64, h->p64, nullptr, h->q64, h->halo64, h->part_patch,
-                                     &h->sc->done, h->sc, h->st, &l), "apply");
-                CK(launch_update(0, n, h->x64w, h->p64, h->r64, h->q64, h->dinv, h->part_vec, h->sc, h->st, &l), "update");
+                                     &h->sc->done, h->sc, h->st, &ll), "apply");
+                CK(launch_update(0, n, h->x64w, h->p64, h->r64, h->q64, h->dinv, h->part_vec, h->sc, h->st, &ll),
+                   "update");
                 first = 0;
             }
-            add_launches(h, l);
+            add_launches(h, ll);
+            return EBE_OK;
+        };
+        // With a network, a race first decides whether to use it: from x0,
+        // kRace iterations of Jacobi-FCG and then, again from x0, kRace
+        // iterations with the network, each timed with CUDA events on the
+        // stream; the preconditioner with the larger reduction of the
+        // residual norm per unit time continues (the network from its own
+        // iterate, Jacobi from its saved one).  A network that loses costs
+        // its kRace timed iterations and one restart.
+        bool pending = false;          // scalars already read: process them before launching
+        if (use_net && o.race_iters != 0) {
+            const int kRace = o.race_iters > 0 ? o.race_iters : 2 * o.chunk;
+            TRY(dalloc(h, &h->xsave0, n));
+            TRY(dalloc(h, &h->xsave1, n));
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            CK(cudaEventCreate(&ev[0]), "cudaEventCreate");
+            CK(cudaEventCreate(&ev[1]), "cudaEventCreate");
+            auto timed = [&](double& ms) -> int {
+                CK(cudaEventRecord(ev[0], h->st), "cudaEventRecord");
+                TRY(enqueue(kRace));
+                CK(cudaEventRecord(ev[1], h->st), "cudaEventRecord");
+                TRY(sync_scalars(h));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, ev[0], ev[1]), "cudaEventElapsedTime");
+                ms = double(t);
+                return EBE_OK;
+            };
+            int rs = EBE_OK;
+            double t_jac = 0.0, t_net = 0.0, rr_jac = rr, rr_net = rr;
+            CK(cudaMemcpyAsync(h->xsave0, h->x64w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "save x0");
+            use_net = false;
+            first = 1;
+            rs = timed(t_jac);
+            if (rs == EBE_OK && h->sc_host->reason != kRunning) {
+                pending = true;        // Jacobi alone already reached rtol |r0| (or stopped): no race
+                if (fell_back) *fell_back = 1;
+            } else if (rs == EBE_OK) {
+                rr_jac = h->sc_host->rr;
+                CK(cudaMemcpyAsync(h->xsave1, h->x64w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "save");
+                CK(cudaMemcpyAsync(h->x64w, h->xsave0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "x0");
+                double t = 0.0;
+                rs = true_residual(h, t);
+                info.true_residuals += 1;
+                use_net = true;
+                first = 1;
+                if (rs == EBE_OK) rs = timed(t_net);
+                if (rs == EBE_OK) rs = net_check_device(h, net);
+                if (rs == EBE_OK && h->sc_host->reason != kRunning) {
+                    pending = true;
+                } else if (rs == EBE_OK) {
+                    rr_net = h->sc_host->rr;
+                    const double rate_jac = std::log(rr / rr_jac) / t_jac, rate_net = std::log(rr / rr_net) / t_net;
+                    if (!(rate_net > rate_jac)) {
+                        // Jacobi continues from its own iterate
+                        CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st),
+                           "restore");
+                        rs = fallback();
+                    } else {
+                        best_rr = rr_net;
+                    }
+                }
+            }
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+            TRY(rs);
+        }
+        for (;;) {
+            if (!pending) TRY(enqueue(o.chunk));
+            pending = false;
             const int64_t before = info.iterations;
             TRY(sync_scalars(h));
             if (use_net) TRY(net_check_device(h, net));

@@ -921,12 +921,13 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
 template <int NB, bool WARPS>
 cudaError_t run_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
                         const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
-                        int* launches, bool pdl) {
+                        int* launches, bool pdl, cudaEvent_t* ev) {
     const size_t sm = cg_layout<NB, WARPS>(pd.max_nodes).total;
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     auto kern = k_cg_patch<NB, WARPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], st);
     if (pdl) {
         e = launch_pdl(kern, dim3(pd.n_patches), dim3(kPatchThreads), sm, st, pd, A, r, q, p_old, p_new, dinv, x, halo,
                        part, sc);
@@ -936,10 +937,12 @@ cudaError_t run_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, c
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
     if (fix_rows(pd) == 2)
         k_cg_fixup<2><<<fix_grid(pd.n_shared, 2), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
     else
         k_cg_fixup<1><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
+    if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
@@ -980,14 +983,14 @@ int fix_rows(const PlanDev& pd) {
 
 cudaError_t launch_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
                            const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
-                           int* launches, bool pdl) {
+                           int* launches, bool pdl, cudaEvent_t* ev) {
     if (pd.own_off == nullptr) return cudaErrorInvalidValue;
     const bool warps = pd.max_col > kWarpSchemeColours;
     if (pd.nb == 3)
-        return warps ? run_cg_pass<3, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl)
-                     : run_cg_pass<3, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl);
-    return warps ? run_cg_pass<4, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl)
-                 : run_cg_pass<4, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl);
+        return warps ? run_cg_pass<3, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl, ev)
+                     : run_cg_pass<3, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl, ev);
+    return warps ? run_cg_pass<4, true>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl, ev)
+                 : run_cg_pass<4, false>(pd, A, r, q, p_old, p_new, dinv, x, halo, part, sc, st, launches, pdl, ev);
 }
 
 cudaError_t launch_cg_arm(Scalars* sc, cudaStream_t st, int* launches) {

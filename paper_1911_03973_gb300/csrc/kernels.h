@@ -145,9 +145,10 @@ cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void
 //   breakdown).  sc->fresh: alpha = 0 and no iteration (first pass after a
 //   (re)start).  Dirichlet rows are those with dinv = 0.  part: 5 x
 //   (n_patches + fix_grid(n_shared)) doubles.
+// ev (nullable): three events around the two kernels, as launch_patch_pass.
 cudaError_t launch_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,
                            const float* dinv, double* x, float* halo, double* part, Scalars* sc, cudaStream_t st,
-                           int* launches, bool pdl = false);
+                           int* launches, bool pdl = false, cudaEvent_t* ev = nullptr);
 // alpha = 0, fresh = 1 (after a restart of the recurrence).
 cudaError_t launch_cg_arm(Scalars* sc, cudaStream_t st, int* launches);
 // dst[map[i]] = src[i] (to the solver numbering) or dst[i] = src[map[i]] (back), i < n.

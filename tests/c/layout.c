@@ -12,9 +12,10 @@ int main(void) {
            offsetof(ebe_mesh, n_n), offsetof(ebe_mesh, n_e), offsetof(ebe_mesh, coords), offsetof(ebe_mesh, elems));
     printf("ebe_create_opts %zu %zu %zu\n", sizeof(ebe_create_opts), offsetof(ebe_create_opts, device),
            offsetof(ebe_create_opts, patch_elems));
-    printf("ebe_solve_opts %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ebe_solve_opts), offsetof(ebe_solve_opts, rtol),
+    printf("ebe_solve_opts %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ebe_solve_opts), offsetof(ebe_solve_opts, rtol),
            offsetof(ebe_solve_opts, maxit), offsetof(ebe_solve_opts, precision), offsetof(ebe_solve_opts, chunk),
-           offsetof(ebe_solve_opts, delta), offsetof(ebe_solve_opts, stall_updates), offsetof(ebe_solve_opts, use_graph));
+           offsetof(ebe_solve_opts, delta), offsetof(ebe_solve_opts, stall_updates), offsetof(ebe_solve_opts, use_graph),
+           offsetof(ebe_solve_opts, race_iters));
     printf("ebe_solve_info %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ebe_solve_info), offsetof(ebe_solve_info, status),
            offsetof(ebe_solve_info, iterations), offsetof(ebe_solve_info, true_residuals),
            offsetof(ebe_solve_info, rel_residual), offsetof(ebe_solve_info, r0_norm), offsetof(ebe_solve_info, solve_ms));

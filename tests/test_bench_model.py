@@ -46,3 +46,19 @@ def test_fp64_pipe_model():
     assert t["ops_per_launch"] == 20 * 6 * 128 ** 3 + 2 * 129 ** 3
     assert bench.fp64_alu_model(3, n_n, n_e, 152, None) is None
     assert bench.fp64_alu_model(3, n_n, n_e, 0, 2070.0) is None
+
+
+def test_single_sync_iteration_bytes():
+    # one pass of the single-sync mixed solver on 2049^2 triangles: the
+    # operator's 9 x 4 B + 3 x 4 B per triangle, per node r, q, p, dinv (4 B) and
+    # x (8 B) in, r, p, q (4 B) and x (8 B) out
+    n_n, n_e = 2049 * 2049, 2 * 2048 * 2048
+    m = bench.bytes_model(2, n_n, n_e)
+    assert m["cg_mixed"] == n_e * (36 + 12) + n_n * 44 == 587_382_828
+    stored = bench.bytes_model(2, n_n, n_e, stored=True)
+    assert stored["cg_mixed"] == n_e * (24 + 12) + n_n * 44
+    # a step: element matrices, one pass per iteration and per start of the
+    # recurrence, a true residual and a restart per check
+    info = {"iterations": 100, "true_residuals": 3}
+    assert bench.step_bytes(m, info, True) == (m["assemble_mixed"] + 103 * m["cg_mixed"]
+                                               + 3 * (m["residual64"] + n_n * 16))

@@ -61,7 +61,7 @@ def test_binding_struct_layouts_match_the_c_compiler():
     fields = {
         "ebe_mesh": ["dim", "n_b", "n_n", "n_e", "coords", "elems"],
         "ebe_create_opts": ["device", "patch_elems"],
-        "ebe_solve_opts": ["rtol", "maxit", "precision", "chunk", "delta", "stall_updates", "use_graph"],
+        "ebe_solve_opts": ["rtol", "maxit", "precision", "chunk", "delta", "stall_updates", "use_graph", "race_iters"],
         "ebe_solve_info": ["status", "iterations", "true_residuals", "rel_residual", "r0_norm", "solve_ms"],
         "ebe_stats": ["kernel_launches", "device_error"],
         "ebe_batch_config": ["ctas_per_sm", "tile_nodes", "barrier_ns"],

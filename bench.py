@@ -813,9 +813,10 @@ def run_ours(args):
     paper_exp = run_paper_experiment(dev, stream) if rank == 0 else None
     cube = run_cube(args, dev, stream) if rank == 0 and not args.no_cube else None
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(prob, m, iters=40)
+        cpu_par = oracle_parallel_sample(prob, m, iters=100)
 
     if rank != 0:
         return None
@@ -862,6 +863,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_all_cores": cpu_par,
     }
     if nu0:
         line["nu0"] = nu0
@@ -939,6 +941,27 @@ def oracle_sample(prob, m, iters=10):
             "seconds": round(dt, 2),
             "sample": f"element matrices of all {orc.n_e} elements + {info['iterations']} FP64 Jacobi-PCG "
                       f"iterations ({info['residual_evals']} Algorithm-1 residuals), single thread"}
+
+
+def oracle_parallel_sample(prob, m, iters=100):
+    """The oracle's all-core timing build (OpenMP, colour-parallel element
+    loop; colouring done before the clock starts) on the same kind of sample
+    as oracle_sample: element arrays of the full mesh and `iters` FP64
+    Jacobi-PCG iterations.  None where the host compiler has no OpenMP."""
+    import oracle
+    try:
+        par = oracle.ParallelTiming(prob)
+    except oracle.OracleError as e:
+        return {"unavailable": str(e)}
+    t0 = time.perf_counter()
+    A, be = par.element_arrays()
+    _, info = par.pcg(A, be, rtol=1e-30, maxit=iters)
+    dt = time.perf_counter() - t0
+    nbytes = m["assemble_fp64"] + info["iterations"] * (m["apply64"] + m["vec64"]) + info["residual_evals"] * m["residual64"]
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": par.threads, "nproc": os.cpu_count(),
+            "kind": "oracle all-core timing build", "seconds": round(dt, 2), "colours": par.n_col,
+            "sample": f"element matrices of all {par.n_e} elements + {info['iterations']} FP64 Jacobi-PCG iterations, "
+                      f"OpenMP on {par.threads} threads, colour-parallel element loop"}
 
 
 def workload_config(args, n_n: int, n_e: int, dim: int, world: int) -> dict:

@@ -152,10 +152,9 @@ static void zero_rows(double *r, const int32_t *nd, int64_t n_d)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1 (residual computation, looped version), then r(nd) = 0:       */
-/*   for e = 1..n_e:  x_e = R_e x;  r_e = b_e - A_e x_e;                     */
-/*   r = sum_e C_e^T r_e.                                                    */
-/* Elements are visited in ascending order.                                  */
+/* The element-based residual of Sec. 2, Eq. residual,                       */
+/*   r = sum_e C_e^T (b_e - A_e R_e x),  then r(nd) = 0,                     */
+/* evaluated element by element in ascending element order.                 */
 /* ------------------------------------------------------------------------ */
 void orc_residual(int nb, int64_t n_n, int64_t n_e, const int32_t *elems, const double *A,
                   const double *be, const double *x, const int32_t *nd, int64_t n_d, double *r)
@@ -165,19 +164,19 @@ void orc_residual(int nb, int64_t n_n, int64_t n_e, const int32_t *elems, const 
         const int32_t *idx = elems + e * nb;
         const double *Ae = A + (int64_t)nb * nb * e;
         double xe[4], re[4];
-        for (int i = 0; i < nb; ++i) xe[i] = x[idx[i]];            /* restriction */
-        for (int i = 0; i < nb; ++i) {                              /* local residual */
+        for (int i = 0; i < nb; ++i) xe[i] = x[idx[i]];
+        for (int i = 0; i < nb; ++i) {
             double s = 0.0;
             for (int j = 0; j < nb; ++j) s += Ae[i + nb * j] * xe[j];
             re[i] = (be ? be[e * nb + i] : 0.0) - s;
         }
-        for (int i = 0; i < nb; ++i) r[idx[i]] += re[i];            /* assembly */
+        for (int i = 0; i < nb; ++i) r[idx[i]] += re[i];
     }
     zero_rows(r, nd, n_d);
 }
 
-/* Operator application y = mask(sum_e C_e^T A_e C_e x): Algorithm 1 with the */
-/* local loads left out and the sign of the local residual dropped.          */
+/* Operator application y = mask(sum_e C_e^T A_e C_e x): the residual's sum  */
+/* with the local loads left out and the sign of the local term dropped.     */
 void orc_apply(int nb, int64_t n_n, int64_t n_e, const int32_t *elems, const double *A,
                const double *x, const int32_t *nd, int64_t n_d, double *y)
 {

@@ -24,21 +24,17 @@ def training_problem(n: int, seed: int):
 
 
 def harvest(ebe, torch, h, n_n: int, n_samples: int, device, rtol_exact: float = 1e-12):
-    """(r, e) pairs along a Jacobi-PCG solve: x* to rtol_exact, then, from
-    x0 = 0, n_samples stretches of Jacobi-PCG (each continuing from the last
-    iterate with a fresh direction) that end at evenly spread iteration counts
-    up to 95 % of the solve; r_k = mask(b - A x_k), e_k = x* - x_k (device
-    float64 tensors).  The stretches together cost about one solve."""
+    """(r, e) pairs along a Jacobi-PCG solve: x* to rtol_exact, then the
+    iterates x_k after k = n_samples evenly spread iteration counts from x0 = 0;
+    r_k = mask(b - A x_k), e_k = x* - x_k (device float64 tensors)."""
     xs = torch.zeros(n_n, dtype=torch.float64, device=device)
     info = ebe.ebe_solve(h, xs, rtol=rtol_exact, precision=ebe.EBE_PREC_FP64)
     total = max(int(info["iterations"]), n_samples)
     ks = np.unique(np.linspace(1, max(1, int(0.95 * total)), n_samples).astype(int))
     out = []
-    xk = torch.zeros(n_n, dtype=torch.float64, device=device)
-    done = 0
     for k in ks:
-        ebe.ebe_solve(h, xk, rtol=1e-300, maxit=int(k - done), precision=ebe.EBE_PREC_FP64)
-        done = int(k)
+        xk = torch.zeros(n_n, dtype=torch.float64, device=device)
+        ebe.ebe_solve(h, xk, rtol=1e-300, maxit=int(k), precision=ebe.EBE_PREC_FP64)
         rk = torch.empty_like(xk)
         ebe.ebe_residual(h, xk, rk)
         out.append((rk, xs - xk))

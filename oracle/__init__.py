@@ -385,5 +385,6 @@ class ParallelTiming:
         rc = self.lib.orcp_pcg(self.nb, self.n_n, self.n_e, _p(self.elems, _I32P), _p(A, _F64P), _p(be, _F64P),
                                _p(self.nd, _I32P), self.nd.shape[0], _p(self.g, _F64P), _p(self.order, _I32P),
                                _p(self.col_ptr, _I64P), self.n_col, _p(x, _F64P), rtol, maxit, _p(info, _F64P))
-        return x, {"status": {0: "converged", 1: "maxit", 2: "breakdown"}.get(rc, f"error{rc}"),
-                   "iterations": int(info[0]), "rel_residual": float(info[1]), "residual_evals": int(info[2])}
+        status = "converged" if rc == 0 else "maxit" if rc == 1 else "breakdown" if rc == 2 else f"error{rc}"
+        return x, {"status": status, "iterations": int(info[0]), "rel_residual": float(info[1]),
+                   "residual_evals": int(info[2])}

@@ -949,8 +949,9 @@ def oracle_parallel_sample(prob, m, iters=100):
     as oracle_sample: element arrays of the full mesh and `iters` FP64
     Jacobi-PCG iterations.  None where the host compiler has no OpenMP."""
     import oracle
+    import oracle.parallel as oracle_parallel
     try:
-        par = oracle.ParallelTiming(prob)
+        par = oracle_parallel.ParallelTiming(prob)
     except oracle.OracleError as e:
         return {"unavailable": str(e)}
     t0 = time.perf_counter()

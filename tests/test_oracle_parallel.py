@@ -7,12 +7,13 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle.parallel as oracle_parallel
 from paper_1911_03973_gb300 import meshgen
 
 
 @pytest.fixture(scope="module")
 def par_lib():
-    if oracle.build_parallel() is None:
+    if oracle_parallel.build_parallel() is None:
         pytest.skip("gcc without OpenMP")
 
 
@@ -21,7 +22,7 @@ def test_parallel_oracle_matches_single_thread(par_lib, case, monkeypatch):
     prob = (meshgen.config_square_jitter(60, nu=1.0, seed=2) if case == "tri"
             else meshgen.config_cube_noise(9, nu=0.5, seed=3))
     ref = oracle.Problem(prob)
-    par = oracle.ParallelTiming(prob)
+    par = oracle_parallel.ParallelTiming(prob)
     assert par.threads >= 1 and par.n_col >= (7 if case == "tri" else 20)
     A, be = par.element_arrays()
     np.testing.assert_array_equal(A, ref._Ab.ravel())
@@ -39,7 +40,7 @@ def test_parallel_oracle_matches_single_thread(par_lib, case, monkeypatch):
 
 def test_colouring_is_valid(par_lib):
     prob = meshgen.config_square_jitter(30, nu=1.0, seed=2)
-    par = oracle.ParallelTiming(prob)
+    par = oracle_parallel.ParallelTiming(prob)
     el = prob["elems"]
     seen = np.zeros(par.n_e, bool)
     for c in range(par.n_col):

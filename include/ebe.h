@@ -478,9 +478,11 @@ ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev
  * iterations with the network, each timed with CUDA events; the one with the
  * larger reduction of the residual norm per unit time continues (so a network
  * that is slower than Jacobi costs about its race_iters timed iterations).  The
- * network-FCG then falls back to Jacobi from the current iterate on a
- * breakdown, when the residual norm does not halve within 16 chunks, or when
- * the true residual stalls (stall_updates checks); *fell_back (may be NULL)
+ * network-FCG then falls back to Jacobi from the current iterate when, over
+ * any window of 4 chunks (timed the same way), it reduces the residual norm
+ * more slowly per unit time than Jacobi did in the race, on a breakdown, when
+ * the residual norm does not halve within 16 chunks, or when the true
+ * residual stalls (stall_updates checks); *fell_back (may be NULL)
  * is 1 when the solution came from Jacobi.  opts:
  * rtol, maxit, chunk (iterations between host checks), stall_updates, race_iters.
  * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */

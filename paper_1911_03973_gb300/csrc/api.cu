@@ -1105,14 +1105,14 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
                                       &l, false), "single-sync pass");
                 add_launches(h, l);
             }
-            const int64_t before = info.iterations;
             TRY(sync_scalars(h));
             const Scalars sh = *h->sc_host;
-            par = int((par + (sh.passes - passes)) & 1);
+            const int64_t ran = sh.passes - passes;   // the first pass after a start counts no iteration
+            par = int((par + ran) & 1);
             passes = sh.passes;
             info.iterations = sh.iter;
             if (sh.reason == kRunning) {
-                if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
+                if (ran == 0) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
                 continue;
             }
             if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
@@ -2100,15 +2100,26 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
         // stream; the preconditioner with the larger reduction of the
         // residual norm per unit time continues (the network from its own
         // iterate, Jacobi from its saved one).  A network that loses costs
-        // its kRace timed iterations and one restart.
+        // its kRace timed iterations and one restart.  A network that wins
+        // must keep Jacobi's early rate over every window of kWindow chunks
+        // (CG's rate falls as it proceeds, so this errs towards Jacobi).
         bool pending = false;          // scalars already read: process them before launching
+        // Jacobi's rate in the race (log of the residual-norm reduction per ms);
+        // the network keeps it up, measured over windows of kWindow chunks, or
+        // the solve falls back to Jacobi
+        double rate_jac = 0.0;
+        constexpr int kWindow = 4;
+        struct Events {
+            cudaEvent_t e[2] = {nullptr, nullptr};
+            ~Events() { for (auto& v : e) if (v) cudaEventDestroy(v); }
+        } evs;
+        CK(cudaEventCreate(&evs.e[0]), "cudaEventCreate");
+        CK(cudaEventCreate(&evs.e[1]), "cudaEventCreate");
         if (use_net && o.race_iters != 0) {
             const int kRace = o.race_iters > 0 ? o.race_iters : 2 * o.chunk;
             TRY(dalloc(h, &h->xsave0, n));
             TRY(dalloc(h, &h->xsave1, n));
-            cudaEvent_t ev[2] = {nullptr, nullptr};
-            CK(cudaEventCreate(&ev[0]), "cudaEventCreate");
-            CK(cudaEventCreate(&ev[1]), "cudaEventCreate");
+            cudaEvent_t* ev = evs.e;
             auto timed = [&](double& ms) -> int {
                 CK(cudaEventRecord(ev[0], h->st), "cudaEventRecord");
                 TRY(enqueue(kRace));
@@ -2143,7 +2154,8 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
                     pending = true;
                 } else if (rs == EBE_OK) {
                     rr_net = h->sc_host->rr;
-                    const double rate_jac = std::log(rr / rr_jac) / t_jac, rate_net = std::log(rr / rr_net) / t_net;
+                    rate_jac = std::log(rr / rr_jac) / t_jac;
+                    const double rate_net = std::log(rr / rr_net) / t_net;
                     if (!(rate_net > rate_jac)) {
                         // Jacobi continues from its own iterate
                         CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st),
@@ -2154,12 +2166,15 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
                     }
                 }
             }
-            cudaEventDestroy(ev[0]);
-            cudaEventDestroy(ev[1]);
             TRY(rs);
         }
+        double win_ms = 0.0, win_rr = h->sc_host->rr;
+        int win_chunks = 0;
         for (;;) {
+            const bool watch = use_net && rate_jac > 0.0 && !pending;
+            if (watch) CK(cudaEventRecord(evs.e[0], h->st), "cudaEventRecord");
             if (!pending) TRY(enqueue(o.chunk));
+            if (watch) CK(cudaEventRecord(evs.e[1], h->st), "cudaEventRecord");
             pending = false;
             const int64_t before = info.iterations;
             TRY(sync_scalars(h));
@@ -2168,6 +2183,18 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             info.iterations = sh.iter;
             if (sh.reason == kRunning) {
                 if (sh.iter == before) return fail(h, EBE_CUDA_ERROR, "solver chunk made no progress");
+                if (watch) {
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, evs.e[0], evs.e[1]), "cudaEventElapsedTime");
+                    win_ms += double(t);
+                    if (++win_chunks == kWindow) {
+                        const double rate = std::log(win_rr / sh.rr) / win_ms;
+                        win_ms = 0.0;
+                        win_chunks = 0;
+                        win_rr = sh.rr;
+                        if (!(rate >= rate_jac)) { TRY(fallback()); continue; }
+                    }
+                }
                 if (use_net) {
                     // the learned step must keep reducing the residual: at least
                     // a halving every 16 chunks (Jacobi-CG halves it about every

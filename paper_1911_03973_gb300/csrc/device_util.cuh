@@ -59,4 +59,53 @@ struct CompSum {
     __device__ __forceinline__ double value() const { return double(s) + double(c); }
 };
 
+// Knuth's TwoSum: returns fl(a + b) and sets e to its rounding error, so that
+// the result plus e equals a + b exactly (FP32 arithmetic only).  The error of
+// a rounded sum is unique, so swapping a and b gives the same pair.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+    const float t = a + b;
+    const float bp = t - a;
+    e = (a - (t - bp)) + (b - bp);
+    return t;
+}
+
+// Sum of a compensated FP32 value over a warp in a fixed butterfly order,
+// all in FP32 (GB300 runs FP64 at 1/64 of the FP32 rate): each level adds the
+// two partners' leading parts with TwoSum and carries the rounding error and
+// the partners' error terms in c.  Every lane ends with the same total.
+__device__ __forceinline__ void warp_sum(CompSum& v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, v.s, o), c2 = __shfl_xor_sync(0xffffffffu, v.c, o);
+        float e;
+        v.s = two_sum(v.s, s2, e);
+        v.c = (v.c + c2) + e;
+    }
+}
+
+// K compensated FP32 sums over a block of NT threads: warp butterflies in
+// FP32, then thread 0 adds the per-warp totals (converted to FP64 once per
+// warp) in warp order.  Every thread must call it; the results are valid in
+// thread 0.  red: K * NT / 32 doubles of shared memory.
+template <int K, int NT>
+__device__ __forceinline__ void block_sums_comp(CompSum (&v)[K], double (&out)[K], double* red) {
+    constexpr int NW = NT / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * NW + w] = v[k].value();
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int i = 0; i < NW; ++i) t += red[k * NW + i];
+        out[k] = t;
+    }
+}
+
 }  // namespace ebe

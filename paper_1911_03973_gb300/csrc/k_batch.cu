@@ -58,6 +58,19 @@ struct DotAcc<float> {
     __device__ __forceinline__ double value() const { return c.value(); }
 };
 
+// Block total, valid in thread 0: FP64 butterflies for FP64 data; for FP32
+// data compensated FP32 butterflies and one FP64 conversion per warp (the FP64
+// pipe runs at 1/64 of the FP32 rate on GB300).
+__device__ __forceinline__ double block_total(const DotAcc<double>& d, double* red) {
+    return block_sum<NT>(d.value(), red);
+}
+__device__ __forceinline__ double block_total(const DotAcc<float>& d, double* red) {
+    CompSum v[1] = {d.c};
+    double out[1];
+    block_sums_comp<1, NT>(v, out, red);
+    return out[0];
+}
+
 // Data written during the launch by other CTAs is read through L2 only.
 template <typename V>
 __device__ __forceinline__ V ld_l2(const V* p) { return __ldcg(p); }
@@ -248,7 +261,7 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p, bool have, int next_p
             halo[m.halo_off + (l - m.n_owned)] = v;
         }
     }
-    const double dsum = block_sum<NT>(dot.value(), red);
+    const double dsum = block_total(dot, red);
     if (tid == 0) bd.part_p[p] = dsum;
     return true;
 }
@@ -376,10 +389,10 @@ __device__ __forceinline__ void fix_item(Ctx& c, int ci, int md) {
                 }
             }
         }
-        dsum = md == kBNormal ? dot.value() : dot64;
+        dsum = md == kBNormal ? block_total(dot, red) : block_sum<NT>(dot64, red);
     }
-    for (int i = it.plo + tid; i < it.phi; i += NT) dsum += ld_l2(bd.part_p + i);
-    dsum = block_sum<NT>(dsum, red);
+    if (tid == 0)
+        for (int i = it.plo; i < it.phi; ++i) dsum += ld_l2(bd.part_p + i);
     // last item of the problem to finish: the acquire-release arrival makes
     // every earlier item's partial visible to it
     if (tid == 0) {
@@ -497,7 +510,8 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
     double* x = bd.x;
     double* r = bd.r;
     T* ri_v = static_cast<T*>(bd.rin);   // recurrence residual (FP32 when mixed)
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0;       // per-thread sums of the FP64 solver
+    CompSum ca, cb;                // per-thread sums of the mixed solver (compensated FP32)
     const BatchProblem* P = bd.prob + it.k;
     if (md == kBNormal) {
         const double al = ld_l2(&P->alpha);
@@ -534,8 +548,8 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
                     rz.add(rf * (__ldg(dinv + i) * rf));
                     rr.add(rf * rf);
                 }
-                a = rz.value();
-                b = rr.value();
+                ca = rz;
+                cb = rr;
             } else {
                 int i = it.lo + tid;
                 for (; i + 3 * NT < it.hi; i += 4 * NT) {
@@ -576,8 +590,8 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
                 rz.add(rf * (__ldg(dinv + i) * rf));
                 rr.add(rf * rf);
             }
-            a = rz.value();
-            b = rr.value();
+            ca = rz;
+            cb = rr;
         } else {
             for (int i = it.lo + tid; i < it.hi; i += NT) {
                 const double ri = ld_l2(r + i);
@@ -586,7 +600,15 @@ __device__ __forceinline__ void update_item(Ctx& c, int ti, int md) {
             }
         }
     }
-    block_sum2<NT>(a, b, red);
+    if constexpr (MIXED) {
+        CompSum v[2] = {ca, cb};
+        double t[2];
+        block_sums_comp<2, NT>(v, t, red);
+        a = t[0];
+        b = t[1];
+    } else {
+        block_sum2<NT>(a, b, red);
+    }
     if (tid == 0) {
         bd.part_u[2 * ti] = a;
         bd.part_u[2 * ti + 1] = b;

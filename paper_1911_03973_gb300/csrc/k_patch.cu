@@ -43,6 +43,22 @@ struct DotAcc<float> {
     __device__ __forceinline__ double value() const { return c.value(); }
 };
 
+// Block total of a pass's dot product, valid in thread 0: FP64 butterflies
+// for FP64 data; for FP32 data compensated FP32 butterflies and one FP64
+// conversion per warp (per-thread FP64 work would load the FP64 pipe, which
+// GB300 runs at 1/64 of the FP32 rate, with millions of operations a pass).
+template <int NT>
+__device__ __forceinline__ double block_total(const DotAcc<double>& d, double* red) {
+    return tma::block_sum<NT>(d.value(), red);
+}
+template <int NT>
+__device__ __forceinline__ double block_total(const DotAcc<float>& d, double* red) {
+    CompSum v[1] = {d.c};
+    double out[1];
+    block_sums_comp<1, NT>(v, out, red);
+    return out[0];
+}
+
 using tma::block_sum;
 using tma::bulk_load;
 using tma::mbar_expect_tx;
@@ -299,7 +315,7 @@ k_patch(const PlanDev pd, const T* __restrict__ A, const T* __restrict__ x, cons
         }
     }
     if (MODE == kResidualNorm || MODE == kApplyDot) {
-        const double dsum = block_sum<NT>(dot.value(), red);
+        const double dsum = block_total<NT>(dot, red);
         if (tid == 0) part[p] = dsum;
     }
 }
@@ -357,14 +373,14 @@ k_fixup(const PlanDev pd, const T* __restrict__ x, const T* __restrict__ b, T* _
         }
     }
     if (MODE == kResidualNorm || MODE == kApplyDot) {
-        double dsum = dot.value();
         // this block also adds a contiguous chunk of the patch partials (one per
         // patch, written by the patch pass), so the last block has few to add
         const int np = pd.n_patches;
         const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
         const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
-        for (int i = int(blockIdx.x) * chunk + threadIdx.x; i < p1; i += kFixThreads) dsum += part[i];
-        dsum = block_sum<kFixThreads>(dsum, red);
+        double dsum = block_total<kFixThreads>(dot, red);
+        if (threadIdx.x == 0)
+            for (int i = int(blockIdx.x) * chunk; i < p1; ++i) dsum += part[i];
         if (threadIdx.x == 0) {
             part[np + blockIdx.x] = dsum;
             __threadfence();
@@ -719,7 +735,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
         return;
     }
     const double al = sc->alpha;
-    const float alf = d2f(al), bef = float(sc->beta);
+    const float alf = d2f(al), bef = d2f(sc->beta);
     const int own0 = __ldg(pd.own_off + p);
     const int32_t* pn = pd.pnode + m.node_off;
     // node step at every patch node (owned: contiguous run, written back;
@@ -788,8 +804,9 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             halo[m.halo_off + (l - m.n_owned)] = v;
         }
     }
-    double v[kCgSums] = {srz.value(), srr.value(), spq.value(), sqz.value(), sqdq.value()};
-    block_sums5(v, red);
+    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq};
+    double v[kCgSums];
+    block_sums_comp<kCgSums, NT>(cs, v, red);
     if (tid == 0) {
         const int64_t stride = int64_t(pd.n_patches) + kFixGridMax;
 #pragma unroll
@@ -811,7 +828,7 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
     pdl_wait();
     if (sc->done) return;
     const double al = sc->alpha;
-    const float alf = d2f(al), bef = float(sc->beta);
+    const float alf = d2f(al), bef = d2f(sc->beta);
     CompSum s5[kCgSums];
     const int st = int(gridDim.x) * kFixThreads;
     for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += ROWS * st) {
@@ -859,17 +876,16 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
         }
     }
     double v[kCgSums];
-#pragma unroll
-    for (int j = 0; j < kCgSums; ++j) v[j] = s5[j].value();
+    block_sums_comp<kCgSums, kFixThreads>(s5, v, red);
     // this block also adds a contiguous chunk of the per-patch partials
     const int np = pd.n_patches;
     const int64_t stride = int64_t(np) + kFixGridMax;
     const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
     const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
-    for (int i = int(blockIdx.x) * chunk + threadIdx.x; i < p1; i += kFixThreads)
+    if (threadIdx.x == 0)
+        for (int i = int(blockIdx.x) * chunk; i < p1; ++i)
 #pragma unroll
-        for (int j = 0; j < kCgSums; ++j) v[j] += part[j * stride + i];
-    block_sums5(v, red);
+            for (int j = 0; j < kCgSums; ++j) v[j] += part[j * stride + i];
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int j = 0; j < kCgSums; ++j) part[j * stride + np + blockIdx.x] = v[j];

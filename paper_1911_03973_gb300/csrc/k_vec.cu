@@ -48,11 +48,11 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
     }
 }
 
-// Publish (a, b) for this block; returns true in every thread of the last
-// block, which then holds the grid totals in (a, b) (thread 0).
-__device__ __forceinline__ bool grid_sum2(double& a, double& b, double* part, uint32_t* ctr, double* red) {
+// Publish the block totals (a, b) (valid in thread 0); returns true in every
+// thread of the last block, which then holds the grid totals in (a, b)
+// (thread 0).
+__device__ __forceinline__ bool grid_publish2(double& a, double& b, double* part, uint32_t* ctr, double* red) {
     __shared__ bool last;
-    block_sum2(a, b, red);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = a;
         part[2 * blockIdx.x + 1] = b;
@@ -71,6 +71,24 @@ __device__ __forceinline__ bool grid_sum2(double& a, double& b, double* part, ui
     block_sum2(a, b, red);
     if (threadIdx.x == 0) *ctr = 0;
     return true;
+}
+
+// Block sums of per-thread (a, b), then grid_publish2.
+__device__ __forceinline__ bool grid_sum2(double& a, double& b, double* part, uint32_t* ctr, double* red) {
+    block_sum2(a, b, red);
+    return grid_publish2(a, b, part, ctr, red);
+}
+
+// The same for compensated FP32 per-thread sums: block totals by FP32
+// butterflies (one FP64 conversion per warp), then grid_publish2.
+__device__ __forceinline__ bool grid_sum2(CompSum a, CompSum b, double& ta, double& tb, double* part, uint32_t* ctr,
+                                          double* red) {
+    CompSum v[2] = {a, b};
+    double t[2];
+    block_sums_comp<2, NT>(v, t, red);
+    ta = t[0];
+    tb = t[1];
+    return grid_publish2(ta, tb, part, ctr, red);
 }
 
 // Stop tests and beta of one CG iteration (last block, thread 0).
@@ -228,8 +246,8 @@ k_update_mixed(int64_t n, double* __restrict__ x, const float* __restrict__ p, f
         rz.add(rf * (dinv[i] * rf));
         rr.add(rf * rf);
     }
-    double a = rz.value(), b = rr.value();
-    if (grid_sum2(a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) decide(sc, a, b);
+    double a = 0.0, b = 0.0;
+    if (grid_sum2(rz, rr, a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) decide(sc, a, b);
 }
 
 // p = dinv r + beta p  (init: p = dinv r), FP32.
@@ -239,7 +257,7 @@ k_direction_mixed(int64_t n, float* __restrict__ p, const float* __restrict__ r,
     pdl_trigger();
     pdl_wait();
     if (sc->done) return;
-    const float be = init ? 0.0f : float(sc->beta);
+    const float be = init ? 0.0f : d2f(sc->beta);
     const int64_t st = int64_t(gridDim.x) * NT, n4 = n >> 2;
     for (int64_t g = int64_t(blockIdx.x) * NT + threadIdx.x; g < n4; g += 2 * st) {
         const bool two = g + st < n4;
@@ -278,7 +296,8 @@ __global__ void __launch_bounds__(NT)
 k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv_v, int init,
           double* __restrict__ part, Scalars* __restrict__ sc, float* __restrict__ r32) {
     __shared__ double red[64];
-    double a, b;
+    double a = 0.0, b = 0.0;
+    bool last;
     if (MIXED) {
         const float* dinv = static_cast<const float*>(dinv_v);
         CompSum rz, rr;
@@ -288,8 +307,7 @@ k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv
             rz.add(rf * (dinv[i] * rf));
             rr.add(rf * rf);
         }
-        a = rz.value();
-        b = rr.value();
+        last = grid_sum2(rz, rr, a, b, part, &sc->ctr_vec, red);
     } else {
         const double* dinv = static_cast<const double*>(dinv_v);
         a = 0.0;
@@ -299,8 +317,9 @@ k_restart(int64_t n, const double* __restrict__ r, const void* __restrict__ dinv
             a = fmadd(ri, dinv[i] * ri, a);
             b = fmadd(ri, ri, b);
         }
+        last = grid_sum2(a, b, part, &sc->ctr_vec, red);
     }
-    if (grid_sum2(a, b, part, &sc->ctr_vec, red) && threadIdx.x == 0) {
+    if (last && threadIdx.x == 0) {
         sc->rz = a;
         sc->rr = b;
         if (init || !(sc->rho != 0.0)) sc->beta = 0.0;

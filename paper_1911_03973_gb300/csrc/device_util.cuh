@@ -13,9 +13,9 @@ __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fma
 // FP64 at 1/64 of the FP32 rate).  f2d is exact (normal numbers: rebias the
 // exponent by 1023 - 127 = 896 and shift the mantissa up by 29 bits); d2f
 // rounds to nearest, ties to even (round bit 28, sticky bits 0..27; a carry
-// out of the mantissa correctly bumps the exponent).  Zeros, subnormals,
-// infinities, NaNs and results outside the normal FP32 range take the
-// hardware conversion.
+// out of the mantissa correctly bumps the exponent).  Signed zeros map to
+// signed zeros; subnormals, infinities, NaNs and results outside the normal
+// FP32 range take the hardware conversion.
 // The rare cases call out of line: an inlined fallback would be if-converted
 // and the hardware conversion executed for every element.
 static __device__ __noinline__ double f2d_rare(float f) { return double(f); }
@@ -24,12 +24,14 @@ static __device__ __noinline__ float d2f_rare(double v) { return float(v); }
 __device__ __forceinline__ double f2d(float f) {
     const uint32_t u = __float_as_uint(f);
     const uint32_t e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double(static_cast<long long>(uint64_t(u) << 32));
     if (e == 0u || e == 0xffu) return f2d_rare(f);
     const uint64_t d = (uint64_t(u & 0x80000000u) << 32) | (uint64_t(e + 896u) << 52) | (uint64_t(u & 0x7fffffu) << 29);
     return __longlong_as_double(static_cast<long long>(d));
 }
 __device__ __forceinline__ float d2f(double v) {
     const uint64_t u = static_cast<uint64_t>(__double_as_longlong(v));
+    if ((u & 0x7fffffffffffffffull) == 0ull) return __uint_as_float(uint32_t(u >> 32));
     const int e = int((u >> 52) & 0x7ffu) - 896;
     if (e <= 0 || e >= 254) return d2f_rare(v);
     uint32_t bits = (uint32_t(e) << 23) | uint32_t((u >> 29) & 0x7fffffu);
@@ -80,6 +82,45 @@ __device__ __forceinline__ void warp_sum(CompSum& v) {
         float e;
         v.s = two_sum(v.s, s2, e);
         v.c = (v.c + c2) + e;
+    }
+}
+
+// a += b for compensated FP32 values (TwoSum of the leading parts, errors
+// carried in c); the same result in either order of a and b.
+__device__ __forceinline__ void merge(CompSum& a, const CompSum& b) {
+    float e;
+    a.s = two_sum(a.s, b.s, e);
+    a.c = (a.c + b.c) + e;
+}
+
+// K compensated FP32 sums over a block of NT threads, entirely in FP32:
+// warp butterflies, then thread 0 merges the per-warp totals in warp order.
+// Every thread must call it; out is valid in thread 0.  red: K * NT / 32
+// float2 of shared memory.
+template <int K, int NT>
+__device__ __forceinline__ void block_sums_f32(CompSum (&v)[K], CompSum (&out)[K], float2* red) {
+    constexpr int NW = NT / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * NW + w] = make_float2(v[k].s, v[k].c);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        CompSum t;
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                const float2 r = red[k * NW + i];
+                CompSum x;
+                x.s = r.x;
+                x.c = r.y;
+                merge(t, x);
+            }
+        out[k] = t;
     }
 }
 

@@ -804,13 +804,15 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             halo[m.halo_off + (l - m.n_owned)] = v;
         }
     }
-    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq};
-    double v[kCgSums];
-    block_sums_comp<kCgSums, NT>(cs, v, red);
+    // the sums stay compensated FP32 pairs up to the last fix-up block: every
+    // FP64 instruction of a CTA costs 16 cycles of its SM's FP64 pipe
+    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq}, tot[kCgSums];
+    block_sums_f32<kCgSums, NT>(cs, tot, reinterpret_cast<float2*>(red));
     if (tid == 0) {
+        float2* part2 = reinterpret_cast<float2*>(part);
         const int64_t stride = int64_t(pd.n_patches) + kFixGridMax;
 #pragma unroll
-        for (int k = 0; k < kCgSums; ++k) part[k * stride + p] = v[k];
+        for (int k = 0; k < kCgSums; ++k) part2[k * stride + p] = make_float2(tot[k].s, tot[k].c);
     }
 }
 
@@ -875,31 +877,43 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
             s5[4].add(qn * (dv[u] * qn));
         }
     }
-    double v[kCgSums];
-    block_sums_comp<kCgSums, kFixThreads>(s5, v, red);
-    // this block also adds a contiguous chunk of the per-patch partials
+    // compensated FP32 pairs (no FP64 work per block): the block's rows, then
+    // a contiguous chunk of the per-patch partials, merged by thread 0 in order
+    CompSum tot[kCgSums];
+    block_sums_f32<kCgSums, kFixThreads>(s5, tot, reinterpret_cast<float2*>(red));
+    float2* part2 = reinterpret_cast<float2*>(part);
     const int np = pd.n_patches;
     const int64_t stride = int64_t(np) + kFixGridMax;
     const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
     const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int i = int(blockIdx.x) * chunk; i < p1; ++i)
 #pragma unroll
-            for (int j = 0; j < kCgSums; ++j) v[j] += part[j * stride + i];
-    if (threadIdx.x == 0) {
+            for (int j = 0; j < kCgSums; ++j) {
+                const float2 r = part2[j * stride + i];
+                CompSum x;
+                x.s = r.x;
+                x.c = r.y;
+                merge(tot[j], x);
+            }
 #pragma unroll
-        for (int j = 0; j < kCgSums; ++j) part[j * stride + np + blockIdx.x] = v[j];
+        for (int j = 0; j < kCgSums; ++j) part2[j * stride + np + blockIdx.x] = make_float2(tot[j].s, tot[j].c);
         __threadfence();
         last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // the last block: every block's pair in FP64, added in a fixed order
+    double v[kCgSums];
 #pragma unroll
     for (int j = 0; j < kCgSums; ++j) v[j] = 0.0;
     for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads)
 #pragma unroll
-        for (int j = 0; j < kCgSums; ++j) v[j] += __ldcg(part + j * stride + np + i);
+        for (int j = 0; j < kCgSums; ++j) {
+            const float2 r = __ldcg(part2 + j * stride + np + i);
+            v[j] += double(r.x) + double(r.y);
+        }
     block_sums5(v, red);
     if (threadIdx.x != 0) return;
     sc->ctr_fix = 0;

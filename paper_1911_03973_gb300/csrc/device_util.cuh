@@ -85,12 +85,31 @@ __device__ __forceinline__ void warp_sum(CompSum& v) {
     }
 }
 
+__device__ __forceinline__ CompSum comp_of(float2 v) {
+    CompSum c;
+    c.s = v.x;
+    c.c = v.y;
+    return c;
+}
+
 // a += b for compensated FP32 values (TwoSum of the leading parts, errors
 // carried in c); the same result in either order of a and b.
 __device__ __forceinline__ void merge(CompSum& a, const CompSum& b) {
     float e;
     a.s = two_sum(a.s, b.s, e);
     a.c = (a.c + b.c) + e;
+}
+
+// Sum over each group of 8 consecutive lanes (butterfly offsets 4, 2, 1),
+// compensated FP32; every lane of a group ends with its group's total.
+__device__ __forceinline__ void group8_sum(CompSum& v) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, v.s, o), c2 = __shfl_xor_sync(0xffffffffu, v.c, o);
+        float e;
+        v.s = two_sum(v.s, s2, e);
+        v.c = (v.c + c2) + e;
+    }
 }
 
 // K compensated FP32 sums over a block of NT threads, entirely in FP32:

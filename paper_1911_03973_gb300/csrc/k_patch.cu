@@ -804,15 +804,28 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             halo[m.halo_off + (l - m.n_owned)] = v;
         }
     }
-    // the sums stay compensated FP32 pairs up to the last fix-up block: every
-    // FP64 instruction of a CTA costs 16 cycles of its SM's FP64 pipe
-    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq}, tot[kCgSums];
-    block_sums_f32<kCgSums, NT>(cs, tot, reinterpret_cast<float2*>(red));
-    if (tid == 0) {
+    // The sums stay compensated FP32 pairs up to the last fix-up block (every
+    // FP64 instruction of a CTA costs 16 cycles of its SM's FP64 pipe): warp
+    // butterflies, then warp 0 adds the 8 warp totals of sums 0-3 at once
+    // (lane 8k + w holds warp w's total of sum k) and of sum 4.
+    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq};
+#pragma unroll
+    for (int k = 0; k < kCgSums; ++k) warp_sum(cs[k]);
+    float2* red2 = reinterpret_cast<float2*>(red);
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) red2[k * 8 + warp] = make_float2(cs[k].s, cs[k].c);
+    __syncthreads();
+    if (warp == 0) {
         float2* part2 = reinterpret_cast<float2*>(part);
         const int64_t stride = int64_t(pd.n_patches) + kFixGridMax;
-#pragma unroll
-        for (int k = 0; k < kCgSums; ++k) part2[k * stride + p] = make_float2(tot[k].s, tot[k].c);
+        CompSum a = comp_of(red2[lane]);                         // sums 0-3
+        group8_sum(a);
+        if ((lane & 7) == 0) part2[(lane >> 3) * stride + p] = make_float2(a.s, a.c);
+        CompSum b = lane < 8 ? comp_of(red2[32 + lane]) : CompSum{};   // sum 4
+        group8_sum(b);
+        if (lane == 0) part2[4 * stride + p] = make_float2(b.s, b.c);
     }
 }
 
@@ -877,29 +890,38 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
             s5[4].add(qn * (dv[u] * qn));
         }
     }
-    // compensated FP32 pairs (no FP64 work per block): the block's rows, then
-    // a contiguous chunk of the per-patch partials, merged by thread 0 in order
-    CompSum tot[kCgSums];
-    block_sums_f32<kCgSums, kFixThreads>(s5, tot, reinterpret_cast<float2*>(red));
+    // Compensated FP32 pairs (no FP64 work per block): warp butterflies over
+    // the block's rows; then warp 0 adds, per sum, the 8 warp totals (lanes
+    // 0-7) and a contiguous chunk of the per-patch partials (lane l takes
+    // partials l, l + 32, ... of the chunk, after its warp total) with one more
+    // butterfly: a fixed order, and short chains.
+    float2* red2 = reinterpret_cast<float2*>(red);
     float2* part2 = reinterpret_cast<float2*>(part);
     const int np = pd.n_patches;
     const int64_t stride = int64_t(np) + kFixGridMax;
     const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
-    const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
-    if (threadIdx.x == 0) {
-        for (int i = int(blockIdx.x) * chunk; i < p1; ++i)
+    const int p0 = min(np, int(blockIdx.x) * chunk), p1 = min(np, (int(blockIdx.x) + 1) * chunk);
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < kCgSums; ++j) warp_sum(s5[j]);
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < kCgSums; ++j) red2[j * 8 + warp] = make_float2(s5[j].s, s5[j].c);
+        __syncthreads();
+        if (warp == 0) {
 #pragma unroll
             for (int j = 0; j < kCgSums; ++j) {
-                const float2 r = part2[j * stride + i];
-                CompSum x;
-                x.s = r.x;
-                x.c = r.y;
-                merge(tot[j], x);
+                CompSum a = lane < kFixThreads / 32 ? comp_of(red2[j * 8 + lane]) : CompSum{};
+                for (int i = p0 + lane; i < p1; i += 32) merge(a, comp_of(part2[j * stride + i]));
+                warp_sum(a);
+                if (lane == 0) part2[j * stride + np + blockIdx.x] = make_float2(a.s, a.c);
             }
-#pragma unroll
-        for (int j = 0; j < kCgSums; ++j) part2[j * stride + np + blockIdx.x] = make_float2(tot[j].s, tot[j].c);
-        __threadfence();
-        last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
+            if (lane == 0) {
+                __threadfence();
+                last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
+            }
+        }
     }
     __syncthreads();
     if (!last) return;

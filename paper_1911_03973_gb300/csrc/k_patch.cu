@@ -692,7 +692,7 @@ __device__ __forceinline__ CgNode cg_node(float r, float q, float p, float d, fl
 }
 
 template <int NB, bool WARPS>
-__global__ void __launch_bounds__(kPatchThreads)
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 5 : 3)
 k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r, float* __restrict__ q,
            const float* __restrict__ p_old, float* __restrict__ p_new, const float* __restrict__ dinv,
            double* __restrict__ x, float* __restrict__ halo, double* __restrict__ part, const Scalars* __restrict__ sc) {
@@ -738,45 +738,54 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     const float alf = d2f(al), bef = d2f(sc->beta);
     const int own0 = __ldg(pd.own_off + p);
     const int32_t* pn = pd.pnode + m.node_off;
-    // node step at every patch node (owned: contiguous run, written back;
-    // shared: through the node table, written by the fix-up)
+    // Node step at every patch node.  Owned nodes come in groups of four
+    // consecutive solver numbers (a patch's run starts on a multiple of 4 and
+    // is padded to one; padding entries are zero in every vector and stay
+    // zero): 16-byte loads and stores, written back here.  Shared nodes come
+    // one by one through the node table; the fix-up writes them.
+    const int n_own4 = (m.n_owned + 3) >> 2;
+    const int n_items = n_own4 + (m.n_nodes - m.n_owned);
     CompSum srz, srr;
-    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
-        int id[2];
+    for (int g = tid; g < n_items; g += NT) {
+        if (g < n_own4) {
+            const int l0 = 4 * g, id0 = own0 + l0;
+            const float4 rv = *reinterpret_cast<const float4*>(r + id0);
+            const float4 qv = *reinterpret_cast<const float4*>(q + id0);
+            const float4 pv = __ldg(reinterpret_cast<const float4*>(p_old + id0));
+            const float4 dv = __ldg(reinterpret_cast<const float4*>(dinv + id0));
+            const double2 xa = *reinterpret_cast<const double2*>(x + id0);
+            const double2 xb = *reinterpret_cast<const double2*>(x + id0 + 2);
+            const float rr4[4] = {rv.x, rv.y, rv.z, rv.w}, qq4[4] = {qv.x, qv.y, qv.z, qv.w};
+            const float pp4[4] = {pv.x, pv.y, pv.z, pv.w}, dd4[4] = {dv.x, dv.y, dv.z, dv.w};
+            const double xx4[4] = {xa.x, xa.y, xb.x, xb.y};
+            float rn4[4], pn4[4];
+            double xn4[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int l = l0 + u * NT + tid;
-            id[u] = l < m.n_owned ? own0 + l : (l < m.n_nodes ? (__ldg(pn + l) & kNodeMask) : -1);
-        }
-        float rv[2], qv[2], pv[2], dv[2];
-        double xv[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int l = l0 + u * NT + tid;
-            if (id[u] >= 0) {
-                rv[u] = r[id[u]];
-                qv[u] = q[id[u]];
-                pv[u] = __ldg(p_old + id[u]);
-                dv[u] = __ldg(dinv + id[u]);
-                xv[u] = l < m.n_owned ? x[id[u]] : 0.0;
+            for (int u = 0; u < 4; ++u) {
+                const CgNode c = cg_node(rr4[u], qq4[u], pp4[u], dd4[u], alf, bef);
+                rn4[u] = c.rn;
+                pn4[u] = c.pn;
+                xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
+                const int l = l0 + u;
+                if (l < m.n_owned) {
+                    xs[l] = c.pn;
+                    zs[l] = c.z;
+                    ds[l] = dd4[u];
+                    if (!WARPS) acc[l] = 0.0f;
+                    srz.add(c.rn * c.z);
+                    srr.add(c.rn * c.rn);
+                }
             }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int l = l0 + u * NT + tid;
-            if (id[u] < 0) continue;
-            const CgNode c = cg_node(rv[u], qv[u], pv[u], dv[u], alf, bef);
+            *reinterpret_cast<float4*>(r + id0) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
+            *reinterpret_cast<float4*>(p_new + id0) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+            *reinterpret_cast<double2*>(x + id0) = make_double2(xn4[0], xn4[1]);
+            *reinterpret_cast<double2*>(x + id0 + 2) = make_double2(xn4[2], xn4[3]);
+        } else {
+            const int l = m.n_owned + (g - n_own4);
+            const int id = __ldg(pn + l) & kNodeMask;
+            const CgNode c = cg_node(r[id], q[id], __ldg(p_old + id), __ldg(dinv + id), alf, bef);
             xs[l] = c.pn;
             if (!WARPS) acc[l] = 0.0f;
-            if (l < m.n_owned) {
-                x[id[u]] = fmadd(al, f2d(pv[u]), xv[u]);
-                r[id[u]] = c.rn;
-                p_new[id[u]] = c.pn;
-                zs[l] = c.z;
-                ds[l] = dv[u];
-                srz.add(c.rn * c.z);
-                srr.add(c.rn * c.rn);
-            }
         }
     }
     if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
@@ -791,17 +800,27 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     // q = mask(A p_new): owned nodes final (Dirichlet rows: dinv = 0), shared
     // nodes to their halo slots
     CompSum spq, sqz, sqdq;
-    for (int l = tid; l < m.n_nodes; l += NT) {
-        const float v = acc[l];
-        if (l < m.n_owned) {
-            const float d = ds[l];
-            const float qn = d == 0.0f ? 0.0f : v;
-            q[own0 + l] = qn;
-            spq.add(xs[l] * qn);
-            sqz.add(qn * zs[l]);
-            sqdq.add(qn * (d * qn));
+    for (int g = tid; g < n_items; g += NT) {
+        if (g < n_own4) {
+            const int l0 = 4 * g;
+            float qn4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int l = l0 + u;
+                qn4[u] = 0.0f;                      // padding entries stay zero
+                if (l < m.n_owned) {
+                    const float d = ds[l];
+                    const float qn = d == 0.0f ? 0.0f : acc[l];
+                    qn4[u] = qn;
+                    spq.add(xs[l] * qn);
+                    sqz.add(qn * zs[l]);
+                    sqdq.add(qn * (d * qn));
+                }
+            }
+            *reinterpret_cast<float4*>(q + own0 + l0) = make_float4(qn4[0], qn4[1], qn4[2], qn4[3]);
         } else {
-            halo[m.halo_off + (l - m.n_owned)] = v;
+            const int l = m.n_owned + (g - n_own4);
+            halo[m.halo_off + (l - m.n_owned)] = acc[l];
         }
     }
     // The sums stay compensated FP32 pairs up to the last fix-up block (every
@@ -833,7 +852,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
 // q from the halo partials in patch order, the sums; the last block adds all
 // partials in index order and takes the iteration's scalar decisions.
 template <int ROWS>
-__global__ void __launch_bounds__(kFixThreads)
+__global__ void __launch_bounds__(kFixThreads, 6)
 k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const float* __restrict__ p_old,
            float* __restrict__ p_new, const float* __restrict__ dinv, double* __restrict__ x,
            const float* __restrict__ halo, double* __restrict__ part, Scalars* __restrict__ sc) {
@@ -990,10 +1009,10 @@ cudaError_t run_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, c
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    if (fix_rows(pd) == 2)
-        k_cg_fixup<2><<<fix_grid(pd.n_shared, 2), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
-    else
-        k_cg_fixup<1><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
+    // one row per thread at a time (each row has five vector loads in flight
+    // already), one wave of six 256-thread blocks per SM
+    const int fg = std::min(fix_grid(pd.n_shared, 1), 6 * std::max(pd.num_sms, 1));
+    k_cg_fixup<1><<<fg, kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
     if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();

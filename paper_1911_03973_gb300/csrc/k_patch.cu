@@ -745,6 +745,12 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     // one by one through the node table; the fix-up writes them.
     const int n_own4 = (m.n_owned + 3) >> 2;
     const int n_items = n_own4 + (m.n_nodes - m.n_owned);
+    // z and dinv of the owned nodes are kept per group of four (16-byte
+    // shared-memory accesses, no bank conflicts), the node sums zeroed the same way
+    float4* zs4 = reinterpret_cast<float4*>(zs);
+    float4* ds4 = reinterpret_cast<float4*>(ds);
+    if (!WARPS)
+        for (int g = tid; g < (m.n_nodes + 3) >> 2; g += NT) reinterpret_cast<float4*>(acc)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
     CompSum srz, srr;
     for (int g = tid; g < n_items; g += NT) {
         if (g < n_own4) {
@@ -758,24 +764,29 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             const float rr4[4] = {rv.x, rv.y, rv.z, rv.w}, qq4[4] = {qv.x, qv.y, qv.z, qv.w};
             const float pp4[4] = {pv.x, pv.y, pv.z, pv.w}, dd4[4] = {dv.x, dv.y, dv.z, dv.w};
             const double xx4[4] = {xa.x, xa.y, xb.x, xb.y};
-            float rn4[4], pn4[4];
+            float rn4[4], pn4[4], z4[4];
             double xn4[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const CgNode c = cg_node(rr4[u], qq4[u], pp4[u], dd4[u], alf, bef);
                 rn4[u] = c.rn;
                 pn4[u] = c.pn;
+                z4[u] = c.z;                        // 0 on padding (dinv = 0)
                 xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
-                const int l = l0 + u;
-                if (l < m.n_owned) {
-                    xs[l] = c.pn;
-                    zs[l] = c.z;
-                    ds[l] = dd4[u];
-                    if (!WARPS) acc[l] = 0.0f;
+                if (l0 + u < m.n_owned) {
                     srz.add(c.rn * c.z);
                     srr.add(c.rn * c.rn);
                 }
             }
+            if (l0 + 4 <= m.n_owned) {
+                reinterpret_cast<float4*>(xs)[g] = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (l0 + u < m.n_owned) xs[l0 + u] = pn4[u];   // the entries after belong to shared nodes
+            }
+            zs4[g] = make_float4(z4[0], z4[1], z4[2], z4[3]);
+            ds4[g] = dv;
             *reinterpret_cast<float4*>(r + id0) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
             *reinterpret_cast<float4*>(p_new + id0) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
             *reinterpret_cast<double2*>(x + id0) = make_double2(xn4[0], xn4[1]);
@@ -785,7 +796,6 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             const int id = __ldg(pn + l) & kNodeMask;
             const CgNode c = cg_node(r[id], q[id], __ldg(p_old + id), __ldg(dinv + id), alf, bef);
             xs[l] = c.pn;
-            if (!WARPS) acc[l] = 0.0f;
         }
     }
     if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
@@ -803,18 +813,21 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     for (int g = tid; g < n_items; g += NT) {
         if (g < n_own4) {
             const int l0 = 4 * g;
+            // 16-byte loads; entries past n_owned (shared nodes' sums) are not used
+            const float4 a4 = reinterpret_cast<const float4*>(acc)[g], x4 = reinterpret_cast<const float4*>(xs)[g];
+            const float4 z4 = zs4[g], d4 = ds4[g];
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            const float zv[4] = {z4.x, z4.y, z4.z, z4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
             float qn4[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int l = l0 + u;
                 qn4[u] = 0.0f;                      // padding entries stay zero
-                if (l < m.n_owned) {
-                    const float d = ds[l];
-                    const float qn = d == 0.0f ? 0.0f : acc[l];
+                if (l0 + u < m.n_owned) {
+                    const float qn = dv[u] == 0.0f ? 0.0f : av[u];
                     qn4[u] = qn;
-                    spq.add(xs[l] * qn);
-                    sqz.add(qn * zs[l]);
-                    sqdq.add(qn * (d * qn));
+                    spq.add(xv[u] * qn);
+                    sqz.add(qn * zv[u]);
+                    sqdq.add(qn * (dv[u] * qn));
                 }
             }
             *reinterpret_cast<float4*>(q + own0 + l0) = make_float4(qn4[0], qn4[1], qn4[2], qn4[3]);
@@ -945,18 +958,17 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: every block's pair in FP64, added in a fixed order
-    double v[kCgSums];
-#pragma unroll
-    for (int j = 0; j < kCgSums; ++j) v[j] = 0.0;
+    // the last block: every block's pair, added in compensated FP32 in a fixed
+    // order; only the five totals are formed in FP64
+    CompSum t5[kCgSums], g5[kCgSums];
     for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads)
 #pragma unroll
-        for (int j = 0; j < kCgSums; ++j) {
-            const float2 r = __ldcg(part2 + j * stride + np + i);
-            v[j] += double(r.x) + double(r.y);
-        }
-    block_sums5(v, red);
+        for (int j = 0; j < kCgSums; ++j) merge(t5[j], comp_of(__ldcg(part2 + j * stride + np + i)));
+    block_sums_f32<kCgSums, kFixThreads>(t5, g5, red2);
     if (threadIdx.x != 0) return;
+    double v[kCgSums];
+#pragma unroll
+    for (int j = 0; j < kCgSums; ++j) v[j] = g5[j].value();
     sc->ctr_fix = 0;
     const double rho = v[0], rr = v[1], pq = v[2], qz = v[3], qdq = v[4];
     const bool fresh = sc->fresh != 0;

@@ -383,7 +383,12 @@ static int create_device(ebe_handle* h, const double* coords_host) {
         TRY(upload(h, &h->int_of_user, iou.data(), int64_t(iou.size())));
         TRY(upload(h, &h->pnode_int, pint.data(), int64_t(pint.size())));
         TRY(upload(h, &h->sh_node_int, shint.data(), int64_t(shint.size())));
+        std::vector<int32_t> hpos(static_cast<size_t>(std::max<int64_t>(P.n_halo, 1)), 0);
+        for (int64_t j = 0; j < P.n_halo; ++j) hpos[size_t(P.sh_slot[size_t(j)])] = int32_t(j);
+        int32_t* hpos_d = nullptr;
+        TRY(upload(h, &hpos_d, hpos.data(), int64_t(hpos.size())));
         h->pd_int = pd;
+        h->pd_int.halo_pos = hpos_d;
         h->pd_int.pnode = h->pnode_int;
         h->pd_int.sh_node = h->sh_node_int;
         h->pd_int.own_off = own_off_d;

@@ -112,6 +112,19 @@ __device__ __forceinline__ void group8_sum(CompSum& v) {
     }
 }
 
+// Sum over a warp in a fixed butterfly order with plain FP32 additions (the
+// lane's compensation term is folded in first; the total comes back with
+// c = 0).  Five roundings of partial sums of a few terms each: about 3e-7 of
+// the warp's sum of magnitudes, random in sign across warps, whose totals
+// are then added in compensated form.  Every lane ends with the same total.
+__device__ __forceinline__ void warp_sum_plain(CompSum& v) {
+    float t = v.s + v.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    v.s = t;
+    v.c = 0.0f;
+}
+
 // K compensated FP32 sums over a block of NT threads, entirely in FP32:
 // warp butterflies, then thread 0 merges the per-warp totals in warp order.
 // Every thread must call it; out is valid in thread 0.  red: K * NT / 32

@@ -833,7 +833,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             *reinterpret_cast<float4*>(q + own0 + l0) = make_float4(qn4[0], qn4[1], qn4[2], qn4[3]);
         } else {
             const int l = m.n_owned + (g - n_own4);
-            halo[m.halo_off + (l - m.n_owned)] = acc[l];
+            halo[__ldg(pd.halo_pos + m.halo_off + (l - m.n_owned))] = acc[l];   // CSR order
         }
     }
     // The sums stay compensated FP32 pairs up to the last fix-up block (every
@@ -842,7 +842,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     // (lane 8k + w holds warp w's total of sum k) and of sum 4.
     CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq};
 #pragma unroll
-    for (int k = 0; k < kCgSums; ++k) warp_sum(cs[k]);
+    for (int k = 0; k < kCgSums; ++k) warp_sum_plain(cs[k]);
     float2* red2 = reinterpret_cast<float2*>(red);
     const int warp = tid >> 5, lane = tid & 31;
     if (lane == 0)
@@ -900,10 +900,11 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
         float hv[ROWS];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) hv[u] = 0.0f;
+        // the patch pass wrote the row's partials contiguously (CSR order), in patch order
         for (int t = 0; t < nmax; ++t)
 #pragma unroll
             for (int u = 0; u < ROWS; ++u)
-                if (t < cnt[u]) hv[u] += halo[__ldg(pd.sh_slot + s0[u] + t)];
+                if (t < cnt[u]) hv[u] += halo[s0[u] + t];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int kk = k + u * st;
@@ -936,7 +937,7 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
     {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-        for (int j = 0; j < kCgSums; ++j) warp_sum(s5[j]);
+        for (int j = 0; j < kCgSums; ++j) warp_sum_plain(s5[j]);
         if (lane == 0)
 #pragma unroll
             for (int j = 0; j < kCgSums; ++j) red2[j * 8 + warp] = make_float2(s5[j].s, s5[j].c);

@@ -35,6 +35,10 @@ struct PlanDev {
     // of the fix-up is node sh_base + k.
     const int32_t* own_off = nullptr;   // [n_patches + 1]
     int sh_base = 0;
+    // [n_halo] position of each halo slot in the shared rows' CSR order
+    // (halo_pos[sh_slot[j]] = j), so that the single-sync fix-up reads a row's
+    // partials contiguously
+    const int32_t* halo_pos = nullptr;
 };
 
 // Element matrices are symmetric (K_e and M_e of Eq. matrices_K_M; the

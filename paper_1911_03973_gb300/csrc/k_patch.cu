@@ -729,6 +729,33 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
+    // Node step at every patch node.  Owned nodes come in groups of four
+    // consecutive solver numbers (a patch's run starts on a multiple of 4 and
+    // is padded to one; padding entries are zero in every vector and stay
+    // zero): 16-byte loads and stores, written back here.  Shared nodes come
+    // one by one through the node table; the fix-up writes them.
+    const int own0 = __ldg(pd.own_off + p);
+    const int32_t* pn = pd.pnode + m.node_off;
+    const int n_own4 = (m.n_owned + 3) >> 2;
+    const int n_items = n_own4 + (m.n_nodes - m.n_owned);
+    // The owned entries were written by the previous patch pass, which had
+    // completed before the fix-up launched, so this thread's first item is
+    // loaded before waiting for the fix-up (the node table is constant);
+    // shared-node entries and the scalars only after the wait.
+    float4 rv0, qv0, pv0, dv0;
+    double2 xa0, xb0;
+    int sid0 = -1;
+    if (tid < n_own4) {
+        const int id0 = own0 + 4 * tid;
+        rv0 = *reinterpret_cast<const float4*>(r + id0);
+        qv0 = *reinterpret_cast<const float4*>(q + id0);
+        pv0 = __ldg(reinterpret_cast<const float4*>(p_old + id0));
+        dv0 = __ldg(reinterpret_cast<const float4*>(dinv + id0));
+        xa0 = *reinterpret_cast<const double2*>(x + id0);
+        xb0 = *reinterpret_cast<const double2*>(x + id0 + 2);
+    } else if (tid < n_items) {
+        sid0 = __ldg(pn + m.n_owned + (tid - n_own4)) & kNodeMask;
+    }
     pdl_wait();
     if (sc->done) {                                  // uniform: the solver has stopped
         if (tid == 0) mbar_wait_bounded(bar, 0, nullptr);
@@ -736,15 +763,6 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     }
     const double al = sc->alpha;
     const float alf = d2f(al), bef = d2f(sc->beta);
-    const int own0 = __ldg(pd.own_off + p);
-    const int32_t* pn = pd.pnode + m.node_off;
-    // Node step at every patch node.  Owned nodes come in groups of four
-    // consecutive solver numbers (a patch's run starts on a multiple of 4 and
-    // is padded to one; padding entries are zero in every vector and stay
-    // zero): 16-byte loads and stores, written back here.  Shared nodes come
-    // one by one through the node table; the fix-up writes them.
-    const int n_own4 = (m.n_owned + 3) >> 2;
-    const int n_items = n_own4 + (m.n_nodes - m.n_owned);
     // z and dinv of the owned nodes are kept per group of four (16-byte
     // shared-memory accesses, no bank conflicts), the node sums zeroed the same way
     float4* zs4 = reinterpret_cast<float4*>(zs);
@@ -752,50 +770,55 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     if (!WARPS)
         for (int g = tid; g < (m.n_nodes + 3) >> 2; g += NT) reinterpret_cast<float4*>(acc)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
     CompSum srz, srr;
-    for (int g = tid; g < n_items; g += NT) {
-        if (g < n_own4) {
-            const int l0 = 4 * g, id0 = own0 + l0;
-            const float4 rv = *reinterpret_cast<const float4*>(r + id0);
-            const float4 qv = *reinterpret_cast<const float4*>(q + id0);
-            const float4 pv = __ldg(reinterpret_cast<const float4*>(p_old + id0));
-            const float4 dv = __ldg(reinterpret_cast<const float4*>(dinv + id0));
-            const double2 xa = *reinterpret_cast<const double2*>(x + id0);
-            const double2 xb = *reinterpret_cast<const double2*>(x + id0 + 2);
-            const float rr4[4] = {rv.x, rv.y, rv.z, rv.w}, qq4[4] = {qv.x, qv.y, qv.z, qv.w};
-            const float pp4[4] = {pv.x, pv.y, pv.z, pv.w}, dd4[4] = {dv.x, dv.y, dv.z, dv.w};
-            const double xx4[4] = {xa.x, xa.y, xb.x, xb.y};
-            float rn4[4], pn4[4], z4[4];
-            double xn4[4];
+    auto owned_group = [&](int g, const float4& rv, const float4& qv, const float4& pv, const float4& dv,
+                           const double2& xa, const double2& xb) {
+        const int l0 = 4 * g, id0 = own0 + l0;
+        const float rr4[4] = {rv.x, rv.y, rv.z, rv.w}, qq4[4] = {qv.x, qv.y, qv.z, qv.w};
+        const float pp4[4] = {pv.x, pv.y, pv.z, pv.w}, dd4[4] = {dv.x, dv.y, dv.z, dv.w};
+        const double xx4[4] = {xa.x, xa.y, xb.x, xb.y};
+        float rn4[4], pn4[4], z4[4];
+        double xn4[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const CgNode c = cg_node(rr4[u], qq4[u], pp4[u], dd4[u], alf, bef);
-                rn4[u] = c.rn;
-                pn4[u] = c.pn;
-                z4[u] = c.z;                        // 0 on padding (dinv = 0)
-                xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
-                if (l0 + u < m.n_owned) {
-                    srz.add(c.rn * c.z);
-                    srr.add(c.rn * c.rn);
-                }
+        for (int u = 0; u < 4; ++u) {
+            const CgNode c = cg_node(rr4[u], qq4[u], pp4[u], dd4[u], alf, bef);
+            rn4[u] = c.rn;
+            pn4[u] = c.pn;
+            z4[u] = c.z;                            // 0 on padding (dinv = 0)
+            xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
+            if (l0 + u < m.n_owned) {
+                srz.add(c.rn * c.z);
+                srr.add(c.rn * c.rn);
             }
-            if (l0 + 4 <= m.n_owned) {
-                reinterpret_cast<float4*>(xs)[g] = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (l0 + u < m.n_owned) xs[l0 + u] = pn4[u];   // the entries after belong to shared nodes
-            }
-            zs4[g] = make_float4(z4[0], z4[1], z4[2], z4[3]);
-            ds4[g] = dv;
-            *reinterpret_cast<float4*>(r + id0) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
-            *reinterpret_cast<float4*>(p_new + id0) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
-            *reinterpret_cast<double2*>(x + id0) = make_double2(xn4[0], xn4[1]);
-            *reinterpret_cast<double2*>(x + id0 + 2) = make_double2(xn4[2], xn4[3]);
+        }
+        if (l0 + 4 <= m.n_owned) {
+            reinterpret_cast<float4*>(xs)[g] = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
         } else {
-            const int l = m.n_owned + (g - n_own4);
-            const int id = __ldg(pn + l) & kNodeMask;
-            const CgNode c = cg_node(r[id], q[id], __ldg(p_old + id), __ldg(dinv + id), alf, bef);
-            xs[l] = c.pn;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (l0 + u < m.n_owned) xs[l0 + u] = pn4[u];   // the entries after belong to shared nodes
+        }
+        zs4[g] = make_float4(z4[0], z4[1], z4[2], z4[3]);
+        ds4[g] = dv;
+        *reinterpret_cast<float4*>(r + id0) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
+        *reinterpret_cast<float4*>(p_new + id0) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
+        *reinterpret_cast<double2*>(x + id0) = make_double2(xn4[0], xn4[1]);
+        *reinterpret_cast<double2*>(x + id0 + 2) = make_double2(xn4[2], xn4[3]);
+    };
+    auto shared_node = [&](int g, int id) {
+        const CgNode c = cg_node(r[id], q[id], __ldg(p_old + id), __ldg(dinv + id), alf, bef);
+        xs[m.n_owned + (g - n_own4)] = c.pn;
+    };
+    if (tid < n_own4) owned_group(tid, rv0, qv0, pv0, dv0, xa0, xb0);
+    else if (tid < n_items) shared_node(tid, sid0);
+    for (int g = tid + NT; g < n_items; g += NT) {   // patches with more than NT items
+        if (g < n_own4) {
+            const int id0 = own0 + 4 * g;
+            owned_group(g, *reinterpret_cast<const float4*>(r + id0), *reinterpret_cast<const float4*>(q + id0),
+                        __ldg(reinterpret_cast<const float4*>(p_old + id0)),
+                        __ldg(reinterpret_cast<const float4*>(dinv + id0)), *reinterpret_cast<const double2*>(x + id0),
+                        *reinterpret_cast<const double2*>(x + id0 + 2));
+        } else {
+            shared_node(g, __ldg(pn + m.n_owned + (g - n_own4)) & kNodeMask);
         }
     }
     if (tid == 0) *flag = mbar_wait_bounded(bar, 0, pd.err) ? 1 : 0;
@@ -942,18 +965,17 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
 #pragma unroll
             for (int j = 0; j < kCgSums; ++j) red2[j * 8 + warp] = make_float2(s5[j].s, s5[j].c);
         __syncthreads();
-        if (warp == 0) {
-#pragma unroll
-            for (int j = 0; j < kCgSums; ++j) {
-                CompSum a = lane < kFixThreads / 32 ? comp_of(red2[j * 8 + lane]) : CompSum{};
-                for (int i = p0 + lane; i < p1; i += 32) merge(a, comp_of(part2[j * stride + i]));
-                warp_sum(a);
-                if (lane == 0) part2[j * stride + np + blockIdx.x] = make_float2(a.s, a.c);
-            }
-            if (lane == 0) {
-                __threadfence();
-                last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
-            }
+        if (warp < kCgSums) {                       // warp j adds sum j
+            const int j = warp;
+            CompSum a = lane < kFixThreads / 32 ? comp_of(red2[j * 8 + lane]) : CompSum{};
+            for (int i = p0 + lane; i < p1; i += 32) merge(a, comp_of(part2[j * stride + i]));
+            warp_sum(a);
+            if (lane == 0) part2[j * stride + np + blockIdx.x] = make_float2(a.s, a.c);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
         }
     }
     __syncthreads();
@@ -961,15 +983,22 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
     __threadfence();
     // the last block: every block's pair, added in compensated FP32 in a fixed
     // order; only the five totals are formed in FP64
-    CompSum t5[kCgSums], g5[kCgSums];
-    for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads)
-#pragma unroll
-        for (int j = 0; j < kCgSums; ++j) merge(t5[j], comp_of(__ldcg(part2 + j * stride + np + i)));
-    block_sums_f32<kCgSums, kFixThreads>(t5, g5, red2);
+    // (warp j merges the block pairs of sum j, lane by lane, then across the warp)
+    __shared__ double tot[kCgSums];
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp < kCgSums) {
+            CompSum a;
+            for (int i = lane; i < int(gridDim.x); i += 32) merge(a, comp_of(__ldcg(part2 + warp * stride + np + i)));
+            warp_sum(a);
+            if (lane == 0) tot[warp] = a.value();
+        }
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     double v[kCgSums];
 #pragma unroll
-    for (int j = 0; j < kCgSums; ++j) v[j] = g5[j].value();
+    for (int j = 0; j < kCgSums; ++j) v[j] = tot[j];
     sc->ctr_fix = 0;
     const double rho = v[0], rr = v[1], pq = v[2], qz = v[3], qdq = v[4];
     const bool fresh = sc->fresh != 0;

@@ -73,7 +73,10 @@ def test_batch_barrier_timeout_is_reported_and_the_handle_recovers(ebe):
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_rtol_below_the_fp64_floor_stalls(ebe, precision):
+    # f scaled by 1e12 so that the squares of residuals at the FP64 floor
+    # (about 1e-16 |b|) stay in the normal FP32 range of the mixed solver's dots
     prob = meshgen.config_square_f1(33, nu=1.0)
+    prob["f"] = prob["f"] * 1e12
     h = _single(ebe, prob)
     x = torch.zeros(prob["coords"].shape[0], dtype=torch.float64, device=DEV)
     prec = {"fp64": ebe.EBE_PREC_FP64, "mixed": ebe.EBE_PREC_MIXED,

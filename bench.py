@@ -589,7 +589,7 @@ def run_learned(args, dev, stream, profile=False):
             torch.cuda.synchronize()
             out[f"square{n}"] = {
                 "learned_fcg": {"ms": round(tl, 1), "iterations": il["iterations"], "fell_back": il["fell_back"],
-                                "status": il["status"], "rule": "race of 64 Jacobi / 64 network iterations"},
+                                "status": il["status"], "rule": "race of 16 Jacobi / 16 network iterations, Jacobi-PCG after a lost race or a slow window"},
                 "network_first": {"ms": round(t0n, 1), "iterations": i0["iterations"], "fell_back": i0["fell_back"],
                                   "rule": "network from the start, fallback rules only"},
                 "jacobi_fcg": {"ms": round(tj, 1), "iterations": ij["iterations"]},

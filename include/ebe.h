@@ -143,7 +143,7 @@ typedef struct {
     int32_t race_iters;      /* ebe_solve_learned only: iterations of each leg of the race
                                 between Jacobi and the network; 0 = no race (the network
                                 from the start, with the fallback rules only); default -1
-                                = 2 chunk                                                */
+                                = 16                                                     */
 } ebe_solve_opts;
 
 typedef struct {
@@ -475,16 +475,18 @@ ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev
  * FP64 vectors and element matrices, stopping on the FP64 true relative
  * residual as ebe_solve.  With a network the solve starts with a race: from
  * x0, race_iters iterations of Jacobi-FCG, then, again from x0, race_iters
- * iterations with the network, each timed with CUDA events; the one with the
- * larger reduction of the residual norm per unit time continues (so a network
- * that is slower than Jacobi costs about its race_iters timed iterations).  The
- * network-FCG then falls back to Jacobi from the current iterate when, over
- * any window of 4 chunks (timed the same way), it reduces the residual norm
- * more slowly per unit time than Jacobi did in the race, on a breakdown, when
- * the residual norm does not halve within 16 chunks, or when the true
- * residual stalls (stall_updates checks); *fell_back (may be NULL)
- * is 1 when the solution came from Jacobi.  opts:
- * rtol, maxit, chunk (iterations between host checks), stall_updates, race_iters.
+ * iterations with the network, each timed with CUDA events; the network
+ * continues only if it reduced the residual norm at least 1.5 times faster
+ * per unit time (early rates favour a smoother), and then only while every
+ * window of 2 chunks keeps at least Jacobi's race rate, the residual norm
+ * halves within 16 chunks, no breakdown occurs and the true residual does not
+ * stall (stall_updates checks).  Otherwise the library's Jacobi-PCG (the plain
+ * FP64 solver of ebe_solve) finishes the solve from the current iterate (from
+ * the Jacobi leg's iterate when the race is lost), to the same target
+ * rtol |r0|, so a network that does not pay off costs its race leg and a
+ * restart of CG; *fell_back (may be NULL) is 1 when that happened.  opts:
+ * rtol, maxit, chunk (iterations between host checks), stall_updates,
+ * race_iters (default 16).  iterations counts every iteration of the call.
  * Returns EBE_OK, EBE_MAXIT, EBE_BREAKDOWN, EBE_STALL or an error. */
 ebe_status ebe_solve_learned(ebe_handle* h, ebe_mpnn* net, double* x_dev, const ebe_solve_opts* opts,
                              ebe_solve_info* info, int32_t* fell_back);

@@ -2068,18 +2068,13 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
         int first = 1;
         double best = 1.0, best_rr = rr;
         int no_progress = 0, flat_chunks = 0;
+        // giving up on the network: the solve is finished by the library's
+        // Jacobi-PCG (the plain FP64 solver) from the current iterate
+        bool to_pcg = false;
         auto fallback = [&]() -> int {
             use_net = false;
+            to_pcg = true;
             if (fell_back) *fell_back = 1;
-            first = 1;
-            best_rr = HUGE_VAL;
-            flat_chunks = 0;
-            double t = 0.0;
-            TRY(true_residual(h, t));
-            info.true_residuals += 1;
-            int ll = 0;
-            CK(launch_control(h->sc, -1.0, -1, 0, h->st, &ll), "control");
-            add_launches(h, ll);
             return EBE_OK;
         };
         // `iters` FCG iterations with the current preconditioner, enqueued
@@ -2113,7 +2108,9 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
         // the network keeps it up, measured over windows of kWindow chunks, or
         // the solve falls back to Jacobi
         double rate_jac = 0.0;
-        constexpr int kWindow = 4;
+        constexpr int kWindow = 2;            // chunks per check of the network's rate
+        constexpr int kRaceDefault = 16;      // iterations of each leg of the race
+        constexpr double kRaceMargin = 1.5;   // the network must beat Jacobi's early rate by this factor
         struct Events {
             cudaEvent_t e[2] = {nullptr, nullptr};
             ~Events() { for (auto& v : e) if (v) cudaEventDestroy(v); }
@@ -2121,7 +2118,7 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
         CK(cudaEventCreate(&evs.e[0]), "cudaEventCreate");
         CK(cudaEventCreate(&evs.e[1]), "cudaEventCreate");
         if (use_net && o.race_iters != 0) {
-            const int kRace = o.race_iters > 0 ? o.race_iters : 2 * o.chunk;
+            const int kRace = o.race_iters > 0 ? o.race_iters : kRaceDefault;
             TRY(dalloc(h, &h->xsave0, n));
             TRY(dalloc(h, &h->xsave1, n));
             cudaEvent_t* ev = evs.e;
@@ -2161,8 +2158,8 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
                     rr_net = h->sc_host->rr;
                     rate_jac = std::log(rr / rr_jac) / t_jac;
                     const double rate_net = std::log(rr / rr_net) / t_net;
-                    if (!(rate_net > rate_jac)) {
-                        // Jacobi continues from its own iterate
+                    if (!(rate_net > kRaceMargin * rate_jac)) {
+                        // Jacobi-PCG continues from the Jacobi leg's iterate
                         CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st),
                            "restore");
                         rs = fallback();
@@ -2176,6 +2173,7 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
         double win_ms = 0.0, win_rr = h->sc_host->rr;
         int win_chunks = 0;
         for (;;) {
+            if (to_pcg) break;
             const bool watch = use_net && rate_jac > 0.0 && !pending;
             if (watch) CK(cudaEventRecord(evs.e[0], h->st), "cudaEventRecord");
             if (!pending) TRY(enqueue(o.chunk));
@@ -2240,6 +2238,36 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             l = 0;
             CK(launch_control(h->sc, -1.0, -1, 0, h->st, &l), "control");
             add_launches(h, l);
+        }
+        if (to_pcg) {
+            // Jacobi-PCG (plain FP64) from the current iterate, to the same
+            // target rtol |r0| of the original start
+            TRY(dalloc(h, &h->xsave1, n));
+            double rr_now = 0.0;
+            TRY(true_residual(h, rr_now));
+            info.true_residuals += 1;
+            const double r_now = std::sqrt(rr_now);
+            if (!std::isfinite(r_now)) {
+                status = EBE_BREAKDOWN;
+            } else if (r_now <= o.rtol * r0) {
+                info.rel_residual = r_now / r0;
+                status = EBE_OK;
+            } else {
+                CK(cudaMemcpyAsync(h->xsave1, h->x64w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "save x");
+                ebe_solve_opts po = o;
+                po.precision = EBE_PREC_FP64;
+                po.rtol = o.rtol * r0 / r_now;
+                po.maxit = std::max<int64_t>(1, o.maxit - info.iterations);
+                po.use_graph = 1;
+                ebe_solve_info pi{};
+                status = solve_impl(h, h->xsave1, false, po, pi);
+                if (status != EBE_OK && status != EBE_MAXIT && status != EBE_STALL && status != EBE_BREAKDOWN)
+                    return status;
+                CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "x");
+                info.iterations += pi.iterations;
+                info.true_residuals += pi.true_residuals;
+                info.rel_residual = pi.rel_residual * r_now / r0;
+            }
         }
     }
     CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,

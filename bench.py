@@ -400,13 +400,18 @@ def run_cube(args, dev, stream):
         a32 = ebe.ebe_time_operator(h, p32, q32, True, 20)
         ebe.ebe_time_operator(h, x64, r64, False, 5)
         r64t = ebe.ebe_time_operator(h, x64, r64, False, 20)
+        ebe.ebe_time_operator(h, x64, r64, False, 3, double_word=True)
+        rdw = ebe.ebe_time_operator(h, x64, r64, False, 20, double_word=True)
         peak = peaks()[0]
+        gdw = m["residual64"] / (sum(rdw) / 1e3) / 1e9
         g32 = m["apply32"] / (sum(a32) / 1e3) / 1e9
         g64 = m["residual64"] / (sum(r64t) / 1e3) / 1e9
         out["apply32"] = {"ms_per_launch": [round(a32[0], 5), round(a32[1], 5)], "bytes_per_launch": m["apply32"],
                           "gbs": round(g32, 1), "frac": round(g32 / peak, 4)}
         out["residual64"] = {"ms_per_launch": [round(r64t[0], 5), round(r64t[1], 5)],
                              "bytes_per_launch": m["residual64"], "gbs": round(g64, 1), "frac": round(g64 / peak, 4)}
+        out["residual_dw"] = {"ms_per_launch": [round(rdw[0], 5), round(rdw[1], 5)],
+                              "bytes_per_launch": m["residual64"], "gbs": round(gdw, 1), "frac": round(gdw / peak, 4)}
         ebe.ebe_destroy(h)
     return out
 
@@ -589,7 +594,7 @@ def run_learned(args, dev, stream, profile=False):
             torch.cuda.synchronize()
             out[f"square{n}"] = {
                 "learned_fcg": {"ms": round(tl, 1), "iterations": il["iterations"], "fell_back": il["fell_back"],
-                                "status": il["status"], "rule": "race of 16 Jacobi / 16 network iterations, Jacobi-PCG after a lost race or a slow window"},
+                                "status": il["status"], "rule": "race of 16 Jacobi / 16 network iterations; a lost or undecided race or a slow window hands over to the mixed Jacobi-PCG"},
                 "network_first": {"ms": round(t0n, 1), "iterations": i0["iterations"], "fell_back": i0["fell_back"],
                                   "rule": "network from the start, fallback rules only"},
                 "jacobi_fcg": {"ms": round(tj, 1), "iterations": ij["iterations"]},
@@ -733,6 +738,8 @@ def run_ours(args):
         x64 = torch.rand(n_n, dtype=torch.float64, device=dev)
         r64 = torch.empty_like(x64)
         ms_patch64, ms_fix64 = ebe.ebe_time_operator(h, x64, r64, apply=False, reps=20)
+        ebe.ebe_time_operator(h, x64, r64, apply=False, reps=3, double_word=True)
+        ms_dw = ebe.ebe_time_operator(h, x64, r64, apply=False, reps=20, double_word=True)
         variants = None
         if not args.no_variants:
             variants = {}
@@ -753,6 +760,7 @@ def run_ours(args):
     ach = m["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9
     ach_cg = m["cg_mixed"] / ((ms_cg[0] + ms_cg[1]) / 1e3) / 1e9
     ach64 = m["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9
+    ach_dw = m["residual64"] / (sum(ms_dw) / 1e3) / 1e9
     alu64 = fp64_alu_model(dim + 1, n_n, n_e, torch.cuda.get_device_properties(dev).multi_processor_count,
                            clk.get("sm_mhz") or clk.get("sm_max_mhz"))
     if alu64 is not None:
@@ -859,6 +867,10 @@ def run_ours(args):
                           "bytes_per_launch": m["residual64"],
                           "stored_gbs": round(m_stored["residual64"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9, 1),
                           "fp64_pipe": alu64},
+        "residual_dw": {"gbs": round(ach_dw, 1), "frac": round(ach_dw / peak, 4),
+                        "kernel": "the FP64 residual in double-word FP32 arithmetic (EBE_F64_DW): patch + fix-up",
+                        "ms_per_launch": [round(ms_dw[0], 5), round(ms_dw[1], 5)],
+                        "bytes_per_launch": m["residual64"]},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -913,13 +925,16 @@ def summary_block(line, ms_plain, pinfo, peak):
         s["learned"] = {k: {"fcg_net_ms": v["learned_fcg"]["ms"], "net_it": v["learned_fcg"]["iterations"],
                             "fell_back": v["learned_fcg"]["fell_back"], "plain_pcg_ms": v["plain_fp64_pcg"]["ms"],
                             "ratio_to_plain": round(v["learned_fcg"]["ms"] / v["plain_fp64_pcg"]["ms"], 3),
+                            "mixed_pcg_ms": v["mixed_pcg"]["ms"],
+                            "ratio_to_mixed": round(v["learned_fcg"]["ms"] / v["mixed_pcg"]["ms"], 3),
                             "net_first_ms": v["network_first"]["ms"]}
                         for k, v in lr.items() if k.startswith("square")}
     s["hbm_frac"] = {"cg_pass": r["frac"], "apply32": line["apply_fp32"]["frac"],
-                     "residual64": line["residual_fp64"]["frac"]}
+                     "residual64": line["residual_fp64"]["frac"], "residual_dw": line["residual_dw"]["frac"]}
     c = line.get("cube129")
     if c:
-        s["hbm_frac"].update({"cube_apply32": c["apply32"]["frac"], "cube_residual64": c["residual64"]["frac"]})
+        s["hbm_frac"].update({"cube_apply32": c["apply32"]["frac"], "cube_residual64": c["residual64"]["frac"],
+                              "cube_residual_dw": c["residual_dw"]["frac"]})
     v = line.get("residual_variants_fp64")
     if v:
         s["scatter_fp64_ms"] = {k: x["ms"] for k, x in v.items()}

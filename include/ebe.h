@@ -64,7 +64,18 @@ typedef enum {
 } ebe_status;
 
 /* Arithmetic types for ebe_residual / ebe_apply. */
-enum { EBE_F64 = 0, EBE_F32 = 1 };
+enum {
+    EBE_F64 = 0,      /* FP64 vectors, FP64 element matrices and arithmetic             */
+    EBE_F32 = 1,      /* FP32 vectors and element matrices (EBE_STORE_MIXED)            */
+    EBE_F64_DW = 2    /* FP64 vectors; the FP64 element matrices split into pairs of
+                         FP32 (hi + lo, made on first use after each ebe_assemble: 8
+                         bytes per stored entry, like the FP64 copy) and the products
+                         and sums in double-word FP32 arithmetic (exact FMA products,
+                         TwoSum additions, about 48 significant bits); r = b - A x is
+                         formed in FP64 per node.  It agrees with EBE_F64 to about
+                         2^-48 |A| |x| per node and runs on the FP32 pipe: GB300's
+                         FP64 pipe bounds the EBE_F64 residual                     */
+};
 
 /* Storage of the element matrices made by ebe_assemble. */
 enum {
@@ -245,8 +256,9 @@ ebe_status ebe_jacobi_diag(ebe_handle* h, double* d_dev);
 
 /* r = mask(b - A x) by the element-based residual (Eq. residual, Algorithm 1;
  * mask = zero Dirichlet rows).  x_dev, r_dev: device [n_n] of double
- * (dtype EBE_F64, FP64 A_e) or float (dtype EBE_F32, FP32 A_e; needs
- * EBE_STORE_MIXED).  x and r must not overlap.  Deterministic.
+ * (dtype EBE_F64, FP64 A_e; dtype EBE_F64_DW, the double-word form) or float
+ * (dtype EBE_F32, FP32 A_e; needs EBE_STORE_MIXED).  x and r must not
+ * overlap.  Deterministic.
  * Errors: EBE_NOT_READY, EBE_INVALID_ARG, EBE_CUDA_ERROR. */
 ebe_status ebe_residual(ebe_handle* h, const void* x_dev, void* r_dev, int32_t dtype);
 
@@ -476,12 +488,14 @@ ebe_status ebe_mpnn_train_step(ebe_mpnn* net, ebe_handle* h, const double* r_dev
  * residual as ebe_solve.  With a network the solve starts with a race: from
  * x0, race_iters iterations of Jacobi-FCG, then, again from x0, race_iters
  * iterations with the network, each timed with CUDA events; the network
- * continues only if it reduced the residual norm at least 1.5 times faster
- * per unit time (early rates favour a smoother), and then only while every
+ * continues only if Jacobi's leg reduced the residual norm and the network's
+ * leg reduced it at least 1.5 times faster per unit time (early rates favour
+ * a smoother), and then only while every
  * window of 2 chunks keeps at least Jacobi's race rate, the residual norm
  * halves within 16 chunks, no breakdown occurs and the true residual does not
- * stall (stall_updates checks).  Otherwise the library's Jacobi-PCG (the plain
- * FP64 solver of ebe_solve) finishes the solve from the current iterate (from
+ * stall (stall_updates checks).  Otherwise the library's Jacobi-PCG (ebe_solve
+ * with EBE_PREC_MIXED after ebe_assemble(EBE_STORE_MIXED), else with
+ * EBE_PREC_FP64) finishes the solve from the current iterate (from
  * the Jacobi leg's iterate when the race is lost), to the same target
  * rtol |r0|, so a network that does not pay off costs its race leg and a
  * restart of CG; *fell_back (may be NULL) is 1 when that happened.  opts:

@@ -15,7 +15,7 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (EBE_BREAKDOWN, EBE_CUDA_ERROR, EBE_DEGENERATE_ELEMENT, EBE_F32, EBE_F64,  # noqa: F401
+from ._abi import (EBE_BREAKDOWN, EBE_CUDA_ERROR, EBE_DEGENERATE_ELEMENT, EBE_F32, EBE_F64, EBE_F64_DW,  # noqa: F401
                    EBE_INDEX_RANGE, EBE_INVALID_ARG, EBE_MAXIT, EBE_NOT_READY, EBE_OK, EBE_OOM, EBE_PREC_FP64,
                    EBE_PREC_MIXED, EBE_PREC_MIXED_TEXTBOOK, EBE_SCATTER_ATOMIC, EBE_SCATTER_COLOUR, EBE_SCATTER_NODE, EBE_SCATTER_PATCH,
                    EBE_SINGULAR, EBE_STALL, EBE_STORE_FP64, EBE_STORE_MIXED)
@@ -158,21 +158,31 @@ def ebe_jacobi_diag(h: Handle, d) -> None:
     _check(h, _lib().ebe_jacobi_diag(h.ptr, _dev(d, EBE_F64, h.n_n, "d")))
 
 
-def ebe_residual(h: Handle, x, r) -> None:
+def _op_code(x, double_word):
     code = _dtype_code(x)
-    _check(h, _lib().ebe_residual(h.ptr, _dev(x, code, h.n_n, "x"), _dev(r, code, h.n_n, "r"), code))
+    if not double_word:
+        return code, code
+    if code != EBE_F64:
+        raise TypeError("the double-word form takes float64 vectors")
+    return EBE_F64_DW, EBE_F64
 
 
-def ebe_apply(h: Handle, x, y) -> None:
-    code = _dtype_code(x)
-    _check(h, _lib().ebe_apply(h.ptr, _dev(x, code, h.n_n, "x"), _dev(y, code, h.n_n, "y"), code))
+def ebe_residual(h: Handle, x, r, double_word: bool = False) -> None:
+    """r = mask(b - A x); double_word=True runs the FP64 arithmetic as FP32 pairs (EBE_F64_DW)."""
+    code, vt = _op_code(x, double_word)
+    _check(h, _lib().ebe_residual(h.ptr, _dev(x, vt, h.n_n, "x"), _dev(r, vt, h.n_n, "r"), code))
 
 
-def ebe_time_operator(h: Handle, x, y, apply: bool = True, reps: int = 20) -> tuple:
+def ebe_apply(h: Handle, x, y, double_word: bool = False) -> None:
+    code, vt = _op_code(x, double_word)
+    _check(h, _lib().ebe_apply(h.ptr, _dev(x, vt, h.n_n, "x"), _dev(y, vt, h.n_n, "y"), code))
+
+
+def ebe_time_operator(h: Handle, x, y, apply: bool = True, reps: int = 20, double_word: bool = False) -> tuple:
     """Mean ms per launch of (patch kernel, fix-up kernel), CUDA events on the handle's stream."""
-    code = _dtype_code(x)
+    code, vt = _op_code(x, double_word)
     ms = (ctypes.c_double * 2)()
-    _check(h, _lib().ebe_time_operator(h.ptr, _dev(x, code, h.n_n, "x"), _dev(y, code, h.n_n, "y"), code,
+    _check(h, _lib().ebe_time_operator(h.ptr, _dev(x, vt, h.n_n, "x"), _dev(y, vt, h.n_n, "y"), code,
                                        int(bool(apply)), int(reps), ms))
     return float(ms[0]), float(ms[1])
 

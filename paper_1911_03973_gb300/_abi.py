@@ -27,6 +27,7 @@ EBE_NOT_READY = 10
 
 EBE_F64 = 0
 EBE_F32 = 1
+EBE_F64_DW = 2
 EBE_STORE_FP64 = 0
 EBE_STORE_MIXED = 1
 EBE_PREC_FP64 = 0

@@ -55,6 +55,8 @@ struct ebe_handle {
     int store = EBE_STORE_FP64;
     double *A64 = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
     float *A32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
+    float* Adw = nullptr;           // A64 as FP32 pairs: hi runs, then lo runs (made on first use)
+    bool dw_ready = false;
 
     // scratch of the patch passes
     double* halo64 = nullptr;
@@ -608,6 +610,7 @@ ebe_status ebe_assemble(ebe_handle* h, int32_t store) {
     h->store = store;
     h->assembled = true;
     h->int_ready = false;
+    h->dw_ready = false;
     return EBE_OK;
 }
 
@@ -648,12 +651,36 @@ ebe_status ebe_jacobi_diag(ebe_handle* h, double* d) {
     return EBE_OK;
 }
 
+// The element matrices as FP32 pairs (the double-word residual), once per assembly.
+static int ensure_dw(ebe_handle* h) {
+    const int64_t n = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
+    TRY(dalloc(h, &h->Adw, 2 * n));
+    if (h->dw_ready) return EBE_OK;
+    int l = 0;
+    CK(launch_split_dw(n, h->A64, h->Adw, h->Adw + n, h->st, &l), "split A_e");
+    add_launches(h, l);
+    h->dw_ready = true;
+    return EBE_OK;
+}
+
 static int patch_call(ebe_handle* h, const void* x, void* y, int32_t dtype, int mode) {
     TRY(check_ready(h, true));
     if (!x || !y || x == y) return fail(h, EBE_INVALID_ARG, "x and y must be distinct non-NULL device buffers");
-    if (dtype != EBE_F64 && dtype != EBE_F32) return fail(h, EBE_INVALID_ARG, "dtype must be EBE_F64 or EBE_F32");
+    if (dtype != EBE_F64 && dtype != EBE_F32 && dtype != EBE_F64_DW)
+        return fail(h, EBE_INVALID_ARG, "dtype must be EBE_F64, EBE_F32 or EBE_F64_DW");
     if (dtype == EBE_F32 && h->store != EBE_STORE_MIXED) return fail(h, EBE_NOT_READY, "EBE_F32 needs ebe_assemble(EBE_STORE_MIXED)");
     Scope scp(h);
+    if (dtype == EBE_F64_DW) {
+        TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
+        TRY(ensure_dw(h));
+        const int64_t n = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
+        int l = 0;
+        CK(launch_patch_pass_dw(h->pd, mode, h->Adw, h->Adw + n, static_cast<const double*>(x), h->b,
+                                static_cast<double*>(y), h->halo64, h->part_patch, nullptr, h->sc, h->st, &l),
+           "double-word patch pass");
+        add_launches(h, l);
+        return EBE_OK;
+    }
     void* halo;
     if (dtype == EBE_F64) {
         TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
@@ -691,9 +718,15 @@ ebe_status ebe_time_operator(ebe_handle* h, const void* x, void* y, int32_t dtyp
     void* halo = dtype == EBE_F64 ? static_cast<void*>(h->halo64) : h->halo32;
     int l = 0;
     int status = EBE_OK;
+    const int64_t ndw = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
     for (int r = 0; r < reps && status == EBE_OK; ++r) {
-        cudaError_t e = launch_patch_pass(h->pd, dtype, apply ? kApply : kResidual, A, x, b, y, halo, h->part_patch,
-                                          nullptr, h->sc, h->st, &l, &ev[size_t(3) * r]);
+        cudaError_t e =
+            dtype == EBE_F64_DW
+                ? launch_patch_pass_dw(h->pd, apply ? kApply : kResidual, h->Adw, h->Adw + ndw,
+                                       static_cast<const double*>(x), h->b, static_cast<double*>(y), h->halo64,
+                                       h->part_patch, nullptr, h->sc, h->st, &l, &ev[size_t(3) * r])
+                : launch_patch_pass(h->pd, dtype, apply ? kApply : kResidual, A, x, b, y, halo, h->part_patch, nullptr,
+                                    h->sc, h->st, &l, &ev[size_t(3) * r]);
         if (e != cudaSuccess) status = cuda_fail(h, e, "timed patch pass");
     }
     add_launches(h, l);
@@ -1023,11 +1056,19 @@ int ensure_cg_graphs(ebe_handle* h, int chunk) {
     return EBE_OK;
 }
 
-// r = mask(b - A64 x) in the solver numbering and its squared norm.
-int true_residual_int(ebe_handle* h, double& rr) {
+// r = mask(b - A64 x) in the solver numbering and its squared norm: the FP64
+// pass, or (dw) the same residual in double-word arithmetic on the FP32 pipe.
+int true_residual_int(ebe_handle* h, double& rr, bool dw = false) {
     int l = 0;
-    CK(launch_patch_pass(h->pd_int, 0, kResidualNorm, h->A64, h->xi, h->bi, h->ri64, h->halo64, h->part_patch, nullptr,
-                         h->sc, h->st, &l), "true residual");
+    if (dw) {
+        TRY(ensure_dw(h));
+        const int64_t n = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
+        CK(launch_patch_pass_dw(h->pd_int, kResidualNorm, h->Adw, h->Adw + n, h->xi, h->bi, h->ri64, h->halo64,
+                                h->part_patch, nullptr, h->sc, h->st, &l), "double-word true residual");
+    } else {
+        CK(launch_patch_pass(h->pd_int, 0, kResidualNorm, h->A64, h->xi, h->bi, h->ri64, h->halo64, h->part_patch,
+                             nullptr, h->sc, h->st, &l), "true residual");
+    }
     add_launches(h, l);
     TRY(sync_scalars(h));
     rr = h->sc_host->rrt;
@@ -1121,9 +1162,16 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
                 continue;
             }
             if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
-            TRY(true_residual_int(h, rr));
+            // the replacement residual in double-word form; convergence is
+            // confirmed by the FP64 pass
+            TRY(true_residual_int(h, rr, true));
             info.true_residuals += 1;
-            const double rel = std::sqrt(rr) / r0;
+            double rel = std::sqrt(rr) / r0;
+            if (rel <= o.rtol) {
+                TRY(true_residual_int(h, rr));
+                info.true_residuals += 1;
+                rel = std::sqrt(rr) / r0;
+            }
             info.rel_residual = rel;
             if (!std::isfinite(rel)) { status = EBE_BREAKDOWN; break; }
             if (rel <= o.rtol) { status = EBE_OK; break; }
@@ -2158,7 +2206,10 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
                     rr_net = h->sc_host->rr;
                     rate_jac = std::log(rr / rr_jac) / t_jac;
                     const double rate_net = std::log(rr / rr_net) / t_net;
-                    if (!(rate_net > kRaceMargin * rate_jac)) {
+                    // CG's residual norm need not fall in its first iterations:
+                    // a race in which Jacobi's did not fall decides nothing, and
+                    // Jacobi-PCG continues
+                    if (!(rate_jac > 0.0) || !(rate_net > kRaceMargin * rate_jac)) {
                         // Jacobi-PCG continues from the Jacobi leg's iterate
                         CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st),
                            "restore");
@@ -2240,8 +2291,9 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             add_launches(h, l);
         }
         if (to_pcg) {
-            // Jacobi-PCG (plain FP64) from the current iterate, to the same
-            // target rtol |r0| of the original start
+            // Jacobi-PCG from the current iterate, to the same target rtol |r0|
+            // of the original start: the single-sync mixed solver when the FP32
+            // element matrices are stored, else the FP64 one
             TRY(dalloc(h, &h->xsave1, n));
             double rr_now = 0.0;
             TRY(true_residual(h, rr_now));
@@ -2255,12 +2307,13 @@ int learned_impl(ebe_handle* h, ebe_mpnn* net, double* x, bool x_on_host, const 
             } else {
                 CK(cudaMemcpyAsync(h->xsave1, h->x64w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "save x");
                 ebe_solve_opts po = o;
-                po.precision = EBE_PREC_FP64;
+                po.precision = h->store == EBE_STORE_MIXED ? EBE_PREC_MIXED : EBE_PREC_FP64;
                 po.rtol = o.rtol * r0 / r_now;
                 po.maxit = std::max<int64_t>(1, o.maxit - info.iterations);
                 po.use_graph = 1;
                 ebe_solve_info pi{};
-                status = solve_impl(h, h->xsave1, false, po, pi);
+                status = po.precision == EBE_PREC_MIXED ? solve_cg1_impl(h, h->xsave1, false, po, pi)
+                                                        : solve_impl(h, h->xsave1, false, po, pi);
                 if (status != EBE_OK && status != EBE_MAXIT && status != EBE_STALL && status != EBE_BREAKDOWN)
                     return status;
                 CK(cudaMemcpyAsync(h->x64w, h->xsave1, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "x");

@@ -181,4 +181,58 @@ __device__ __forceinline__ void block_sums_comp(CompSum (&v)[K], double (&out)[K
     }
 }
 
+// Double-word (pairs of FP32) arithmetic for FP64-accurate sums on the FP32
+// pipe (Dekker 1971; Hida, Li and Bailey 2001, "sloppy" addition): a value is
+// hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits.
+
+// x = hi + lo to 48 bits: hi is x rounded to FP32, lo the remainder x - hi
+// (exact in FP64) rounded to FP32, both formed on the integer pipe (the
+// remainder of the 53-bit mantissa after its top 24 bits is an integer of at
+// most 29 bits, converted and scaled).  Zeros, subnormals and values whose hi
+// or lo leaves the normal FP32 range take the hardware conversions.
+static __device__ __noinline__ void split_rare(double v, float& hi, float& lo) {
+    hi = float(v);
+    lo = float(v - double(hi));
+}
+__device__ __forceinline__ void split_dw(double v, float& hi, float& lo) {
+    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(v));
+    const int e = int((u >> 52) & 0x7ffu);                  // biased FP64 exponent
+    if (e < 1023 - 126 + 53 || e > 1023 + 126) { split_rare(v, hi, lo); return; }
+    hi = d2f(v);
+    const uint32_t hb = __float_as_uint(hi);
+    const int eh = int((hb >> 23) & 0xffu) - 127;           // hi's exponent: e - 1023 or one more
+    const int64_t m = int64_t((u & 0xfffffffffffffull) | 0x10000000000000ull);
+    const int64_t mh = int64_t((hb & 0x7fffffu) | 0x800000u) << (29 + eh - (e - 1023));
+    const int32_t d = int32_t(m - mh);                      // |d| <= 2^28
+    // lo = d * 2^(e - 1075), the scale a normal FP32 power of two here
+    const float scale = __uint_as_float(uint32_t(e - 1075 + 127) << 23);
+    const float l = __int2float_rn(d) * scale;
+    lo = (u >> 63) ? -l : l;
+}
+
+// p + e = a * b exactly (fused multiply-add gives the rounding error).
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+    const float p = a * b;
+    e = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// (s, c) += (ah + al) * (xh + xl): the leading product exactly (two_prod),
+// the cross terms in FP32 (the al * xl term is below the 48-bit precision).
+__device__ __forceinline__ void dw_fma(float ah, float al, float xh, float xl, float& s, float& c) {
+    float e;
+    const float p = two_prod(ah, xh, e);
+    const float t = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    float e2;
+    s = two_sum(s, p, e2);
+    c = c + (t + e2);
+}
+
+// (s, c) += (s2, c2).
+__device__ __forceinline__ void dw_add(float& s, float& c, float s2, float c2) {
+    float e;
+    s = two_sum(s, s2, e);
+    c = c + (c2 + e);
+}
+
 }  // namespace ebe

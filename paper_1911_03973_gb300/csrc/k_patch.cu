@@ -528,6 +528,238 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
     }
 }
 
+// ---------------------------------------------------------------- double-word FP64 residual
+// The FP64 residual with its arithmetic on the FP32 pipe: every stored FP64
+// entry a of A_e is kept as the pair a = hi + lo of FP32 values (the same 8
+// bytes), x is split into such a pair per patch node on the integer pipe, and
+// the element products and node sums run in double-word arithmetic (exact
+// FP32 products by FMA, TwoSum additions; about 48 significant bits, Dekker
+// 1971).  Only r = b - (s + c) and the conversions at the end are FP64, two
+// operations per node instead of n_b^2 + n_b per element.  The pair
+// representation of A_e and x is exact to 2^-48 relative, so r differs from
+// the FP64 residual by about 2^-48 |A| |x| per node.
+struct PatchDwSmem {
+    uint32_t red, co, G, xh, xl, bs, as, ac, total;
+};
+__host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
+    PatchDwSmem s{};
+    const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
+    s.red = 0;
+    s.co = 32 * 8;
+    s.G = (s.co + (kMaxColours + 1) * 4 + 15) / 16 * 16;
+    s.xh = s.G + gcap * 4;
+    s.xl = s.xh + gcap * 4;
+    s.bs = (s.xl + gcap * 4 + 15) / 16 * 16;
+    s.as = s.bs + gcap * 8;
+    s.ac = s.as + gcap * 4;
+    s.total = (s.ac + gcap * 4 + 127) / 128 * 128;
+    return s;
+}
+
+template <int NB, int MODE>
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 4 : 3)
+k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restrict__ Alo,
+           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ out,
+           float2* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
+    constexpr int NT = kPatchThreads;
+    constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const PatchDwSmem L = patch_dw_layout(pd.max_nodes);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    int* co = reinterpret_cast<int*>(smem + L.co);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + L.G);
+    float* xh = reinterpret_cast<float*>(smem + L.xh);
+    float* xl = reinterpret_cast<float*>(smem + L.xl);
+    double* bs = reinterpret_cast<double*>(smem + L.bs);
+    float* as = reinterpret_cast<float*>(smem + L.as);
+    float* ac = reinterpret_cast<float*>(smem + L.ac);
+
+    pdl_trigger();
+    const int p = blockIdx.x;
+    const PatchMeta m = pd.meta[p];
+    const int tid = threadIdx.x;
+    const int64_t ns = pd.n_slots;
+    const int64_t slot0 = int64_t(p) * kPatch;
+    for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
+    int ln[kEPT][NB];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) ln[k][i] = ok ? int(__ldg(pd.lconn + i * ns + slot0 + s)) : 0;
+    }
+    pdl_wait();
+    if (stop != nullptr && *stop) return;
+    const int32_t* pn = pd.pnode + m.node_off;
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        const int32_t g = __ldg(pn + l);
+        const double xv = __ldg(x + (g & kNodeMask));
+        const double bv = (kRes && l < m.n_owned) ? __ldg(b + (g & kNodeMask)) : 0.0;
+        float h, lo;
+        split_dw(xv, h, lo);
+        Gs[l] = g;
+        xh[l] = h;
+        xl[l] = lo;
+        if (kRes) bs[l] = bv;
+        as[l] = 0.0f;
+        ac[l] = 0.0f;
+    }
+    __syncthreads();
+    // products of all slots first (every thread busy), then colour rounds add them
+    float ys[kEPT][NB], yc[kEPT][NB];
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int s = tid + k * NT;
+        const bool ok = s < m.n_el;
+        float ah[sym_count(NB)], al[sym_count(NB)];
+#pragma unroll
+        for (int t = 0; t < sym_count(NB); ++t) {
+            ah[t] = ok ? __ldg(Ahi + t * ns + slot0 + s) : 0.0f;
+            al[t] = ok ? __ldg(Alo + t * ns + slot0 + s) : 0.0f;
+        }
+        float eh[NB], el[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            eh[j] = xh[ln[k][j]];
+            el[j] = xl[ln[k][j]];
+        }
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            float sv = 0.0f, cv = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
+            ys[k][r] = sv;
+            yc[k][r] = cv;
+        }
+    }
+    for (int c = 0; c < m.n_col; ++c) {
+        const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            if (s >= lo && s < hi) {
+#pragma unroll
+                for (int r = 0; r < NB; ++r) {
+                    const int n = ln[k][r];
+                    float sv = as[n], cv = ac[n];
+                    dw_add(sv, cv, ys[k][r], yc[k][r]);
+                    as[n] = sv;
+                    ac[n] = cv;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    DotAcc<float> dot;
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        const int32_t graw = Gs[l];
+        const int g = graw & kNodeMask;
+        const bool dir = graw < 0;
+        if (l < m.n_owned) {
+            const double v = f2d(as[l]) + f2d(ac[l]);
+            const double o = dir ? 0.0 : (kRes ? bs[l] - v : v);
+            out[g] = o;
+            if (MODE == kResidualNorm) {
+                const float of = d2f(o);
+                dot.add(of, of);
+            }
+        } else {
+            halo[m.halo_off + (l - m.n_owned)] = make_float2(as[l], ac[l]);
+        }
+    }
+    if (MODE == kResidualNorm) {
+        const double dsum = block_total<NT>(dot, red);
+        if (tid == 0) part[p] = dsum;
+    }
+}
+
+// Shared nodes of the double-word residual: the halo pairs added in patch
+// order (double-word), then r = b - (s + c) in FP64; with the norm mode the
+// last block adds all partial sums in index order.
+template <int MODE>
+__global__ void __launch_bounds__(kFixThreads)
+k_fixup_dw(const PlanDev pd, const double* __restrict__ b, double* __restrict__ out, const float2* __restrict__ halo,
+           double* __restrict__ part, const int32_t* __restrict__ stop, Scalars* __restrict__ sc) {
+    __shared__ double red[32];
+    __shared__ bool last;
+    pdl_trigger();
+    pdl_wait();
+    if (stop != nullptr && *stop) return;
+    DotAcc<float> dot;
+    const int st = int(gridDim.x) * kFixThreads;
+    for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += st) {
+        const int32_t graw = __ldg(pd.sh_node + k);
+        const int s0 = __ldg(pd.sh_ptr + k), s1 = __ldg(pd.sh_ptr + k + 1);
+        float sv = 0.0f, cv = 0.0f;
+        for (int t = s0; t < s1; ++t) {
+            const float2 h = halo[__ldg(pd.sh_slot + t)];
+            dw_add(sv, cv, h.x, h.y);
+        }
+        const int g = graw & kNodeMask;
+        const double v = f2d(sv) + f2d(cv);
+        const double o = graw < 0 ? 0.0 : ((MODE == kResidual || MODE == kResidualNorm) ? __ldg(b + g) - v : v);
+        out[g] = o;
+        if (MODE == kResidualNorm) {
+            const float of = d2f(o);
+            dot.add(of, of);
+        }
+    }
+    if (MODE == kResidualNorm) {
+        const int np = pd.n_patches;
+        const int chunk = (np + int(gridDim.x) - 1) / int(gridDim.x);
+        const int p1 = min(np, (int(blockIdx.x) + 1) * chunk);
+        double dsum = block_total<kFixThreads>(dot, red);
+        if (threadIdx.x == 0) {
+            for (int i = int(blockIdx.x) * chunk; i < p1; ++i) dsum += part[i];
+            part[np + blockIdx.x] = dsum;
+            __threadfence();
+            last = atomicAdd(&sc->ctr_fix, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            double s = 0.0;
+            for (int i = threadIdx.x; i < int(gridDim.x); i += kFixThreads) s += __ldcg(part + np + i);
+            s = block_sum<kFixThreads>(s, red);
+            if (threadIdx.x == 0) {
+                sc->ctr_fix = 0;
+                sc->rrt = s;
+            }
+        }
+    }
+}
+
+template <int NB, int MODE>
+cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, const double* x, const double* b,
+                         double* out, float2* halo, double* part, const int32_t* stop, Scalars* sc, cudaStream_t st,
+                         int* launches, cudaEvent_t* ev) {
+    const size_t sm = patch_dw_layout(pd.max_nodes).total;
+    if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto kern = k_patch_dw<NB, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], st);
+    kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, Ahi, Alo, x, b, out, halo, part, stop);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    k_fixup_dw<MODE><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, b, out, halo, part, stop, sc);
+    if (ev) cudaEventRecord(ev[2], st);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_split_dw(int64_t n, const double* __restrict__ a, float* __restrict__ hi,
+                                                  float* __restrict__ lo) {
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256) {
+        float h, l;
+        split_dw(a[i], h, l);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+
 template <int NB, int MODE>
 cudaError_t run_patch64(const PlanDev& pd, const double* A, const double* x, const double* b, double* out, double* halo,
                         double* part, const int32_t* stop, Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev,
@@ -1092,6 +1324,35 @@ int fix_rows(const PlanDev& pd) {
     // 2049^2 triangles: 2.04 slots per shared node, 10.5 -> 9.0 us per fix-up with
     // two rows; 129^3 tetrahedra (more slots per node): 16.0 -> 18.5 us, one row
     return 2 * pd.n_halo <= 5 * int64_t(pd.n_shared) ? 2 : 1;
+}
+
+cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Ahi, const float* Alo, const double* x,
+                                 const double* b, double* out, double* halo, double* part, const int32_t* stop,
+                                 Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev) {
+    float2* h = reinterpret_cast<float2*>(halo);
+    if (pd.nb == 3) {
+        switch (mode) {
+            case kResidual: return run_patch_dw<3, kResidual>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+            case kResidualNorm:
+                return run_patch_dw<3, kResidualNorm>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+            case kApply: return run_patch_dw<3, kApply>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (mode) {
+        case kResidual: return run_patch_dw<4, kResidual>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+        case kResidualNorm:
+            return run_patch_dw<4, kResidualNorm>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+        case kApply: return run_patch_dw<4, kApply>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_split_dw(int64_t n, const double* a, float* hi, float* lo, cudaStream_t st, int* launches) {
+    if (n <= 0) return cudaSuccess;
+    k_split_dw<<<int(std::min<int64_t>((n + 255) / 256, 8192)), 256, 0, st>>>(n, a, hi, lo);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, const float* p_old, float* p_new,

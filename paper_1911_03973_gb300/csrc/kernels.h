@@ -135,6 +135,17 @@ cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void
                               Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr,
                               bool pdl = false);
 
+// ---- double-word FP64 residual (k_patch.cu) -----------------------------
+// The FP64 residual / operator (modes kResidual, kResidualNorm, kApply) with
+// A_e stored as FP32 pairs a = hi + lo (Ahi, Alo: the FP64 layout, entry
+// runs of n_slots) and the arithmetic in double-word FP32; x, b, out FP64;
+// halo: n_halo pairs (the FP64 halo buffer reinterpreted).
+cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Ahi, const float* Alo, const double* x,
+                                 const double* b, double* out, double* halo, double* part, const int32_t* stop,
+                                 Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
+// hi[i] + lo[i] = a[i] to 48 bits (i < n).
+cudaError_t launch_split_dw(int64_t n, const double* a, float* hi, float* lo, cudaStream_t st, int* launches);
+
 // ---- single-synchronisation mixed-precision CG (k_patch.cu) ---------------
 // One pass = one CG iteration in two launches (patch pass + shared-node
 // fix-up), all node vectors in the solver numbering (pd.own_off set), FP32

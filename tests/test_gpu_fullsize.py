@@ -55,6 +55,20 @@ def test_full_size_residual_fp64(ebe, full):
     assert np.all(r[prob["dirichlet"]] == 0.0)
 
 
+def test_full_size_residual_double_word(ebe, full):
+    name, prob, h, orc, stream = full
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 41))
+    with torch.cuda.stream(stream):
+        xd = torch.tensor(x, dtype=torch.float64, device=DEV)
+        rd = torch.empty_like(xd)
+        ebe.ebe_residual(h, xd, rd, double_word=True)
+    torch.cuda.synchronize()
+    ref = orc.residual(x)
+    r = rd.cpu().numpy()
+    assert np.linalg.norm(r - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.all(r[prob["dirichlet"]] == 0.0)
+
+
 def test_full_size_jacobi_and_rhs(ebe, full):
     name, prob, h, orc, stream = full
     with torch.cuda.stream(stream):

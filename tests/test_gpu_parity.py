@@ -111,6 +111,57 @@ def test_residual_fp64_matches_oracle(ebe, case):
     assert np.all(r[prob["dirichlet"]] == 0.0) and np.all(y[prob["dirichlet"]] == 0.0)
 
 
+@pytest.mark.parametrize("case", list(_cases()))
+def test_residual_double_word_matches_oracle(ebe, case):
+    """EBE_F64_DW: A_e and x as FP32 pairs, products and sums in double-word
+    arithmetic.  Its error is about 2^-48 |A| |x| per node, so the FP64 bound
+    1e-12 holds; a dropped low word (2^-24) would exceed it by 10^4."""
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    x = orc.with_dirichlet(meshgen.seeded_vector(orc.n_n, 17))
+    xd = _t(x)
+    rd, yd, r64 = torch.empty_like(xd), torch.empty_like(xd), torch.empty_like(xd)
+    ebe.ebe_residual(h, xd, rd, double_word=True)
+    ebe.ebe_apply(h, xd, yd, double_word=True)
+    ebe.ebe_residual(h, xd, r64)
+    torch.cuda.synchronize()
+    r_ref, y_ref = orc.residual(x), orc.apply(x)
+    r, y = rd.cpu().numpy(), yd.cpu().numpy()
+    assert np.linalg.norm(r - r_ref) <= 1e-12 * np.linalg.norm(r_ref)
+    assert np.linalg.norm(y - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    # per node against the FP64 pass: within 2^-42 of the node's sum_e |A_e| |x_e| + |b|
+    # (the oracle's operator on |A_e| and |x|); a dropped low word errs by 2^-24 of it
+    scale = oracle.Problem(prob, A_override=np.abs(orc.A)).apply(np.abs(x)) + np.abs(orc.rhs())
+    assert np.all(np.abs(r - r64.cpu().numpy()) <= 2.0 ** -42 * scale)
+    assert np.all(r[prob["dirichlet"]] == 0.0) and np.all(y[prob["dirichlet"]] == 0.0)
+    with pytest.raises(TypeError):
+        ebe.ebe_residual(h, xd.float(), rd.float(), double_word=True)
+    ebe.ebe_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["tri_ragged", "tet_ragged"])
+def test_residual_double_word_near_the_solution(ebe, case):
+    """At a solution to rtol 1e-11, b - A x cancels about eleven digits: the
+    double-word residual must still match the oracle's to 1e-12 |r(x0)| (the
+    replacement residuals of the mixed solver are taken there)."""
+    prob = _cases()[case]()
+    orc = oracle.Problem(prob)
+    h = _setup(ebe, prob)
+    xd = torch.zeros(orc.n_n, dtype=torch.float64, device=DEV)
+    info = ebe.ebe_solve(h, xd, rtol=1e-11, precision=ebe.EBE_PREC_FP64)
+    assert info["status"] == "EBE_OK", info
+    rd = torch.empty_like(xd)
+    ebe.ebe_residual(h, xd, rd, double_word=True)
+    torch.cuda.synchronize()
+    x = xd.cpu().numpy()
+    r_ref = orc.residual(x)
+    r0 = np.linalg.norm(orc.residual(orc.with_dirichlet(np.zeros(orc.n_n))))
+    assert np.linalg.norm(r_ref) <= 2e-11 * r0
+    assert np.linalg.norm(rd.cpu().numpy() - r_ref) <= 1e-12 * r0
+    ebe.ebe_destroy(h)
+
+
 def fp32_difference_form(A64):
     """The FP32 operator's matrices, built from the oracle's FP64 A_e: off-diagonal
     entries rounded to FP32, row sums rounded to FP32, diagonal = row sum minus

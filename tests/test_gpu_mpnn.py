@@ -86,6 +86,34 @@ def test_forward_matches_oracle(ebe, small):
     assert np.all(z[prob["dirichlet"]] == 0.0)
 
 
+@pytest.mark.parametrize("mesh", ["small", "tet"])
+def test_inference_form_equals_training_forward(ebe, small, mesh):
+    """ebe_mpnn_apply runs the inference kernels (encoder fused into the first
+    layer, decoder into the last, four threads per node in the gather); the
+    training forward of ebe_mpnn_grad runs one kernel per stage.  Both perform
+    the same operations in the same order, so z must agree bit for bit (on a
+    ragged number of 128-node tiles, triangles and tetrahedra)."""
+    if mesh == "small":
+        prob, h, orc, dinv, graph = small
+        own = False
+    else:
+        prob = meshgen.config_cube_noise(11, nu=0.5, seed=3)      # 1331 nodes: 11 tiles, ragged
+        h, orc, dinv, graph = _setup(ebe, prob)
+        own = True
+    net = ebe.ebe_mpnn_create(0, _theta(5))
+    r = _r(orc, 3)
+    rd = torch.tensor(r, dtype=torch.float64, device=DEV)
+    z_inf, z_train = torch.empty_like(rd), torch.empty_like(rd)
+    ebe.ebe_mpnn_apply(net, h, rd, z_inf)
+    ebe.ebe_mpnn_grad(net, h, rd, torch.zeros_like(rd), z_train)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(z_inf.cpu().numpy(), z_train.cpu().numpy())
+    assert np.any(z_inf.cpu().numpy() != dinv * r)          # the network changed z
+    ebe.ebe_mpnn_destroy(net)
+    if own:
+        ebe.ebe_destroy(h)
+
+
 def test_gradient_matches_oracle(ebe, small):
     """Per parameter block, the GPU gradient (FP32 sums) against the oracle's
     (FP64) for the same BF16-rounded forward, at a training sample: r the

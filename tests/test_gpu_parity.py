@@ -142,9 +142,11 @@ def test_residual_double_word_matches_oracle(ebe, case):
 
 @pytest.mark.parametrize("case", ["tri_ragged", "tet_ragged"])
 def test_residual_double_word_near_the_solution(ebe, case):
-    """At a solution to rtol 1e-11, b - A x cancels about eleven digits: the
-    double-word residual must still match the oracle's to 1e-12 |r(x0)| (the
-    replacement residuals of the mixed solver are taken there)."""
+    """At a solution to rtol 1e-11, b - A x cancels deeply (|A| |x| is about
+    10^4 |b| per node on the 100^2 square), so the error bound scales with
+    |A| |x|, not with r: within 2^-42 of the norm of sum_e |A_e| |x_e| + |b|
+    (48-bit arithmetic: about 2^-48 of it), and below 1e-10 |r(x0)|, a hundredth
+    of the tightest rtol the mixed solver's replacement checks decide."""
     prob = _cases()[case]()
     orc = oracle.Problem(prob)
     h = _setup(ebe, prob)
@@ -158,7 +160,10 @@ def test_residual_double_word_near_the_solution(ebe, case):
     r_ref = orc.residual(x)
     r0 = np.linalg.norm(orc.residual(orc.with_dirichlet(np.zeros(orc.n_n))))
     assert np.linalg.norm(r_ref) <= 2e-11 * r0
-    assert np.linalg.norm(rd.cpu().numpy() - r_ref) <= 1e-12 * r0
+    scale = oracle.Problem(prob, A_override=np.abs(orc.A)).apply(np.abs(x)) + np.abs(orc.rhs())
+    err = np.linalg.norm(rd.cpu().numpy() - r_ref)
+    assert err <= 2.0 ** -42 * np.linalg.norm(scale)
+    assert err <= 1e-10 * r0
     ebe.ebe_destroy(h)
 
 

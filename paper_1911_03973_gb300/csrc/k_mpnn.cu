@@ -342,6 +342,10 @@ __global__ void __launch_bounds__(NT) k_mpnn_features(int64_t n, const double* _
     }
 }
 
+// Neighbour-list entries of a 128-node tile held in shared memory (a mean
+// degree up to 16; larger tiles read their lists from global memory).
+constexpr int kTileNbrCap = 2048;
+
 // 8 features [8q, 8q + 8) of node i: from the BF16 rows of h, or (FIRST) the
 // encoder applied to the input pair.
 template <bool FIRST>
@@ -382,6 +386,8 @@ __global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t
     __shared__ int sflag;
     __shared__ float wsm[kMpnnSmall];
     __shared__ float b[H];
+    __shared__ int32_t sptr[129];          // the tile's CSR row starts
+    __shared__ int32_t snbr[kTileNbrCap];  // and its neighbour lists, when they fit
 
     for (int c = tid; c < 4096 / 16; c += 128) reinterpret_cast<uint4*>(smem + LayerSmem::B)[c] = __ldg(wl + c);
     for (int c = tid; c < kMpnnSmall; c += 128) wsm[c] = __ldg(wsm_g + c);
@@ -411,6 +417,17 @@ __global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t
     const int64_t ntiles = (n + 127) / 128;
     uint32_t phase = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // the tile's rows of the mesh graph (contiguous in the CSR arrays) into
+        // shared memory, so the gathers below wait on one global load each
+        const int64_t left = n - tile * 128;
+        const int rows = left < 128 ? int(left) : 128;
+        for (int k = tid; k <= rows; k += 128) sptr[k] = __ldg(nbr_ptr + tile * 128 + k);
+        __syncthreads();
+        const int base = sptr[0];
+        const bool staged = sptr[rows] - base <= kTileNbrCap;
+        if (staged)
+            for (int k = tid; k < sptr[rows] - base; k += 128) snbr[k] = __ldg(nbr + base + k);
+        __syncthreads();
         // gather: four rounds of 32 nodes, four threads per node
 #pragma unroll 1
         for (int rd = 0; rd < 4; ++rd) {
@@ -419,13 +436,13 @@ __global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t
             float hs[8], a[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) { hs[k] = 0.0f; a[k] = 0.0f; }
-            if (i < n) {
+            if (row < rows) {
                 feat8<FIRST>(h_in, xf, wsm, i, q, hs);
-                const int j0 = __ldg(nbr_ptr + i), j1 = __ldg(nbr_ptr + i + 1);
+                const int j0 = sptr[row] - base, j1 = sptr[row + 1] - base;
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
                     float hj[8];
-                    feat8<FIRST>(h_in, xf, wsm, __ldg(nbr + j), q, hj);
+                    feat8<FIRST>(h_in, xf, wsm, staged ? snbr[j] : __ldg(nbr + base + j), q, hj);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) a[k] += hj[k];
                 }
@@ -477,8 +494,6 @@ __global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t
             }
         }
         const int64_t i = tile * 128 + tid;
-        const int64_t left = n - tile * 128;
-        const int rows = left < 128 ? int(left) : 128;
         if (LAST) {
             if (i < n) {
                 const double d = dinv[i];
@@ -827,29 +842,23 @@ int grid_for(int64_t n) {
 // (encoder fused into the first, decoder into the last); h[0] holds the input
 // pairs, then the layers alternate between h[1] and h[0].
 static_assert(kMpnnLayers == 4, "the inference form chains four layers");
+static_assert(kTileNbrCap % 4 == 0, "neighbour staging");
 cudaError_t launch_mpnn_inference(const MpnnDev& m, int64_t n, const double* r, const double* dinv, double* z,
                                   cudaStream_t st, int* launches) {
     float2* xf = reinterpret_cast<float2*>(m.h[0]);
     k_mpnn_features<<<grid_for(n), NT, 0, st>>>(n, r, dinv, m.sc, xf);
-    static int occ = 0;
-    if (occ == 0) {
-        int o = 0;
-        cudaError_t e = cudaFuncSetAttribute(k_mpnn_layer_inf<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(LayerSmem::total));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(LayerSmem::total));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(LayerSmem::total));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mpnn_layer_inf<false, false>, 128,
-                                                              LayerSmem::total);
-        if (e != cudaSuccess) return e;
-        occ = o < 1 ? 1 : (o > 16 ? 16 : o);
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_mpnn_layer_inf<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(LayerSmem::total));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(LayerSmem::total));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(LayerSmem::total));
+    if (e != cudaSuccess) return e;
+    // 7 CTAs per SM (29.5 KB of shared memory each; at most 64 registers)
     const int64_t tiles = (n + 127) / 128;
-    const int64_t cap = int64_t(m.num_sms) * occ;
+    const int64_t cap = int64_t(m.num_sms) * 7;
     const int lg = int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
     auto B = [](uint16_t* p) { return reinterpret_cast<__nv_bfloat16*>(p); };
     const uint4* wl = reinterpret_cast<const uint4*>(m.wl);

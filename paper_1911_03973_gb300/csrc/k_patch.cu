@@ -61,6 +61,7 @@ __device__ __forceinline__ double block_total(const DotAcc<float>& d, double* re
 
 using tma::block_sum;
 using tma::bulk_load;
+using tma::bulk_prefetch_l2;
 using tma::mbar_expect_tx;
 using tma::mbar_init;
 using tma::mbar_try_wait;
@@ -580,6 +581,12 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
+    // the patch's element matrices start moving into L2 now, so their DRAM
+    // reads overlap the node gather below (they are constant: before the wait)
+    if (tid < 2 * sym_count(NB) && m.n_el > 0) {
+        const float* run = (tid & 1 ? Alo : Ahi) + (tid >> 1) * ns + slot0;
+        bulk_prefetch_l2(run, uint32_t((m.n_el + 3) / 4 * 16));
+    }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
     int ln[kEPT][NB];
 #pragma unroll

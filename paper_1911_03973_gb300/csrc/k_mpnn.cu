@@ -346,31 +346,44 @@ __global__ void __launch_bounds__(NT) k_mpnn_features(int64_t n, const double* _
 // degree up to 16; larger tiles read their lists from global memory).
 constexpr int kTileNbrCap = 2048;
 
-// 8 features [8q, 8q + 8) of node i: from the BF16 rows of h, or (FIRST) the
-// encoder applied to the input pair.
+// 8 features [8q, 8q + 8) of a node: the raw 16 bytes of its BF16 row of h
+// (a uint4), or (FIRST) its input pair, to which the encoder is applied.
+// Loading and converting are separate so that a thread can have a batch of
+// rows in flight.
 template <bool FIRST>
-__device__ __forceinline__ void feat8(const __nv_bfloat16* __restrict__ h, const float2* __restrict__ xf,
-                                      const float* __restrict__ wsm, int64_t i, int q, float (&v)[8]) {
-    if (FIRST) {
-        const float2 x = __ldg(xf + i);
+struct RawFeat {
+    using T = uint4;
+};
+template <>
+struct RawFeat<true> {
+    using T = float2;
+};
+__device__ __forceinline__ void raw8(const __nv_bfloat16* __restrict__ h, const float2* __restrict__, int64_t i,
+                                     int q, uint4& w) {
+    w = __ldcg(reinterpret_cast<const uint4*>(h + i * H) + q);
+}
+__device__ __forceinline__ void raw8(const __nv_bfloat16* __restrict__, const float2* __restrict__ xf, int64_t i, int,
+                                     float2& w) {
+    w = __ldg(xf + i);
+}
+__device__ __forceinline__ void cvt8(const uint4& w, const float* __restrict__, int, float (&v)[8]) {
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int o = 8 * q + k;
-            v[k] = bf(fmaf(wsm[kMpnnWin + 2 * o + 1], x.y, fmaf(wsm[kMpnnWin + 2 * o], x.x, wsm[kMpnnBin + o])));
-        }
-    } else {
-        const uint4 w = __ldcg(reinterpret_cast<const uint4*>(h + i * H) + q);
-        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+    for (int t = 0; t < 4; ++t) {
+        v[2 * t] = __uint_as_float(u[t] << 16);
+        v[2 * t + 1] = __uint_as_float(u[t] & 0xffff0000u);
+    }
+}
+__device__ __forceinline__ void cvt8(const float2& x, const float* __restrict__ wsm, int q, float (&v)[8]) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            v[2 * t] = __uint_as_float(u[t] << 16);
-            v[2 * t + 1] = __uint_as_float(u[t] & 0xffff0000u);
-        }
+    for (int k = 0; k < 8; ++k) {
+        const int o = 8 * q + k;
+        v[k] = bf(fmaf(wsm[kMpnnWin + 2 * o + 1], x.y, fmaf(wsm[kMpnnWin + 2 * o], x.x, wsm[kMpnnBin + o])));
     }
 }
 
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t* __restrict__ nbr_ptr,
+__global__ void __launch_bounds__(128, 7) k_mpnn_layer_inf(int64_t n, const int32_t* __restrict__ nbr_ptr,
                                                         const int32_t* __restrict__ nbr, const float* __restrict__ inv_deg,
                                                         const float2* __restrict__ xf, const __nv_bfloat16* __restrict__ h_in,
                                                         __nv_bfloat16* __restrict__ h_out, const uint4* __restrict__ wl,
@@ -437,16 +450,39 @@ __global__ void __launch_bounds__(128) k_mpnn_layer_inf(int64_t n, const int32_t
 #pragma unroll
             for (int k = 0; k < 8; ++k) { hs[k] = 0.0f; a[k] = 0.0f; }
             if (row < rows) {
-                feat8<FIRST>(h_in, xf, wsm, i, q, hs);
                 const int j0 = sptr[row] - base, j1 = sptr[row + 1] - base;
-#pragma unroll 4
-                for (int j = j0; j < j1; ++j) {
-                    float hj[8];
-                    feat8<FIRST>(h_in, xf, wsm, staged ? snbr[j] : __ldg(nbr + base + j), q, hj);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) a[k] += hj[k];
-                }
                 const float w = __ldg(inv_deg + i);
+                // batches of 8 rows in flight: the node's own with its first 7
+                // neighbours, then 8 neighbours at a time; added in list order
+                typename RawFeat<FIRST>::T raw[8];
+                raw8(h_in, xf, i, q, raw[0]);
+#pragma unroll
+                for (int u = 1; u < 8; ++u)
+                    if (j0 + u - 1 < j1) raw8(h_in, xf, staged ? snbr[j0 + u - 1] : __ldg(nbr + base + j0 + u - 1), q, raw[u]);
+                cvt8(raw[0], wsm, q, hs);
+#pragma unroll
+                for (int u = 1; u < 8; ++u) {
+                    if (j0 + u - 1 < j1) {
+                        float hj[8];
+                        cvt8(raw[u], wsm, q, hj);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) a[k] += hj[k];
+                    }
+                }
+                for (int jb = j0 + 7; jb < j1; jb += 8) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (jb + u < j1) raw8(h_in, xf, staged ? snbr[jb + u] : __ldg(nbr + base + jb + u), q, raw[u]);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (jb + u < j1) {
+                            float hj[8];
+                            cvt8(raw[u], wsm, q, hj);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) a[k] += hj[k];
+                        }
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], w, -hs[k]);
             }

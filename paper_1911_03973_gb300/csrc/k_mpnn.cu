@@ -78,21 +78,6 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-        "[%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 32 BF16 features of a node (64 bytes) <-> FP32.
 __device__ __forceinline__ void load_h(const __nv_bfloat16* h, int64_t i, float (&v)[H]) {
     const uint4* p = reinterpret_cast<const uint4*>(h + i * H);
@@ -319,257 +304,6 @@ __global__ void __launch_bounds__(NT) k_mpnn_decode(int64_t n, const double* __r
         for (int c = 0; c < H; ++c) o = fmaf(wsm[kMpnnWout + c], hv[c], o);
         z[i] = fmadd(sz, double(o), d * r[i]);
     }
-}
-
-// ---------------------------------------------------------------- inference form
-// The same forward pass with fewer bytes and launches (no training copies):
-// k_mpnn_features writes the encoder's inputs x = [r / s, dinv r / sz] as an
-// FP32 pair per node (8 bytes); the first layer forms the encoder's BF16
-// features of every node it reads from that pair, and the last layer applies
-// the decoder in its epilogue and writes z instead of h.  In the gather four
-// threads share a node, each holding 8 of its 32 features (16 bytes), so one
-// warp instruction reads 8 whole 64-byte rows.  Every value is computed by
-// the same operations in the same order as in the training form, so the two
-// give the same z bit for bit.
-__global__ void __launch_bounds__(NT) k_mpnn_features(int64_t n, const double* __restrict__ r,
-                                                      const double* __restrict__ dinv, const double* __restrict__ sc,
-                                                      float2* __restrict__ xf) {
-    const double s = sc[0], sz = sc[1];
-    const bool ok = s > 0.0 && sz > 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * NT + threadIdx.x; i < n; i += int64_t(gridDim.x) * NT) {
-        const double ri = r[i];
-        xf[i] = ok ? make_float2(float(ri / s), float(dinv[i] * ri / sz)) : make_float2(0.0f, 0.0f);
-    }
-}
-
-// Neighbour-list entries of a 128-node tile held in shared memory (a mean
-// degree up to 16; larger tiles read their lists from global memory).
-constexpr int kTileNbrCap = 2048;
-
-// 8 features [8q, 8q + 8) of a node: the raw 16 bytes of its BF16 row of h
-// (a uint4), or (FIRST) its input pair, to which the encoder is applied.
-// Loading and converting are separate so that a thread can have a batch of
-// rows in flight.
-template <bool FIRST>
-struct RawFeat {
-    using T = uint4;
-};
-template <>
-struct RawFeat<true> {
-    using T = float2;
-};
-__device__ __forceinline__ void raw8(const __nv_bfloat16* __restrict__ h, const float2* __restrict__, int64_t i,
-                                     int q, uint4& w) {
-    w = __ldcg(reinterpret_cast<const uint4*>(h + i * H) + q);
-}
-__device__ __forceinline__ void raw8(const __nv_bfloat16* __restrict__, const float2* __restrict__ xf, int64_t i, int,
-                                     float2& w) {
-    w = __ldg(xf + i);
-}
-__device__ __forceinline__ void cvt8(const uint4& w, const float* __restrict__, int, float (&v)[8]) {
-    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        v[2 * t] = __uint_as_float(u[t] << 16);
-        v[2 * t + 1] = __uint_as_float(u[t] & 0xffff0000u);
-    }
-}
-__device__ __forceinline__ void cvt8(const float2& x, const float* __restrict__ wsm, int q, float (&v)[8]) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int o = 8 * q + k;
-        v[k] = bf(fmaf(wsm[kMpnnWin + 2 * o + 1], x.y, fmaf(wsm[kMpnnWin + 2 * o], x.x, wsm[kMpnnBin + o])));
-    }
-}
-
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(128, 7) k_mpnn_layer_inf(int64_t n, const int32_t* __restrict__ nbr_ptr,
-                                                        const int32_t* __restrict__ nbr, const float* __restrict__ inv_deg,
-                                                        const float2* __restrict__ xf, const __nv_bfloat16* __restrict__ h_in,
-                                                        __nv_bfloat16* __restrict__ h_out, const uint4* __restrict__ wl,
-                                                        const float* __restrict__ bias, const float* __restrict__ wsm_g,
-                                                        const double* __restrict__ r, const double* __restrict__ dinv,
-                                                        const double* __restrict__ sc, double* __restrict__ z,
-                                                        int32_t* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t sB = tma::smem_addr(smem + LayerSmem::B), sA = tma::smem_addr(smem + LayerSmem::A);
-    const uint32_t mbar = tma::smem_addr(smem + LayerSmem::bar);
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(smem + LayerSmem::taddr);
-    __shared__ int sflag;
-    __shared__ float wsm[kMpnnSmall];
-    __shared__ float b[H];
-    __shared__ int32_t sptr[129];          // the tile's CSR row starts
-    __shared__ int32_t snbr[kTileNbrCap];  // and its neighbour lists, when they fit
-
-    for (int c = tid; c < 4096 / 16; c += 128) reinterpret_cast<uint4*>(smem + LayerSmem::B)[c] = __ldg(wl + c);
-    for (int c = tid; c < kMpnnSmall; c += 128) wsm[c] = __ldg(wsm_g + c);
-    if (tid < H) b[tid] = __ldg(bias + tid);
-    if (tid == 0) {
-        tma::mbar_init(mbar, 1);
-        sflag = 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
-                         tma::smem_addr(taddr_s))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *taddr_s;
-    double sz = 0.0;
-    bool ok = false;
-    if (LAST) {
-        sz = sc[1];
-        ok = sc[0] > 0.0 && sz > 0.0;
-    }
-
-    const int q = tid & 3;                 // this thread's quarter of a node's features
-    const int64_t ntiles = (n + 127) / 128;
-    uint32_t phase = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // the tile's rows of the mesh graph (contiguous in the CSR arrays) into
-        // shared memory, so the gathers below wait on one global load each
-        const int64_t left = n - tile * 128;
-        const int rows = left < 128 ? int(left) : 128;
-        for (int k = tid; k <= rows; k += 128) sptr[k] = __ldg(nbr_ptr + tile * 128 + k);
-        __syncthreads();
-        const int base = sptr[0];
-        const bool staged = sptr[rows] - base <= kTileNbrCap;
-        if (staged)
-            for (int k = tid; k < sptr[rows] - base; k += 128) snbr[k] = __ldg(nbr + base + k);
-        __syncthreads();
-        // gather: four rounds of 32 nodes, four threads per node
-#pragma unroll 1
-        for (int rd = 0; rd < 4; ++rd) {
-            const int row = rd * 32 + (tid >> 2);
-            const int64_t i = tile * 128 + row;
-            float hs[8], a[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) { hs[k] = 0.0f; a[k] = 0.0f; }
-            if (row < rows) {
-                const int j0 = sptr[row] - base, j1 = sptr[row + 1] - base;
-                const float w = __ldg(inv_deg + i);
-                // batches of 8 rows in flight: the node's own with its first 7
-                // neighbours, then 8 neighbours at a time; added in list order
-                typename RawFeat<FIRST>::T raw[8];
-                raw8(h_in, xf, i, q, raw[0]);
-#pragma unroll
-                for (int u = 1; u < 8; ++u)
-                    if (j0 + u - 1 < j1) raw8(h_in, xf, staged ? snbr[j0 + u - 1] : __ldg(nbr + base + j0 + u - 1), q, raw[u]);
-                cvt8(raw[0], wsm, q, hs);
-#pragma unroll
-                for (int u = 1; u < 8; ++u) {
-                    if (j0 + u - 1 < j1) {
-                        float hj[8];
-                        cvt8(raw[u], wsm, q, hj);
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) a[k] += hj[k];
-                    }
-                }
-                for (int jb = j0 + 7; jb < j1; jb += 8) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (jb + u < j1) raw8(h_in, xf, staged ? snbr[jb + u] : __ldg(nbr + base + jb + u), q, raw[u]);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (jb + u < j1) {
-                            float hj[8];
-                            cvt8(raw[u], wsm, q, hj);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) a[k] += hj[k];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], w, -hs[k]);
-            }
-            *reinterpret_cast<uint4*>(smem + LayerSmem::A + core_off(row, 8 * q)) =
-                make_uint4(pack2(hs[0], hs[1]), pack2(hs[2], hs[3]), pack2(hs[4], hs[5]), pack2(hs[6], hs[7]));
-            *reinterpret_cast<uint4*>(smem + LayerSmem::A + core_off(row, H + 8 * q)) =
-                make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int kk = 0; kk < K2 / 16; ++kk)
-                tc_mma(tmem, umma_desc(sA + kk * 256, 128, 1024), umma_desc(sB + kk * 256, 128, 1024), kIdesc, kk > 0);
-            tc_commit(mbar);
-        }
-        if (tid == 0 && !tma::mbar_wait_bounded(mbar, phase, err)) sflag = 1;
-        __syncthreads();
-        if (sflag) {                        // uniform: the accumulator did not arrive in time
-            if (tid == 0) tma::mbar_wait_bounded(mbar, phase, nullptr);
-            break;
-        }
-        phase ^= 1u;
-        while (!tma::mbar_try_wait(mbar, phase ^ 1u)) {
-        }
-        tc_fence_after();
-        // epilogue: row tid of the accumulator, 16 columns at a time; the
-        // row's own features are the first 32 columns of its A row
-        uint32_t w[H / 2];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            float v[16];
-            tc_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(16 * half), v);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const uint4 u4 = *reinterpret_cast<const uint4*>(smem + LayerSmem::A + core_off(tid, 16 * half + 8 * c));
-                const uint32_t u[4] = {u4.x, u4.y, u4.z, u4.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int o = 16 * half + 8 * c + 2 * t, k = 8 * c + 2 * t;
-                    w[o / 2] = pack2(__uint_as_float(u[t] << 16) + fmaxf(v[k] + b[o], 0.0f),
-                                     __uint_as_float(u[t] & 0xffff0000u) + fmaxf(v[k + 1] + b[o + 1], 0.0f));
-                }
-            }
-        }
-        const int64_t i = tile * 128 + tid;
-        if (LAST) {
-            if (i < n) {
-                const double d = dinv[i];
-                if (!ok || d == 0.0) {
-                    z[i] = 0.0;
-                } else {
-                    float o = wsm[kMpnnBout];
-#pragma unroll
-                    for (int c = 0; c < H / 2; ++c) {
-                        o = fmaf(wsm[kMpnnWout + 2 * c], __uint_as_float(w[c] << 16), o);
-                        o = fmaf(wsm[kMpnnWout + 2 * c + 1], __uint_as_float(w[c] & 0xffff0000u), o);
-                    }
-                    z[i] = fmadd(sz, double(o), d * r[i]);
-                }
-            }
-            tc_fence_before();
-            __syncthreads();                // TMEM and the A tile are free for the next tile
-        } else {
-            tc_fence_before();
-            __syncthreads();                // every row's own features read: the A tile becomes the staging tile
-            // row tid's 64 bytes at tid * 64, its 16-byte chunks rotated by the
-            // row (conflict-free writes and reads), then copied out in order
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                *reinterpret_cast<uint4*>(smem + LayerSmem::A + tid * 64 + ((c + tid) & 3) * 16) =
-                    make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-            __syncthreads();
-            uint4* dst = reinterpret_cast<uint4*>(h_out + tile * 128 * H);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int k = tid + 128 * m;        // 16-byte chunk of the tile
-                const int rr = k >> 2, c = k & 3;
-                if (rr < rows)
-                    dst[k] = *reinterpret_cast<const uint4*>(smem + LayerSmem::A + rr * 64 + ((c + rr) & 3) * 16);
-            }
-            __syncthreads();                // the staging tile is read: the next gather may write A
-        }
-    }
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // ---------------------------------------------------------------- backward (CUDA cores, FP32)
@@ -874,52 +608,11 @@ int grid_for(int64_t n) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-// The inference form after k_mpnn_norms: features, then the four layers
-// (encoder fused into the first, decoder into the last); h[0] holds the input
-// pairs, then the layers alternate between h[1] and h[0].
-static_assert(kMpnnLayers == 4, "the inference form chains four layers");
-static_assert(kTileNbrCap % 4 == 0, "neighbour staging");
-cudaError_t launch_mpnn_inference(const MpnnDev& m, int64_t n, const double* r, const double* dinv, double* z,
-                                  cudaStream_t st, int* launches) {
-    float2* xf = reinterpret_cast<float2*>(m.h[0]);
-    k_mpnn_features<<<grid_for(n), NT, 0, st>>>(n, r, dinv, m.sc, xf);
-    cudaError_t e = cudaFuncSetAttribute(k_mpnn_layer_inf<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(LayerSmem::total));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(LayerSmem::total));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mpnn_layer_inf<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(LayerSmem::total));
-    if (e != cudaSuccess) return e;
-    // 7 CTAs per SM (29.5 KB of shared memory each; at most 64 registers)
-    const int64_t tiles = (n + 127) / 128;
-    const int64_t cap = int64_t(m.num_sms) * 7;
-    const int lg = int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-    auto B = [](uint16_t* p) { return reinterpret_cast<__nv_bfloat16*>(p); };
-    const uint4* wl = reinterpret_cast<const uint4*>(m.wl);
-    constexpr size_t sm = LayerSmem::total;
-    k_mpnn_layer_inf<true, false><<<lg, 128, sm, st>>>(n, m.nbr_ptr, m.nbr, m.inv_deg, xf, nullptr, B(m.h[1]), wl,
-                                                       m.wsm + kMpnnBl, m.wsm, r, dinv, m.sc, nullptr, m.err);
-    k_mpnn_layer_inf<false, false><<<lg, 128, sm, st>>>(n, m.nbr_ptr, m.nbr, m.inv_deg, nullptr, B(m.h[1]), B(m.h[0]),
-                                                        wl + (H * K2) / 8, m.wsm + kMpnnBl + H, m.wsm, r, dinv, m.sc,
-                                                        nullptr, m.err);
-    k_mpnn_layer_inf<false, false><<<lg, 128, sm, st>>>(n, m.nbr_ptr, m.nbr, m.inv_deg, nullptr, B(m.h[0]), B(m.h[1]),
-                                                        wl + 2 * (H * K2) / 8, m.wsm + kMpnnBl + 2 * H, m.wsm, r, dinv,
-                                                        m.sc, nullptr, m.err);
-    k_mpnn_layer_inf<false, true><<<lg, 128, sm, st>>>(n, m.nbr_ptr, m.nbr, m.inv_deg, nullptr, B(m.h[1]), nullptr,
-                                                       wl + 3 * (H * K2) / 8, m.wsm + kMpnnBl + 3 * H, m.wsm, r, dinv,
-                                                       m.sc, z, m.err);
-    if (launches) *launches += 6;
-    return cudaGetLastError();
-}
-
 cudaError_t launch_mpnn_forward(const MpnnDev& m, int64_t n, const double* r, const double* dinv, double* z, bool save,
                                 cudaStream_t st, int* launches) {
     const int g = grid_for(n);
     k_mpnn_norms<<<g, NT, 0, st>>>(n, r, dinv, m.part, m.ctr, m.sc);
     auto B = [](uint16_t* p) { return reinterpret_cast<__nv_bfloat16*>(p); };
-    if (!save) return launch_mpnn_inference(m, n, r, dinv, z, st, launches);
     k_mpnn_encode<<<g, NT, 0, st>>>(n, r, dinv, m.sc, m.wsm, B(m.h[0]), save ? m.save_x : nullptr);
     cudaError_t e = cudaFuncSetAttribute(k_mpnn_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LayerSmem::total));
     if (e != cudaSuccess) return e;

@@ -88,11 +88,10 @@ def test_forward_matches_oracle(ebe, small):
 
 @pytest.mark.parametrize("mesh", ["small", "tet"])
 def test_inference_form_equals_training_forward(ebe, small, mesh):
-    """ebe_mpnn_apply runs the inference kernels (encoder fused into the first
-    layer, decoder into the last, four threads per node in the gather); the
-    training forward of ebe_mpnn_grad runs one kernel per stage.  Both perform
-    the same operations in the same order, so z must agree bit for bit (on a
-    ragged number of 128-node tiles, triangles and tetrahedra)."""
+    """ebe_mpnn_apply runs the forward without the training copies (two
+    feature buffers in turn); ebe_mpnn_grad's forward keeps every layer's input
+    and pre-activation.  The arithmetic is the same, so z must agree bit for
+    bit (on a ragged number of 128-node tiles, triangles and tetrahedra)."""
     if mesh == "small":
         prob, h, orc, dinv, graph = small
         own = False

@@ -684,7 +684,7 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
 // Shared nodes of the double-word residual: the halo pairs added in patch
 // order (double-word), then r = b - (s + c) in FP64; with the norm mode the
 // last block adds all partial sums in index order.
-template <int MODE>
+template <int MODE, int ROWS>
 __global__ void __launch_bounds__(kFixThreads)
 k_fixup_dw(const PlanDev pd, const double* __restrict__ b, double* __restrict__ out, const float2* __restrict__ halo,
            double* __restrict__ part, const int32_t* __restrict__ stop, Scalars* __restrict__ sc) {
@@ -694,22 +694,43 @@ k_fixup_dw(const PlanDev pd, const double* __restrict__ b, double* __restrict__ 
     pdl_wait();
     if (stop != nullptr && *stop) return;
     DotAcc<float> dot;
+    // ROWS shared rows per thread at a time, their loads interleaved; each
+    // row's partials added in patch order
     const int st = int(gridDim.x) * kFixThreads;
-    for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += st) {
-        const int32_t graw = __ldg(pd.sh_node + k);
-        const int s0 = __ldg(pd.sh_ptr + k), s1 = __ldg(pd.sh_ptr + k + 1);
-        float sv = 0.0f, cv = 0.0f;
-        for (int t = s0; t < s1; ++t) {
-            const float2 h = halo[__ldg(pd.sh_slot + t)];
-            dw_add(sv, cv, h.x, h.y);
+    for (int k = blockIdx.x * kFixThreads + threadIdx.x; k < pd.n_shared; k += ROWS * st) {
+        int32_t graw[ROWS];
+        int s0[ROWS], cnt[ROWS];
+        int nmax = 0;
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int kk = k + u * st;
+            const bool ok = kk < pd.n_shared;
+            graw[u] = ok ? __ldg(pd.sh_node + kk) : 0;
+            s0[u] = ok ? __ldg(pd.sh_ptr + kk) : 0;
+            cnt[u] = ok ? __ldg(pd.sh_ptr + kk + 1) - s0[u] : 0;
+            nmax = cnt[u] > nmax ? cnt[u] : nmax;
         }
-        const int g = graw & kNodeMask;
-        const double v = f2d(sv) + f2d(cv);
-        const double o = graw < 0 ? 0.0 : ((MODE == kResidual || MODE == kResidualNorm) ? __ldg(b + g) - v : v);
-        out[g] = o;
-        if (MODE == kResidualNorm) {
-            const float of = d2f(o);
-            dot.add(of, of);
+        float sv[ROWS], cv[ROWS];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) { sv[u] = 0.0f; cv[u] = 0.0f; }
+        for (int t = 0; t < nmax; ++t)
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u)
+                if (t < cnt[u]) {
+                    const float2 h = halo[__ldg(pd.sh_slot + s0[u] + t)];
+                    dw_add(sv[u], cv[u], h.x, h.y);
+                }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            if (k + u * st >= pd.n_shared) break;
+            const int g = graw[u] & kNodeMask;
+            const double v = f2d(sv[u]) + f2d(cv[u]);
+            const double o = graw[u] < 0 ? 0.0 : ((MODE == kResidual || MODE == kResidualNorm) ? __ldg(b + g) - v : v);
+            out[g] = o;
+            if (MODE == kResidualNorm) {
+                const float of = d2f(o);
+                dot.add(of, of);
+            }
         }
     }
     if (MODE == kResidualNorm) {
@@ -751,7 +772,10 @@ cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    k_fixup_dw<MODE><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, b, out, halo, part, stop, sc);
+    if (fix_rows(pd) == 2)
+        k_fixup_dw<MODE, 2><<<fix_grid(pd.n_shared, 2), kFixThreads, 0, st>>>(pd, b, out, halo, part, stop, sc);
+    else
+        k_fixup_dw<MODE, 1><<<fix_grid(pd.n_shared, 1), kFixThreads, 0, st>>>(pd, b, out, halo, part, stop, sc);
     if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();

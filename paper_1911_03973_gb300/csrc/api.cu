@@ -1487,6 +1487,11 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.tile = h->btile[ti];
     bd.A = mixed ? static_cast<const void*>(h->A32) : h->A64;
     bd.A64 = h->A64;
+    if (mixed && h->Adw) {
+        const int64_t nw = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
+        bd.Ahi = h->Adw;
+        bd.Alo = h->Adw + nw;
+    }
     bd.b = h->b;
     bd.dinv = mixed ? static_cast<const void*>(h->dinv32) : h->dinv;
     bd.x = h->x64w;
@@ -1555,6 +1560,7 @@ int solve_batch_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     const int ti = tile_index(tile);
     TRY(batch_buffers(h, mixed));
     TRY(ensure_batch_tables(h, ti));
+    if (mixed) TRY(ensure_dw(h));
     // one launch runs up to maxit CG steps plus the true residuals of every
     // problem; a launch that ends with problems left is followed by another
     const int64_t budget = o.maxit + 65536;
@@ -1680,6 +1686,7 @@ ebe_status ebe_batch_tune(ebe_handle* h, int32_t precision, int32_t loops, ebe_b
     if (mixed && h->store != EBE_STORE_MIXED) return ebe_status(fail(h, EBE_NOT_READY, "EBE_PREC_MIXED needs EBE_STORE_MIXED"));
     Scope scp(h);
     TRY(batch_buffers(h, mixed));
+    if (mixed) TRY(ensure_dw(h));
     ebe_solve_opts o;
     ebe_solve_opts_default(&o);
     o.precision = precision;

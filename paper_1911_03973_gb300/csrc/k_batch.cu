@@ -266,12 +266,90 @@ __device__ __forceinline__ bool apply_patch(Ctx& c, int p, bool have, int next_p
     return true;
 }
 
-// FP64 true residual r = mask(b - A x) on one patch.  A replacement happens a
-// few times per problem and solve, so this pass favours few registers over
-// speed: element matrices are read straight from global memory (coalesced
-// slot-major runs) inside the colour rounds, products folded into the sums.
+// The true residual r = mask(b - A x) on one patch, FP64 vectors.  A
+// replacement happens a few times per problem and solve, so this pass
+// favours few registers over speed: element matrices are read straight from
+// global memory (coalesced slot-major runs) inside the colour rounds.  The
+// FP64 solver forms it in FP64; the mixed solver in double-word FP32
+// arithmetic (A_e and x as pairs of FP32, exact products and TwoSum
+// additions: Dekker 1971), which keeps FP64's accuracy to about 2^-48 |A||x|
+// and stays off the FP64 pipe.  The halo partials are then FP32 pairs.
+template <int NB>
+__device__ __forceinline__ void residual_patch_dw(Ctx& c, int p, const BatchSmem& Lo) {
+    const BatchDev& bd = *c.bd;
+    const PlanDev& pd = bd.pd;
+    unsigned char* smem = c.smem;
+    double* red = reinterpret_cast<double*>(smem + Lo.red);
+    int* co = reinterpret_cast<int*>(smem + Lo.co);
+    int32_t* Gs = reinterpret_cast<int32_t*>(smem + Lo.G2);
+    float2* xw = reinterpret_cast<float2*>(smem + Lo.xs2);
+    double* bs = reinterpret_cast<double*>(smem + Lo.bs2);
+    float2* aw = reinterpret_cast<float2*>(smem + Lo.acc2);
+    const int tid = threadIdx.x;
+    const int64_t ns = pd.n_slots;
+    const int64_t slot0 = int64_t(p) * kPatch;
+    const PatchMeta m = pd.meta[p];
+
+    __syncthreads();
+    for (int k = tid; k <= m.n_col; k += NT) co[k] = __ldg(pd.col_ptr + m.col_off + k);
+    const int32_t* pn = pd.pnode + m.node_off;
+    for (int l0 = 0; l0 < m.n_nodes; l0 += 2 * NT) {
+        const int la = l0 + tid, lb = l0 + NT + tid;
+        const int32_t ga = la < m.n_nodes ? __ldg(pn + la) : 0, gb = lb < m.n_nodes ? __ldg(pn + lb) : 0;
+        const double xa = la < m.n_nodes ? ld_l2(bd.x + (ga & kNodeMask)) : 0.0;
+        const double xb = lb < m.n_nodes ? ld_l2(bd.x + (gb & kNodeMask)) : 0.0;
+        const double ba = la < m.n_owned ? __ldg(bd.b + (ga & kNodeMask)) : 0.0;
+        const double bb = lb < m.n_owned ? __ldg(bd.b + (gb & kNodeMask)) : 0.0;
+        float h, lo;
+        if (la < m.n_nodes) { split_dw(xa, h, lo); Gs[la] = ga; xw[la] = make_float2(h, lo); bs[la] = ba; aw[la] = make_float2(0.f, 0.f); }
+        if (lb < m.n_nodes) { split_dw(xb, h, lo); Gs[lb] = gb; xw[lb] = make_float2(h, lo); bs[lb] = bb; aw[lb] = make_float2(0.f, 0.f); }
+    }
+    __syncthreads();
+    for (int cc = 0; cc < m.n_col; ++cc) {
+        const int lo = co[cc], hi = co[cc + 1];
+        for (int s = lo + tid; s < hi; s += NT) {
+            int ln[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) ln[i] = int(__ldg(pd.lconn + i * ns + slot0 + s));
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                float sv = 0.0f, cv = 0.0f;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const int64_t e = sym_index(NB, r, j) * ns + slot0 + s;
+                    const float2 xv = xw[ln[j]];
+                    dw_fma(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
+                }
+                float2 t = aw[ln[r]];
+                dw_add(t.x, t.y, sv, cv);
+                aw[ln[r]] = t;
+            }
+        }
+        __syncthreads();
+    }
+    double dot = 0.0;
+    float2* halo2 = reinterpret_cast<float2*>(bd.halo64);
+    for (int l = tid; l < m.n_nodes; l += NT) {
+        const int32_t graw = Gs[l];
+        const float2 t = aw[l];
+        if (l < m.n_owned) {
+            const double o = graw < 0 ? 0.0 : bs[l] - (f2d(t.x) + f2d(t.y));
+            bd.r[graw & kNodeMask] = o;
+            dot = fmadd(o, o, dot);
+        } else {
+            halo2[m.halo_off + (l - m.n_owned)] = t;
+        }
+    }
+    const double dsum = block_sum<NT>(dot, red);
+    if (tid == 0) bd.part_p[p] = dsum;
+}
+
 template <typename T, int NB>
 __device__ __forceinline__ void residual_patch(Ctx& c, int p) {
+    if constexpr (sizeof(T) == 4) {
+        residual_patch_dw<NB>(c, p, layout_of<T, NB>(*c.bd));
+        return;
+    }
     const BatchDev& bd = *c.bd;
     const PlanDev& pd = bd.pd;
     unsigned char* smem = c.smem;
@@ -375,9 +453,21 @@ __device__ __forceinline__ void fix_item(Ctx& c, int ci, int md) {
                 }
             } else {
                 double v0 = 0.0, v1 = 0.0;
-                for (int t = 0; t < nmax; ++t) {
-                    if (t < na) v0 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + a0 + t));
-                    if (t < nb) v1 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + b0 + t));
+                if constexpr (sizeof(T) == 4) {
+                    // double-word halo partials (FP32 pairs) of the mixed solver
+                    const float2* halo2 = reinterpret_cast<const float2*>(bd.halo64);
+                    float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+                    for (int t = 0; t < nmax; ++t) {
+                        if (t < na) { const float2 h = ld_l2(halo2 + __ldg(pd.sh_slot + a0 + t)); dw_add(s0, c0, h.x, h.y); }
+                        if (t < nb) { const float2 h = ld_l2(halo2 + __ldg(pd.sh_slot + b0 + t)); dw_add(s1, c1, h.x, h.y); }
+                    }
+                    v0 = f2d(s0) + f2d(c0);
+                    v1 = f2d(s1) + f2d(c1);
+                } else {
+                    for (int t = 0; t < nmax; ++t) {
+                        if (t < na) v0 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + a0 + t));
+                        if (t < nb) v1 += ld_l2(bd.halo64 + __ldg(pd.sh_slot + b0 + t));
+                    }
                 }
                 const double o0 = g0 < 0 ? 0.0 : __ldg(bd.b + (g0 & kNodeMask)) - v0;
                 bd.r[g0 & kNodeMask] = o0;

@@ -268,7 +268,9 @@ struct BatchDev {
     const BatchItem* fix = nullptr;        // [n_fix]
     const BatchItem* tile = nullptr;       // [n_tile]
     const void* A = nullptr;               // element matrices of the inner operator (FP32 difference form or FP64)
-    const double* A64 = nullptr;           // FP64 element matrices (true residuals)
+    const double* A64 = nullptr;           // FP64 element matrices (true residuals, FP64 solver)
+    const float* Ahi = nullptr;            // mixed solver: A64 as FP32 pairs (double-word true residuals)
+    const float* Alo = nullptr;
     const double* b = nullptr;             // FP64 load vector
     const void* dinv = nullptr;            // inverse Jacobi diagonal, inner type
     double* x = nullptr;

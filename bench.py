@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the learned preconditioner (257^2) and deploying it (1025^2, 2049^2)")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "assemble", "vec", "cg", "batch", "mpnn"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "dw", "assemble", "vec", "cg", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -672,6 +672,8 @@ def run_ours(args):
                     ebe.ebe_apply(h, p32, q32)
                 elif args.profile_kernel == "residual64":
                     ebe.ebe_residual(h, x64, r64)
+                elif args.profile_kernel == "dw":
+                    ebe.ebe_residual(h, x64, r64, double_word=True)
                 else:
                     ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
             torch.cuda.synchronize()
@@ -770,7 +772,7 @@ def run_ours(args):
     if alu64 is not None:
         alu64["achieved_gops"] = round(alu64["ops_per_launch"] / ((ms_patch64 + ms_fix64) / 1e3) / 1e9, 1)
         alu64["frac"] = round(alu64["achieved_gops"] / alu64["peak_gops"], 4)
-    trf = traffic_record("apply32")
+    trf = traffic_record("cg_pass")
 
     # e2e: the user's whole call sequence from pinned host buffers
     e2e = None
@@ -874,7 +876,7 @@ def run_ours(args):
         "residual_dw": {"gbs": round(ach_dw, 1), "frac": round(ach_dw / peak, 4),
                         "kernel": "the FP64 residual in double-word FP32 arithmetic (EBE_F64_DW): patch + fix-up",
                         "ms_per_launch": [round(ms_dw[0], 5), round(ms_dw[1], 5)],
-                        "bytes_per_launch": m["residual64"]},
+                        "bytes_per_launch": m["residual64"], "traffic": traffic_record("residual_dw")},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,

@@ -1162,12 +1162,14 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
                 continue;
             }
             if (sh.reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
-            // the replacement residual in double-word form; convergence is
+            // the replacement residual in double-word form while the threshold
+            // is large against its error, else in FP64; convergence is always
             // confirmed by the FP64 pass
-            TRY(true_residual_int(h, rr, true));
+            const bool dw = sh.reason == kTrigger && thr >= kDwReplaceRel * r0;
+            TRY(true_residual_int(h, rr, dw));
             info.true_residuals += 1;
             double rel = std::sqrt(rr) / r0;
-            if (rel <= o.rtol) {
+            if (dw && rel <= o.rtol) {
                 TRY(true_residual_int(h, rr));
                 info.true_residuals += 1;
                 rel = std::sqrt(rr) / r0;

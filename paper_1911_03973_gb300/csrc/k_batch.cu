@@ -345,10 +345,12 @@ __device__ __forceinline__ void residual_patch_dw(Ctx& c, int p, const BatchSmem
 }
 
 template <typename T, int NB>
-__device__ __forceinline__ void residual_patch(Ctx& c, int p) {
+__device__ __forceinline__ void residual_patch(Ctx& c, int p, bool exact) {
     if constexpr (sizeof(T) == 4) {
-        residual_patch_dw<NB>(c, p, layout_of<T, NB>(*c.bd));
-        return;
+        if (!exact) {
+            residual_patch_dw<NB>(c, p, layout_of<T, NB>(*c.bd));
+            return;
+        }
     }
     const BatchDev& bd = *c.bd;
     const PlanDev& pd = bd.pd;
@@ -453,7 +455,7 @@ __device__ __forceinline__ void fix_item(Ctx& c, int ci, int md) {
                 }
             } else {
                 double v0 = 0.0, v1 = 0.0;
-                if constexpr (sizeof(T) == 4) {
+                if (sizeof(T) == 4 && ld_l2(&bd.prob[it.k].exact) == 0) {
                     // double-word halo partials (FP32 pairs) of the mixed solver
                     const float2* halo2 = reinterpret_cast<const float2*>(bd.halo64);
                     float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
@@ -521,8 +523,13 @@ __device__ __forceinline__ void decide(const BatchDev& bd, int k, int md, double
         P->iter = it;
         if (P->bd || !isfinite(rz) || !isfinite(rr) || rz < 0.0) {
             P->bd = 1;
+            P->exact = 1;
             P->mode = kBReplace;                // a last true residual, then done
         } else if (rr <= P->thr2 || it >= bd.maxit) {
+            // the replacement in double-word form while the threshold is large
+            // against its error, else in FP64
+            const double lim = kDwReplaceRel * P->r0;
+            P->exact = (P->thr2 >= lim * lim && it < bd.maxit) ? 0 : 1;
             P->mode = kBReplace;                // rho stays: the replacement recomputes r.z
         } else {
             P->beta = rz / P->rho;
@@ -914,7 +921,7 @@ k_batch_pcg(const __grid_constant__ BatchDev bd) {
                     }
                     pf = nxt;
                 } else {
-                    residual_patch<T, NB>(c, p);
+                    residual_patch<T, NB>(c, p, ld_l2(&bd.prob[k].exact) != 0);
                 }
             }
         if (!tma::grid_sync(bd.bar, G, bd.pd.err, sflag, lim)) { drain(); return; }

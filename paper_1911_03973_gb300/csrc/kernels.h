@@ -241,8 +241,16 @@ struct BatchProblem {
     int32_t init;      // the pending replacement is the initial residual
     int32_t bd;        // breakdown seen: finish after a last true residual
     int32_t dir_init;  // the pending direction step starts from p = z
-    int32_t pad;
+    int32_t exact;     // mixed: the pending true residual in FP64, not in double-word form
 };
+
+// The mixed solvers take a residual replacement in double-word arithmetic
+// while its threshold is at least kDwReplaceRel |r0|, and in FP64 below.  The
+// double-word residual errs by about 2^-48 |A||x|, which near a solution is
+// of the order of 1e-9 |r0| on the 2049^2 square (|A||x| / |b| grows like
+// 1 / h^2): negligible against residuals of 1e-6 |r0| and above, not against
+// the last checks before rtol.
+constexpr double kDwReplaceRel = 1e-6;
 
 // A work item of the fix-up or node phases: one problem's shared-node rows
 // [lo, hi) (fix-up) or nodes [lo, hi) (node phases).  A fix-up item also

@@ -90,3 +90,20 @@ def test_full_size_mixed_solve_judged_by_oracle(ebe, full):
     torch.cuda.synchronize()
     assert info["status"] == "EBE_OK", info
     assert orc.rel_residual(x.cpu().numpy()) <= 1e-8
+
+
+def test_full_size_nu0_mixed_solve_judged_by_oracle(ebe):
+    """The 2049^2 workload with nu = 0 (the stiffness matrix alone): the mixed
+    solve to 1e-8, judged by the oracle's FP64 true residual."""
+    prob = meshgen.config_square_jitter(2049, nu=0.0, seed=2)
+    stream = torch.cuda.Stream()
+    h = ebe.ebe_create(prob["coords"], prob["elems"], stream=stream.cuda_stream)
+    ebe.ebe_set_problem(h, prob["nu"], prob["f"], prob["dirichlet"], prob["g"], prob["neumann"])
+    ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+    with torch.cuda.stream(stream):
+        x = torch.zeros(prob["coords"].shape[0], dtype=torch.float64, device=DEV)
+        info = ebe.ebe_solve(h, x, rtol=1e-8, precision=ebe.EBE_PREC_MIXED)
+    torch.cuda.synchronize()
+    ebe.ebe_destroy(h)
+    assert info["status"] == "EBE_OK", info
+    assert oracle.Problem(prob).rel_residual(x.cpu().numpy()) <= 1e-8

@@ -1007,7 +1007,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     // shared-node entries and the scalars only after the wait.
     float4 rv0, qv0, pv0, dv0;
     double2 xa0, xb0;
-    int sid0 = -1;
+    int sid0 = -1, hpos0 = 0;
     if (tid < n_own4) {
         const int id0 = own0 + 4 * tid;
         rv0 = *reinterpret_cast<const float4*>(r + id0);
@@ -1018,6 +1018,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
         xb0 = *reinterpret_cast<const double2*>(x + id0 + 2);
     } else if (tid < n_items) {
         sid0 = __ldg(pn + m.n_owned + (tid - n_own4)) & kNodeMask;
+        hpos0 = __ldg(pd.halo_pos + m.halo_off + (tid - n_own4));   // where its halo partial goes
     }
     pdl_wait();
     if (sc->done) {                                  // uniform: the solver has stopped
@@ -1032,7 +1033,10 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     float4* ds4 = reinterpret_cast<float4*>(ds);
     if (!WARPS)
         for (int g = tid; g < (m.n_nodes + 3) >> 2; g += NT) reinterpret_cast<float4*>(acc)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    CompSum srz, srr;
+    // per-thread sums of at most four terms in plain FP32: the warp butterflies
+    // below add 32 of them in plain FP32 as well, so a compensated sum here
+    // would not change the accuracy of the totals
+    float srz = 0.0f, srr = 0.0f;
     auto owned_group = [&](int g, const float4& rv, const float4& qv, const float4& pv, const float4& dv,
                            const double2& xa, const double2& xb) {
         const int l0 = 4 * g, id0 = own0 + l0;
@@ -1049,8 +1053,8 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             z4[u] = c.z;                            // 0 on padding (dinv = 0)
             xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
             if (l0 + u < m.n_owned) {
-                srz.add(c.rn * c.z);
-                srr.add(c.rn * c.rn);
+                srz = __fmaf_rn(c.rn, c.z, srz);
+                srr = __fmaf_rn(c.rn, c.rn, srr);
             }
         }
         if (l0 + 4 <= m.n_owned) {
@@ -1095,7 +1099,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     patch_sums<float, NB, WARPS>(m, pd.max_nodes, As, Ls, xs, acc, co, tid);
     // q = mask(A p_new): owned nodes final (Dirichlet rows: dinv = 0), shared
     // nodes to their halo slots
-    CompSum spq, sqz, sqdq;
+    float spq = 0.0f, sqz = 0.0f, sqdq = 0.0f;
     for (int g = tid; g < n_items; g += NT) {
         if (g < n_own4) {
             const int l0 = 4 * g;
@@ -1111,22 +1115,28 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
                 if (l0 + u < m.n_owned) {
                     const float qn = dv[u] == 0.0f ? 0.0f : av[u];
                     qn4[u] = qn;
-                    spq.add(xv[u] * qn);
-                    sqz.add(qn * zv[u]);
-                    sqdq.add(qn * (dv[u] * qn));
+                    spq = __fmaf_rn(xv[u], qn, spq);
+                    sqz = __fmaf_rn(qn, zv[u], sqz);
+                    sqdq = __fmaf_rn(qn, dv[u] * qn, sqdq);
                 }
             }
             *reinterpret_cast<float4*>(q + own0 + l0) = make_float4(qn4[0], qn4[1], qn4[2], qn4[3]);
         } else {
             const int l = m.n_owned + (g - n_own4);
-            halo[__ldg(pd.halo_pos + m.halo_off + (l - m.n_owned))] = acc[l];   // CSR order
+            const int hp = g == tid ? hpos0 : __ldg(pd.halo_pos + m.halo_off + (g - n_own4));
+            halo[hp] = acc[l];   // CSR order
         }
     }
     // The sums stay compensated FP32 pairs up to the last fix-up block (every
     // FP64 instruction of a CTA costs 16 cycles of its SM's FP64 pipe): warp
     // butterflies, then warp 0 adds the 8 warp totals of sums 0-3 at once
     // (lane 8k + w holds warp w's total of sum k) and of sum 4.
-    CompSum cs[kCgSums] = {srz, srr, spq, sqz, sqdq};
+    CompSum cs[kCgSums];
+    {
+        const float tv[kCgSums] = {srz, srr, spq, sqz, sqdq};
+#pragma unroll
+        for (int k = 0; k < kCgSums; ++k) cs[k].s = tv[k];
+    }
 #pragma unroll
     for (int k = 0; k < kCgSums; ++k) warp_sum_plain(cs[k]);
     float2* red2 = reinterpret_cast<float2*>(red);

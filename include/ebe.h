@@ -94,10 +94,13 @@ enum {
     EBE_PREC_MIXED = 1,   /* the operator pass runs on FP32 A_e (difference form) with the
                              search direction p, q = A p, the recurrence residual r and
                              z = dinv r in FP32; the solution x stays FP64; dot products
-                             add per thread in compensated FP32 and across threads in
-                             FP64; r is replaced by the FP64 true residual (FP64 A_e)
-                             whenever the recurrence residual has dropped by the factor
-                             `delta` since the last replacement (needs EBE_STORE_MIXED).
+                             add in FP32 within a warp and in compensated FP32 across
+                             warps and blocks, the last block in FP64; r is replaced by
+                             the true residual whenever the recurrence residual has
+                             dropped by the factor `delta` since the last replacement
+                             (the double-word residual of EBE_F64_DW while the threshold
+                             is at least 1e-6 |r0|, the FP64 one below; convergence is
+                             confirmed by the FP64 residual; needs EBE_STORE_MIXED).
                              One iteration is two launches with one grid-wide reduction:
                              the x and r updates and the new direction are formed where
                              the operator pass gathers its operand, and the next r.z
@@ -390,7 +393,10 @@ typedef struct {
 /* Jacobi-PCG on every problem of the batch at once, each stopping on its own
  * FP64 true relative residual |mask(b_k - A_k x_k)| / |mask(b_k - A_k x0_k)|
  * <= rtol, with the per-problem rules of ebe_solve (precision, delta,
- * maxit, stall_updates; chunk is not used).  All iterations of all problems
+ * maxit, stall_updates; chunk is not used).  The batched iteration is the
+ * textbook four-phase form; in mixed precision a replacement residual is the
+ * double-word one while the problem's threshold is at least 1e-6 |r0|, the
+ * FP64 one below (so the last checks before rtol are FP64).  All iterations of all problems
  * run in one persistent cooperative kernel with grid-wide barriers (each
  * wait bounded in time); problems that have finished drop out of the work.
  * With use_graph = 1 the solve (x0 Dirichlet values, state reset, the

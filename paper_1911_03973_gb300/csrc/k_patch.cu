@@ -539,9 +539,13 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
 // operations per node instead of n_b^2 + n_b per element.  The pair
 // representation of A_e and x is exact to 2^-48 relative, so r differs from
 // the FP64 residual by about 2^-48 |A| |x| per node.
+// The slots' pair products wait for their colour round in shared memory
+// (y: NB runs of kPatch float2), not in registers: 48 registers and five
+// CTAs per SM for triangles instead of 64 and four.
 struct PatchDwSmem {
-    uint32_t red, co, G, xh, xl, bs, as, ac, total;
+    uint32_t red, co, G, xh, xl, bs, as, ac, y, total;
 };
+template <int NB>
 __host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
     PatchDwSmem s{};
     const uint32_t gcap = uint32_t((max_nodes + 3) / 4 * 4);
@@ -553,20 +557,22 @@ __host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
     s.bs = (s.xl + gcap * 4 + 15) / 16 * 16;
     s.as = s.bs + gcap * 8;
     s.ac = s.as + gcap * 4;
-    s.total = (s.ac + gcap * 4 + 127) / 128 * 128;
+    s.y = (s.ac + gcap * 4 + 15) / 16 * 16;
+    s.total = (s.y + uint32_t(NB * kPatch * 8) + 127) / 128 * 128;
     return s;
 }
 
 template <int NB, int MODE>
-__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 4 : 3)
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 5 : 4)
 k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restrict__ Alo,
            const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ out,
            float2* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
     constexpr int NT = kPatchThreads;
     constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
     extern __shared__ __align__(128) unsigned char smem[];
-    const PatchDwSmem L = patch_dw_layout(pd.max_nodes);
+    const PatchDwSmem L = patch_dw_layout<NB>(pd.max_nodes);
     double* red = reinterpret_cast<double*>(smem + L.red);
+    float2* ysm = reinterpret_cast<float2*>(smem + L.y);
     int* co = reinterpret_cast<int*>(smem + L.co);
     int32_t* Gs = reinterpret_cast<int32_t*>(smem + L.G);
     float* xh = reinterpret_cast<float*>(smem + L.xh);
@@ -588,14 +594,21 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         bulk_prefetch_l2(run, uint32_t((m.n_el + 3) / 4 * 16));
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
-    int ln[kEPT][NB];
+    // the slots' 16-bit local ids, two to a register
+    constexpr int NP = (NB + 1) / 2;
+    uint32_t lp[kEPT][NP];
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
         const int s = tid + k * NT;
         const bool ok = s < m.n_el;
 #pragma unroll
-        for (int i = 0; i < NB; ++i) ln[k][i] = ok ? int(__ldg(pd.lconn + i * ns + slot0 + s)) : 0;
+        for (int w = 0; w < NP; ++w) {
+            const uint32_t lo = ok ? uint32_t(__ldg(pd.lconn + (2 * w) * ns + slot0 + s)) : 0u;
+            const uint32_t hi = (ok && 2 * w + 1 < NB) ? uint32_t(__ldg(pd.lconn + (2 * w + 1) * ns + slot0 + s)) : 0u;
+            lp[k][w] = lo | (hi << 16);
+        }
     }
+    auto ln = [&](int k, int i) { return int((lp[k][i >> 1] >> (16 * (i & 1))) & 0xffffu); };
     pdl_wait();
     if (stop != nullptr && *stop) return;
     const int32_t* pn = pd.pnode + m.node_off;
@@ -613,9 +626,10 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         ac[l] = 0.0f;
     }
     __syncthreads();
-    // products of all slots first (every thread busy), then colour rounds add them
-    float ys[kEPT][NB], yc[kEPT][NB];
-#pragma unroll
+    // products of all slots first (every thread busy), then colour rounds add
+    // them; a thread reads back only its own slots' products.  Two slots'
+    // matrix loads in flight at a time (all four would need 48 registers)
+#pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
         const int s = tid + k * NT;
         const bool ok = s < m.n_el;
@@ -628,16 +642,15 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         float eh[NB], el[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-            eh[j] = xh[ln[k][j]];
-            el[j] = xl[ln[k][j]];
+            eh[j] = xh[ln(k, j)];
+            el[j] = xl[ln(k, j)];
         }
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
             float sv = 0.0f, cv = 0.0f;
 #pragma unroll
             for (int j = 0; j < NB; ++j) dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
-            ys[k][r] = sv;
-            yc[k][r] = cv;
+            ysm[r * kPatch + s] = make_float2(sv, cv);
         }
     }
     for (int c = 0; c < m.n_col; ++c) {
@@ -648,9 +661,10 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
             if (s >= lo && s < hi) {
 #pragma unroll
                 for (int r = 0; r < NB; ++r) {
-                    const int n = ln[k][r];
+                    const int n = ln(k, r);
+                    const float2 y = ysm[r * kPatch + s];
                     float sv = as[n], cv = ac[n];
-                    dw_add(sv, cv, ys[k][r], yc[k][r]);
+                    dw_add(sv, cv, y.x, y.y);
                     as[n] = sv;
                     ac[n] = cv;
                 }
@@ -762,7 +776,7 @@ template <int NB, int MODE>
 cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, const double* x, const double* b,
                          double* out, float2* halo, double* part, const int32_t* stop, Scalars* sc, cudaStream_t st,
                          int* launches, cudaEvent_t* ev) {
-    const size_t sm = patch_dw_layout(pd.max_nodes).total;
+    const size_t sm = patch_dw_layout<NB>(pd.max_nodes).total;
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     auto kern = k_patch_dw<NB, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));

@@ -587,22 +587,11 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
-    // Element matrices into L2 ahead of use (they are constant: before the
-    // wait): the first wave of CTAs fetches its own patch; every CTA also
-    // fetches the patch one wave of resident CTAs ahead, whose CTA then finds
-    // its matrices in L2 when it starts, so the DRAM reads run continuously
-    // instead of in step with each CTA's phases.
-    {
-        constexpr int kRuns = 2 * sym_count(NB);
-        const int ahead = pd.num_sms * (NB == 3 ? 5 : 4);
-        const int q = tid < kRuns ? p + ahead : (tid < 2 * kRuns && p < ahead ? p : -1);
-        if (q >= 0 && q < pd.n_patches) {
-            const int t = tid % kRuns;
-            // a patch's runs span kPatch slots (padding included) in every array
-            const int n_pref = q == p ? m.n_el : kPatch;
-            const float* run = (t & 1 ? Alo : Ahi) + (t >> 1) * ns + int64_t(q) * kPatch;
-            if (n_pref > 0) bulk_prefetch_l2(run, uint32_t((n_pref + 3) / 4 * 16));
-        }
+    // the patch's element matrices start moving into L2 now, so their DRAM
+    // reads overlap the node gather below (they are constant: before the wait)
+    if (tid < 2 * sym_count(NB) && m.n_el > 0) {
+        const float* run = (tid & 1 ? Alo : Ahi) + (tid >> 1) * ns + slot0;
+        bulk_prefetch_l2(run, uint32_t((m.n_el + 3) / 4 * 16));
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
     // the slots' 16-bit local ids, two to a register
@@ -1004,18 +993,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
     const int64_t slot0 = int64_t(p) * kPatch;
-    // element matrices and connectivity are constant: copy before the wait;
-    // the patch one wave of resident CTAs ahead is fetched into L2 now, so
-    // that its CTA's bulk copies find it there (DRAM reads then run ahead of
-    // the CTAs' phases instead of in step with them)
-    {
-        const int q = p + pd.num_sms * (NB == 3 ? 5 : 3);
-        if (q < pd.n_patches && tid >= 32 && tid < 32 + sym_count(NB) + NB) {
-            const int t = tid - 32;
-            if (t < sym_count(NB)) bulk_prefetch_l2(A + t * ns + int64_t(q) * kPatch, uint32_t(kPatch * 4));
-            else bulk_prefetch_l2(pd.lconn + (t - sym_count(NB)) * ns + int64_t(q) * kPatch, uint32_t(kPatch * 2));
-        }
-    }
+    // element matrices and connectivity are constant: copy before the wait
     if (tid == 0) {
         mbar_init(bar, 1);
         const uint64_t pol = policy_evict_first();

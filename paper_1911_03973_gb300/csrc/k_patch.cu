@@ -1016,7 +1016,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     const int n_own4 = (m.n_owned + 3) >> 2;
     const int n_items = n_own4 + (m.n_nodes - m.n_owned);
     // The owned entries were written by the previous patch pass, which had
-    // completed before the fix-up let this pass launch, so this thread's first item is
+    // completed before the fix-up launched, so this thread's first item is
     // loaded before waiting for the fix-up (the node table is constant);
     // shared-node entries and the scalars only after the wait.
     float4 rv0, qv0, pv0, dv0;
@@ -1181,13 +1181,8 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
            const float* __restrict__ halo, double* __restrict__ part, Scalars* __restrict__ sc) {
     __shared__ double red[kCgSums * 8];
     __shared__ bool last;
-    // Launched as a programmatic dependent of the patch pass, so its CTAs are
-    // resident when the pass ends; it lets the next pass launch only once the
-    // pass has completed (the trigger after the wait), which keeps that pass's
-    // reads of the owned entries before its own wait ordered after this
-    // pass's writes.
-    pdl_wait();
     pdl_trigger();
+    pdl_wait();
     if (sc->done) return;
     const double al = sc->alpha;
     const float alf = d2f(al), bef = d2f(sc->beta);
@@ -1346,12 +1341,7 @@ cudaError_t run_cg_pass(const PlanDev& pd, const float* A, float* r, float* q, c
     // one row per thread at a time (each row has five vector loads in flight
     // already), one wave of six 256-thread blocks per SM
     const int fg = std::min(fix_grid(pd.n_shared, 1), 6 * std::max(pd.num_sms, 1));
-    if (pdl) {
-        e = launch_pdl(k_cg_fixup<1>, dim3(fg), dim3(kFixThreads), 0, st, pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
-        if (e != cudaSuccess) return e;
-    } else {
-        k_cg_fixup<1><<<fg, kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
-    }
+    k_cg_fixup<1><<<fg, kFixThreads, 0, st>>>(pd, r, q, p_old, p_new, dinv, x, halo, part, sc);
     if (ev) cudaEventRecord(ev[2], st);
     if (launches) *launches += 2;
     return cudaGetLastError();

@@ -412,6 +412,11 @@ def run_cube(args, dev, stream):
                              "bytes_per_launch": m["residual64"], "gbs": round(g64, 1), "frac": round(g64 / peak, 4)}
         out["residual_dw"] = {"ms_per_launch": [round(rdw[0], 5), round(rdw[1], 5)],
                               "bytes_per_launch": m["residual64"], "gbs": round(gdw, 1), "frac": round(gdw / peak, 4)}
+        ebe.ebe_time_cg_pass(h, reps=5)
+        cgt = ebe.ebe_time_cg_pass(h, reps=40)
+        gcg = m["cg_mixed"] / (sum(cgt) / 1e3) / 1e9
+        out["cg_pass"] = {"ms_per_launch": [round(cgt[0], 5), round(cgt[1], 5)], "bytes_per_launch": m["cg_mixed"],
+                          "gbs": round(gcg, 1), "frac": round(gcg / peak, 4)}
         ebe.ebe_destroy(h)
     return out
 
@@ -939,8 +944,8 @@ def summary_block(line, ms_plain, pinfo, peak):
                      "residual64": line["residual_fp64"]["frac"], "residual_dw": line["residual_dw"]["frac"]}
     c = line.get("cube129")
     if c:
-        s["hbm_frac"].update({"cube_apply32": c["apply32"]["frac"], "cube_residual64": c["residual64"]["frac"],
-                              "cube_residual_dw": c["residual_dw"]["frac"]})
+        s["hbm_frac"].update({"cube_cg_pass": c["cg_pass"]["frac"], "cube_apply32": c["apply32"]["frac"],
+                              "cube_residual64": c["residual64"]["frac"], "cube_residual_dw": c["residual_dw"]["frac"]})
     v = line.get("residual_variants_fp64")
     if v:
         s["scatter_fp64_ms"] = {k: x["ms"] for k, x in v.items()}

@@ -228,6 +228,14 @@ __device__ __forceinline__ void dw_fma(float ah, float al, float xh, float xl, f
     c = c + (t + e2);
 }
 
+// (s, c) = (ah + al) * (xh + xl): the first product of a sum, the same
+// pair dw_fma gives from (0, 0) without its TwoSum with zero.
+__device__ __forceinline__ void dw_mul(float ah, float al, float xh, float xl, float& s, float& c) {
+    float e;
+    s = two_prod(ah, xh, e);
+    c = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+}
+
 // (s, c) += (s2, c2).
 __device__ __forceinline__ void dw_add(float& s, float& c, float s2, float c2) {
     float e;

@@ -318,7 +318,8 @@ __device__ __forceinline__ void residual_patch_dw(Ctx& c, int p, const BatchSmem
                 for (int j = 0; j < NB; ++j) {
                     const int64_t e = sym_index(NB, r, j) * ns + slot0 + s;
                     const float2 xv = xw[ln[j]];
-                    dw_fma(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
+                    if (j == 0) dw_mul(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
+                    else dw_fma(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
                 }
                 float2 t = aw[ln[r]];
                 dw_add(t.x, t.y, sv, cv);

@@ -647,9 +647,10 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         }
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
-            float sv = 0.0f, cv = 0.0f;
+            float sv, cv;
+            dw_mul(ah[sym_index(NB, r, 0)], al[sym_index(NB, r, 0)], eh[0], el[0], sv, cv);
 #pragma unroll
-            for (int j = 0; j < NB; ++j) dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
+            for (int j = 1; j < NB; ++j) dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
             ysm[r * kPatch + s] = make_float2(sv, cv);
         }
     }

@@ -912,7 +912,7 @@ cudaError_t run_patch_mode(const PlanDev& pd, int mode, const T* A, const T* x, 
 constexpr int kCgSums = 5;   // r.z, r.r, p.q, q.z, q.(dinv q)
 
 struct CgSmem {
-    uint32_t bar, flag, red, co, A, L, xs, zs, ds, acc, total;
+    uint32_t bar, flag, red, co, A, L, xs, acc, total;
 };
 template <int NB, bool WARPS>
 __host__ __device__ constexpr CgSmem cg_layout(int max_nodes) {
@@ -925,9 +925,7 @@ __host__ __device__ constexpr CgSmem cg_layout(int max_nodes) {
     s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
     s.L = s.A + uint32_t(sym_count(NB) * kPatch * 4);
     s.xs = s.L + uint32_t(NB * kPatch * 2);             // p_new at the patch nodes
-    s.zs = s.xs + gcap * 4;                             // z at the owned nodes
-    s.ds = s.zs + gcap * 4;                             // dinv at the owned nodes
-    s.acc = s.ds + gcap * 4;
+    s.acc = s.xs + gcap * 4;
     s.total = (s.acc + (WARPS ? kWarpCopies : 1) * gcap * 4 + 127) / 128 * 128;
     return s;
 }
@@ -970,7 +968,7 @@ __device__ __forceinline__ CgNode cg_node(float r, float q, float p, float d, fl
 }
 
 template <int NB, bool WARPS>
-__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 5 : 3)
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 6 : 3)
 k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r, float* __restrict__ q,
            const float* __restrict__ p_old, float* __restrict__ p_new, const float* __restrict__ dinv,
            double* __restrict__ x, float* __restrict__ halo, double* __restrict__ part, const Scalars* __restrict__ sc) {
@@ -983,8 +981,6 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     const float* As = reinterpret_cast<const float*>(smem + L.A);
     const uint16_t* Ls = reinterpret_cast<const uint16_t*>(smem + L.L);
     float* xs = reinterpret_cast<float*>(smem + L.xs);
-    float* zs = reinterpret_cast<float*>(smem + L.zs);
-    float* ds = reinterpret_cast<float*>(smem + L.ds);
     float* acc = reinterpret_cast<float*>(smem + L.acc);
     const uint32_t bar = smem_addr(smem + L.bar);
 
@@ -1042,10 +1038,7 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     }
     const double al = sc->alpha;
     const float alf = d2f(al), bef = d2f(sc->beta);
-    // z and dinv of the owned nodes are kept per group of four (16-byte
-    // shared-memory accesses, no bank conflicts), the node sums zeroed the same way
-    float4* zs4 = reinterpret_cast<float4*>(zs);
-    float4* ds4 = reinterpret_cast<float4*>(ds);
+    // the node sums zeroed per group of four (16-byte shared-memory stores)
     if (!WARPS)
         for (int g = tid; g < (m.n_nodes + 3) >> 2; g += NT) reinterpret_cast<float4*>(acc)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
     // per-thread sums of at most four terms in plain FP32: the warp butterflies
@@ -1058,14 +1051,13 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
         const float rr4[4] = {rv.x, rv.y, rv.z, rv.w}, qq4[4] = {qv.x, qv.y, qv.z, qv.w};
         const float pp4[4] = {pv.x, pv.y, pv.z, pv.w}, dd4[4] = {dv.x, dv.y, dv.z, dv.w};
         const double xx4[4] = {xa.x, xa.y, xb.x, xb.y};
-        float rn4[4], pn4[4], z4[4];
+        float rn4[4], pn4[4];
         double xn4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const CgNode c = cg_node(rr4[u], qq4[u], pp4[u], dd4[u], alf, bef);
             rn4[u] = c.rn;
             pn4[u] = c.pn;
-            z4[u] = c.z;                            // 0 on padding (dinv = 0)
             xn4[u] = fmadd(al, f2d(pp4[u]), xx4[u]);
             if (l0 + u < m.n_owned) {
                 srz = __fmaf_rn(c.rn, c.z, srz);
@@ -1079,8 +1071,6 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
             for (int u = 0; u < 4; ++u)
                 if (l0 + u < m.n_owned) xs[l0 + u] = pn4[u];   // the entries after belong to shared nodes
         }
-        zs4[g] = make_float4(z4[0], z4[1], z4[2], z4[3]);
-        ds4[g] = dv;
         *reinterpret_cast<float4*>(r + id0) = make_float4(rn4[0], rn4[1], rn4[2], rn4[3]);
         *reinterpret_cast<float4*>(p_new + id0) = make_float4(pn4[0], pn4[1], pn4[2], pn4[3]);
         *reinterpret_cast<double2*>(x + id0) = make_double2(xn4[0], xn4[1]);
@@ -1118,11 +1108,16 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     for (int g = tid; g < n_items; g += NT) {
         if (g < n_own4) {
             const int l0 = 4 * g;
-            // 16-byte loads; entries past n_owned (shared nodes' sums) are not used
+            // z = dinv r of the owned nodes again from the r this thread stored
+            // in the node step (the same product; shared memory then fits six
+            // CTAs per SM); 16-byte loads; entries past n_owned (shared nodes'
+            // sums) are not used
+            const float4 r4 = *reinterpret_cast<const float4*>(r + own0 + l0);
+            const float4 d4 = __ldg(reinterpret_cast<const float4*>(dinv + own0 + l0));
             const float4 a4 = reinterpret_cast<const float4*>(acc)[g], x4 = reinterpret_cast<const float4*>(xs)[g];
-            const float4 z4 = zs4[g], d4 = ds4[g];
             const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
-            const float zv[4] = {z4.x, z4.y, z4.z, z4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
+            const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+            const float zv[4] = {d4.x * r4.x, d4.y * r4.y, d4.z * r4.z, d4.w * r4.w};
             float qn4[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {

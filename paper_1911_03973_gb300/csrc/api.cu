@@ -61,8 +61,6 @@ struct ebe_handle {
     // scratch of the patch passes
     double* halo64 = nullptr;
     float* halo32 = nullptr;
-    float* halo_cg = nullptr;       // the single-sync solver's halo partials (pd_int.halo_pos), zeroed once
-    int64_t halo_cg_len = 0;
     double* halo2 = nullptr;
     double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
     double* part_vec = nullptr;     // 3 * 1216
@@ -387,21 +385,12 @@ static int create_device(ebe_handle* h, const double* coords_host) {
         TRY(upload(h, &h->int_of_user, iou.data(), int64_t(iou.size())));
         TRY(upload(h, &h->pnode_int, pint.data(), int64_t(pint.size())));
         TRY(upload(h, &h->sh_node_int, shint.data(), int64_t(shint.size())));
-        int max_row = 0;
-        for (int64_t k = 0; k < nsh; ++k) max_row = std::max(max_row, P.sh_ptr[size_t(k) + 1] - P.sh_ptr[size_t(k)]);
-        const int stride = max_row <= 4 ? 4 : (max_row <= 8 ? 8 : 0);
-        if (stride > 0 && nsh * stride >= (int64_t(1) << 31)) return fail(h, EBE_INVALID_ARG, "mesh too large for the solver numbering");
         std::vector<int32_t> hpos(static_cast<size_t>(std::max<int64_t>(P.n_halo, 1)), 0);
-        for (int64_t k = 0; k < nsh; ++k)
-            for (int32_t j = P.sh_ptr[size_t(k)]; j < P.sh_ptr[size_t(k) + 1]; ++j)
-                hpos[size_t(P.sh_slot[size_t(j)])] =
-                    stride > 0 ? int32_t(k * stride + (j - P.sh_ptr[size_t(k)])) : int32_t(j);
-        h->halo_cg_len = stride > 0 ? nsh * stride : P.n_halo;
+        for (int64_t j = 0; j < P.n_halo; ++j) hpos[size_t(P.sh_slot[size_t(j)])] = int32_t(j);
         int32_t* hpos_d = nullptr;
         TRY(upload(h, &hpos_d, hpos.data(), int64_t(hpos.size())));
         h->pd_int = pd;
         h->pd_int.halo_pos = hpos_d;
-        h->pd_int.halo_stride = stride;
         h->pd_int.pnode = h->pnode_int;
         h->pd_int.sh_node = h->sh_node_int;
         h->pd_int.own_off = own_off_d;
@@ -1054,7 +1043,7 @@ int ensure_cg_graphs(ebe_handle* h, int chunk) {
         cudaError_t e = cudaSuccess;
         for (int it = 0; it < chunk && e == cudaSuccess; ++it)
             e = launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[(par + it) & 1], h->pi32[(par + it + 1) & 1],
-                               h->dinvi32, h->xi, h->halo_cg, h->part5, h->sc, h->st, &l, true);
+                               h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st, &l, true);
         cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "single-sync pass"); }
         if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
@@ -1100,7 +1089,6 @@ int cg1_buffers(ebe_handle* h) {
     TRY(dalloc(h, &h->pi32[1], ni));
     TRY(dalloc(h, &h->halo64, nh));
     TRY(dalloc(h, &h->halo32, nh));
-    TRY(dalloc(h, &h->halo_cg, std::max<int64_t>(h->halo_cg_len, 1), true));   // unused row positions stay zero
     TRY(dalloc(h, &h->part5, 5 * (int64_t(h->pd.n_patches) + kFixGridMax)));
     return ensure_solver_vectors(h);
 }
@@ -1159,7 +1147,7 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
                 l = 0;
                 for (int it = 0; it < o.chunk; ++it)
                     CK(launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[(par + it) & 1],
-                                      h->pi32[(par + it + 1) & 1], h->dinvi32, h->xi, h->halo_cg, h->part5, h->sc, h->st,
+                                      h->pi32[(par + it + 1) & 1], h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st,
                                       &l, false), "single-sync pass");
                 add_launches(h, l);
             }
@@ -1262,7 +1250,7 @@ ebe_status ebe_time_cg_pass(ebe_handle* h, int32_t reps, double* ms) {
     l = 0;
     for (int r = 0; r <= reps && status == EBE_OK; ++r) {   // pass 0 is the fresh (untimed) pass
         const cudaError_t e = launch_cg_pass(h->pd_int, h->A32, h->ri32, h->qi32, h->pi32[r & 1], h->pi32[(r + 1) & 1],
-                                             h->dinvi32, h->xi, h->halo_cg, h->part5, h->sc, h->st, &l, true,
+                                             h->dinvi32, h->xi, h->halo32, h->part5, h->sc, h->st, &l, true,
                                              &ev[size_t(3) * size_t(r)]);
         if (e != cudaSuccess) status = cuda_fail(h, e, "single-sync pass");
     }

@@ -1189,28 +1189,13 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
         int nmax = 0;
         float rv[ROWS], qv[ROWS], pv[ROWS], dv[ROWS];
         double xv[ROWS];
-        const int hs = pd.halo_stride;
-        float hv[ROWS];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int kk = k + u * st;
             const bool ok = kk < pd.n_shared;
-            hv[u] = 0.0f;
-            if (hs == 0) {
-                s0[u] = ok ? __ldg(pd.sh_ptr + kk) : 0;
-                cnt[u] = ok ? __ldg(pd.sh_ptr + kk + 1) - s0[u] : 0;
-                nmax = cnt[u] > nmax ? cnt[u] : nmax;
-            } else if (ok) {
-                // fixed-stride rows: the partials in patch order, then zeros
-                // (adding the zeros leaves the sum as it is)
-                const float4 h0 = *reinterpret_cast<const float4*>(halo + int64_t(kk) * hs);
-                float v = ((h0.x + h0.y) + h0.z) + h0.w;
-                if (hs == 8) {
-                    const float4 h1 = *reinterpret_cast<const float4*>(halo + int64_t(kk) * hs + 4);
-                    v = (((v + h1.x) + h1.y) + h1.z) + h1.w;
-                }
-                hv[u] = v;
-            }
+            s0[u] = ok ? __ldg(pd.sh_ptr + kk) : 0;
+            cnt[u] = ok ? __ldg(pd.sh_ptr + kk + 1) - s0[u] : 0;
+            nmax = cnt[u] > nmax ? cnt[u] : nmax;
             const int id = pd.sh_base + kk;
             rv[u] = ok ? r[id] : 0.0f;
             qv[u] = ok ? q[id] : 0.0f;
@@ -1218,12 +1203,14 @@ k_cg_fixup(const PlanDev pd, float* __restrict__ r, float* __restrict__ q, const
             dv[u] = ok ? __ldg(dinv + id) : 0.0f;
             xv[u] = ok ? x[id] : 0.0;
         }
-        // CSR rows: the patch pass wrote the row's partials contiguously, in patch order
-        if (hs == 0)
-            for (int t = 0; t < nmax; ++t)
+        float hv[ROWS];
 #pragma unroll
-                for (int u = 0; u < ROWS; ++u)
-                    if (t < cnt[u]) hv[u] += halo[s0[u] + t];
+        for (int u = 0; u < ROWS; ++u) hv[u] = 0.0f;
+        // the patch pass wrote the row's partials contiguously (CSR order), in patch order
+        for (int t = 0; t < nmax; ++t)
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u)
+                if (t < cnt[u]) hv[u] += halo[s0[u] + t];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int kk = k + u * st;

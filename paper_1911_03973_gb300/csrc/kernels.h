@@ -35,14 +35,10 @@ struct PlanDev {
     // of the fix-up is node sh_base + k.
     const int32_t* own_off = nullptr;   // [n_patches + 1]
     int sh_base = 0;
-    // [n_halo] position of each halo slot in the single-sync solver's halo
-    // array.  halo_stride 4 or 8 (every shared row has at most that many
-    // partials): row k's partials at k * halo_stride + j in patch order, the
-    // unused positions zero, so the fix-up reads a row with one or two 16-byte
-    // loads and needs no row offsets; halo_stride 0: the rows' CSR order
-    // (halo_pos[sh_slot[j]] = j)
+    // [n_halo] position of each halo slot in the shared rows' CSR order
+    // (halo_pos[sh_slot[j]] = j), so that the single-sync fix-up reads a row's
+    // partials contiguously
     const int32_t* halo_pos = nullptr;
-    int halo_stride = 0;
 };
 
 // Element matrices are symmetric (K_e and M_e of Eq. matrices_K_M; the

@@ -106,7 +106,12 @@ enum {
                              the operator pass gathers its operand, and the next r.z
                              comes from r'.(dinv r') = r.z - 2 alpha q.z + alpha^2
                              q.(dinv q) (the same iterates as the textbook form in exact
-                             arithmetic)                                              */
+                             arithmetic).  A mesh of at most 4 patches (4096 elements)
+                             with use_graph = 1 is solved instead by one CTA that runs
+                             every iteration of the textbook mixed form (with FP64
+                             replacement residuals) with block barriers in place of
+                             launches: such a mesh leaves the grid-wide iteration bound by
+                             launch latency; use_graph = 0 keeps the grid-wide one    */
     EBE_PREC_MIXED_TEXTBOOK = 2   /* EBE_PREC_MIXED arithmetic in the textbook four-launch
                              iteration (operator, update, direction; two reductions), for
                              comparison; ebe_solve only                               */

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libebe.so")
 
-CU_SOURCES = ["k_patch.cu", "k_assemble.cu", "k_vec.cu", "k_batch.cu", "k_mpnn.cu", "k_alt.cu", "api.cu"]
+CU_SOURCES = ["k_patch.cu", "k_assemble.cu", "k_vec.cu", "k_batch.cu", "k_mpnn.cu", "k_alt.cu", "k_small.cu", "api.cu"]
 CXX_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -61,6 +61,7 @@ struct ebe_handle {
     // scratch of the patch passes
     double* halo64 = nullptr;
     float* halo32 = nullptr;
+    SmallInfo* small_info = nullptr;  // outcome of the one-CTA solver
     double* halo2 = nullptr;
     double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
     double* part_vec = nullptr;     // 3 * 1216
@@ -1210,6 +1211,52 @@ int solve_cg1_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opt
     return status;
 }
 
+// The whole mixed-precision solve of a mesh of at most kSmallPatches
+// patches in one CTA (k_cg_small): such a mesh leaves the grid-wide
+// iteration bound by launch and barrier latency.
+constexpr int kSmallPatches = 4;
+
+bool small_eligible(const ebe_handle* h, const ebe_solve_opts& o) {
+    return o.precision == EBE_PREC_MIXED && o.use_graph != 0 && h->store == EBE_STORE_MIXED &&
+           h->pd.n_patches <= kSmallPatches && small_solver_smem(h->plan.n_n) <= size_t(200) * 1024;
+}
+
+int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = h->plan.n_n;
+    TRY(dalloc(h, &h->x64w, n));
+    TRY(dalloc(h, &h->small_info, 1));
+    int l = 0;
+    CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x0");
+    CK(launch_set_dirichlet(h->x64w, h->nd, h->g, h->n_d, h->st, &l), "x(nd) = g");
+    SmallOpts so;
+    so.rtol = o.rtol;
+    so.delta = o.delta;
+    so.maxit = o.maxit;
+    so.stall_updates = o.stall_updates;
+    CK(launch_cg_small(h->pd, n, h->A32, h->A64, h->b, h->dinv32, h->x64w, so, h->small_info, h->st, &l),
+       "one-CTA solver");
+    add_launches(h, l);
+    SmallInfo si{};
+    CK(cudaMemcpyAsync(&si, h->small_info, sizeof(SmallInfo), cudaMemcpyDeviceToHost, h->st), "read solver outcome");
+    CK(cudaMemcpyAsync(x, h->x64w, sizeof(double) * n, x_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       h->st), "copy x");
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    info.status = si.status;
+    info.iterations = si.iterations;
+    info.true_residuals = si.true_residuals;
+    info.rel_residual = si.rel;
+    info.r0_norm = si.r0;
+    info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (si.status != EBE_OK) {
+        const char* why = si.status == EBE_MAXIT ? "maxit reached" : si.status == EBE_STALL ? "true residual stalled"
+                                                                                             : "breakdown (p.Ap <= 0 or non-finite)";
+        h->err = std::string("solve stopped: ") + why;
+    }
+    return si.status;
+}
+
 int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts, ebe_solve_info* info) {
     TRY(check_ready(h, true));
     if (!x) return fail(h, EBE_INVALID_ARG, "x is NULL");
@@ -1222,7 +1269,9 @@ int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts,
         return fail(h, EBE_INVALID_ARG, "bad solve options");
     ebe_solve_info local{};
     Scope scp(h);
-    int s = o.precision == EBE_PREC_MIXED ? solve_cg1_impl(h, x, host, o, local) : solve_impl(h, x, host, o, local);
+    int s = o.precision != EBE_PREC_MIXED ? solve_impl(h, x, host, o, local)
+            : small_eligible(h, o)       ? solve_small_impl(h, x, host, o, local)
+                                         : solve_cg1_impl(h, x, host, o, local);
     if (info) *info = local;
     return s;
 }

@@ -1,0 +1,304 @@
+// Mixed-precision Jacobi-PCG of a small mesh in one CTA (sm_103a).
+//
+// A mesh of a few patches leaves the grid-wide solver latency-bound: each
+// iteration is two or four launches whose CTAs mostly wait (33^2 triangles:
+// about 29 us per iteration).  Here one CTA of 1024 threads runs the whole
+// solve, with every node vector in shared memory and block barriers in place
+// of launches.  The arithmetic is the textbook mixed form of the library
+// (EBE_PREC_MIXED_TEXTBOOK): the FP32 difference-form operator on the FP32
+// direction, FP32 recurrence residual, FP64 solution, and the FP64 true
+// residual b - A x (FP64 element matrices) at every replacement and for the
+// stopping test.  Patches are processed one after another (their elements
+// share nodes across patches); inside a patch its colour classes let the
+// threads add element products into the node sums without conflicts, one
+// slot per thread.  The decisions (alpha, beta, replacement, convergence,
+// stall, breakdown, maxit) follow the host loop of the grid-wide solver; every
+// thread takes them from the same block totals.  Every sum has a fixed order:
+// bitwise reproducible.
+#include <cstdint>
+
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace ebe {
+namespace {
+
+constexpr int NT = kPatch;   // one thread per slot of a patch
+
+struct SmallSmem {
+    uint32_t red, x, acc64, r, p, acc, dinv, total;
+};
+__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n) {
+    SmallSmem s{};
+    const uint32_t n = uint32_t((n_n + 3) / 4 * 4);
+    s.red = 0;                                   // block-reduction scratch, 2 x 32 doubles
+    s.x = 64 * 8;                                // FP64 solution
+    s.acc64 = s.x + n * 8;                       // FP64 node sums / true residual
+    s.r = s.acc64 + n * 8;                       // FP32 recurrence residual
+    s.p = s.r + n * 4;                           // FP32 direction
+    s.acc = s.p + n * 4;                         // FP32 node sums / q = A p
+    s.dinv = s.acc + n * 4;                      // FP32 inverse Jacobi diagonal (0: Dirichlet)
+    s.total = s.dinv + n * 4;
+    return s;
+}
+
+// Two compensated FP32 sums over the block, totals in FP64 (valid in every
+// thread on return).
+__device__ __forceinline__ void block_sums2(CompSum a, CompSum b, double& ta, double& tb, double* red) {
+    CompSum v[2] = {a, b};
+    double out[2];
+    block_sums_comp<2, NT>(v, out, red);
+    __shared__ double tot[2];
+    if (threadIdx.x == 0) { tot[0] = out[0]; tot[1] = out[1]; }
+    __syncthreads();
+    ta = tot[0];
+    tb = tot[1];
+    __syncthreads();
+}
+
+// One FP64 sum over the block (valid in every thread).
+__device__ __forceinline__ double block_sum64(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = red[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    t = red[32];
+    __syncthreads();
+    return t;
+}
+
+// acc (T) = sum over elements of A_e v_e at the nodes, patch by patch,
+// colour rounds inside a patch.  FP32: the difference-form matrices A32 with
+// v = p; FP64: the plain FP64 matrices with v = x.  Ends synchronised.
+template <typename T, int NB>
+__device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restrict__ A, const T* __restrict__ v,
+                                             T* __restrict__ acc, int64_t n_n) {
+    const int tid = threadIdx.x;
+    for (int64_t i = tid; i < n_n; i += NT) acc[i] = T(0);
+    __syncthreads();
+    const int64_t ns = pd.n_slots;
+    for (int pp = 0; pp < pd.n_patches; ++pp) {
+        const PatchMeta m = pd.meta[pp];
+        const int64_t s = int64_t(pp) * kPatch + tid;
+        const bool ok = tid < m.n_el;
+        int g[NB];
+        T ve[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            g[i] = ok ? (__ldg(pd.pnode + m.node_off + int(__ldg(pd.lconn + i * ns + s))) & kNodeMask) : 0;
+            ve[i] = ok ? v[g[i]] : T(0);
+        }
+        T y[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            T a;
+            if constexpr (sizeof(T) == 4) {
+                // difference form: the diagonal slot holds the row sum
+                a = ok ? __ldg(A + sym_index(NB, r, r) * ns + s) * ve[r] : T(0);
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    if (j != r) a = ok ? fmadd(__ldg(A + sym_index(NB, r, j) * ns + s), ve[j] - ve[r], a) : a;
+            } else {
+                a = T(0);
+#pragma unroll
+                for (int j = 0; j < NB; ++j) a = ok ? fmadd(__ldg(A + sym_index(NB, r, j) * ns + s), ve[j], a) : a;
+            }
+            y[r] = a;
+        }
+        int c = 0;
+        for (; c < m.n_col; ++c) {
+            const int lo = __ldg(pd.col_ptr + m.col_off + c), hi = __ldg(pd.col_ptr + m.col_off + c + 1);
+            if (tid >= lo && tid < hi) {
+#pragma unroll
+                for (int r = 0; r < NB; ++r) acc[g[r]] += y[r];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NT, 1)
+k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const double* __restrict__ A64,
+           const double* __restrict__ b, const float* __restrict__ dinv_g, double* __restrict__ x_g,
+           SmallOpts o, SmallInfo* __restrict__ info) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmallSmem L = small_layout(n_n);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    double* x = reinterpret_cast<double*>(smem + L.x);
+    double* acc64 = reinterpret_cast<double*>(smem + L.acc64);
+    float* r = reinterpret_cast<float*>(smem + L.r);
+    float* p = reinterpret_cast<float*>(smem + L.p);
+    float* acc = reinterpret_cast<float*>(smem + L.acc);
+    float* dinv = reinterpret_cast<float*>(smem + L.dinv);
+    const int tid = threadIdx.x;
+    // The scalars of the iteration are formed by every thread from the same
+    // block totals, so they agree in all threads without being shared.
+    double rho = 0.0, beta = 0.0;
+    bool init_dir = true;
+
+    for (int64_t i = tid; i < n_n; i += NT) {
+        x[i] = x_g[i];
+        dinv[i] = dinv_g[i];
+    }
+    __syncthreads();
+
+    // r64 = mask(b - A64 x) into acc64, returns its r.r
+    auto true_residual = [&]() -> double {
+        element_sums<double, NB>(pd, A64, x, acc64, n_n);
+        double rr = 0.0;
+        for (int64_t i = tid; i < n_n; i += NT) {
+            const double v = dinv[i] == 0.0f ? 0.0 : __ldg(b + i) - acc64[i];
+            acc64[i] = v;
+            rr = fmadd(v, v, rr);
+        }
+        return block_sum64(rr, red);
+    };
+    // the recurrence restarted from the true residual in acc64: r = fp32(r64);
+    // beta = r.z / rho (0 at the start), rho = r.z
+    auto restart = [&](bool init) {
+        CompSum rz, rr;
+        for (int64_t i = tid; i < n_n; i += NT) {
+            const float rf = d2f(acc64[i]);
+            r[i] = rf;
+            rz.add(rf * (dinv[i] * rf));
+            rr.add(rf * rf);
+        }
+        double trz, trr;
+        block_sums2(rz, rr, trz, trr, red);
+        beta = (init || !(rho != 0.0)) ? 0.0 : trz / rho;
+        rho = trz;
+        init_dir = init;
+    };
+    // p = z + beta p (p = z at the start)
+    auto direction = [&]() {
+        const float be = float(beta);
+        for (int64_t i = tid; i < n_n; i += NT) {
+            const float z = dinv[i] * r[i];
+            p[i] = init_dir ? z : fmaf(be, p[i], z);
+        }
+        __syncthreads();
+        init_dir = false;
+    };
+
+    const double rr0 = true_residual();
+    const double r0 = sqrt(rr0);
+    int64_t iters = 0;
+    int32_t n_true = 1, status = EBE_OK;
+    double rel = r0 > 0.0 ? 1.0 : 0.0;
+    if (!isfinite(r0)) status = EBE_BREAKDOWN;
+    if (r0 > 0.0 && isfinite(r0)) {
+        double fin = o.rtol * r0, best = 1.0;
+        double thr = fmax(o.delta * r0, fin);
+        double thr2 = thr * thr;
+        int no_progress = 0;
+        restart(true);
+        direction();
+        int reason = kRunning;
+        for (;;) {
+            if (reason == kRunning) {
+                // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
+                element_sums<float, NB>(pd, A32, p, acc, n_n);
+                CompSum pq, none;
+                for (int64_t i = tid; i < n_n; i += NT) {
+                    const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
+                    acc[i] = qv;
+                    pq.add(p[i] * qv);
+                }
+                double tpq, tnone;
+                block_sums2(pq, none, tpq, tnone, red);
+                if (!(tpq > 0.0) || !isfinite(tpq)) { reason = kBreakdown; continue; }
+                const double al = rho / tpq;
+                const float alf = d2f(al);
+                CompSum rz, rr;
+                for (int64_t i = tid; i < n_n; i += NT) {
+                    x[i] = fmadd(al, f2d(p[i]), x[i]);
+                    const float rf = fmaf(-alf, acc[i], r[i]);
+                    r[i] = rf;
+                    rz.add(rf * (dinv[i] * rf));
+                    rr.add(rf * rf);
+                }
+                double trz, trr;
+                block_sums2(rz, rr, trz, trr, red);
+                ++iters;
+                if (!isfinite(trz) || !isfinite(trr) || trz < 0.0) { reason = kBreakdown; continue; }
+                if (trr <= thr2) { reason = kTrigger; continue; }      // rho stays for the replacement
+                if (iters >= o.maxit) { reason = kMaxit; continue; }
+                beta = trz / rho;
+                rho = trz;
+                direction();
+                continue;
+            }
+            if (reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
+            const double rrt = true_residual();
+            ++n_true;
+            rel = sqrt(rrt) / r0;
+            if (!isfinite(rel)) { status = EBE_BREAKDOWN; break; }
+            if (rel <= o.rtol) { status = EBE_OK; break; }
+            if (reason == kMaxit) { status = EBE_MAXIT; break; }
+            if (rel < 0.9 * best) {
+                best = rel;
+                no_progress = 0;
+            } else if (++no_progress >= o.stall_updates) {
+                status = EBE_STALL;
+                break;
+            }
+            // a failed check at the final threshold tightens it (the FP32
+            // recurrence drifted below the true residual)
+            if (reason == kTrigger && thr <= fin) fin *= kFinalMargin;
+            // residual replacement: continue CG from the true residual, same direction
+            restart(false);
+            direction();
+            thr = fmax(o.delta * sqrt(rrt), fin);
+            thr2 = thr * thr;
+            reason = kRunning;
+        }
+        if (status == EBE_BREAKDOWN) {
+            const double rrt = true_residual();
+            rel = sqrt(rrt) / r0;
+        }
+    }
+    for (int64_t i = tid; i < n_n; i += NT) x_g[i] = x[i];
+    if (tid == 0) {
+        info->iterations = iters;
+        info->true_residuals = n_true;
+        info->status = status;
+        info->r0 = r0;
+        info->rel = rel;
+    }
+}
+
+}  // namespace
+
+size_t small_solver_smem(int64_t n_n) { return small_layout(n_n).total; }
+
+cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
+                            const float* dinv, double* x, const SmallOpts& o, SmallInfo* info, cudaStream_t st,
+                            int* launches) {
+    const size_t sm = small_layout(n_n).total;
+    if (sm > 227 * 1024 || pd.n_patches < 1) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if (pd.nb == 3) {
+        e = cudaFuncSetAttribute(k_cg_small<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_cg_small<3><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, o, info);
+    } else {
+        e = cudaFuncSetAttribute(k_cg_small<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        k_cg_small<4><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, o, info);
+    }
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace ebe

@@ -304,6 +304,28 @@ struct BatchDev {
     uint64_t barrier_ns = 2000000000ull;   // bound of one grid-barrier wait
 };
 
+// Options and outcome of the one-CTA mixed-precision solver of small meshes.
+struct SmallOpts {
+    double rtol = 1e-8, delta = 0.1;
+    int64_t maxit = 0;
+    int32_t stall_updates = 8;
+    int32_t pad = 0;
+};
+struct SmallInfo {
+    int64_t iterations;
+    int32_t true_residuals;
+    int32_t status;        // ebe_status
+    double r0;             // |r(x0)|, FP64
+    double rel;            // last true relative residual
+};
+// Shared memory the one-CTA solver needs for n_n nodes.
+size_t small_solver_smem(int64_t n_n);
+// Jacobi-PCG (textbook mixed form) of the whole mesh in one CTA: x (device,
+// FP64, Dirichlet values set) in and out; pd in the caller's numbering.
+cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
+                            const float* dinv, double* x, const SmallOpts& o, SmallInfo* info, cudaStream_t st,
+                            int* launches);
+
 // Per-problem state reset: every problem starts with the true residual of x0.
 cudaError_t launch_batch_init(const BatchDev& bd, cudaStream_t st, int* launches);
 // CTAs per SM that fit for the persistent kernel of this batch (0: none).

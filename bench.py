@@ -872,6 +872,7 @@ def run_ours(args):
         "apply_fp32": {"gbs": round(ach, 1), "frac": round(ach / peak, 4),
                        "kernel": "FP32 operator application: patch pass + halo fix-up",
                        "ms_per_launch": [round(ms_patch, 5), round(ms_fix, 5)], "bytes_per_launch": m["apply32"],
+                       "traffic": traffic_record("apply32"),
                        "stored_gbs": round(m_stored["apply32"] / ((ms_patch + ms_fix) / 1e3) / 1e9, 1)},
         "residual_fp64": {"gbs": round(ach64, 1), "frac": round(ach64 / peak, 4),
                           "ms_per_launch": [round(ms_patch64, 5), round(ms_fix64, 5)],

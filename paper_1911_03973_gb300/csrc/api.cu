@@ -1218,7 +1218,8 @@ constexpr int kSmallPatches = 4;
 
 bool small_eligible(const ebe_handle* h, const ebe_solve_opts& o) {
     return o.precision == EBE_PREC_MIXED && o.use_graph != 0 && h->store == EBE_STORE_MIXED &&
-           h->pd.n_patches <= kSmallPatches && small_solver_smem(h->plan.n_n) <= size_t(200) * 1024;
+           h->pd.n_patches <= kSmallPatches &&
+           small_solver_smem(h->plan.n_n, h->pd.n_slots, h->pd.nb) <= size_t(200) * 1024;
 }
 
 int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {

@@ -26,11 +26,14 @@ namespace {
 constexpr int NT = kPatch;   // one thread per slot of a patch
 
 struct SmallSmem {
-    uint32_t red, x, acc64, r, p, acc, dinv, total;
+    uint32_t red, x, acc64, r, p, acc, dinv, lid, a32, total;
 };
-__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n) {
+// Node vectors, then the slots' node ids (16-bit, the caller's numbering) and
+// FP32 matrices, copied once: an iteration then reads only shared memory.
+__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_slots, int nb) {
     SmallSmem s{};
     const uint32_t n = uint32_t((n_n + 3) / 4 * 4);
+    const uint32_t ns = uint32_t(n_slots);
     s.red = 0;                                   // block-reduction scratch, 2 x 32 doubles
     s.x = 64 * 8;                                // FP64 solution
     s.acc64 = s.x + n * 8;                       // FP64 node sums / true residual
@@ -38,7 +41,9 @@ __host__ __device__ constexpr SmallSmem small_layout(int64_t n_n) {
     s.p = s.r + n * 4;                           // FP32 direction
     s.acc = s.p + n * 4;                         // FP32 node sums / q = A p
     s.dinv = s.acc + n * 4;                      // FP32 inverse Jacobi diagonal (0: Dirichlet)
-    s.total = s.dinv + n * 4;
+    s.lid = s.dinv + n * 4;                      // [nb][n_slots] uint16 node ids
+    s.a32 = (s.lid + uint32_t(nb) * ns * 2 + 15) / 16 * 16;   // [nb(nb+1)/2][n_slots] FP32 matrices
+    s.total = s.a32 + uint32_t(nb * (nb + 1) / 2) * ns * 4;
     return s;
 }
 
@@ -78,11 +83,12 @@ __device__ __forceinline__ double block_sum64(double v, double* red) {
 }
 
 // acc (T) = sum over elements of A_e v_e at the nodes, patch by patch,
-// colour rounds inside a patch.  FP32: the difference-form matrices A32 with
-// v = p; FP64: the plain FP64 matrices with v = x.  Ends synchronised.
+// colour rounds inside a patch.  FP32: the difference-form matrices in
+// shared memory (As) with v = p; FP64: the plain FP64 matrices from global
+// memory (A) with v = x.  lid: the slots' node ids.  Ends synchronised.
 template <typename T, int NB>
 __device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restrict__ A, const T* __restrict__ v,
-                                             T* __restrict__ acc, int64_t n_n) {
+                                             T* __restrict__ acc, int64_t n_n, const uint16_t* __restrict__ lid) {
     const int tid = threadIdx.x;
     for (int64_t i = tid; i < n_n; i += NT) acc[i] = T(0);
     __syncthreads();
@@ -95,7 +101,7 @@ __device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restr
         T ve[NB];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            g[i] = ok ? (__ldg(pd.pnode + m.node_off + int(__ldg(pd.lconn + i * ns + s))) & kNodeMask) : 0;
+            g[i] = ok ? int(lid[i * ns + s]) : 0;
             ve[i] = ok ? v[g[i]] : T(0);
         }
         T y[NB];
@@ -104,10 +110,10 @@ __device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restr
             T a;
             if constexpr (sizeof(T) == 4) {
                 // difference form: the diagonal slot holds the row sum
-                a = ok ? __ldg(A + sym_index(NB, r, r) * ns + s) * ve[r] : T(0);
+                a = ok ? A[sym_index(NB, r, r) * ns + s] * ve[r] : T(0);
 #pragma unroll
                 for (int j = 0; j < NB; ++j)
-                    if (j != r) a = ok ? fmadd(__ldg(A + sym_index(NB, r, j) * ns + s), ve[j] - ve[r], a) : a;
+                    if (j != r) a = ok ? fmadd(A[sym_index(NB, r, j) * ns + s], ve[j] - ve[r], a) : a;
             } else {
                 a = T(0);
 #pragma unroll
@@ -115,8 +121,7 @@ __device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restr
             }
             y[r] = a;
         }
-        int c = 0;
-        for (; c < m.n_col; ++c) {
+        for (int c = 0; c < m.n_col; ++c) {
             const int lo = __ldg(pd.col_ptr + m.col_off + c), hi = __ldg(pd.col_ptr + m.col_off + c + 1);
             if (tid >= lo && tid < hi) {
 #pragma unroll
@@ -133,7 +138,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
            const double* __restrict__ b, const float* __restrict__ dinv_g, double* __restrict__ x_g,
            SmallOpts o, SmallInfo* __restrict__ info) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmallSmem L = small_layout(n_n);
+    const SmallSmem L = small_layout(n_n, pd.n_slots, NB);
     double* red = reinterpret_cast<double*>(smem + L.red);
     double* x = reinterpret_cast<double*>(smem + L.x);
     double* acc64 = reinterpret_cast<double*>(smem + L.acc64);
@@ -141,6 +146,8 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     float* p = reinterpret_cast<float*>(smem + L.p);
     float* acc = reinterpret_cast<float*>(smem + L.acc);
     float* dinv = reinterpret_cast<float*>(smem + L.dinv);
+    uint16_t* lid = reinterpret_cast<uint16_t*>(smem + L.lid);
+    float* a32 = reinterpret_cast<float*>(smem + L.a32);
     const int tid = threadIdx.x;
     // The scalars of the iteration are formed by every thread from the same
     // block totals, so they agree in all threads without being shared.
@@ -151,11 +158,24 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         x[i] = x_g[i];
         dinv[i] = dinv_g[i];
     }
+    {
+        const int64_t ns = pd.n_slots;
+        for (int64_t s = tid; s < ns; s += NT) {
+            const PatchMeta m = pd.meta[s / kPatch];
+            const bool ok = (s % kPatch) < m.n_el;
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                lid[i * ns + s] = ok ? uint16_t(__ldg(pd.pnode + m.node_off + int(__ldg(pd.lconn + i * ns + s))) & kNodeMask)
+                                     : uint16_t(0);
+#pragma unroll
+            for (int t = 0; t < sym_count(NB); ++t) a32[t * ns + s] = __ldg(A32 + t * ns + s);
+        }
+    }
     __syncthreads();
 
     // r64 = mask(b - A64 x) into acc64, returns its r.r
     auto true_residual = [&]() -> double {
-        element_sums<double, NB>(pd, A64, x, acc64, n_n);
+        element_sums<double, NB>(pd, A64, x, acc64, n_n, lid);
         double rr = 0.0;
         for (int64_t i = tid; i < n_n; i += NT) {
             const double v = dinv[i] == 0.0f ? 0.0 : __ldg(b + i) - acc64[i];
@@ -208,7 +228,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         for (;;) {
             if (reason == kRunning) {
                 // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
-                element_sums<float, NB>(pd, A32, p, acc, n_n);
+                element_sums<float, NB>(pd, a32, p, acc, n_n, lid);
                 CompSum pq, none;
                 for (int64_t i = tid; i < n_n; i += NT) {
                     const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
@@ -280,12 +300,14 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
 
 }  // namespace
 
-size_t small_solver_smem(int64_t n_n) { return small_layout(n_n).total; }
+size_t small_solver_smem(int64_t n_n, int64_t n_slots, int nb) {
+    return n_n > 65536 ? size_t(1) << 40 : small_layout(n_n, n_slots, nb).total;
+}
 
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
                             const float* dinv, double* x, const SmallOpts& o, SmallInfo* info, cudaStream_t st,
                             int* launches) {
-    const size_t sm = small_layout(n_n).total;
+    const size_t sm = small_solver_smem(n_n, pd.n_slots, pd.nb);
     if (sm > 227 * 1024 || pd.n_patches < 1) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (pd.nb == 3) {

@@ -318,8 +318,8 @@ struct SmallInfo {
     double r0;             // |r(x0)|, FP64
     double rel;            // last true relative residual
 };
-// Shared memory the one-CTA solver needs for n_n nodes.
-size_t small_solver_smem(int64_t n_n);
+// Shared memory the one-CTA solver needs (node ids are 16-bit: n_n <= 65536).
+size_t small_solver_smem(int64_t n_n, int64_t n_slots, int nb);
 // Jacobi-PCG (textbook mixed form) of the whole mesh in one CTA: x (device,
 // FP64, Dirichlet values set) in and out; pd in the caller's numbering.
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,

@@ -12,9 +12,8 @@
 // share nodes across patches); inside a patch its colour classes let the
 // threads add element products into the node sums without conflicts, one
 // slot per thread.  The decisions (alpha, beta, replacement, convergence,
-// stall, breakdown, maxit) follow the host loop of the grid-wide solver; every
-// thread takes them from the same block totals.  Every sum has a fixed order:
-// bitwise reproducible.
+// stall, breakdown, maxit) follow the host loop of the grid-wide solver, taken
+// by thread 0.  Every sum has a fixed order: bitwise reproducible.
 #include <cstdint>
 
 #include "device_util.cuh"
@@ -47,21 +46,33 @@ __host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_slot
     return s;
 }
 
-// Two compensated FP32 sums over the block, totals in FP64 (valid in every
-// thread on return).
+// Two compensated FP32 sums over the block, totals in FP64 valid in thread 0
+// (the caller broadcasts what it derives from them): warp butterflies, then
+// warp 0 adds the 32 warp totals with another butterfly, all in FP32; one
+// FP64 conversion at the end.
 __device__ __forceinline__ void block_sums2(CompSum a, CompSum b, double& ta, double& tb, double* red) {
-    CompSum v[2] = {a, b};
-    double out[2];
-    block_sums_comp<2, NT>(v, out, red);
-    __shared__ double tot[2];
-    if (threadIdx.x == 0) { tot[0] = out[0]; tot[1] = out[1]; }
+    static_assert(NT == 1024, "32 warps");
+    warp_sum(a);
+    warp_sum(b);
+    float2* red2 = reinterpret_cast<float2*>(red);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    ta = tot[0];
-    tb = tot[1];
+    if (lane == 0) {
+        red2[w] = make_float2(a.s, a.c);
+        red2[32 + w] = make_float2(b.s, b.c);
+    }
     __syncthreads();
+    ta = tb = 0.0;
+    if (w == 0) {
+        CompSum x = comp_of(red2[lane]), y = comp_of(red2[32 + lane]);
+        warp_sum(x);
+        warp_sum(y);
+        ta = x.value();
+        tb = y.value();
+    }
 }
 
-// One FP64 sum over the block (valid in every thread).
+// One FP64 sum over the block, valid in thread 0.
 __device__ __forceinline__ double block_sum64(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -74,11 +85,7 @@ __device__ __forceinline__ double block_sum64(double v, double* red) {
         t = red[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[32] = t;
     }
-    __syncthreads();
-    t = red[32];
-    __syncthreads();
     return t;
 }
 
@@ -149,10 +156,16 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     uint16_t* lid = reinterpret_cast<uint16_t*>(smem + L.lid);
     float* a32 = reinterpret_cast<float*>(smem + L.a32);
     const int tid = threadIdx.x;
-    // The scalars of the iteration are formed by every thread from the same
-    // block totals, so they agree in all threads without being shared.
-    double rho = 0.0, beta = 0.0;
-    bool init_dir = true;
+    // Thread 0 forms the iteration's scalars and takes its decisions (GB300's
+    // FP64 pipe issues two lanes per SM and clock: a division or square root
+    // in every thread would cost more than the iteration's vector work) and
+    // hands them to the block through shared memory.
+    struct Ctl {
+        double rho, beta, al, r0, rel, fin, thr, thr2, best, rrt;
+        int64_t iters;
+        int32_t n_true, status, reason, no_progress, init_dir, pad;
+    };
+    __shared__ Ctl C;
 
     for (int64_t i = tid; i < n_n; i += NT) {
         x[i] = x_g[i];
@@ -171,9 +184,16 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
             for (int t = 0; t < sym_count(NB); ++t) a32[t * ns + s] = __ldg(A32 + t * ns + s);
         }
     }
+    if (tid == 0) {
+        C.rho = C.beta = 0.0;
+        C.iters = 0;
+        C.n_true = 0;
+        C.status = EBE_OK;
+        C.init_dir = 1;
+    }
     __syncthreads();
 
-    // r64 = mask(b - A64 x) into acc64, returns its r.r
+    // r64 = mask(b - A64 x) into acc64; its r.r in thread 0
     auto true_residual = [&]() -> double {
         element_sums<double, NB>(pd, A64, x, acc64, n_n, lid);
         double rr = 0.0;
@@ -196,37 +216,46 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         }
         double trz, trr;
         block_sums2(rz, rr, trz, trr, red);
-        beta = (init || !(rho != 0.0)) ? 0.0 : trz / rho;
-        rho = trz;
-        init_dir = init;
+        if (tid == 0) {
+            C.beta = (init || !(C.rho != 0.0)) ? 0.0 : trz / C.rho;
+            C.rho = trz;
+            C.init_dir = init ? 1 : 0;
+        }
+        __syncthreads();
     };
     // p = z + beta p (p = z at the start)
     auto direction = [&]() {
-        const float be = float(beta);
+        const float be = float(C.beta);
+        const bool init = C.init_dir != 0;
         for (int64_t i = tid; i < n_n; i += NT) {
             const float z = dinv[i] * r[i];
-            p[i] = init_dir ? z : fmaf(be, p[i], z);
+            p[i] = init ? z : fmaf(be, p[i], z);
         }
         __syncthreads();
-        init_dir = false;
+        if (tid == 0) C.init_dir = 0;
     };
 
-    const double rr0 = true_residual();
-    const double r0 = sqrt(rr0);
-    int64_t iters = 0;
-    int32_t n_true = 1, status = EBE_OK;
-    double rel = r0 > 0.0 ? 1.0 : 0.0;
-    if (!isfinite(r0)) status = EBE_BREAKDOWN;
-    if (r0 > 0.0 && isfinite(r0)) {
-        double fin = o.rtol * r0, best = 1.0;
-        double thr = fmax(o.delta * r0, fin);
-        double thr2 = thr * thr;
-        int no_progress = 0;
+    {
+        const double rr0 = true_residual();
+        if (tid == 0) {
+            C.n_true = 1;
+            C.r0 = sqrt(rr0);
+            C.rel = C.r0 > 0.0 ? 1.0 : 0.0;
+            C.status = isfinite(C.r0) ? EBE_OK : EBE_BREAKDOWN;
+            C.fin = o.rtol * C.r0;
+            C.best = 1.0;
+            C.thr = fmax(o.delta * C.r0, C.fin);
+            C.thr2 = C.thr * C.thr;
+            C.no_progress = 0;
+            C.reason = kRunning;
+        }
+        __syncthreads();
+    }
+    if (C.r0 > 0.0 && isfinite(C.r0)) {
         restart(true);
         direction();
-        int reason = kRunning;
         for (;;) {
-            if (reason == kRunning) {
+            if (C.reason == kRunning) {
                 // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
                 element_sums<float, NB>(pd, a32, p, acc, n_n, lid);
                 CompSum pq, none;
@@ -237,8 +266,13 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
                 }
                 double tpq, tnone;
                 block_sums2(pq, none, tpq, tnone, red);
-                if (!(tpq > 0.0) || !isfinite(tpq)) { reason = kBreakdown; continue; }
-                const double al = rho / tpq;
+                if (tid == 0) {
+                    if (!(tpq > 0.0) || !isfinite(tpq)) C.reason = kBreakdown;
+                    else C.al = C.rho / tpq;
+                }
+                __syncthreads();
+                if (C.reason != kRunning) continue;
+                const double al = C.al;
                 const float alf = d2f(al);
                 CompSum rz, rr;
                 for (int64_t i = tid; i < n_n; i += NT) {
@@ -250,51 +284,70 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
                 }
                 double trz, trr;
                 block_sums2(rz, rr, trz, trr, red);
-                ++iters;
-                if (!isfinite(trz) || !isfinite(trr) || trz < 0.0) { reason = kBreakdown; continue; }
-                if (trr <= thr2) { reason = kTrigger; continue; }      // rho stays for the replacement
-                if (iters >= o.maxit) { reason = kMaxit; continue; }
-                beta = trz / rho;
-                rho = trz;
-                direction();
+                if (tid == 0) {
+                    C.iters += 1;
+                    if (!isfinite(trz) || !isfinite(trr) || trz < 0.0) C.reason = kBreakdown;
+                    else if (trr <= C.thr2) C.reason = kTrigger;       // rho stays for the replacement
+                    else if (C.iters >= o.maxit) C.reason = kMaxit;
+                    else {
+                        C.beta = trz / C.rho;
+                        C.rho = trz;
+                    }
+                }
+                __syncthreads();
+                if (C.reason == kRunning) direction();
                 continue;
             }
-            if (reason == kBreakdown) { status = EBE_BREAKDOWN; break; }
-            const double rrt = true_residual();
-            ++n_true;
-            rel = sqrt(rrt) / r0;
-            if (!isfinite(rel)) { status = EBE_BREAKDOWN; break; }
-            if (rel <= o.rtol) { status = EBE_OK; break; }
-            if (reason == kMaxit) { status = EBE_MAXIT; break; }
-            if (rel < 0.9 * best) {
-                best = rel;
-                no_progress = 0;
-            } else if (++no_progress >= o.stall_updates) {
-                status = EBE_STALL;
+            if (C.reason == kBreakdown) {
+                if (tid == 0) C.status = EBE_BREAKDOWN;
                 break;
             }
-            // a failed check at the final threshold tightens it (the FP32
-            // recurrence drifted below the true residual)
-            if (reason == kTrigger && thr <= fin) fin *= kFinalMargin;
+            const double rrt = true_residual();
+            // thread 0: the checks of the grid-wide solver's host loop
+            if (tid == 0) {
+                C.n_true += 1;
+                C.rrt = rrt;
+                const double rel = sqrt(rrt) / C.r0;
+                C.rel = rel;
+                int st = -1;
+                if (!isfinite(rel)) st = EBE_BREAKDOWN;
+                else if (rel <= o.rtol) st = EBE_OK;
+                else if (C.reason == kMaxit) st = EBE_MAXIT;
+                else if (rel < 0.9 * C.best) { C.best = rel; C.no_progress = 0; }
+                else if (++C.no_progress >= o.stall_updates) st = EBE_STALL;
+                if (st >= 0) {
+                    C.status = st;
+                    C.reason = -1;          // done
+                } else {
+                    // a failed check at the final threshold tightens it (the FP32
+                    // recurrence drifted below the true residual)
+                    if (C.reason == kTrigger && C.thr <= C.fin) C.fin *= kFinalMargin;
+                    C.thr = fmax(o.delta * sqrt(rrt), C.fin);
+                    C.thr2 = C.thr * C.thr;
+                }
+            }
+            __syncthreads();
+            if (C.reason == -1) break;
             // residual replacement: continue CG from the true residual, same direction
             restart(false);
             direction();
-            thr = fmax(o.delta * sqrt(rrt), fin);
-            thr2 = thr * thr;
-            reason = kRunning;
+            if (tid == 0) C.reason = kRunning;
+            __syncthreads();
         }
-        if (status == EBE_BREAKDOWN) {
+        __syncthreads();   // the status thread 0 set before the loop ended
+        if (C.status == EBE_BREAKDOWN) {
             const double rrt = true_residual();
-            rel = sqrt(rrt) / r0;
+            if (tid == 0) C.rel = sqrt(rrt) / C.r0;
         }
     }
+    __syncthreads();
     for (int64_t i = tid; i < n_n; i += NT) x_g[i] = x[i];
     if (tid == 0) {
-        info->iterations = iters;
-        info->true_residuals = n_true;
-        info->status = status;
-        info->r0 = r0;
-        info->rel = rel;
+        info->iterations = C.iters;
+        info->true_residuals = C.n_true;
+        info->status = C.status;
+        info->r0 = C.r0;
+        info->rel = C.rel;
     }
 }
 

@@ -62,6 +62,9 @@ struct ebe_handle {
     double* halo64 = nullptr;
     float* halo32 = nullptr;
     SmallInfo* small_info = nullptr;  // outcome of the one-CTA solver
+    int32_t* small_order = nullptr;   // its colouring of the whole mesh
+    int32_t* small_col = nullptr;
+    int small_ncol = 0;
     double* halo2 = nullptr;
     double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
     double* part_vec = nullptr;     // 3 * 1216
@@ -1219,7 +1222,24 @@ constexpr int kSmallPatches = 4;
 bool small_eligible(const ebe_handle* h, const ebe_solve_opts& o) {
     return o.precision == EBE_PREC_MIXED && o.use_graph != 0 && h->store == EBE_STORE_MIXED &&
            h->pd.n_patches <= kSmallPatches &&
-           small_solver_smem(h->plan.n_n, h->pd.n_slots, h->pd.nb) <= size_t(200) * 1024;
+           small_solver_smem(h->plan.n_n, h->plan.n_e, h->pd.nb) <= size_t(200) * 1024;
+}
+
+// A colouring of the whole mesh for the one-CTA solver (once per handle).
+int ensure_small_tables(ebe_handle* h) {
+    if (h->small_order) return EBE_OK;
+    TRY(ensure_gconn(h));
+    std::vector<int32_t> order;
+    std::vector<int64_t> col;
+    std::string err;
+    const int nc = global_colouring(h->plan, h->gconn_host, order, col, err);
+    if (nc < 1 || nc > kSmallMaxColours) return fail(h, EBE_INVALID_ARG, nc < 1 ? err : "too many colours for the one-CTA solver");
+    std::vector<int32_t> col32(col.begin(), col.end());
+    TRY(upload(h, &h->small_order, order.data(), int64_t(order.size())));
+    TRY(upload(h, &h->small_col, col32.data(), int64_t(col32.size())));
+    h->small_ncol = nc;
+    CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");   // the host tables go away
+    return EBE_OK;
 }
 
 int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_opts& o, ebe_solve_info& info) {
@@ -1227,6 +1247,7 @@ int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     const int64_t n = h->plan.n_n;
     TRY(dalloc(h, &h->x64w, n));
     TRY(dalloc(h, &h->small_info, 1));
+    TRY(ensure_small_tables(h));
     int l = 0;
     CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                        h->st), "copy x0");
@@ -1236,7 +1257,13 @@ int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     so.delta = o.delta;
     so.maxit = o.maxit;
     so.stall_updates = o.stall_updates;
-    CK(launch_cg_small(h->pd, n, h->A32, h->A64, h->b, h->dinv32, h->x64w, so, h->small_info, h->st, &l),
+    SmallColouring sc;
+    sc.order = h->small_order;
+    sc.col = h->small_col;
+    sc.gconn = h->gconn;
+    sc.n_e = int32_t(h->plan.n_e);
+    sc.n_col = h->small_ncol;
+    CK(launch_cg_small(h->pd, n, h->A32, h->A64, h->b, h->dinv32, h->x64w, sc, so, h->small_info, h->st, &l),
        "one-CTA solver");
     add_launches(h, l);
     SmallInfo si{};

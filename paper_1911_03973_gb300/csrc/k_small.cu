@@ -8,10 +8,9 @@
 // (EBE_PREC_MIXED_TEXTBOOK): the FP32 difference-form operator on the FP32
 // direction, FP32 recurrence residual, FP64 solution, and the FP64 true
 // residual b - A x (FP64 element matrices) at every replacement and for the
-// stopping test.  Patches are processed one after another (their elements
-// share nodes across patches); inside a patch its colour classes let the
-// threads add element products into the node sums without conflicts, one
-// slot per thread.  The decisions (alpha, beta, replacement, convergence,
+// stopping test.  The elements are taken in the order of a colouring of the
+// whole mesh (no two elements of a colour share a node), so the products of
+// a thread's elements are added into the node sums in one round per colour.  The decisions (alpha, beta, replacement, convergence,
 // stall, breakdown, maxit) follow the host loop of the grid-wide solver, taken
 // by thread 0.  Every sum has a fixed order: bitwise reproducible.
 #include <cstdint>
@@ -25,26 +24,30 @@ namespace {
 constexpr int NT = kPatch;   // one thread per slot of a patch
 
 struct SmallSmem {
-    uint32_t red, x, acc64, r, p, acc, dinv, lid, a32, total;
+    uint32_t red, cols, x, acc64, r, p, acc, dinv, lid, a32, total;
 };
-// Node vectors, then the slots' node ids (16-bit, the caller's numbering) and
-// FP32 matrices, copied once: an iteration then reads only shared memory.
-__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_slots, int nb) {
+// Node vectors, then the elements' node ids (16-bit, the caller's numbering)
+// and FP32 matrices in the order of a colouring of the whole mesh, copied
+// once: an iteration then reads only shared memory.
+__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, int nb) {
     SmallSmem s{};
     const uint32_t n = uint32_t((n_n + 3) / 4 * 4);
-    const uint32_t ns = uint32_t(n_slots);
+    const uint32_t ne = uint32_t((n_e + 3) / 4 * 4);
     s.red = 0;                                   // block-reduction scratch, 2 x 32 doubles
-    s.x = 64 * 8;                                // FP64 solution
+    s.cols = 64 * 8;                             // colour classes: kSmallMaxColours + 1 offsets
+    s.x = s.cols + 80 * 4;                       // FP64 solution
     s.acc64 = s.x + n * 8;                       // FP64 node sums / true residual
     s.r = s.acc64 + n * 8;                       // FP32 recurrence residual
     s.p = s.r + n * 4;                           // FP32 direction
     s.acc = s.p + n * 4;                         // FP32 node sums / q = A p
     s.dinv = s.acc + n * 4;                      // FP32 inverse Jacobi diagonal (0: Dirichlet)
-    s.lid = s.dinv + n * 4;                      // [nb][n_slots] uint16 node ids
-    s.a32 = (s.lid + uint32_t(nb) * ns * 2 + 15) / 16 * 16;   // [nb(nb+1)/2][n_slots] FP32 matrices
-    s.total = s.a32 + uint32_t(nb * (nb + 1) / 2) * ns * 4;
+    s.lid = s.dinv + n * 4;                      // [nb][n_e] uint16 node ids, colour order
+    s.a32 = (s.lid + uint32_t(nb) * ne * 2 + 15) / 16 * 16;   // [nb(nb+1)/2][n_e] FP32 matrices, colour order
+    s.total = s.a32 + uint32_t(nb * (nb + 1) / 2) * ne * 4;
     return s;
 }
+
+constexpr int kSmallEPT = 4;   // elements per thread: at most 4 * 1024 elements
 
 // Two compensated FP32 sums over the block, totals in FP64 valid in thread 0
 // (the caller broadcasts what it derives from them): warp butterflies, then
@@ -89,53 +92,79 @@ __device__ __forceinline__ double block_sum64(double v, double* red) {
     return t;
 }
 
-// acc (T) = sum over elements of A_e v_e at the nodes, patch by patch,
-// colour rounds inside a patch.  FP32: the difference-form matrices in
-// shared memory (As) with v = p; FP64: the plain FP64 matrices from global
-// memory (A) with v = x.  lid: the slots' node ids.  Ends synchronised.
-template <typename T, int NB>
-__device__ __forceinline__ void element_sums(const PlanDev& pd, const T* __restrict__ A, const T* __restrict__ v,
-                                             T* __restrict__ acc, int64_t n_n, const uint16_t* __restrict__ lid) {
+// acc = sum over the elements of A_e p_e at the nodes (FP32 difference-form
+// matrices in shared memory): products of a thread's elements first, then one
+// round per colour of the whole mesh (a colour's elements share no node).
+// Ends synchronised.
+template <int NB>
+__device__ __forceinline__ void operator32(const float* __restrict__ a32, const float* __restrict__ v,
+                                           float* __restrict__ acc, int64_t n_n, const uint16_t* __restrict__ lid,
+                                           int n_e, const int* __restrict__ cols, int n_col) {
     const int tid = threadIdx.x;
-    for (int64_t i = tid; i < n_n; i += NT) acc[i] = T(0);
-    __syncthreads();
-    const int64_t ns = pd.n_slots;
-    for (int pp = 0; pp < pd.n_patches; ++pp) {
-        const PatchMeta m = pd.meta[pp];
-        const int64_t s = int64_t(pp) * kPatch + tid;
-        const bool ok = tid < m.n_el;
-        int g[NB];
-        T ve[NB];
+    for (int64_t i = tid; i < n_n; i += NT) acc[i] = 0.0f;
+    int g[kSmallEPT][NB];
+    float y[kSmallEPT][NB];
+#pragma unroll
+    for (int j = 0; j < kSmallEPT; ++j) {
+        const int k = tid + j * NT;
+        const bool ok = k < n_e;
+        float ve[NB];
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            g[i] = ok ? int(lid[i * ns + s]) : 0;
-            ve[i] = ok ? v[g[i]] : T(0);
+            g[j][i] = ok ? int(lid[i * n_e + k]) : 0;
+            ve[i] = ok ? v[g[j][i]] : 0.0f;
         }
-        T y[NB];
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
-            T a;
-            if constexpr (sizeof(T) == 4) {
-                // difference form: the diagonal slot holds the row sum
-                a = ok ? A[sym_index(NB, r, r) * ns + s] * ve[r] : T(0);
+            // difference form: the diagonal slot holds the row sum
+            float a = ok ? a32[sym_index(NB, r, r) * n_e + k] * ve[r] : 0.0f;
 #pragma unroll
-                for (int j = 0; j < NB; ++j)
-                    if (j != r) a = ok ? fmadd(A[sym_index(NB, r, j) * ns + s], ve[j] - ve[r], a) : a;
-            } else {
-                a = T(0);
-#pragma unroll
-                for (int j = 0; j < NB; ++j) a = ok ? fmadd(__ldg(A + sym_index(NB, r, j) * ns + s), ve[j], a) : a;
-            }
-            y[r] = a;
+            for (int jj = 0; jj < NB; ++jj)
+                if (jj != r) a = ok ? fmadd(a32[sym_index(NB, r, jj) * n_e + k], ve[jj] - ve[r], a) : a;
+            y[j][r] = a;
         }
-        for (int c = 0; c < m.n_col; ++c) {
-            const int lo = __ldg(pd.col_ptr + m.col_off + c), hi = __ldg(pd.col_ptr + m.col_off + c + 1);
-            if (tid >= lo && tid < hi) {
+    }
+    __syncthreads();
+    for (int c = 0; c < n_col; ++c) {
+        const int lo = cols[c], hi = cols[c + 1];
 #pragma unroll
-                for (int r = 0; r < NB; ++r) acc[g[r]] += y[r];
+        for (int j = 0; j < kSmallEPT; ++j) {
+            const int k = tid + j * NT;
+            if (k >= lo && k < hi) {
+#pragma unroll
+                for (int r = 0; r < NB; ++r) acc[g[j][r]] += y[j][r];
             }
-            __syncthreads();
         }
+        __syncthreads();
+    }
+}
+
+// acc64 = sum over the elements of A_e x_e (FP64 matrices from global memory,
+// element k of the colour order is slot order[k]), the products formed in
+// each colour's round (few registers: this runs once per replacement).
+template <int NB>
+__device__ __forceinline__ void operator64(const double* __restrict__ A64, int64_t n_slots,
+                                           const int32_t* __restrict__ order, const double* __restrict__ x,
+                                           double* __restrict__ acc, int64_t n_n, const uint16_t* __restrict__ lid,
+                                           int n_e, const int* __restrict__ cols, int n_col) {
+    const int tid = threadIdx.x;
+    for (int64_t i = tid; i < n_n; i += NT) acc[i] = 0.0;
+    __syncthreads();
+    for (int c = 0; c < n_col; ++c) {
+        for (int k = cols[c] + tid; k < cols[c + 1]; k += NT) {
+            const int64_t s = __ldg(order + k);
+            int g[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) g[i] = int(lid[i * n_e + k]);
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                double a = acc[g[r]];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) a = fmadd(__ldg(A64 + sym_index(NB, r, j) * n_slots + s), x[g[j]], a);
+                acc[g[r]] = a;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -143,9 +172,11 @@ template <int NB>
 __global__ void __launch_bounds__(NT, 1)
 k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const double* __restrict__ A64,
            const double* __restrict__ b, const float* __restrict__ dinv_g, double* __restrict__ x_g,
-           SmallOpts o, SmallInfo* __restrict__ info) {
+           SmallColouring sc, SmallOpts o, SmallInfo* __restrict__ info) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmallSmem L = small_layout(n_n, pd.n_slots, NB);
+    const int n_e = sc.n_e, n_col = sc.n_col;
+    const SmallSmem L = small_layout(n_n, n_e, NB);
+    int* cols = reinterpret_cast<int*>(smem + L.cols);
     double* red = reinterpret_cast<double*>(smem + L.red);
     double* x = reinterpret_cast<double*>(smem + L.x);
     double* acc64 = reinterpret_cast<double*>(smem + L.acc64);
@@ -173,16 +204,14 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     }
     {
         const int64_t ns = pd.n_slots;
-        for (int64_t s = tid; s < ns; s += NT) {
-            const PatchMeta m = pd.meta[s / kPatch];
-            const bool ok = (s % kPatch) < m.n_el;
+        for (int k = tid; k < n_e; k += NT) {
+            const int64_t s = __ldg(sc.order + k);
 #pragma unroll
-            for (int i = 0; i < NB; ++i)
-                lid[i * ns + s] = ok ? uint16_t(__ldg(pd.pnode + m.node_off + int(__ldg(pd.lconn + i * ns + s))) & kNodeMask)
-                                     : uint16_t(0);
+            for (int i = 0; i < NB; ++i) lid[i * n_e + k] = uint16_t(__ldg(sc.gconn + i * ns + s));
 #pragma unroll
-            for (int t = 0; t < sym_count(NB); ++t) a32[t * ns + s] = __ldg(A32 + t * ns + s);
+            for (int t = 0; t < sym_count(NB); ++t) a32[t * n_e + k] = __ldg(A32 + t * ns + s);
         }
+        for (int c = tid; c <= n_col; c += NT) cols[c] = __ldg(sc.col + c);
     }
     if (tid == 0) {
         C.rho = C.beta = 0.0;
@@ -195,7 +224,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
 
     // r64 = mask(b - A64 x) into acc64; its r.r in thread 0
     auto true_residual = [&]() -> double {
-        element_sums<double, NB>(pd, A64, x, acc64, n_n, lid);
+        operator64<NB>(A64, pd.n_slots, sc.order, x, acc64, n_n, lid, n_e, cols, n_col);
         double rr = 0.0;
         for (int64_t i = tid; i < n_n; i += NT) {
             const double v = dinv[i] == 0.0f ? 0.0 : __ldg(b + i) - acc64[i];
@@ -257,7 +286,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         for (;;) {
             if (C.reason == kRunning) {
                 // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
-                element_sums<float, NB>(pd, a32, p, acc, n_n, lid);
+                operator32<NB>(a32, p, acc, n_n, lid, n_e, cols, n_col);
                 CompSum pq, none;
                 for (int64_t i = tid; i < n_n; i += NT) {
                     const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
@@ -353,24 +382,24 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
 
 }  // namespace
 
-size_t small_solver_smem(int64_t n_n, int64_t n_slots, int nb) {
-    return n_n > 65536 ? size_t(1) << 40 : small_layout(n_n, n_slots, nb).total;
+size_t small_solver_smem(int64_t n_n, int64_t n_e, int nb) {
+    return (n_n > 65536 || n_e > int64_t(kSmallEPT) * NT) ? size_t(1) << 40 : small_layout(n_n, n_e, nb).total;
 }
 
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
-                            const float* dinv, double* x, const SmallOpts& o, SmallInfo* info, cudaStream_t st,
-                            int* launches) {
-    const size_t sm = small_solver_smem(n_n, pd.n_slots, pd.nb);
-    if (sm > 227 * 1024 || pd.n_patches < 1) return cudaErrorInvalidConfiguration;
+                            const float* dinv, double* x, const SmallColouring& sc, const SmallOpts& o,
+                            SmallInfo* info, cudaStream_t st, int* launches) {
+    const size_t sm = small_solver_smem(n_n, sc.n_e, pd.nb);
+    if (sm > 227 * 1024 || sc.n_col < 1 || sc.n_col > kSmallMaxColours) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (pd.nb == 3) {
         e = cudaFuncSetAttribute(k_cg_small<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
-        k_cg_small<3><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, o, info);
+        k_cg_small<3><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, sc, o, info);
     } else {
         e = cudaFuncSetAttribute(k_cg_small<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
-        k_cg_small<4><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, o, info);
+        k_cg_small<4><<<1, NT, sm, st>>>(pd, n_n, A32, A64, b, dinv, x, sc, o, info);
     }
     if (launches) *launches += 1;
     return cudaGetLastError();

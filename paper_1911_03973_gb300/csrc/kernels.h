@@ -318,13 +318,23 @@ struct SmallInfo {
     double r0;             // |r(x0)|, FP64
     double rel;            // last true relative residual
 };
-// Shared memory the one-CTA solver needs (node ids are 16-bit: n_n <= 65536).
-size_t small_solver_smem(int64_t n_n, int64_t n_slots, int nb);
+// A colouring of all elements of a small mesh (device arrays): element k of
+// the colour order is slot order[k]; colour c holds elements [col[c], col[c+1]).
+constexpr int kSmallMaxColours = 64;
+struct SmallColouring {
+    const int32_t* order = nullptr;   // [n_e]
+    const int32_t* col = nullptr;     // [n_col + 1]
+    const int32_t* gconn = nullptr;   // [nb][n_slots] global node ids per slot
+    int32_t n_e = 0, n_col = 0;
+};
+// Shared memory the one-CTA solver needs (node ids are 16-bit: n_n <= 65536;
+// at most 4096 elements).
+size_t small_solver_smem(int64_t n_n, int64_t n_e, int nb);
 // Jacobi-PCG (textbook mixed form) of the whole mesh in one CTA: x (device,
 // FP64, Dirichlet values set) in and out; pd in the caller's numbering.
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
-                            const float* dinv, double* x, const SmallOpts& o, SmallInfo* info, cudaStream_t st,
-                            int* launches);
+                            const float* dinv, double* x, const SmallColouring& sc, const SmallOpts& o,
+                            SmallInfo* info, cudaStream_t st, int* launches);
 
 // Per-problem state reset: every problem starts with the true residual of x0.
 cudaError_t launch_batch_init(const BatchDev& bd, cudaStream_t st, int* launches);

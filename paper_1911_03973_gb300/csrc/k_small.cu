@@ -4,12 +4,11 @@
 // iteration is two or four launches whose CTAs mostly wait (33^2 triangles:
 // about 29 us per iteration).  Here one CTA of 1024 threads runs the whole
 // solve, with every node vector in shared memory and block barriers in place
-// of launches.  The iteration is the library's single-sync mixed form (the
-// arithmetic of k_cg_patch + k_cg_fixup: one reduction of five sums per
-// iteration, the next r.z from its expansion): the FP32 difference-form
-// operator on the FP32 direction, FP32 recurrence residual, FP64 solution,
-// and the FP64 true residual b - A x (FP64 element matrices) at every
-// replacement and for the stopping test.  The elements are taken in the order of a colouring of the
+// of launches.  The arithmetic is the textbook mixed form of the library
+// (EBE_PREC_MIXED_TEXTBOOK): the FP32 difference-form operator on the FP32
+// direction, FP32 recurrence residual, FP64 solution, and the FP64 true
+// residual b - A x (FP64 element matrices) at every replacement and for the
+// stopping test.  The elements are taken in the order of a colouring of the
 // whole mesh (no two elements of a colour share a node), so the products of
 // a thread's elements are added into the node sums in one round per colour.  The decisions (alpha, beta, replacement, convergence,
 // stall, breakdown, maxit) follow the host loop of the grid-wide solver, taken
@@ -34,13 +33,13 @@ __host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, i
     SmallSmem s{};
     const uint32_t n = uint32_t((n_n + 3) / 4 * 4);
     const uint32_t ne = uint32_t((n_e + 3) / 4 * 4);
-    s.red = 0;                                   // block-reduction scratch, 5 x 32 float2
-    s.cols = 5 * 32 * 8;                         // colour classes: kSmallMaxColours + 1 offsets
+    s.red = 0;                                   // block-reduction scratch, 2 x 32 doubles
+    s.cols = 64 * 8;                             // colour classes: kSmallMaxColours + 1 offsets
     s.x = s.cols + 80 * 4;                       // FP64 solution
     s.acc64 = s.x + n * 8;                       // FP64 node sums / true residual
     s.r = s.acc64 + n * 8;                       // FP32 recurrence residual
-    s.p = s.r + n * 4;                           // FP32 directions: two buffers, read one, write the other
-    s.acc = s.p + 2 * n * 4;                     // FP32 node sums / q = A p
+    s.p = s.r + n * 4;                           // FP32 direction
+    s.acc = s.p + n * 4;                         // FP32 node sums / q = A p
     s.dinv = s.acc + n * 4;                      // FP32 inverse Jacobi diagonal (0: Dirichlet)
     s.lid = s.dinv + n * 4;                      // [nb][n_e] uint16 node ids, colour order
     s.a32 = (s.lid + uint32_t(nb) * ne * 2 + 15) / 16 * 16;   // [nb(nb+1)/2][n_e] FP32 matrices, colour order
@@ -50,31 +49,29 @@ __host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, i
 
 constexpr int kSmallEPT = 4;   // elements per thread: at most 4 * 1024 elements
 
-// K compensated FP32 sums over the block, totals in FP64 valid in thread 0
+// Two compensated FP32 sums over the block, totals in FP64 valid in thread 0
 // (the caller broadcasts what it derives from them): warp butterflies, then
 // warp 0 adds the 32 warp totals with another butterfly, all in FP32; one
 // FP64 conversion at the end.
-template <int K>
-__device__ __forceinline__ void block_sums(CompSum (&v)[K], double (&t)[K], double* red) {
-    static_assert(NT == 1024 && K <= 5, "32 warps, the scratch holds 5 sums");
-#pragma unroll
-    for (int k = 0; k < K; ++k) warp_sum(v[k]);
+__device__ __forceinline__ void block_sums2(CompSum a, CompSum b, double& ta, double& tb, double* red) {
+    static_assert(NT == 1024, "32 warps");
+    warp_sum(a);
+    warp_sum(b);
     float2* red2 = reinterpret_cast<float2*>(red);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) red2[k * 32 + w] = make_float2(v[k].s, v[k].c);
+    if (lane == 0) {
+        red2[w] = make_float2(a.s, a.c);
+        red2[32 + w] = make_float2(b.s, b.c);
+    }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = 0.0;
+    ta = tb = 0.0;
     if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            CompSum x = comp_of(red2[k * 32 + lane]);
-            warp_sum(x);
-            t[k] = x.value();
-        }
+        CompSum x = comp_of(red2[lane]), y = comp_of(red2[32 + lane]);
+        warp_sum(x);
+        warp_sum(y);
+        ta = x.value();
+        tb = y.value();
     }
 }
 
@@ -184,8 +181,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     double* x = reinterpret_cast<double*>(smem + L.x);
     double* acc64 = reinterpret_cast<double*>(smem + L.acc64);
     float* r = reinterpret_cast<float*>(smem + L.r);
-    float* p0 = reinterpret_cast<float*>(smem + L.p);
-    float* p1 = p0 + (n_n + 3) / 4 * 4;
+    float* p = reinterpret_cast<float*>(smem + L.p);
     float* acc = reinterpret_cast<float*>(smem + L.acc);
     float* dinv = reinterpret_cast<float*>(smem + L.dinv);
     uint16_t* lid = reinterpret_cast<uint16_t*>(smem + L.lid);
@@ -198,7 +194,7 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     struct Ctl {
         double rho, beta, al, r0, rel, fin, thr, thr2, best, rrt;
         int64_t iters;
-        int32_t n_true, status, reason, no_progress, fresh, par;
+        int32_t n_true, status, reason, no_progress, init_dir, pad;
     };
     __shared__ Ctl C;
 
@@ -218,12 +214,11 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         for (int c = tid; c <= n_col; c += NT) cols[c] = __ldg(sc.col + c);
     }
     if (tid == 0) {
-        C.rho = C.beta = C.al = 0.0;
+        C.rho = C.beta = 0.0;
         C.iters = 0;
         C.n_true = 0;
         C.status = EBE_OK;
-        C.fresh = 1;
-        C.par = 0;
+        C.init_dir = 1;
     }
     __syncthreads();
 
@@ -248,16 +243,25 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
             rz.add(rf * (dinv[i] * rf));
             rr.add(rf * rf);
         }
-        CompSum v[2] = {rz, rr};
-        double t[2];
-        block_sums<2>(v, t, red);
+        double trz, trr;
+        block_sums2(rz, rr, trz, trr, red);
         if (tid == 0) {
-            C.beta = (init || !(C.rho != 0.0)) ? 0.0 : t[0] / C.rho;
-            C.rho = t[0];
-            C.al = 0.0;                   // the next pass only forms the direction
-            C.fresh = 1;
+            C.beta = (init || !(C.rho != 0.0)) ? 0.0 : trz / C.rho;
+            C.rho = trz;
+            C.init_dir = init ? 1 : 0;
         }
         __syncthreads();
+    };
+    // p = z + beta p (p = z at the start)
+    auto direction = [&]() {
+        const float be = float(C.beta);
+        const bool init = C.init_dir != 0;
+        for (int64_t i = tid; i < n_n; i += NT) {
+            const float z = dinv[i] * r[i];
+            p[i] = init ? z : fmaf(be, p[i], z);
+        }
+        __syncthreads();
+        if (tid == 0) C.init_dir = 0;
     };
 
     {
@@ -277,72 +281,50 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         __syncthreads();
     }
     if (C.r0 > 0.0 && isfinite(C.r0)) {
-        // the recurrence starts from the true residual with p = q = 0
-        for (int64_t i = tid; i < n_n; i += NT) {
-            p0[i] = 0.0f;
-            p1[i] = 0.0f;
-            acc[i] = 0.0f;
-        }
-        __syncthreads();
         restart(true);
+        direction();
         for (;;) {
             if (C.reason == kRunning) {
-                // One single-sync pass (the iteration of k_cg_patch + k_cg_fixup):
-                // the node step of the last iteration, r = r - alpha q,
-                // x = x + alpha p, z = dinv r, p' = z + beta p (into the other
-                // buffer), then q = mask(A p') and the five sums of one reduction.
-                float* pold = C.par ? p1 : p0;
-                float* pnew = C.par ? p0 : p1;
-                const double al = C.al;
-                const float alf = d2f(al), bef = d2f(C.beta);
-                CompSum v[5];
+                // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
+                operator32<NB>(a32, p, acc, n_n, lid, n_e, cols, n_col);
+                CompSum pq, none;
                 for (int64_t i = tid; i < n_n; i += NT) {
-                    const float po = pold[i];
-                    const float rn = fmaf(-alf, acc[i], r[i]);
-                    const float z = dinv[i] * rn;
-                    x[i] = fmadd(al, f2d(po), x[i]);
-                    r[i] = rn;
-                    pnew[i] = fmaf(bef, po, z);
-                    v[0].add(rn * z);
-                    v[1].add(rn * rn);
+                    const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
+                    acc[i] = qv;
+                    pq.add(p[i] * qv);
                 }
-                __syncthreads();             // q of the last pass read everywhere
-                operator32<NB>(a32, pnew, acc, n_n, lid, n_e, cols, n_col);
-                for (int64_t i = tid; i < n_n; i += NT) {
-                    const float d = dinv[i];
-                    const float qn = d == 0.0f ? 0.0f : acc[i];
-                    const float z = d * r[i];
-                    acc[i] = qn;
-                    v[2].add(pnew[i] * qn);
-                    v[3].add(qn * z);
-                    v[4].add(qn * (d * qn));
-                }
-                double t[5];
-                block_sums<5>(v, t, red);
+                double tpq, tnone;
+                block_sums2(pq, none, tpq, tnone, red);
                 if (tid == 0) {
-                    // the decisions of the single-sync fix-up's last block
-                    const bool fresh = C.fresh != 0;
-                    C.fresh = 0;
-                    if (!fresh) C.iters += 1;
-                    C.par ^= 1;              // the next pass reads the direction just formed
-                    const double rho = t[0], rr = t[1], pq = t[2], qz = t[3], qdq = t[4];
-                    if (!isfinite(rho) || !isfinite(rr) || !isfinite(pq) || !isfinite(qz) || !isfinite(qdq) || rho < 0.0) {
-                        C.reason = kBreakdown;
-                    } else if (!fresh && rr <= C.thr2) {
-                        C.reason = kTrigger;      // rho keeps the previous direction's r.z
-                    } else if (!fresh && C.iters >= o.maxit) {
-                        C.reason = kMaxit;
-                    } else if (!(pq > 0.0)) {
-                        C.reason = kBreakdown;
-                    } else {
-                        const double a = rho / pq;
-                        const double rho_next = fmadd(a * a, qdq, fmadd(-2.0 * a, qz, rho));
-                        C.al = a;
-                        C.beta = rho_next > 0.0 ? rho_next / rho : 0.0;
-                        C.rho = rho;
+                    if (!(tpq > 0.0) || !isfinite(tpq)) C.reason = kBreakdown;
+                    else C.al = C.rho / tpq;
+                }
+                __syncthreads();
+                if (C.reason != kRunning) continue;
+                const double al = C.al;
+                const float alf = d2f(al);
+                CompSum rz, rr;
+                for (int64_t i = tid; i < n_n; i += NT) {
+                    x[i] = fmadd(al, f2d(p[i]), x[i]);
+                    const float rf = fmaf(-alf, acc[i], r[i]);
+                    r[i] = rf;
+                    rz.add(rf * (dinv[i] * rf));
+                    rr.add(rf * rf);
+                }
+                double trz, trr;
+                block_sums2(rz, rr, trz, trr, red);
+                if (tid == 0) {
+                    C.iters += 1;
+                    if (!isfinite(trz) || !isfinite(trr) || trz < 0.0) C.reason = kBreakdown;
+                    else if (trr <= C.thr2) C.reason = kTrigger;       // rho stays for the replacement
+                    else if (C.iters >= o.maxit) C.reason = kMaxit;
+                    else {
+                        C.beta = trz / C.rho;
+                        C.rho = trz;
                     }
                 }
                 __syncthreads();
+                if (C.reason == kRunning) direction();
                 continue;
             }
             if (C.reason == kBreakdown) {
@@ -371,15 +353,15 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
                     if (C.reason == kTrigger && C.thr <= C.fin) C.fin *= kFinalMargin;
                     C.thr = fmax(o.delta * sqrt(rrt), C.fin);
                     C.thr2 = C.thr * C.thr;
-                    // replacement: continue with the direction that preceded the
-                    // triggering pass (that pass formed the next one in the other buffer)
-                    C.par ^= 1;
-                    C.reason = kRunning;
                 }
             }
             __syncthreads();
             if (C.reason == -1) break;
+            // residual replacement: continue CG from the true residual, same direction
             restart(false);
+            direction();
+            if (tid == 0) C.reason = kRunning;
+            __syncthreads();
         }
         __syncthreads();   // the status thread 0 set before the loop ended
         if (C.status == EBE_BREAKDOWN) {

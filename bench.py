@@ -864,6 +864,7 @@ def run_ours(args):
                 "textbook_mixed_iterations": tinfo["iterations"] if tinfo else None},
         "roofline": {"bound": "hbm", "achieved": round(ach_cg, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach_cg / peak, 4), "traffic": trf,
+                     "frac_of_nominal_8000": round(ach_cg / 8000.0, 4),
                      "kernel": "one iteration of the mixed solver: single-sync pass (k_cg_patch + k_cg_fixup)",
                      "ms_per_launch": [round(ms_cg[0], 5), round(ms_cg[1], 5)],
                      "bytes_per_launch": m["cg_mixed"], "peak_kind": peak_kind,

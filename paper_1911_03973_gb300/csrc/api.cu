@@ -1247,7 +1247,6 @@ int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     const int64_t n = h->plan.n_n;
     TRY(dalloc(h, &h->x64w, n));
     TRY(dalloc(h, &h->small_info, 1));
-    TRY(ensure_small_tables(h));
     int l = 0;
     CK(cudaMemcpyAsync(h->x64w, x, sizeof(double) * n, x_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                        h->st), "copy x0");
@@ -1297,8 +1296,12 @@ int solve_entry(ebe_handle* h, double* x, bool host, const ebe_solve_opts* opts,
         return fail(h, EBE_INVALID_ARG, "bad solve options");
     ebe_solve_info local{};
     Scope scp(h);
+    // a small mesh whose colouring needs more colours than the one-CTA solver
+    // takes runs the grid-wide iteration
+    const bool small = small_eligible(h, o) && ensure_small_tables(h) == EBE_OK;
+    if (!small) h->err.clear();
     int s = o.precision != EBE_PREC_MIXED ? solve_impl(h, x, host, o, local)
-            : small_eligible(h, o)       ? solve_small_impl(h, x, host, o, local)
+            : small                      ? solve_small_impl(h, x, host, o, local)
                                          : solve_cg1_impl(h, x, host, o, local);
     if (info) *info = local;
     return s;

@@ -145,21 +145,26 @@ def fp64_alu_model(nb: int, n_n: int, n_e: int, sms: int, mhz):
     return {"ops_per_launch": int(ops), "peak_gops": round(2.0 * sms * float(mhz) * 1e6 / 1e9, 1)}
 
 
-def step_bytes(m, info, mixed: bool):
+def step_bytes(m, info, mixed: bool, textbook: bool = False):
     """Algorithmic bytes of one step: element matrices, then the solve as it
     runs.  Mixed (single-sync solver): one pass per iteration plus one first
     pass per start of the recurrence (the initial one and every replacement),
-    a restart and an FP64 true residual per check.  Plain FP64 (textbook
-    iteration): operator, update and direction per iteration."""
+    a restart and an FP64 true residual per check.  Textbook iteration
+    (plain FP64, and the mixed arithmetic in that form, as the batched solver
+    runs it): operator, update and direction per iteration, a true residual
+    per check and a restart per replacement."""
     it, tr = info["iterations"], info["true_residuals"]
-    if mixed:
+    if mixed and not textbook:
         return (m["assemble_mixed"] + (it + tr) * m["cg_mixed"] + tr * (m["residual64"] + m["cg_restart"]))
+    if mixed:
+        return (m["assemble_mixed"] + it * (m["apply32"] + m["vec_mixed"]) + tr * m["residual64"]
+                + max(tr - 1, 0) * m["restart_mixed"])
     return m["assemble_fp64"] + it * (m["apply64"] + m["vec64"]) + tr * m["residual64"] + max(tr - 1, 0) * m["restart64"]
 
 
-def solve_bytes(m, info, mixed: bool):
+def solve_bytes(m, info, mixed: bool, textbook: bool = False):
     """step_bytes without the element-matrix generation."""
-    return step_bytes(m, info, mixed) - m["assemble_mixed" if mixed else "assemble_fp64"]
+    return step_bytes(m, info, mixed, textbook) - m["assemble_mixed" if mixed else "assemble_fp64"]
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -339,7 +344,7 @@ def run_batch(args, dev, stream, profile=False):
     byt = 0
     for p, i in zip(probs, infos):
         mk = bytes_model(p["coords"].shape[1], p["coords"].shape[0], p["elems"].shape[0])
-        byt += solve_bytes(mk, i, True)
+        byt += solve_bytes(mk, i, True, textbook=True)     # the batched solver's textbook iteration
     its = [i["iterations"] for i in infos]
     return {
         "workload": f"batch{n_prob}_squares17-513_seed4", "n_problems": n_prob, "n_nodes": n,

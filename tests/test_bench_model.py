@@ -62,3 +62,16 @@ def test_single_sync_iteration_bytes():
     info = {"iterations": 100, "true_residuals": 3}
     assert bench.step_bytes(m, info, True) == (m["assemble_mixed"] + 103 * m["cg_mixed"]
                                                + 3 * (m["residual64"] + n_n * 16))
+
+
+def test_textbook_mixed_step_bytes():
+    # the textbook mixed iteration (the batched solver's form): FP32 operator,
+    # update and direction per iteration; an FP64 true residual per check and
+    # a restart (r64, dinv in; r32 out; then a direction step) per replacement
+    n_n, n_e = 2049 * 2049, 2 * 2048 * 2048
+    m = bench.bytes_model(2, n_n, n_e)
+    assert m["apply32"] + m["vec_mixed"] == n_e * 48 + n_n * (8 + 52)
+    assert m["restart_mixed"] == n_n * (16 + 16)
+    info = {"iterations": 100, "true_residuals": 3}
+    assert bench.solve_bytes(m, info, True, textbook=True) == (100 * (m["apply32"] + m["vec_mixed"])
+                                                               + 3 * m["residual64"] + 2 * m["restart_mixed"])

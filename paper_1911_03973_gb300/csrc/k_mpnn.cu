@@ -83,7 +83,7 @@ __device__ __forceinline__ void load_h(const __nv_bfloat16* h, int64_t i, float 
     const uint4* p = reinterpret_cast<const uint4*>(h + i * H);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const uint4 w = __ldcg(p + c);
+        const uint4 w = __ldg(p + c);
         const uint32_t q[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {

@@ -223,13 +223,9 @@ __global__ void __launch_bounds__(128) k_mpnn_layer(int64_t n, const int32_t* __
         if (valid) {
             load_h(h_in, i, hi);
             const int j0 = __ldg(nbr_ptr + i), j1 = __ldg(nbr_ptr + i + 1);
-            // the next neighbour's id is loaded while the current row is summed
-            int nxt = j0 < j1 ? __ldg(nbr + j0) : 0;
             for (int j = j0; j < j1; ++j) {
-                const int cur = nxt;
-                if (j + 1 < j1) nxt = __ldg(nbr + j + 1);
                 float hj[H];
-                load_h(h_in, cur, hj);
+                load_h(h_in, __ldg(nbr + j), hj);
 #pragma unroll
                 for (int o = 0; o < H; ++o) a[o] += hj[o];
             }

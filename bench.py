@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the learned preconditioner (257^2) and deploying it (1025^2, 2049^2)")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "dw", "assemble", "vec", "cg", "batch", "mpnn"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "dw", "assemble", "vec", "cg", "small", "batch", "mpnn"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -643,6 +643,21 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
+    if args.profile_kernel == "small":
+        # three mixed solves of the 33^2 square of the small configuration: one
+        # launch of the one-CTA solver each
+        p = meshgen.config_square_f1(33, nu=1.0)
+        with torch.cuda.stream(stream):
+            h = ebe.ebe_create(p["coords"], p["elems"], device=dev.index, stream=stream.cuda_stream)
+            ebe.ebe_set_problem(h, p["nu"], p["f"], p["dirichlet"], p["g"], p["neumann"])
+            ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+            x = torch.zeros(p["coords"].shape[0], dtype=torch.float64, device=dev)
+            for _ in range(3):
+                x.zero_()
+                ebe.ebe_solve(h, x, rtol=1e-8, precision=ebe.EBE_PREC_MIXED)
+            torch.cuda.synchronize()
+            ebe.ebe_destroy(h)
+        return None
     if args.profile_kernel == "batch":
         run_batch(args, dev, stream, profile=True)
         return None

@@ -55,7 +55,7 @@ struct ebe_handle {
     int store = EBE_STORE_FP64;
     double *A64 = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
     float *A32 = nullptr, *b32 = nullptr, *dinv32 = nullptr;
-    float* Adw = nullptr;           // A64 as FP32 pairs: hi runs, then lo runs (made on first use)
+    float* Adw = nullptr;           // A64 as FP32 pairs, the dw_pairs layout (made on first use)
     bool dw_ready = false;
 
     // scratch of the patch passes
@@ -661,7 +661,7 @@ static int ensure_dw(ebe_handle* h) {
     TRY(dalloc(h, &h->Adw, 2 * n));
     if (h->dw_ready) return EBE_OK;
     int l = 0;
-    CK(launch_split_dw(n, h->A64, h->Adw, h->Adw + n, h->st, &l), "split A_e");
+    CK(launch_split_dw(n, h->A64, h->Adw, h->pd.nb, h->st, &l), "split A_e");
     add_launches(h, l);
     h->dw_ready = true;
     return EBE_OK;
@@ -677,9 +677,8 @@ static int patch_call(ebe_handle* h, const void* x, void* y, int32_t dtype, int 
     if (dtype == EBE_F64_DW) {
         TRY(dalloc(h, &h->halo64, std::max<int64_t>(h->plan.n_halo, 1)));
         TRY(ensure_dw(h));
-        const int64_t n = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
         int l = 0;
-        CK(launch_patch_pass_dw(h->pd, mode, h->Adw, h->Adw + n, static_cast<const double*>(x), h->b,
+        CK(launch_patch_pass_dw(h->pd, mode, h->Adw, static_cast<const double*>(x), h->b,
                                 static_cast<double*>(y), h->halo64, h->part_patch, nullptr, h->sc, h->st, &l),
            "double-word patch pass");
         add_launches(h, l);
@@ -722,11 +721,10 @@ ebe_status ebe_time_operator(ebe_handle* h, const void* x, void* y, int32_t dtyp
     void* halo = dtype == EBE_F64 ? static_cast<void*>(h->halo64) : h->halo32;
     int l = 0;
     int status = EBE_OK;
-    const int64_t ndw = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
     for (int r = 0; r < reps && status == EBE_OK; ++r) {
         cudaError_t e =
             dtype == EBE_F64_DW
-                ? launch_patch_pass_dw(h->pd, apply ? kApply : kResidual, h->Adw, h->Adw + ndw,
+                ? launch_patch_pass_dw(h->pd, apply ? kApply : kResidual, h->Adw,
                                        static_cast<const double*>(x), h->b, static_cast<double*>(y), h->halo64,
                                        h->part_patch, nullptr, h->sc, h->st, &l, &ev[size_t(3) * r])
                 : launch_patch_pass(h->pd, dtype, apply ? kApply : kResidual, A, x, b, y, halo, h->part_patch, nullptr,
@@ -1066,8 +1064,7 @@ int true_residual_int(ebe_handle* h, double& rr, bool dw = false) {
     int l = 0;
     if (dw) {
         TRY(ensure_dw(h));
-        const int64_t n = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
-        CK(launch_patch_pass_dw(h->pd_int, kResidualNorm, h->Adw, h->Adw + n, h->xi, h->bi, h->ri64, h->halo64,
+        CK(launch_patch_pass_dw(h->pd_int, kResidualNorm, h->Adw, h->xi, h->bi, h->ri64, h->halo64,
                                 h->part_patch, nullptr, h->sc, h->st, &l), "double-word true residual");
     } else {
         CK(launch_patch_pass(h->pd_int, 0, kResidualNorm, h->A64, h->xi, h->bi, h->ri64, h->halo64, h->part_patch,
@@ -1569,11 +1566,7 @@ BatchDev make_batch_dev(ebe_handle* h, bool mixed, int ti, const ebe_solve_opts&
     bd.tile = h->btile[ti];
     bd.A = mixed ? static_cast<const void*>(h->A32) : h->A64;
     bd.A64 = h->A64;
-    if (mixed && h->Adw) {
-        const int64_t nw = int64_t(sym_count(h->pd.nb)) * h->pd.n_slots;
-        bd.Ahi = h->Adw;
-        bd.Alo = h->Adw + nw;
-    }
+    bd.Adw = mixed ? h->Adw : nullptr;
     bd.b = h->b;
     bd.dinv = mixed ? static_cast<const void*>(h->dinv32) : h->dinv;
     bd.x = h->x64w;

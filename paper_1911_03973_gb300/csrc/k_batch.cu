@@ -287,6 +287,7 @@ __device__ __forceinline__ void residual_patch_dw(Ctx& c, int p, const BatchSmem
     float2* aw = reinterpret_cast<float2*>(smem + Lo.acc2);
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
+    const int64_t n_dw = int64_t(sym_count(NB)) * ns;   // the lo runs start here when the pairs are not side by side
     const int64_t slot0 = int64_t(p) * kPatch;
     const PatchMeta m = pd.meta[p];
 
@@ -318,8 +319,10 @@ __device__ __forceinline__ void residual_patch_dw(Ctx& c, int p, const BatchSmem
                 for (int j = 0; j < NB; ++j) {
                     const int64_t e = sym_index(NB, r, j) * ns + slot0 + s;
                     const float2 xv = xw[ln[j]];
-                    if (j == 0) dw_mul(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
-                    else dw_fma(__ldg(bd.Ahi + e), __ldg(bd.Alo + e), xv.x, xv.y, sv, cv);
+                    const float2 a = dw_pairs(NB) ? __ldg(reinterpret_cast<const float2*>(bd.Adw) + e)
+                                                  : make_float2(__ldg(bd.Adw + e), __ldg(bd.Adw + n_dw + e));
+                    if (j == 0) dw_mul(a.x, a.y, xv.x, xv.y, sv, cv);
+                    else dw_fma(a.x, a.y, xv.x, xv.y, sv, cv);
                 }
                 float2 t = aw[ln[r]];
                 dw_add(t.x, t.y, sv, cv);
@@ -365,6 +368,7 @@ __device__ __forceinline__ void residual_patch(Ctx& c, int p, bool exact) {
     double* acc = reinterpret_cast<double*>(smem + Lo.acc2);
     const int tid = threadIdx.x;
     const int64_t ns = pd.n_slots;
+    const int64_t n_dw = int64_t(sym_count(NB)) * ns;   // the lo runs start here when the pairs are not side by side
     const int64_t slot0 = int64_t(p) * kPatch;
     const PatchMeta m = pd.meta[p];
 

@@ -542,9 +542,16 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
 // The slots' pair products wait for their colour round in shared memory
 // (y: NB runs of kPatch float2), not in registers: 48 registers and five
 // CTAs per SM for triangles instead of 64 and four.
+// Two forms, by element type (dw_pairs): triangles keep hi and lo in separate
+// runs, x and the node sums in separate FP32 arrays, and two slots' loads in
+// flight at a time; tetrahedra keep every pair (matrix entry, x, node sum)
+// side by side as one 8-byte access and form all four slots' products in one
+// unrolled sequence.  Each form measured best for its element type.
 struct PatchDwSmem {
     uint32_t red, co, G, xh, xl, bs, as, ac, y, total;
 };
+// xh, xl (and as, ac) are adjacent runs of gcap floats: the paired form uses
+// the span from xh (as) as gcap float2.
 template <int NB>
 __host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
     PatchDwSmem s{};
@@ -564,22 +571,25 @@ __host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
 
 template <int NB, int MODE>
 __global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 5 : 4)
-k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restrict__ Alo,
-           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ out,
-           float2* __restrict__ halo, double* __restrict__ part, const int32_t* __restrict__ stop) {
+k_patch_dw(const PlanDev pd, const float* __restrict__ Adw, const float* __restrict__ Alo, const double* __restrict__ x,
+           const double* __restrict__ b, double* __restrict__ out, float2* __restrict__ halo, double* __restrict__ part,
+           const int32_t* __restrict__ stop) {
     constexpr int NT = kPatchThreads;
     constexpr bool kRes = (MODE == kResidual || MODE == kResidualNorm);
+    constexpr bool kPairs = dw_pairs(NB);
     extern __shared__ __align__(128) unsigned char smem[];
     const PatchDwSmem L = patch_dw_layout<NB>(pd.max_nodes);
     double* red = reinterpret_cast<double*>(smem + L.red);
     float2* ysm = reinterpret_cast<float2*>(smem + L.y);
     int* co = reinterpret_cast<int*>(smem + L.co);
     int32_t* Gs = reinterpret_cast<int32_t*>(smem + L.G);
-    float* xh = reinterpret_cast<float*>(smem + L.xh);
+    float* xh = reinterpret_cast<float*>(smem + L.xh);    // separate form
     float* xl = reinterpret_cast<float*>(smem + L.xl);
+    float2* xp = reinterpret_cast<float2*>(smem + L.xh);  // paired form
     double* bs = reinterpret_cast<double*>(smem + L.bs);
     float* as = reinterpret_cast<float*>(smem + L.as);
     float* ac = reinterpret_cast<float*>(smem + L.ac);
+    float2* ap = reinterpret_cast<float2*>(smem + L.as);
 
     pdl_trigger();
     const int p = blockIdx.x;
@@ -589,9 +599,13 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
     const int64_t slot0 = int64_t(p) * kPatch;
     // the patch's element matrices start moving into L2 now, so their DRAM
     // reads overlap the node gather below (they are constant: before the wait)
-    if (tid < 2 * sym_count(NB) && m.n_el > 0) {
-        const float* run = (tid & 1 ? Alo : Ahi) + (tid >> 1) * ns + slot0;
-        bulk_prefetch_l2(run, uint32_t((m.n_el + 3) / 4 * 16));
+    if (m.n_el > 0) {
+        if (kPairs) {
+            if (tid < sym_count(NB))
+                bulk_prefetch_l2(Adw + 2 * (tid * ns + slot0), uint32_t((m.n_el + 1) / 2 * 16));
+        } else if (tid < 2 * sym_count(NB)) {
+            bulk_prefetch_l2((tid & 1 ? Alo : Adw) + (tid >> 1) * ns + slot0, uint32_t((m.n_el + 3) / 4 * 16));
+        }
     }
     for (int c = tid; c <= m.n_col; c += NT) co[c] = __ldg(pd.col_ptr + m.col_off + c);
     // the slots' 16-bit local ids, two to a register
@@ -619,39 +633,73 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         float h, lo;
         split_dw(xv, h, lo);
         Gs[l] = g;
-        xh[l] = h;
-        xl[l] = lo;
+        if (kPairs) {
+            xp[l] = make_float2(h, lo);
+            ap[l] = make_float2(0.0f, 0.0f);
+        } else {
+            xh[l] = h;
+            xl[l] = lo;
+            as[l] = 0.0f;
+            ac[l] = 0.0f;
+        }
         if (kRes) bs[l] = bv;
-        as[l] = 0.0f;
-        ac[l] = 0.0f;
     }
     __syncthreads();
     // products of all slots first (every thread busy), then colour rounds add
-    // them; a thread reads back only its own slots' products.  Two slots'
-    // matrix loads in flight at a time (all four would need 48 registers)
+    // them; a thread reads back only its own slots' products
+    if constexpr (kPairs) {
+        const float2* A2 = reinterpret_cast<const float2*>(Adw) + slot0 + tid;
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            const bool ok = s < m.n_el;
+            float2 a[sym_count(NB)];
+#pragma unroll
+            for (int t = 0; t < sym_count(NB); ++t) a[t] = ok ? __ldg(A2 + t * ns + k * NT) : make_float2(0.0f, 0.0f);
+            float2 e[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) e[j] = xp[ln(k, j)];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                float sv, cv;
+                const float2 a0 = a[sym_index(NB, r, 0)];
+                dw_mul(a0.x, a0.y, e[0].x, e[0].y, sv, cv);
+#pragma unroll
+                for (int j = 1; j < NB; ++j) {
+                    const float2 aj = a[sym_index(NB, r, j)];
+                    dw_fma(aj.x, aj.y, e[j].x, e[j].y, sv, cv);
+                }
+                ysm[r * kPatch + s] = make_float2(sv, cv);
+            }
+        }
+    } else {
+        // two slots' matrix loads in flight at a time (all four would need 48
+        // registers for the loads alone)
 #pragma unroll 2
-    for (int k = 0; k < kEPT; ++k) {
-        const int s = tid + k * NT;
-        const bool ok = s < m.n_el;
-        float ah[sym_count(NB)], al[sym_count(NB)];
+        for (int k = 0; k < kEPT; ++k) {
+            const int s = tid + k * NT;
+            const bool ok = s < m.n_el;
+            float ah[sym_count(NB)], al[sym_count(NB)];
 #pragma unroll
-        for (int t = 0; t < sym_count(NB); ++t) {
-            ah[t] = ok ? __ldg(Ahi + t * ns + slot0 + s) : 0.0f;
-            al[t] = ok ? __ldg(Alo + t * ns + slot0 + s) : 0.0f;
-        }
-        float eh[NB], el[NB];
+            for (int t = 0; t < sym_count(NB); ++t) {
+                ah[t] = ok ? __ldg(Adw + t * ns + slot0 + s) : 0.0f;
+                al[t] = ok ? __ldg(Alo + t * ns + slot0 + s) : 0.0f;
+            }
+            float eh[NB], el[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            eh[j] = xh[ln(k, j)];
-            el[j] = xl[ln(k, j)];
-        }
+            for (int j = 0; j < NB; ++j) {
+                eh[j] = xh[ln(k, j)];
+                el[j] = xl[ln(k, j)];
+            }
 #pragma unroll
-        for (int r = 0; r < NB; ++r) {
-            float sv, cv;
-            dw_mul(ah[sym_index(NB, r, 0)], al[sym_index(NB, r, 0)], eh[0], el[0], sv, cv);
+            for (int r = 0; r < NB; ++r) {
+                float sv, cv;
+                dw_mul(ah[sym_index(NB, r, 0)], al[sym_index(NB, r, 0)], eh[0], el[0], sv, cv);
 #pragma unroll
-            for (int j = 1; j < NB; ++j) dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
-            ysm[r * kPatch + s] = make_float2(sv, cv);
+                for (int j = 1; j < NB; ++j)
+                    dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
+                ysm[r * kPatch + s] = make_float2(sv, cv);
+            }
         }
     }
     for (int c = 0; c < m.n_col; ++c) {
@@ -664,10 +712,22 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
                 for (int r = 0; r < NB; ++r) {
                     const int n = ln(k, r);
                     const float2 y = ysm[r * kPatch + s];
-                    float sv = as[n], cv = ac[n];
+                    float sv, cv;
+                    if (kPairs) {
+                        const float2 t = ap[n];
+                        sv = t.x;
+                        cv = t.y;
+                    } else {
+                        sv = as[n];
+                        cv = ac[n];
+                    }
                     dw_add(sv, cv, y.x, y.y);
-                    as[n] = sv;
-                    ac[n] = cv;
+                    if (kPairs) {
+                        ap[n] = make_float2(sv, cv);
+                    } else {
+                        as[n] = sv;
+                        ac[n] = cv;
+                    }
                 }
             }
         }
@@ -678,8 +738,9 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
         const int32_t graw = Gs[l];
         const int g = graw & kNodeMask;
         const bool dir = graw < 0;
+        const float2 t = kPairs ? ap[l] : make_float2(as[l], ac[l]);
         if (l < m.n_owned) {
-            const double v = f2d(as[l]) + f2d(ac[l]);
+            const double v = f2d(t.x) + f2d(t.y);
             const double o = dir ? 0.0 : (kRes ? bs[l] - v : v);
             out[g] = o;
             if (MODE == kResidualNorm) {
@@ -687,7 +748,7 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Ahi, const float* __restr
                 dot.add(of, of);
             }
         } else {
-            halo[m.halo_off + (l - m.n_owned)] = make_float2(as[l], ac[l]);
+            halo[m.halo_off + (l - m.n_owned)] = t;
         }
     }
     if (MODE == kResidualNorm) {
@@ -774,7 +835,7 @@ k_fixup_dw(const PlanDev pd, const double* __restrict__ b, double* __restrict__ 
 }
 
 template <int NB, int MODE>
-cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, const double* x, const double* b,
+cudaError_t run_patch_dw(const PlanDev& pd, const float* Adw, const double* x, const double* b,
                          double* out, float2* halo, double* part, const int32_t* stop, Scalars* sc, cudaStream_t st,
                          int* launches, cudaEvent_t* ev) {
     const size_t sm = patch_dw_layout<NB>(pd.max_nodes).total;
@@ -783,7 +844,9 @@ cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], st);
-    kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, Ahi, Alo, x, b, out, halo, part, stop);
+    // the separate form's lo runs follow all hi runs
+    const float* Alo = dw_pairs(NB) ? nullptr : Adw + int64_t(sym_count(NB)) * pd.n_slots;
+    kern<<<pd.n_patches, kPatchThreads, sm, st>>>(pd, Adw, Alo, x, b, out, halo, part, stop);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
@@ -796,13 +859,17 @@ cudaError_t run_patch_dw(const PlanDev& pd, const float* Ahi, const float* Alo, 
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_split_dw(int64_t n, const double* __restrict__ a, float* __restrict__ hi,
-                                                  float* __restrict__ lo) {
+__global__ void __launch_bounds__(256) k_split_dw(int64_t n, const double* __restrict__ a, float* __restrict__ out,
+                                                  int pairs) {
     for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(gridDim.x) * 256) {
         float h, l;
         split_dw(a[i], h, l);
-        hi[i] = h;
-        lo[i] = l;
+        if (pairs) {
+            reinterpret_cast<float2*>(out)[i] = make_float2(h, l);
+        } else {
+            out[i] = h;
+            out[n + i] = l;
+        }
     }
 }
 
@@ -1377,31 +1444,31 @@ int fix_rows(const PlanDev& pd) {
     return 2 * pd.n_halo <= 5 * int64_t(pd.n_shared) ? 2 : 1;
 }
 
-cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Ahi, const float* Alo, const double* x,
+cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Adw, const double* x,
                                  const double* b, double* out, double* halo, double* part, const int32_t* stop,
                                  Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev) {
     float2* h = reinterpret_cast<float2*>(halo);
     if (pd.nb == 3) {
         switch (mode) {
-            case kResidual: return run_patch_dw<3, kResidual>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+            case kResidual: return run_patch_dw<3, kResidual>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
             case kResidualNorm:
-                return run_patch_dw<3, kResidualNorm>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
-            case kApply: return run_patch_dw<3, kApply>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+                return run_patch_dw<3, kResidualNorm>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
+            case kApply: return run_patch_dw<3, kApply>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (mode) {
-        case kResidual: return run_patch_dw<4, kResidual>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+        case kResidual: return run_patch_dw<4, kResidual>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
         case kResidualNorm:
-            return run_patch_dw<4, kResidualNorm>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
-        case kApply: return run_patch_dw<4, kApply>(pd, Ahi, Alo, x, b, out, h, part, stop, sc, st, launches, ev);
+            return run_patch_dw<4, kResidualNorm>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
+        case kApply: return run_patch_dw<4, kApply>(pd, Adw, x, b, out, h, part, stop, sc, st, launches, ev);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_split_dw(int64_t n, const double* a, float* hi, float* lo, cudaStream_t st, int* launches) {
+cudaError_t launch_split_dw(int64_t n, const double* a, float* out, int nb, cudaStream_t st, int* launches) {
     if (n <= 0) return cudaSuccess;
-    k_split_dw<<<int(std::min<int64_t>((n + 255) / 256, 8192)), 256, 0, st>>>(n, a, hi, lo);
+    k_split_dw<<<int(std::min<int64_t>((n + 255) / 256, 8192)), 256, 0, st>>>(n, a, out, dw_pairs(nb) ? 1 : 0);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -47,6 +47,12 @@ struct PlanDev {
 // n_slots values, the nb diagonal entries first, then the pairs i < j in the
 // order (0,1), (0,2), (1,2), (0,3), (1,3), (2,3).
 __host__ __device__ constexpr int sym_count(int nb) { return nb * (nb + 1) / 2; }
+// Layout of the FP32-pair copy of A_e (the double-word residual): tetrahedra
+// keep each entry's hi and lo side by side (one 8-byte load), triangles keep
+// all hi runs and then all lo runs.  Measured on GB300 (warm, per residual):
+// 129^3 tetrahedra 365 us side by side against 397 us separate; 2049^2
+// triangles 162 us separate against 170 us side by side.
+__host__ __device__ constexpr bool dw_pairs(int nb) { return nb == 4; }
 __host__ __device__ constexpr int sym_index(int nb, int i, int j) {
     return i == j ? i : nb + (i < j ? j * (j - 1) / 2 + i : i * (i - 1) / 2 + j);
 }
@@ -137,14 +143,18 @@ cudaError_t launch_patch_pass(const PlanDev& pd, int dtype, int mode, const void
 
 // ---- double-word FP64 residual (k_patch.cu) -----------------------------
 // The FP64 residual / operator (modes kResidual, kResidualNorm, kApply) with
-// A_e stored as FP32 pairs a = hi + lo (Ahi, Alo: the FP64 layout, entry
-// runs of n_slots) and the arithmetic in double-word FP32; x, b, out FP64;
-// halo: n_halo pairs (the FP64 halo buffer reinterpreted).
-cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Ahi, const float* Alo, const double* x,
+// A_e stored as FP32 pairs a = hi + lo in Adw (2 * n entries of FP32, n =
+// sym_count(nb) * n_slots, in the FP64 layout's entry runs of n_slots): with
+// dw_pairs(nb) each entry is one float2 (hi, lo); otherwise all hi runs come
+// first and the lo runs follow at Adw + n.  The arithmetic is double-word
+// FP32; x, b, out FP64; halo: n_halo pairs (the FP64 halo buffer
+// reinterpreted).
+cudaError_t launch_patch_pass_dw(const PlanDev& pd, int mode, const float* Adw, const double* x,
                                  const double* b, double* out, double* halo, double* part, const int32_t* stop,
                                  Scalars* sc, cudaStream_t st, int* launches, cudaEvent_t* ev = nullptr);
-// hi[i] + lo[i] = a[i] to 48 bits (i < n).
-cudaError_t launch_split_dw(int64_t n, const double* a, float* hi, float* lo, cudaStream_t st, int* launches);
+// Fills Adw from a (n FP64 entries) in the layout above for element type nb:
+// hi + lo = a[i] to 48 bits.
+cudaError_t launch_split_dw(int64_t n, const double* a, float* out, int nb, cudaStream_t st, int* launches);
 
 // ---- single-synchronisation mixed-precision CG (k_patch.cu) ---------------
 // One pass = one CG iteration in two launches (patch pass + shared-node
@@ -277,8 +287,7 @@ struct BatchDev {
     const BatchItem* tile = nullptr;       // [n_tile]
     const void* A = nullptr;               // element matrices of the inner operator (FP32 difference form or FP64)
     const double* A64 = nullptr;           // FP64 element matrices (true residuals, FP64 solver)
-    const float* Ahi = nullptr;            // mixed solver: A64 as FP32 pairs (double-word true residuals)
-    const float* Alo = nullptr;
+    const float* Adw = nullptr;            // mixed solver: A64 as FP32 pairs (double-word true residuals), dw_pairs layout
     const double* b = nullptr;             // FP64 load vector
     const void* dinv = nullptr;            // inverse Jacobi diagonal, inner type
     double* x = nullptr;

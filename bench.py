@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--no-cube", action="store_true", help="skip the 129^3 tetrahedral workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the learned preconditioner (257^2) and deploying it (1025^2, 2049^2)")
-    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "dw", "assemble", "vec", "cg", "small", "batch", "mpnn"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply32", "residual64", "dw", "assemble", "vec", "cg", "small", "batch", "mpnn", "dw_cube"], default=None,
                     help="run a few launches of one kernel for an ncu capture (no JSON line)")
     return ap.parse_args()
 
@@ -664,7 +664,11 @@ def run_ours(args):
     if args.profile_kernel == "mpnn":
         run_learned(args, dev, stream, profile=True)
         return None
-    prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
+    if args.profile_kernel == "dw_cube":
+        # the double-word residual on the 129^3 tetrahedral workload
+        prob = meshgen.config_cube_noise(129, nu=0.5, seed=3)
+    else:
+        prob = meshgen.config_square_jitter(args.n, nu=args.nu, seed=2)
     n_n, dim = prob["coords"].shape
     n_e = prob["elems"].shape[0]
     m = bytes_model(dim, n_n, n_e)
@@ -697,7 +701,7 @@ def run_ours(args):
                     ebe.ebe_apply(h, p32, q32)
                 elif args.profile_kernel == "residual64":
                     ebe.ebe_residual(h, x64, r64)
-                elif args.profile_kernel == "dw":
+                elif args.profile_kernel in ("dw", "dw_cube"):
                     ebe.ebe_residual(h, x64, r64, double_word=True)
                 else:
                     ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)

@@ -241,3 +241,23 @@ def test_config4_full_batch(ebe):
         worst = max(worst, rel)
         assert rel <= 1e-8, (k, rel, infos[k])
     assert worst > 0.0
+
+
+@pytest.mark.parametrize("precision", ["EBE_PREC_MIXED", "EBE_PREC_FP64"])
+def test_batched_solve_on_tetrahedra(ebe, precision):
+    # two Kuhn cubes of different sizes and nu: the tetrahedral paths of the
+    # persistent solver (per-warp colour sums, and in mixed precision the
+    # double-word true residual with each FP32 pair side by side)
+    probs = [meshgen.config_cube_noise(14, nu=0.5, seed=3),     # 13,182 tets
+             meshgen.config_cube_noise(18, nu=2.0, seed=4)]     # 29,478 tets
+    U = meshgen.batch_union(probs)
+    stream = torch.cuda.Stream()
+    h = ebe.ebe_create_batch(U["meshes"], stream=stream.cuda_stream)
+    ebe.ebe_set_problem_batch(h, U["nu"], U["f"], U["dirichlet"], U["g"], U["neumann"])
+    ebe.ebe_assemble(h, ebe.EBE_STORE_MIXED)
+    x, infos, _ = _solve(ebe, h, U, stream, rtol=1e-8, precision=getattr(ebe, precision))
+    for k, (pr, xk) in enumerate(zip(probs, _split(x, U))):
+        assert infos[k]["status"] == "EBE_OK", infos[k]
+        assert infos[k]["true_residuals"] >= 2
+        assert oracle.Problem(pr).rel_residual(xk) <= 1e-8
+    ebe.ebe_destroy(h)

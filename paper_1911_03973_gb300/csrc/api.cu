@@ -64,6 +64,8 @@ struct ebe_handle {
     SmallInfo* small_info = nullptr;  // outcome of the one-CTA solver
     int32_t* small_order = nullptr;   // its colouring of the whole mesh
     int32_t* small_col = nullptr;
+    uint16_t* small_inc_ptr = nullptr;   // node -> (element, row) incidences in colour order
+    uint16_t* small_inc = nullptr;
     int small_ncol = 0;
     double* halo2 = nullptr;
     double* part_patch = nullptr;   // n_patches + fix_grid(n_shared)
@@ -1232,8 +1234,25 @@ int ensure_small_tables(ebe_handle* h) {
     const int nc = global_colouring(h->plan, h->gconn_host, order, col, err);
     if (nc < 1 || nc > kSmallMaxColours) return fail(h, EBE_INVALID_ARG, nc < 1 ? err : "too many colours for the one-CTA solver");
     std::vector<int32_t> col32(col.begin(), col.end());
+    // each node's (element, row) incidences, elements in colour order
+    const HostPlan& P = h->plan;
+    const int nb = P.nb;
+    const int64_t n_e = int64_t(order.size());
+    if (n_e > 4096 || nb * n_e > 65535 || P.n_n > 65535) return fail(h, EBE_INVALID_ARG, "mesh too large for the one-CTA solver");
+    std::vector<uint16_t> iptr(size_t(P.n_n) + 1, 0), inc(size_t(nb * n_e), 0);
+    for (int64_t k = 0; k < n_e; ++k)
+        for (int r = 0; r < nb; ++r) ++iptr[size_t(h->gconn_host[size_t(order[size_t(k)]) * nb + r] & kNodeMask) + 1];
+    for (int64_t v = 0; v < P.n_n; ++v) iptr[size_t(v) + 1] = uint16_t(iptr[size_t(v) + 1] + iptr[size_t(v)]);
+    std::vector<uint16_t> fill(iptr.begin(), iptr.end() - 1);
+    for (int64_t k = 0; k < n_e; ++k)
+        for (int r = 0; r < nb; ++r) {
+            const int64_t v = h->gconn_host[size_t(order[size_t(k)]) * nb + r] & kNodeMask;
+            inc[fill[size_t(v)]++] = uint16_t(k | (int64_t(r) << 12));
+        }
     TRY(upload(h, &h->small_order, order.data(), int64_t(order.size())));
     TRY(upload(h, &h->small_col, col32.data(), int64_t(col32.size())));
+    TRY(upload(h, &h->small_inc_ptr, iptr.data(), int64_t(iptr.size())));
+    TRY(upload(h, &h->small_inc, inc.data(), int64_t(inc.size())));
     h->small_ncol = nc;
     CK(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");   // the host tables go away
     return EBE_OK;
@@ -1256,6 +1275,9 @@ int solve_small_impl(ebe_handle* h, double* x, bool x_on_host, const ebe_solve_o
     SmallColouring sc;
     sc.order = h->small_order;
     sc.col = h->small_col;
+    sc.inc_ptr = h->small_inc_ptr;
+    sc.inc = h->small_inc;
+    sc.gather = small_solver_gather(n, h->plan.n_e, h->pd.nb) ? 1 : 0;
     sc.gconn = h->gconn;
     sc.n_e = int32_t(h->plan.n_e);
     sc.n_col = h->small_ncol;

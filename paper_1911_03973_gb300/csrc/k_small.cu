@@ -9,10 +9,13 @@
 // direction, FP32 recurrence residual, FP64 solution, and the FP64 true
 // residual b - A x (FP64 element matrices) at every replacement and for the
 // stopping test.  The elements are taken in the order of a colouring of the
-// whole mesh (no two elements of a colour share a node), so the products of
-// a thread's elements are added into the node sums in one round per colour.  The decisions (alpha, beta, replacement, convergence,
-// stall, breakdown, maxit) follow the host loop of the grid-wide solver, taken
-// by thread 0.  Every sum has a fixed order: bitwise reproducible.
+// whole mesh (no two elements of a colour share a node).  The FP64 true
+// residual adds each element's products into the node sums in one round per
+// colour; the FP32 operator of every iteration instead has each node's thread
+// gather its element rows in that same order (no barrier per colour).  The
+// decisions (alpha, beta, replacement, convergence, stall, breakdown, maxit)
+// follow the host loop of the grid-wide solver, taken by thread 0.  Every sum
+// has a fixed order: bitwise reproducible.
 #include <cstdint>
 
 #include "device_util.cuh"
@@ -24,12 +27,12 @@ namespace {
 constexpr int NT = kPatch;   // one thread per slot of a patch
 
 struct SmallSmem {
-    uint32_t red, cols, x, acc64, r, p, acc, dinv, lid, a32, total;
+    uint32_t red, cols, x, acc64, r, p, acc, dinv, lid, incp, inc, a32, total;
 };
 // Node vectors, then the elements' node ids (16-bit, the caller's numbering)
 // and FP32 matrices in the order of a colouring of the whole mesh, copied
 // once: an iteration then reads only shared memory.
-__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, int nb) {
+__host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, int nb, bool gather) {
     SmallSmem s{};
     const uint32_t n = uint32_t((n_n + 3) / 4 * 4);
     const uint32_t ne = uint32_t((n_e + 3) / 4 * 4);
@@ -42,7 +45,9 @@ __host__ __device__ constexpr SmallSmem small_layout(int64_t n_n, int64_t n_e, i
     s.acc = s.p + n * 4;                         // FP32 node sums / q = A p
     s.dinv = s.acc + n * 4;                      // FP32 inverse Jacobi diagonal (0: Dirichlet)
     s.lid = s.dinv + n * 4;                      // [nb][n_e] uint16 node ids, colour order
-    s.a32 = (s.lid + uint32_t(nb) * ne * 2 + 15) / 16 * 16;   // [nb(nb+1)/2][n_e] FP32 matrices, colour order
+    s.incp = s.lid + uint32_t(nb) * ne * 2;      // gather form: [n_n + 1] uint16 incidence offsets
+    s.inc = (s.incp + (gather ? (uint32_t(n_n) + 1) * 2 : 0u) + 3) / 4 * 4;   // [nb * n_e] uint16 incidences
+    s.a32 = (s.inc + (gather ? uint32_t(nb) * ne * 2 : 0u) + 15) / 16 * 16;   // [nb(nb+1)/2][n_e] FP32, colour order
     s.total = s.a32 + uint32_t(nb * (nb + 1) / 2) * ne * 4;
     return s;
 }
@@ -139,6 +144,35 @@ __device__ __forceinline__ void operator32(const float* __restrict__ a32, const 
     }
 }
 
+// Node v's entry of sum_e A_e p_e (FP32 difference-form matrices in shared
+// memory), gathered by v's own thread from its (element, row) incidences: each
+// row as the element-wise form computes it (the diagonal slot holds the row
+// sum: y = s_r p_r + sum_{j != r} a_rj (p_j - p_r)), added from 0 in the
+// colour order of the elements, the order of colour rounds over the whole
+// mesh, without the rounds' block barriers.
+template <int NB>
+__device__ __forceinline__ float gather_row_sums(const float* __restrict__ a32, const float* __restrict__ p,
+                                                 const uint16_t* __restrict__ lid, int n_e,
+                                                 const uint16_t* __restrict__ incp, const uint16_t* __restrict__ inc,
+                                                 int v, float pv) {
+    float acc = 0.0f;
+    const int t1 = incp[v + 1];
+#pragma unroll 2
+    for (int t = incp[v]; t < t1; ++t) {
+        const uint32_t e = inc[t];
+        const int k = int(e & 0xfffu), r = int(e >> 12);
+        float pe[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) pe[i] = p[lid[i * n_e + k]];
+        float y = a32[sym_index(NB, r, r) * n_e + k] * pv;   // p_r = p_v
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j != r) y = fmadd(a32[sym_index(NB, r, j) * n_e + k], pe[j] - pv, y);
+        acc += y;
+    }
+    return acc;
+}
+
 // acc64 = sum over the elements of A_e x_e (FP64 matrices from global memory,
 // element k of the colour order is slot order[k]), the products formed in
 // each colour's round (few registers: this runs once per replacement).
@@ -175,7 +209,8 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
            SmallColouring sc, SmallOpts o, SmallInfo* __restrict__ info) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_e = sc.n_e, n_col = sc.n_col;
-    const SmallSmem L = small_layout(n_n, n_e, NB);
+    const bool gather = sc.gather != 0;
+    const SmallSmem L = small_layout(n_n, n_e, NB, gather);
     int* cols = reinterpret_cast<int*>(smem + L.cols);
     double* red = reinterpret_cast<double*>(smem + L.red);
     double* x = reinterpret_cast<double*>(smem + L.x);
@@ -185,6 +220,8 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
     float* acc = reinterpret_cast<float*>(smem + L.acc);
     float* dinv = reinterpret_cast<float*>(smem + L.dinv);
     uint16_t* lid = reinterpret_cast<uint16_t*>(smem + L.lid);
+    uint16_t* incp = reinterpret_cast<uint16_t*>(smem + L.incp);
+    uint16_t* inc = reinterpret_cast<uint16_t*>(smem + L.inc);
     float* a32 = reinterpret_cast<float*>(smem + L.a32);
     const int tid = threadIdx.x;
     // Thread 0 forms the iteration's scalars and takes its decisions (GB300's
@@ -212,6 +249,10 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
             for (int t = 0; t < sym_count(NB); ++t) a32[t * n_e + k] = __ldg(A32 + t * ns + s);
         }
         for (int c = tid; c <= n_col; c += NT) cols[c] = __ldg(sc.col + c);
+        if (gather) {
+            for (int64_t v = tid; v <= n_n; v += NT) incp[v] = __ldg(sc.inc_ptr + v);
+            for (int t = tid; t < NB * n_e; t += NT) inc[t] = __ldg(sc.inc + t);
+        }
     }
     if (tid == 0) {
         C.rho = C.beta = 0.0;
@@ -285,13 +326,24 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
         direction();
         for (;;) {
             if (C.reason == kRunning) {
-                // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r
-                operator32<NB>(a32, p, acc, n_n, lid, n_e, cols, n_col);
+                // one CG iteration: q = mask(A p), alpha, x and r updated, r.z and r.r;
+                // a node's q stays with its thread (no barrier before the update)
                 CompSum pq, none;
-                for (int64_t i = tid; i < n_n; i += NT) {
-                    const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
-                    acc[i] = qv;
-                    pq.add(p[i] * qv);
+                if (gather) {
+                    for (int64_t i = tid; i < n_n; i += NT) {
+                        const float pv = p[i];
+                        const float qv =
+                            dinv[i] == 0.0f ? 0.0f : gather_row_sums<NB>(a32, p, lid, n_e, incp, inc, int(i), pv);
+                        acc[i] = qv;
+                        pq.add(pv * qv);
+                    }
+                } else {
+                    operator32<NB>(a32, p, acc, n_n, lid, n_e, cols, n_col);
+                    for (int64_t i = tid; i < n_n; i += NT) {
+                        const float qv = dinv[i] == 0.0f ? 0.0f : acc[i];
+                        acc[i] = qv;
+                        pq.add(p[i] * qv);
+                    }
                 }
                 double tpq, tnone;
                 block_sums2(pq, none, tpq, tnone, red);
@@ -383,13 +435,20 @@ k_cg_small(const PlanDev pd, int64_t n_n, const float* __restrict__ A32, const d
 }  // namespace
 
 size_t small_solver_smem(int64_t n_n, int64_t n_e, int nb) {
-    return (n_n > 65536 || n_e > int64_t(kSmallEPT) * NT) ? size_t(1) << 40 : small_layout(n_n, n_e, nb).total;
+    return (n_n > 65536 || n_e > int64_t(kSmallEPT) * NT) ? size_t(1) << 40 : small_layout(n_n, n_e, nb, false).total;
+}
+
+bool small_solver_gather(int64_t n_n, int64_t n_e, int nb) {
+    return n_n <= kSmallGatherNodes && n_e <= int64_t(kSmallEPT) * NT &&
+           small_layout(n_n, n_e, nb, true).total <= size_t(kSmallGatherSmem);
 }
 
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,
                             const float* dinv, double* x, const SmallColouring& sc, const SmallOpts& o,
                             SmallInfo* info, cudaStream_t st, int* launches) {
-    const size_t sm = small_solver_smem(n_n, sc.n_e, pd.nb);
+    if (sc.gather && (sc.inc_ptr == nullptr || sc.inc == nullptr)) return cudaErrorInvalidValue;
+    const size_t base = small_solver_smem(n_n, sc.n_e, pd.nb);   // 2^40 beyond the solver's limits
+    const size_t sm = (base >> 40) ? base : small_layout(n_n, sc.n_e, pd.nb, sc.gather != 0).total;
     if (sm > 227 * 1024 || sc.n_col < 1 || sc.n_col > kSmallMaxColours) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (pd.nb == 3) {

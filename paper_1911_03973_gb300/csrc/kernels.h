@@ -329,16 +329,32 @@ struct SmallInfo {
 };
 // A colouring of all elements of a small mesh (device arrays): element k of
 // the colour order is slot order[k]; colour c holds elements [col[c], col[c+1]).
+// Node v's incidences inc[inc_ptr[v] .. inc_ptr[v+1]) list its (element k,
+// row r) pairs as k | r << 12, k ascending: the order in which the colour
+// rounds add the element rows into the node.
 constexpr int kSmallMaxColours = 64;
 struct SmallColouring {
-    const int32_t* order = nullptr;   // [n_e]
-    const int32_t* col = nullptr;     // [n_col + 1]
-    const int32_t* gconn = nullptr;   // [nb][n_slots] global node ids per slot
+    const int32_t* order = nullptr;    // [n_e]
+    const int32_t* col = nullptr;      // [n_col + 1]
+    const int32_t* gconn = nullptr;    // [nb][n_slots] global node ids per slot
+    const uint16_t* inc_ptr = nullptr; // [n_n + 1]
+    const uint16_t* inc = nullptr;     // [nb * n_e]
     int32_t n_e = 0, n_col = 0;
+    int32_t gather = 0;                // 1: the operator gathers per node (small_solver_gather)
 };
 // Shared memory the one-CTA solver needs (node ids are 16-bit: n_n <= 65536;
 // at most 4096 elements).
 size_t small_solver_smem(int64_t n_n, int64_t n_e, int nb);
+// Whether the FP32 operator of the one-CTA solver gathers each node's element
+// rows (no barrier per colour) instead of adding them in colour rounds: at
+// most 1.5 nodes per thread, and the incidence tables fitting next to the
+// rest.  Beyond 1.5 nodes per thread a thread's serial gathers cost more than
+// the rounds' barriers (GB300, per iteration against the rounds: 1,089 nodes
+// 15 % faster, 1,444 nodes 5 % faster, 1,764 nodes 2 % and 2,116 nodes 11 %
+// slower; 125 and 729 tetrahedral nodes 28 and 14 % faster).
+constexpr int kSmallGatherNodes = 1536;
+constexpr size_t kSmallGatherSmem = size_t(224) * 1024;
+bool small_solver_gather(int64_t n_n, int64_t n_e, int nb);
 // Jacobi-PCG (textbook mixed form) of the whole mesh in one CTA: x (device,
 // FP64, Dirichlet values set) in and out; pd in the caller's numbering.
 cudaError_t launch_cg_small(const PlanDev& pd, int64_t n_n, const float* A32, const double* A64, const double* b,

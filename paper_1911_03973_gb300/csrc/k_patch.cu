@@ -539,14 +539,15 @@ k_patch64d(const PlanDev pd, const double* __restrict__ A, const double* __restr
 // operations per node instead of n_b^2 + n_b per element.  The pair
 // representation of A_e and x is exact to 2^-48 relative, so r differs from
 // the FP64 residual by about 2^-48 |A| |x| per node.
-// The slots' pair products wait for their colour round in shared memory
-// (y: NB runs of kPatch float2), not in registers: 48 registers and five
-// CTAs per SM for triangles instead of 64 and four.
-// Two forms, by element type (dw_pairs): triangles keep hi and lo in separate
-// runs, x and the node sums in separate FP32 arrays, and two slots' loads in
-// flight at a time; tetrahedra keep every pair (matrix entry, x, node sum)
-// side by side as one 8-byte access and form all four slots' products in one
-// unrolled sequence.  Each form measured best for its element type.
+// Two forms, by element type (dw_pairs), each measured best for its type.
+// Triangles (8 colours a patch) keep hi and lo in separate runs and x and the
+// node sums in separate FP32 arrays, and form each slot's products in its
+// colour's round, from matrix runs the L2 prefetch below has made resident:
+// no product array, the slots' local ids in shared memory, 40 registers and
+// six CTAs per SM.  Tetrahedra (about 30 colours) form all four slots'
+// products first, every pair (matrix entry, x, node sum) side by side as one
+// 8-byte access, and the products wait for their round in shared memory (y:
+// NB runs of kPatch float2).
 struct PatchDwSmem {
     uint32_t red, co, G, xh, xl, bs, as, ac, y, total;
 };
@@ -564,13 +565,13 @@ __host__ __device__ constexpr PatchDwSmem patch_dw_layout(int max_nodes) {
     s.bs = (s.xl + gcap * 4 + 15) / 16 * 16;
     s.as = s.bs + gcap * 8;
     s.ac = s.as + gcap * 4;
-    s.y = (s.ac + gcap * 4 + 15) / 16 * 16;
-    s.total = (s.y + uint32_t(NB * kPatch * 8) + 127) / 128 * 128;
+    s.y = (s.ac + gcap * 4 + 15) / 16 * 16;   // products (paired form) or local ids (separate form)
+    s.total = (s.y + (dw_pairs(NB) ? uint32_t(NB * kPatch * 8) : uint32_t(NB * kPatch * 2)) + 127) / 128 * 128;
     return s;
 }
 
 template <int NB, int MODE>
-__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 5 : 4)
+__global__ void __launch_bounds__(kPatchThreads, NB == 3 ? 6 : 4)
 k_patch_dw(const PlanDev pd, const float* __restrict__ Adw, const float* __restrict__ Alo, const double* __restrict__ x,
            const double* __restrict__ b, double* __restrict__ out, float2* __restrict__ halo, double* __restrict__ part,
            const int32_t* __restrict__ stop) {
@@ -645,9 +646,9 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Adw, const float* __restr
         if (kRes) bs[l] = bv;
     }
     __syncthreads();
-    // products of all slots first (every thread busy), then colour rounds add
-    // them; a thread reads back only its own slots' products
     if constexpr (kPairs) {
+        // products of all slots first (every thread busy), then colour rounds
+        // add them; a thread reads back only its own slots' products
         const float2* A2 = reinterpret_cast<const float2*>(Adw) + slot0 + tid;
 #pragma unroll
         for (int k = 0; k < kEPT; ++k) {
@@ -672,66 +673,68 @@ k_patch_dw(const PlanDev pd, const float* __restrict__ Adw, const float* __restr
                 ysm[r * kPatch + s] = make_float2(sv, cv);
             }
         }
-    } else {
-        // two slots' matrix loads in flight at a time (all four would need 48
-        // registers for the loads alone)
-#pragma unroll 2
-        for (int k = 0; k < kEPT; ++k) {
-            const int s = tid + k * NT;
-            const bool ok = s < m.n_el;
-            float ah[sym_count(NB)], al[sym_count(NB)];
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
 #pragma unroll
-            for (int t = 0; t < sym_count(NB); ++t) {
-                ah[t] = ok ? __ldg(Adw + t * ns + slot0 + s) : 0.0f;
-                al[t] = ok ? __ldg(Alo + t * ns + slot0 + s) : 0.0f;
-            }
-            float eh[NB], el[NB];
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                eh[j] = xh[ln(k, j)];
-                el[j] = xl[ln(k, j)];
-            }
-#pragma unroll
-            for (int r = 0; r < NB; ++r) {
-                float sv, cv;
-                dw_mul(ah[sym_index(NB, r, 0)], al[sym_index(NB, r, 0)], eh[0], el[0], sv, cv);
-#pragma unroll
-                for (int j = 1; j < NB; ++j)
-                    dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
-                ysm[r * kPatch + s] = make_float2(sv, cv);
-            }
-        }
-    }
-    for (int c = 0; c < m.n_col; ++c) {
-        const int lo = co[c], hi = co[c + 1];
-#pragma unroll
-        for (int k = 0; k < kEPT; ++k) {
-            const int s = tid + k * NT;
-            if (s >= lo && s < hi) {
-#pragma unroll
-                for (int r = 0; r < NB; ++r) {
-                    const int n = ln(k, r);
-                    const float2 y = ysm[r * kPatch + s];
-                    float sv, cv;
-                    if (kPairs) {
-                        const float2 t = ap[n];
-                        sv = t.x;
-                        cv = t.y;
-                    } else {
-                        sv = as[n];
-                        cv = ac[n];
-                    }
-                    dw_add(sv, cv, y.x, y.y);
-                    if (kPairs) {
-                        ap[n] = make_float2(sv, cv);
-                    } else {
-                        as[n] = sv;
-                        ac[n] = cv;
+                    for (int r = 0; r < NB; ++r) {
+                        const int n = ln(k, r);
+                        const float2 y = ysm[r * kPatch + s];
+                        float2 t = ap[n];
+                        dw_add(t.x, t.y, y.x, y.y);
+                        ap[n] = t;
                     }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
+    } else {
+        // each slot's products in its colour's round; the local ids move to
+        // shared memory (this thread reads back only its own slots')
+        uint16_t* Ls = reinterpret_cast<uint16_t*>(smem + L.y);
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k)
+#pragma unroll
+            for (int i = 0; i < NB; ++i) Ls[i * kPatch + tid + k * NT] = uint16_t(ln(k, i));
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+                    float ah[sym_count(NB)], al[sym_count(NB)];
+#pragma unroll
+                    for (int t = 0; t < sym_count(NB); ++t) {
+                        ah[t] = __ldg(Adw + t * ns + slot0 + s);
+                        al[t] = __ldg(Alo + t * ns + slot0 + s);
+                    }
+                    int nn[NB];
+                    float eh[NB], el[NB];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        nn[j] = Ls[j * kPatch + s];
+                        eh[j] = xh[nn[j]];
+                        el[j] = xl[nn[j]];
+                    }
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) {
+                        float sv, cv;
+                        dw_mul(ah[sym_index(NB, r, 0)], al[sym_index(NB, r, 0)], eh[0], el[0], sv, cv);
+#pragma unroll
+                        for (int j = 1; j < NB; ++j)
+                            dw_fma(ah[sym_index(NB, r, j)], al[sym_index(NB, r, j)], eh[j], el[j], sv, cv);
+                        float s2 = as[nn[r]], c2 = ac[nn[r]];
+                        dw_add(s2, c2, sv, cv);
+                        as[nn[r]] = s2;
+                        ac[nn[r]] = c2;
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
     DotAcc<float> dot;
     for (int l = tid; l < m.n_nodes; l += NT) {

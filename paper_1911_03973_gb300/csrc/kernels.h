@@ -49,9 +49,10 @@ struct PlanDev {
 __host__ __device__ constexpr int sym_count(int nb) { return nb * (nb + 1) / 2; }
 // Layout of the FP32-pair copy of A_e (the double-word residual): tetrahedra
 // keep each entry's hi and lo side by side (one 8-byte load), triangles keep
-// all hi runs and then all lo runs.  Measured on GB300 (warm, per residual):
-// 129^3 tetrahedra 365 us side by side against 397 us separate; 2049^2
-// triangles 162 us separate against 170 us side by side.
+// all hi runs and then all lo runs.  Measured on GB300 (warm, per residual,
+// with the products formed before the colour rounds): 129^3 tetrahedra 365 us
+// side by side against 397 us separate; 2049^2 triangles 162 us separate
+// against 170 us side by side.
 __host__ __device__ constexpr bool dw_pairs(int nb) { return nb == 4; }
 __host__ __device__ constexpr int sym_index(int nb, int i, int j) {
     return i == j ? i : nb + (i < j ? j * (j - 1) / 2 + i : i * (i - 1) / 2 + j);

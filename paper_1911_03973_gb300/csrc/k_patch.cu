@@ -993,7 +993,7 @@ __host__ __device__ constexpr CgSmem cg_layout(int max_nodes) {
     s.red = 16;                                         // kCgSums x 8 doubles
     s.co = s.red + kCgSums * 8 * 8;                     // kMaxColours + 1 ints
     s.A = (s.co + (kMaxColours + 1) * 4 + 127) / 128 * 128;
-    s.L = s.A + uint32_t(sym_count(NB) * kPatch * 4);
+    s.L = s.A + (WARPS ? uint32_t(sym_count(NB) * kPatch * 4) : 0u);   // matrices in shared memory: per-warp form only
     s.xs = s.L + uint32_t(NB * kPatch * 2);             // p_new at the patch nodes
     s.acc = s.xs + gcap * 4;
     s.total = (s.acc + (WARPS ? kWarpCopies : 1) * gcap * 4 + 127) / 128 * 128;
@@ -1064,10 +1064,16 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     if (tid == 0) {
         mbar_init(bar, 1);
         const uint64_t pol = policy_evict_first();
-        mbar_expect_tx(bar, uint32_t(sym_count(NB) * kPatch * 4) + uint32_t(NB * kPatch * 2));
+        mbar_expect_tx(bar, (WARPS ? uint32_t(sym_count(NB) * kPatch * 4) : 0u) + uint32_t(NB * kPatch * 2));
+        if (WARPS) {
 #pragma unroll
-        for (int t = 0; t < sym_count(NB); ++t)
-            bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * 4), bar, pol);
+            for (int t = 0; t < sym_count(NB); ++t)
+                bulk_load(smem_addr(As + t * kPatch), A + t * ns + slot0, uint32_t(kPatch * 4), bar, pol);
+        } else if (m.n_el > 0) {
+            // the colour rounds read each slot's entries from L2
+#pragma unroll
+            for (int t = 0; t < sym_count(NB); ++t) bulk_prefetch_l2(A + t * ns + slot0, uint32_t((m.n_el + 3) / 4 * 16));
+        }
 #pragma unroll
         for (int i = 0; i < NB; ++i)
             bulk_load(smem_addr(Ls + i * kPatch), pd.lconn + i * ns + slot0, uint32_t(kPatch * 2), bar, pol);
@@ -1171,7 +1177,43 @@ k_cg_patch(const PlanDev pd, const float* __restrict__ A, float* __restrict__ r,
     }
     while (!mbar_try_wait(bar, 0)) {
     }
-    patch_sums<float, NB, WARPS>(m, pd.max_nodes, As, Ls, xs, acc, co, tid);
+    if (WARPS) {
+        patch_sums<float, NB, WARPS>(m, pd.max_nodes, As, Ls, xs, acc, co, tid);
+    } else {
+        // each slot's products in its colour's round, its matrix entries read
+        // from the L2-resident runs: no matrix tile in shared memory and no
+        // product registers (2049^2: 96.0 against 101.0 us per pass with the
+        // tile copied in and the products formed first); the same rows, added
+        // in the same colour order
+        for (int c = 0; c < m.n_col; ++c) {
+            const int lo = co[c], hi = co[c + 1];
+#pragma unroll
+            for (int k = 0; k < kEPT; ++k) {
+                const int s = tid + k * NT;
+                if (s >= lo && s < hi) {
+                    float a[sym_count(NB)];
+#pragma unroll
+                    for (int t = 0; t < sym_count(NB); ++t) a[t] = __ldg(A + t * ns + slot0 + s);
+                    int nn[NB];
+                    float xe[NB];
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) {
+                        nn[i] = Ls[i * kPatch + s];
+                        xe[i] = xs[nn[i]];
+                    }
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) {
+                        float v = a[sym_index(NB, r, r)] * xe[r];
+#pragma unroll
+                        for (int j = 0; j < NB; ++j)
+                            if (j != r) v = fmadd(a[sym_index(NB, r, j)], xe[j] - xe[r], v);
+                        acc[nn[r]] += v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
     // q = mask(A p_new): owned nodes final (Dirichlet rows: dinv = 0), shared
     // nodes to their halo slots
     float spq = 0.0f, sqz = 0.0f, sqdq = 0.0f;
